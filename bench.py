@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the VQE hot path on GB300.
+
+Workload (default): 20 qubits, plain FP64 state (16 MiB), 10-site periodic
+1D Fermi-Hubbard (t = 1, U in {2, 4, 8}, Jordan-Wigner, interleaved spins),
+hardware-efficient ansatz of depth 10, 1000 seeded parameter vectors per U,
+energy only.  One step = for each U: Hamiltonian canonicalisation + cutoff
+(threshold 0) on the host, then 1000 energy evaluations (parameter staging,
+fused ansatz passes, grouped expectation) on the GPU.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_QUBITS, DEPTH, SITES, N_VEC = 20, 10, 10, 1000
+U_VALUES = (2.0, 4.0, 8.0)
+CHUNK = 64                      # states per workspace chunk (64 x 16 MiB = 1 GiB > L2)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
+METRIC = "energy+gradient evals/s at 8-32 qubits; achieved HBM GB/s vs GB300 peak"
+WORKLOAD = ("20q FP64 (complex128) 10-site periodic 1D Hubbard t=1 U in {2,4,8}, "
+            "HEA depth 10, 1000 param vectors per U, energy only")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def seeds_for(rank: int, u_index: int) -> int:
+    return 1_000_000 * (rank + 1) + 1000 * u_index
+
+
+def make_params(rank: int):
+    import numpy as np
+    import vqe_inputs as vi
+    out = []
+    for ui, _ in enumerate(U_VALUES):
+        base = seeds_for(rank, ui)
+        out.append(np.stack([vi.ansatz_params(base + j, N_QUBITS, DEPTH) for j in range(N_VEC)]))
+    return out
+
+
+def hamiltonians():
+    import vqe_inputs as vi
+    return [vi.hubbard_1d(SITES, 1.0, U, periodic=True) for U in U_VALUES]
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.device_index = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device])
+        else:
+            pg.barrier()
+
+
+def run_reference(args, world, rank, pg):
+    """The FP64 CPU oracle on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build.build()
+    H = hamiltonians()
+    P = make_params(0)
+    per_step = 1
+    def step(i):
+        k = i % len(U_VALUES)
+        h = H[k]
+        xs, zs, cs, _ = oracle.slim(h.x, h.z, h.c, 0.0)
+        psi = oracle.ansatz_state(N_QUBITS, DEPTH, P[k][i % N_VEC])
+        oracle.energy(psi, xs, zs, cs)
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{per_step} energy evaluation per step"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": oracle.threads(),
+                         "kind": "oracle",
+                         "sample": f"{per_step} of the 3000 energy evaluations per step"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(budget_s: float = 15.0):
+    """Oracle evaluations of the same workload for about ``budget_s`` seconds."""
+    import oracle
+    oracle.build.build()
+    H = hamiltonians()
+    P = make_params(0)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        k = done % len(U_VALUES)
+        h = H[k]
+        xs, zs, cs, _ = oracle.slim(h.x, h.z, h.c, 0.0)
+        psi = oracle.ansatz_state(N_QUBITS, DEPTH, P[k][done])
+        oracle.energy(psi, xs, zs, cs)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s and done >= 2:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "evals/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{done} energy evaluations (20q FP64 Hubbard, U cycling 2/4/8), {dt:.1f} s"}
+
+
+def run_gpu(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2402_11878_gb300 as pkg
+
+    stream = torch.cuda.current_stream(dev)
+    H = hamiltonians()
+    P_host = make_params(rank)
+    P_dev = [torch.tensor(p, device=dev) for p in P_host]
+    E_dev = [torch.empty(N_VEC, dtype=torch.float64, device=dev) for _ in U_VALUES]
+    engines = [pkg.Engine(N_QUBITS, DEPTH, "c128", stream=stream) for _ in U_VALUES]
+    ws = torch.empty(engines[0].workspace_size(CHUNK) // 16, dtype=torch.complex128, device=dev)
+    for e in engines:
+        e.bind_workspace(ws)
+
+    def step(pergate=False, profile_engines=None):
+        for k, eng in enumerate(engines):
+            eng.set_hamiltonian(H[k].x, H[k].z, H[k].c)
+            eng.slim(0.0)
+            eng.energy_batch_dev(P_dev[k], E_dev[k], pergate=pergate)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    launches0 = sum(e.stats()["kernel_launches"] for e in engines)
+    for e in engines:
+        e.profile(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(pg, local)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(pg, local)
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    prof = [e.profile_read() for e in engines]
+    for e in engines:
+        e.profile(False)
+    launches = sum(e.stats()["kernel_launches"] for e in engines) - launches0
+    # max over ranks
+    if pg is not None:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    evals = len(U_VALUES) * N_VEC * args.steps * world
+    value = evals / (ms / 1e3)
+
+    # dominant kernel: the fused forward pass; FP64 FLOP model per amplitude
+    # and layer = 4 per gated qubit (scaled rotation, 2 FMA per real pair)
+    # + 6 (one complex multiply by the RZ/CZ diagonal).
+    fwd_ms = sum(p["forward_passes"]["ms"] for p in prof)
+    fwd_launches = sum(p["forward_passes"]["launches"] for p in prof)
+    en_ms = sum(p["energy"]["ms"] for p in prof)
+    flops_fwd = len(U_VALUES) * N_VEC * args.steps * DEPTH * (4 * N_QUBITS + 6) * (1 << N_QUBITS)
+    achieved_tflops = flops_fwd / (fwd_ms / 1e3) / 1e12
+    n_pass = engines[0].stats()["ansatz_passes"]
+    bytes_fwd = len(U_VALUES) * N_VEC * args.steps * n_pass * 2 * 16 * (1 << N_QUBITS)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as f:
+                traffic = json.load(f).get("k_pass_fwd_c128_20q")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                "traffic": traffic, "kernel": "k_pass<double,3,fwd>",
+                "peak_source": "FP64 units x max SM clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "mean_launch_us": 1e3 * fwd_ms / max(fwd_launches, 1),
+                "share_of_step": fwd_ms / ms if ms else None,
+                "hbm_algorithmic_gbs": bytes_fwd / (fwd_ms / 1e3) / 1e9,
+                "hbm_peak_gbs": hbm_peak}
+
+    # end to end through the public host-buffer API (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        P_pin = [torch.from_numpy(p).pin_memory() for p in P_host]
+        E_pin = [torch.empty(N_VEC, dtype=torch.float64).pin_memory() for _ in U_VALUES]
+        N_pin = [torch.empty(N_VEC, dtype=torch.float64).pin_memory() for _ in U_VALUES]
+
+        def step_host():
+            for k, eng in enumerate(engines):
+                eng.set_hamiltonian(H[k].x, H[k].z, H[k].c)
+                eng.slim(0.0)
+                eng.energy_batch_into(P_pin[k], E_pin[k], N_pin[k])
+        step_host()
+        torch.cuda.synchronize(dev)
+        barrier(pg, local)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        if pg is not None:
+            t = torch.tensor([dt], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = sum(p.numel() * 8 for p in P_pin) + sum(h.x.nbytes + h.z.nbytes + h.c.nbytes for h in H)
+        d2h = 2 * len(U_VALUES) * N_VEC * 8
+        e2e = {"value": evals / dt, "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+        # the host path must agree with the device path bit for bit
+        for k in range(len(U_VALUES)):
+            assert np.array_equal(E_pin[k].numpy(), E_dev[k].cpu().numpy()), "e2e mismatch"
+
+    pergate = None
+    if args.pergate and rank == 0:
+        # one-gate-per-pass reference kernel on one U, 64 vectors
+        sub = P_dev[0][:CHUNK]
+        e_sub = torch.empty(CHUNK, dtype=torch.float64, device=dev)
+        engines[0].energy_batch_dev(sub, e_sub, pergate=True)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        engines[0].energy_batch_dev(sub, e_sub, pergate=True)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        t_pg = a.elapsed_time(b)
+        a.record(stream)
+        engines[0].energy_batch_dev(sub, E_dev[0][:CHUNK])
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        t_fu = a.elapsed_time(b)
+        pergate = {"pergate_evals_per_s": CHUNK / (t_pg / 1e3),
+                   "fused_evals_per_s": CHUNK / (t_fu / 1e3), "speedup": t_pg / t_fu,
+                   "max_abs_energy_diff": float((e_sub - E_dev[0][:CHUNK]).abs().max())}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "depth": DEPTH,
+                       "evals_per_step_per_gpu": len(U_VALUES) * N_VEC,
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"working set > L2: {CHUNK} states x 16 MiB per chunk, 1 GiB"},
+            "clocks": clocks, "gpu_launches": int(launches), "roofline": roofline,
+            "energy_kernel_ms_per_step": en_ms / args.steps,
+            "e2e": e2e,
+        }
+        if pergate:
+            line["pergate_vs_fused"] = pergate
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline_sample(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    for e in engines:
+        e.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--pergate", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank, pg)
+    else:
+        run_gpu(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

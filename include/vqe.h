@@ -1,0 +1,186 @@
+/*
+ * vqe.h -- C ABI of the GB300 VQE hot-path library (libvqe_gb300.so).
+ *
+ * The library evaluates, on one GPU, the inner loop of the variational
+ * quantum eigensolver of Morita, Tomita, Koyama, Kimura, "Simulator
+ * Demonstration of Large Scale Variational Quantum Algorithm on HPC Cluster"
+ * (2024):
+ *   - a parameterised hardware-efficient ansatz applied to a 2^n-amplitude
+ *     state vector (Sec. II-B, Eq. 6; the paper names this ansatz class),
+ *   - the energy <psi|H|psi>/<psi|psi> of a qubit Hamiltonian given as a
+ *     Pauli sum H = sum_i w_i P_i (Sec. II-B, Eqs. 2-4 and 7),
+ *   - the Hamiltonian cutoff ("slimming"): terms with |w| below a threshold
+ *     are dropped and the bound sum |w_dropped| is reported (Sec. II-D,
+ *     Sec. III-D),
+ *   - the gradient of the energy by adjoint differentiation (the paper
+ *     instead spends one circuit evaluation per parameter, Sec. II-C).
+ *
+ * Conventions (all calls):
+ *   - Qubit q is bit q of a basis-state index; |0...0> is index 0.
+ *   - A Pauli string is a pair of bit masks (x, z): per qubit (0,0)=I,
+ *     (1,0)=X, (0,1)=Z, (1,1)=Y.  The coefficient multiplies the tensor
+ *     product of those matrices.
+ *   - Ansatz: depth D layers; layer l applies, on every qubit q,
+ *     RY(theta_{l,q}) = [[c,-s],[s,c]] (c = cos theta/2, s = sin theta/2)
+ *     then RZ(phi_{l,q}) = diag(e^{-i phi/2}, e^{+i phi/2}), then CZ(q, q+1)
+ *     for q = 0..n-2.  Parameter layout (2nD doubles):
+ *     params[(l*n + q)*2] = theta_{l,q}, params[(l*n + q)*2 + 1] = phi_{l,q}.
+ *     The circuit starts from |0...0>.
+ *   - State layout: 2^n interleaved complex numbers (re, im): float2 in
+ *     VQE_C64 mode, double2 in VQE_C128 mode; batched states are stored
+ *     back to back.
+ *   - Energies are <psi|H|psi>/<psi|psi> (Eq. 7); gradients are of the
+ *     unnormalised <psi|H|psi> (equal for the unitary circuit).
+ *   - Precision: VQE_C128 computes everything in FP64.  VQE_C64 keeps the
+ *     state in complex64 and does gate arithmetic in FP32, and accumulates
+ *     energies, norms and gradients in FP64.
+ *
+ * Ownership and threading: a handle is used by one host thread at a time.
+ * Host arrays passed in are copied before the call returns.  Device pointers
+ * passed in stay owned by the caller.  All device work is queued on the
+ * stream given at creation; calls that return numbers to host memory
+ * synchronise that stream before returning, the *_dev batch calls do not.
+ *
+ * Errors: every call returns a vqe_status; on error the handle's previous
+ * Hamiltonian, state and workspace are left as they were, and
+ * vqe_last_error() describes the failure.  A CUDA error inside a call is
+ * returned as VQE_ERR_CUDA.
+ */
+#ifndef VQE_GB300_H
+#define VQE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vqe_ctx *vqe_handle;
+
+typedef enum {
+    VQE_OK = 0,
+    VQE_ERR_ARG = 1,      /* invalid argument (range, NULL, size, non-finite value) */
+    VQE_ERR_STATE = 2,    /* call out of order (e.g. energy before any ansatz) */
+    VQE_ERR_OOM = 3,      /* device memory could not be allocated */
+    VQE_ERR_CUDA = 4,     /* a CUDA runtime call or kernel launch failed */
+    VQE_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+    VQE_ERR_DEVICE = 6    /* a kernel reported an internal error through its error word */
+} vqe_status;
+
+typedef enum { VQE_C64 = 0, VQE_C128 = 1 } vqe_precision;
+
+/* Per-handle counters, for reports and tests. */
+typedef struct {
+    uint64_t kernel_launches;   /* kernels this handle launched since creation (graph nodes count) */
+    uint64_t n_terms_input;     /* terms passed to vqe_set_hamiltonian */
+    uint64_t n_terms_canonical; /* after merging equal strings and removing zeros */
+    uint64_t n_terms_kept;      /* after the last vqe_slim */
+    uint64_t n_groups;          /* distinct x masks among kept terms */
+    double   sum_abs_dropped;   /* bound of the last vqe_slim */
+    double   threshold;         /* threshold of the last vqe_slim */
+    uint32_t ansatz_passes;     /* tile passes per circuit evaluation */
+    uint32_t tile_bits_max;     /* largest tile (log2 amplitudes) the pass plan uses */
+} vqe_stats;
+
+/* Create a handle for n_qubits (1..32) and depth (>= 1) layers.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  The device is
+ * the one current on the calling thread. */
+vqe_status vqe_create(int n_qubits, int depth, vqe_precision precision, void *cuda_stream,
+                      vqe_handle *out);
+/* Free the handle and every device buffer the library allocated. */
+vqe_status vqe_destroy(vqe_handle h);
+
+/* Device bytes of state workspace for `batch` states, with (want_gradient=1)
+ * or without the adjoint buffers. */
+vqe_status vqe_workspace_size(vqe_handle h, int batch, int want_gradient, size_t *bytes);
+/* Use caller-owned device memory (at least 256-byte aligned) as the state
+ * workspace; the library never frees it.  Pass NULL to return to
+ * library-allocated workspace.  The batch capacity follows from `bytes`. */
+vqe_status vqe_bind_workspace(vqe_handle h, void *dev_ptr, size_t bytes);
+
+/* Set the Hamiltonian H = sum_t coeffs[t] * P(x_masks[t], z_masks[t])
+ * (Sec. II-B, Eqs. 2-4).  Host arrays of length n_terms; masks must have no
+ * bit at or above n_qubits; coefficients must be finite.  Equal strings are
+ * merged (coefficients summed) and exact zeros removed; the kept set is the
+ * whole canonical Hamiltonian until vqe_slim is called. */
+vqe_status vqe_set_hamiltonian(vqe_handle h, const uint64_t *x_masks, const uint64_t *z_masks,
+                               const double *coeffs, size_t n_terms);
+
+/* Hamiltonian cutoff (Sec. II-D and III-D): keep exactly the canonical
+ * terms with |c| >= threshold (threshold 0 keeps all), report the kept count
+ * and sum |c| over dropped terms, the bound on |E_full - E_slim| * <psi|psi>
+ * (Sec. II-D).  Always starts again from the full canonical set.  Either
+ * output pointer may be NULL. */
+vqe_status vqe_slim(vqe_handle h, double threshold, size_t *n_kept, double *sum_abs_dropped);
+
+/* Apply the ansatz with host parameters (2*n*depth doubles) to |0...0> and
+ * keep the state in the handle (batch slot 0). */
+vqe_status vqe_apply_ansatz(vqe_handle h, const double *params);
+
+/* Energy <psi|H|psi>/<psi|psi> and <psi|psi> of the state left by the last
+ * vqe_apply_ansatz (Eq. 7), with the kept terms.  Either pointer may be NULL. */
+vqe_status vqe_energy(vqe_handle h, double *energy, double *norm);
+
+/* Copy the state of batch slot 0 to host memory (bytes = 2^n * 8 for C64,
+ * 2^n * 16 for C128). */
+vqe_status vqe_get_state(vqe_handle h, void *host_out, size_t bytes);
+
+/* Run the ansatz with host params, then return the adjoint gradient
+ * d<psi|H|psi>/d params (2*n*depth doubles, host) and the energy.  The state
+ * afterwards is undefined (the backward sweep consumes it). */
+vqe_status vqe_gradient(vqe_handle h, const double *params, double *grad, double *energy);
+
+/* Batched evaluation with device-resident buffers, queued on the handle's
+ * stream without synchronising:
+ *   params_dev:   batch * 2*n*depth doubles
+ *   energies_dev: batch doubles (E = <H>/<psi|psi>), norms_dev: batch doubles or NULL
+ *   grads_dev:    batch * 2*n*depth doubles (gradient call only)
+ * Batches larger than the workspace capacity run in chunks. */
+vqe_status vqe_energy_batch_dev(vqe_handle h, const double *params_dev, int batch,
+                                double *energies_dev, double *norms_dev);
+vqe_status vqe_gradient_batch_dev(vqe_handle h, const double *params_dev, int batch,
+                                  double *grads_dev, double *energies_dev);
+
+/* The same with host buffers (copies inside; synchronises). */
+vqe_status vqe_energy_batch(vqe_handle h, const double *params, int batch, double *energies,
+                            double *norms);
+vqe_status vqe_gradient_batch(vqe_handle h, const double *params, int batch, double *grads,
+                              double *energies);
+
+/* Reference kernel for comparison: the same circuit with one gate per pass
+ * over the state (RY, RZ and each CZ separately, as a per-gate simulator
+ * does), then the same energy kernel.  Device buffers as above. */
+vqe_status vqe_energy_batch_pergate_dev(vqe_handle h, const double *params_dev, int batch,
+                                        double *energies_dev, double *norms_dev);
+
+vqe_status vqe_get_stats(vqe_handle h, vqe_stats *out);
+
+/* Kernel timing by CUDA events on the handle's stream.  When enabled, each
+ * evaluation chunk records an event pair around each of its kernel groups:
+ *   0 = forward ansatz passes, 1 = energy kernel, 2 = apply-H kernel,
+ *   3 = backward (adjoint) passes.
+ * ms[i] sums the elapsed times of group i; launches[i] counts the kernels
+ * inside those intervals (back-to-back launches, so ms/launches is the mean
+ * launch duration).  Enabling clears the counters; vqe_profile_read
+ * synchronises the stream.  Event recording adds a few microseconds per
+ * chunk. */
+typedef struct {
+    uint64_t launches[4];
+    double ms[4];
+    uint64_t chunks[4];
+} vqe_kernel_times;
+vqe_status vqe_profile(vqe_handle h, int enable);
+vqe_status vqe_profile_read(vqe_handle h, vqe_kernel_times *out);
+
+/* Message of the last failed call on this handle ("" if none).  The pointer
+ * stays valid until the next call on the handle. */
+const char *vqe_last_error(vqe_handle h);
+
+/* Library version string. */
+const char *vqe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

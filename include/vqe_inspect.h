@@ -1,0 +1,49 @@
+/*
+ * vqe_inspect.h -- host-only inspection of the plans libvqe_gb300 builds.
+ *
+ * These calls run the library's own planners on the host and copy their
+ * output out, without touching a GPU, so tests can check the plans' index
+ * arithmetic and semantics on a machine with no GPU.  The record layouts
+ * are the library's internal structures; vqe_inspect_sizeof() reports their
+ * sizes so a caller can verify that it mirrors them correctly.
+ */
+#ifndef VQE_GB300_INSPECT_H
+#define VQE_GB300_INSPECT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* sizeof of internal record `which`: 0 = pass descriptor, 1 = staging slot,
+ * 2 = term group; 0 for an unknown `which`. */
+size_t vqe_inspect_sizeof(int which);
+
+/* Tile-pass plan of the ansatz for (n, depth, precision): forward and
+ * backward pass descriptors (max_passes each), staging slots (max_stage),
+ * and the gradient reduction map grad_map[3 * 2*n*depth] = (offset, count,
+ * step) per parameter.  strides[3] = per-state coefficient, table and
+ * gradient-partial sizes; counts[3] = passes, staging slots, parameters.
+ * Returns 0, or -1 on invalid arguments or too-small buffers. */
+int vqe_inspect_plan(int n_qubits, int depth, int precision, void *fwd, void *bwd, int max_passes,
+                     void *stage, int max_stage, int *grad_map, int max_params,
+                     uint64_t strides[3], int counts[3]);
+
+/* Canonicalisation, cutoff and X-mask grouping of a Pauli sum, exactly as
+ * vqe_set_hamiltonian followed by vqe_slim(threshold) prepare it: term
+ * groups (max_groups), per-term z masks and sign-folded coefficients
+ * (max_terms).  counts[2] = groups, terms; *sum_abs_dropped and
+ * *n_canonical as vqe_slim and vqe_get_stats report them.  Returns 0, or -1
+ * on invalid input (masks beyond n_qubits, non-finite values) or
+ * too-small buffers. */
+int vqe_inspect_hamiltonian(int n_qubits, const uint64_t *x_masks, const uint64_t *z_masks,
+                            const double *coeffs, size_t n_terms, double threshold, void *groups,
+                            int max_groups, uint32_t *tz, double *tc, int max_terms, int counts[2],
+                            double *sum_abs_dropped, uint64_t *n_canonical);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,18 @@
+"""GB300-native hot path of the VQE simulation of arXiv 2402.11878.
+
+``Engine`` wraps one handle of the C ABI in ``include/vqe.h`` (the CUDA
+library ``_lib/libvqe_gb300.so``); ``energy_and_grad`` exposes the adjoint
+gradient to ``torch.autograd``.  The library is loaded on first use and its
+absence raises ImportError (there is no other code path).
+"""
+from .binding import Engine, VQEError, load, version, library_path  # noqa: F401
+
+__all__ = ["Engine", "VQEError", "load", "version", "library_path", "EnergyFunction",
+           "energy_and_grad"]
+
+
+def __getattr__(name):
+    if name in ("EnergyFunction", "energy_and_grad"):
+        from . import autograd as _ag
+        return getattr(_ag, name)
+    raise AttributeError(name)

@@ -1,0 +1,528 @@
+// Ansatz kernels: parameter staging, fused tile passes (forward and adjoint
+// backward), and the one-gate-per-pass reference kernels.
+//
+// Method: the hardware-efficient ansatz (Sec. II-B names the class) applied
+// to a 2^n state vector, psi(theta) = U(theta)|0...0> (Eq. 6).  Layer l is
+//     CZ_chain * prod_q RZ(phi_{l,q}) * prod_q RY(theta_{l,q}),
+// because gates on different qubits commute.  A pass stages a tile of 2^k
+// amplitudes spanning one qubit group in shared memory and applies all gates
+// of one or more layers on those qubits; RY(theta) is applied as scale * B
+// with B = [[1,-t],[t,1]] (t = tan theta/2) or [[u,-1],[1,u]] (u = cot),
+// one FMA per real output, and the scale is folded with the RZ phases into a
+// per-slot diagonal table.  CZ signs are integer sign flips.
+//
+// The backward pass is the adjoint method: it un-applies the same slots in
+// reverse on psi and lambda = H psi, and for each gated qubit q accumulates
+//     dE/dtheta = Im <lambda| Y_q |psi>,   dE/dphi = Im <lambda| Z_q |psi>
+// at a point of the sweep where both are valid (after the slot's diagonal is
+// undone and before q's own rotation is undone).
+#include "vqe_internal.h"
+
+namespace vqe {
+
+template <typename T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+
+__device__ __forceinline__ uint32_t elem_of(uint32_t t, uint32_t r, int p, int R) {
+    const uint32_t lo = t & ((1u << p) - 1u);
+    return lo | (r << p) | ((t >> p) << (p + R));
+}
+
+// Shared-memory slot of tile element e: XOR-fold of the higher bits into the
+// bank-selecting low bits, so that every register chunk of the plan reads
+// and writes conflict-free (16-byte elements: 8 per 128 B; 8-byte: 16).
+template <typename T> __device__ __forceinline__ uint32_t swz(uint32_t e);
+template <> __device__ __forceinline__ uint32_t swz<double>(uint32_t e) {
+    const uint32_t f = (e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12);
+    return e ^ (f & 7u);
+}
+template <> __device__ __forceinline__ uint32_t swz<float>(uint32_t e) {
+    const uint32_t f = (e >> 4) ^ (e >> 8) ^ (e >> 12);
+    return e ^ (f & 15u);
+}
+
+__device__ __forceinline__ double flip_sign(double v, uint32_t s) {
+    return __longlong_as_double(__double_as_longlong(v) ^ ((unsigned long long)s << 63));
+}
+__device__ __forceinline__ float flip_sign(float v, uint32_t s) {
+    return __int_as_float(__float_as_int(v) ^ (int)(s << 31));
+}
+
+template <typename C>
+__device__ __forceinline__ C cmul(C x, C d) {
+    C r;
+    r.x = fma(x.x, d.x, -x.y * d.y);
+    r.y = fma(x.x, d.y, x.y * d.x);
+    return r;
+}
+template <typename C>
+__device__ __forceinline__ C cmul_conj(C x, C d) {   // x * conj(d)
+    C r;
+    r.x = fma(x.x, d.x, x.y * d.y);
+    r.y = fma(x.y, d.x, -x.x * d.y);
+    return r;
+}
+
+// ---------------------------------------------------------------- staging
+
+template <typename T>
+__global__ void k_stage(const StageSlot *__restrict__ slots, int n, int depth,
+                        const double *__restrict__ params, RotCoef<T> *__restrict__ coefs,
+                        size_t coef_stride, typename V2<T>::type *__restrict__ dtab,
+                        size_t dtab_stride) {
+    using C = typename V2<T>::type;
+    __shared__ double ph_c[kMaxTileBits], ph_s[kMaxTileBits], scl[kMaxTileBits], ph_v[kMaxTileBits];
+    __shared__ int ph_m[kMaxTileBits];
+    __shared__ double sigma;
+    const StageSlot S = slots[blockIdx.x];
+    const int b = blockIdx.y;
+    const double *pr = params + (size_t)b * (2 * (size_t)n * depth);
+    if (threadIdx.x < (unsigned)S.n_gated) {
+        const int j = threadIdx.x;
+        const int q = S.qubit[j];
+        const double th = pr[((size_t)S.layer * n + q) * 2];
+        const double phi = pr[((size_t)S.layer * n + q) * 2 + 1];
+        double s, c;
+        sincos(0.5 * th, &s, &c);
+        if (fabs(c) >= fabs(s)) { ph_v[j] = s / c; ph_m[j] = 0; scl[j] = c; }
+        else                    { ph_v[j] = c / s; ph_m[j] = 1; scl[j] = s; }
+        double sp, cp;
+        sincos(0.5 * phi, &sp, &cp);
+        ph_c[j] = cp;
+        ph_s[j] = sp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double p = 1.0;
+        for (int u = 0; u < S.n_gated; ++u) p *= scl[u];
+        sigma = p;
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)S.n_gated) {
+        const int j = threadIdx.x;
+        double pb = 1.0;
+        for (int u = 0; u < S.n_gated; ++u)
+            if ((S.before[j] >> S.tile_bit[u]) & 1u) pb *= scl[u];
+        const double f = sigma / pb;
+        RotCoef<T> rc;
+        rc.v = (T)ph_v[j];
+        rc.gs = (T)(1.0 / (f * f));
+        rc.mode = ph_m[j];
+        coefs[(size_t)b * coef_stride + S.coef_off + S.tile_bit[j]] = rc;
+    }
+    // table[e] = sigma * prod_j (bit_j(e) ? e^{+i phi_j/2} : e^{-i phi_j/2})
+    C *tab = dtab + (size_t)b * dtab_stride + S.dtab_off;
+    const uint32_t size = 1u << S.k;
+    const double sg = sigma;
+    for (uint32_t e = threadIdx.x; e < size; e += blockDim.x) {
+        double re = sg, im = 0.0;
+        for (int j = 0; j < S.n_gated; ++j) {
+            const double c = ph_c[j];
+            const double s = ((e >> S.tile_bit[j]) & 1u) ? ph_s[j] : -ph_s[j];
+            const double nr = re * c - im * s;
+            const double ni = re * s + im * c;
+            re = nr;
+            im = ni;
+        }
+        C d;
+        d.x = (T)re;
+        d.y = (T)im;
+        tab[e] = d;
+    }
+}
+
+template <typename T>
+cudaError_t launch_stage(const StageSlot *slots_dev, int n_slots, int n_qubits, int depth,
+                         const double *params, int batch, RotCoef<T> *coefs, size_t coef_stride,
+                         void *dtab, size_t dtab_stride, cudaStream_t s) {
+    if (n_slots == 0 || batch == 0) return cudaSuccess;
+    dim3 grid(n_slots, batch);
+    k_stage<T><<<grid, 256, 0, s>>>(slots_dev, n_qubits, depth, params, coefs, coef_stride,
+                                    static_cast<typename V2<T>::type *>(dtab), dtab_stride);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- tile pass
+
+// Plans keep k - R <= 9, so a pass block has at most 512 threads.
+constexpr int kPassMaxThreads = 512;
+
+template <typename T, int R, bool BWD>
+__global__ void __launch_bounds__(kPassMaxThreads)
+k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *__restrict__ psi,
+       typename V2<T>::type *__restrict__ lam, size_t stride, const RotCoef<T> *__restrict__ coefs,
+       size_t coef_stride, const typename V2<T>::type *__restrict__ dtab, size_t dtab_stride,
+       double *__restrict__ gpart, size_t grad_stride) {
+    using C = typename V2<T>::type;
+    constexpr int NR = 1 << R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int k = desc->k, m = desc->m, a = desc->a;
+    const int hbits = k - m;
+    C *sp = reinterpret_cast<C *>(smem_raw);
+    C *sl = sp + (BWD ? (1u << k) : 0u);
+    double *gsh = reinterpret_cast<double *>(sp + (BWD ? (2u << k) : (1u << k)));
+    // Blocks of fewer than 32 threads (tiles of < 2^(R+5) amplitudes) form one
+    // partial warp; the shuffles below then stay inside its active lanes.
+    const int nwarps = (blockDim.x + 31) >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned wmask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+    const int wlanes = blockDim.x >= 32 ? 32 : (int)blockDim.x;
+
+    const uint32_t t = threadIdx.x;
+    const uint64_t tile = blockIdx.x;
+    const int b = blockIdx.y;
+    const int mid = a - m;
+    const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + hbits));
+    const uint32_t lowmask = (1u << m) - 1u;
+    C *P = psi + (size_t)b * stride;
+    C *L = BWD ? lam + (size_t)b * stride : nullptr;
+    const RotCoef<T> *cf = coefs + (size_t)b * coef_stride;
+    const C *dt = dtab + (size_t)b * dtab_stride;
+
+    auto gaddr = [&](uint32_t e) -> uint64_t {
+        return base | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a);
+    };
+
+    C v[NR];
+    C w[NR];
+    int chunk = -1;
+    const int nops = desc->n_ops;
+    for (int oi = 0; oi < nops; ++oi) {
+        const PassOp op = desc->ops[oi];
+        if (op.kind == OP_ROUND) {
+            const int p = op.chunk;
+            if (chunk < 0) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const uint64_t g = gaddr(elem_of(t, r, p, R));
+                    if (init_zero) {
+                        v[r].x = (g == 0) ? T(1) : T(0);
+                        v[r].y = T(0);
+                    } else {
+                        v[r] = P[g];
+                    }
+                    if (BWD) w[r] = L[g];
+                }
+            } else {
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t s = swz<T>(elem_of(t, r, chunk, R));
+                    sp[s] = v[r];
+                    if (BWD) sl[s] = w[r];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t s = swz<T>(elem_of(t, r, p, R));
+                    v[r] = sp[s];
+                    if (BWD) w[r] = sl[s];
+                }
+            }
+            chunk = p;
+        } else if (op.kind == OP_BF) {
+            const int coff = desc->slot_coef_off[op.slot];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (!((op.mask >> j) & 1)) continue;
+                const RotCoef<T> rc = cf[coff + chunk + j];
+                const T cv = rc.v;
+                if (BWD) {
+                    T gt = T(0), gp = T(0);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        if (r & (1 << j)) continue;
+                        const C p0 = v[r], p1 = v[r | (1 << j)];
+                        const C l0 = w[r], l1 = w[r | (1 << j)];
+                        // Im<l|Y|p> over the pair: Re(conj(l1) p0) - Re(conj(l0) p1)
+                        gt += fma(l1.x, p0.x, l1.y * p0.y) - fma(l0.x, p1.x, l0.y * p1.y);
+                        // Im<l|Z|p> over the pair: Im(conj(l0) p0) - Im(conj(l1) p1)
+                        gp += fma(l0.x, p0.y, -l0.y * p0.x) - fma(l1.x, p1.y, -l1.y * p1.x);
+                    }
+                    double dgt = (double)(gt * rc.gs), dgp = (double)(gp * rc.gs);
+                    for (int o = wlanes >> 1; o > 0; o >>= 1) {
+                        dgt += __shfl_xor_sync(wmask, dgt, o);
+                        dgp += __shfl_xor_sync(wmask, dgp, o);
+                    }
+                    if (lane == 0) {
+                        gsh[(warp * k + chunk + j) * 2 + 0] = dgt;
+                        gsh[(warp * k + chunk + j) * 2 + 1] = dgp;
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (r & (1 << j)) continue;
+                    const int r1 = r | (1 << j);
+                    if (!BWD) {
+                        const C x = v[r], y = v[r1];
+                        if (rc.mode == 0) {   // [[1,-t],[t,1]]
+                            v[r].x = fma(-cv, y.x, x.x);  v[r].y = fma(-cv, y.y, x.y);
+                            v[r1].x = fma(cv, x.x, y.x);  v[r1].y = fma(cv, x.y, y.y);
+                        } else {              // [[u,-1],[1,u]]
+                            v[r].x = fma(cv, x.x, -y.x);  v[r].y = fma(cv, x.y, -y.y);
+                            v[r1].x = fma(cv, y.x, x.x);  v[r1].y = fma(cv, y.y, x.y);
+                        }
+                    } else {
+#pragma unroll
+                        for (int bufi = 0; bufi < 2; ++bufi) {
+                            C *u = bufi ? w : v;
+                            const C x = u[r], y = u[r1];
+                            if (rc.mode == 0) {   // transpose: [[1,t],[-t,1]]
+                                u[r].x = fma(cv, y.x, x.x);    u[r].y = fma(cv, y.y, x.y);
+                                u[r1].x = fma(-cv, x.x, y.x);  u[r1].y = fma(-cv, x.y, y.y);
+                            } else {              // transpose: [[u,1],[-1,u]]
+                                u[r].x = fma(cv, x.x, y.x);    u[r].y = fma(cv, x.y, y.y);
+                                u[r1].x = fma(cv, y.x, -x.x);  u[r1].y = fma(cv, y.y, -x.y);
+                            }
+                        }
+                    }
+                }
+            }
+        } else if (op.kind == OP_DIAG) {
+            const uint32_t cz = desc->slot_czmask[op.slot];
+            const C *tab = dt + desc->slot_dtab_off[op.slot];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const uint32_t e = elem_of(t, r, chunk, R);
+                const uint32_t g32 = (uint32_t)gaddr(e);
+                const uint32_t sgn = __popc(g32 & (g32 >> 1) & cz) & 1u;
+                const C d = tab[e];
+                if (!BWD) {
+                    C y = cmul(v[r], d);
+                    y.x = flip_sign(y.x, sgn);
+                    y.y = flip_sign(y.y, sgn);
+                    v[r] = y;
+                } else {
+                    C y = cmul_conj(v[r], d);
+                    y.x = flip_sign(y.x, sgn);
+                    y.y = flip_sign(y.y, sgn);
+                    v[r] = y;
+                    C z = cmul_conj(w[r], d);
+                    z.x = flip_sign(z.x, sgn);
+                    z.y = flip_sign(z.y, sgn);
+                    w[r] = z;
+                }
+            }
+        } else if (BWD && op.kind == OP_FLUSH) {
+            __syncthreads();
+            const uint32_t gated = desc->slot_gated[op.slot];
+            double *out = gpart + (size_t)b * grad_stride + desc->slot_grad_off[op.slot] +
+                          tile * (uint64_t)(2 * k);
+            for (int idx = threadIdx.x; idx < 2 * k; idx += blockDim.x) {
+                if (!((gated >> (idx >> 1)) & 1u)) continue;
+                double s = 0.0;
+                for (int wi = 0; wi < nwarps; ++wi) s += gsh[wi * 2 * k + idx];
+                out[idx] = s;
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const uint64_t g = gaddr(elem_of(t, r, chunk, R));
+        P[g] = v[r];
+        if (BWD) L[g] = w[r];
+    }
+}
+
+int pass_threads(const PassDesc &d) { return 1 << (d.k - d.R); }
+
+size_t pass_smem_bytes(const PassDesc &d, bool backward, size_t elem_bytes) {
+    size_t tiles = (size_t(1) << d.k) * elem_bytes * (backward ? 2 : 1);
+    int warps = (pass_threads(d) + 31) / 32;
+    size_t gsh = backward ? size_t(warps) * d.k * 2 * sizeof(double) : 0;
+    return tiles + gsh;
+}
+
+template <typename T, int R, bool BWD>
+static cudaError_t launch_pass_r(const PassDesc *desc_dev, const PassDesc &dh, int n_qubits,
+                                 int batch, void *psi, void *lam, size_t stride,
+                                 const RotCoef<T> *coefs, size_t coef_stride, const void *dtab,
+                                 size_t dtab_stride, double *gpart, size_t grad_stride,
+                                 int init_zero, cudaStream_t s) {
+    using C = typename V2<T>::type;
+    const int threads = pass_threads(dh);
+    if (threads > kPassMaxThreads) return cudaErrorInvalidConfiguration;
+    const size_t smem = pass_smem_bytes(dh, BWD, sizeof(C));
+    auto kern = k_pass<T, R, BWD>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)(1ull << (n_qubits - dh.k)), batch);
+    kern<<<grid, threads, smem, s>>>(desc_dev, init_zero, static_cast<C *>(psi),
+                                     static_cast<C *>(lam), stride, coefs, coef_stride,
+                                     static_cast<const C *>(dtab), dtab_stride, gpart, grad_stride);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pass(const PassDesc *desc_dev, const PassDesc &dh, int n_qubits, int batch,
+                        void *psi, void *lam, size_t stride, const RotCoef<T> *coefs,
+                        size_t coef_stride, const void *dtab, size_t dtab_stride,
+                        double *gpart, size_t grad_stride, bool backward, int init_zero,
+                        cudaStream_t s) {
+#define VQE_PASS_CASE(RR)                                                                       \
+    case RR:                                                                                    \
+        return backward ? launch_pass_r<T, RR, true>(desc_dev, dh, n_qubits, batch, psi, lam,   \
+                                                     stride, coefs, coef_stride, dtab,          \
+                                                     dtab_stride, gpart, grad_stride, 0, s)     \
+                        : launch_pass_r<T, RR, false>(desc_dev, dh, n_qubits, batch, psi,       \
+                                                      nullptr, stride, coefs, coef_stride,      \
+                                                      dtab, dtab_stride, gpart, grad_stride,    \
+                                                      init_zero, s);
+    switch (dh.R) {
+        VQE_PASS_CASE(1)
+        VQE_PASS_CASE(2)
+        VQE_PASS_CASE(3)
+        VQE_PASS_CASE(4)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef VQE_PASS_CASE
+}
+
+// ---------------------------------------------------------------- one gate per pass
+
+template <typename T>
+__global__ void k_gate_ry(typename V2<T>::type *psi, size_t stride, int n, int q,
+                          const double *params, int pidx, int pstride) {
+    using C = typename V2<T>::type;
+    __shared__ T cs[2];
+    const int b = blockIdx.y;
+    if (threadIdx.x == 0) {
+        double s, c;
+        sincos(0.5 * params[(size_t)b * pstride + pidx], &s, &c);
+        cs[0] = (T)c;
+        cs[1] = (T)s;
+    }
+    __syncthreads();
+    const T c = cs[0], s = cs[1];
+    C *P = psi + (size_t)b * stride;
+    const uint64_t half = 1ull << (n - 1);
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < half;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i0 = ((p >> q) << (q + 1)) | (p & ((1ull << q) - 1));
+        const uint64_t i1 = i0 | (1ull << q);
+        const C x = P[i0], y = P[i1];
+        C nx, ny;
+        nx.x = c * x.x - s * y.x;  nx.y = c * x.y - s * y.y;
+        ny.x = s * x.x + c * y.x;  ny.y = s * x.y + c * y.y;
+        P[i0] = nx;
+        P[i1] = ny;
+    }
+}
+
+template <typename T>
+__global__ void k_gate_rz(typename V2<T>::type *psi, size_t stride, int n, int q,
+                          const double *params, int pidx, int pstride) {
+    using C = typename V2<T>::type;
+    __shared__ T cs[2];
+    const int b = blockIdx.y;
+    if (threadIdx.x == 0) {
+        double s, c;
+        sincos(0.5 * params[(size_t)b * pstride + pidx], &s, &c);
+        cs[0] = (T)c;
+        cs[1] = (T)s;
+    }
+    __syncthreads();
+    const T c = cs[0], s0 = cs[1];
+    C *P = psi + (size_t)b * stride;
+    const uint64_t dim = 1ull << n;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < dim;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const T s = ((i >> q) & 1) ? s0 : -s0;   // e^{+-i phi/2}
+        const C x = P[i];
+        C y;
+        y.x = x.x * c - x.y * s;
+        y.y = x.x * s + x.y * c;
+        P[i] = y;
+    }
+}
+
+template <typename T>
+__global__ void k_gate_cz(typename V2<T>::type *psi, size_t stride, int n, int q) {
+    using C = typename V2<T>::type;
+    C *P = psi + (size_t)blockIdx.y * stride;
+    const uint64_t dim = 1ull << n;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < dim;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if (((i >> q) & 3ull) == 3ull) {
+            C x = P[i];
+            x.x = -x.x;
+            x.y = -x.y;
+            P[i] = x;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_zero_state(typename V2<T>::type *psi, size_t stride, int n) {
+    using C = typename V2<T>::type;
+    C *P = psi + (size_t)blockIdx.y * stride;
+    const uint64_t dim = 1ull << n;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < dim;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        C x;
+        x.x = (i == 0) ? T(1) : T(0);
+        x.y = T(0);
+        P[i] = x;
+    }
+}
+
+static unsigned grid_for(uint64_t work, int threads) {
+    uint64_t g = (work + threads - 1) / threads;
+    if (g > 152ull * 16) g = 152ull * 16;
+    if (g == 0) g = 1;
+    return (unsigned)g;
+}
+
+template <typename T>
+cudaError_t launch_gate_ry(void *psi, size_t stride, int n, int batch, int q, const double *params,
+                           int pidx, int pstride, cudaStream_t s) {
+    dim3 grid(grid_for(1ull << (n - 1), 256), batch);
+    k_gate_ry<T><<<grid, 256, 0, s>>>(static_cast<typename V2<T>::type *>(psi), stride, n, q,
+                                      params, pidx, pstride);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_gate_rz(void *psi, size_t stride, int n, int batch, int q, const double *params,
+                           int pidx, int pstride, cudaStream_t s) {
+    dim3 grid(grid_for(1ull << n, 256), batch);
+    k_gate_rz<T><<<grid, 256, 0, s>>>(static_cast<typename V2<T>::type *>(psi), stride, n, q,
+                                      params, pidx, pstride);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_gate_cz(void *psi, size_t stride, int n, int batch, int q, cudaStream_t s) {
+    dim3 grid(grid_for(1ull << n, 256), batch);
+    k_gate_cz<T><<<grid, 256, 0, s>>>(static_cast<typename V2<T>::type *>(psi), stride, n, q);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_init_zero_state(void *psi, size_t stride, int n, int batch, cudaStream_t s) {
+    dim3 grid(grid_for(1ull << n, 256), batch);
+    k_zero_state<T><<<grid, 256, 0, s>>>(static_cast<typename V2<T>::type *>(psi), stride, n);
+    return cudaGetLastError();
+}
+
+#define VQE_INSTANTIATE(T)                                                                      \
+    template cudaError_t launch_stage<T>(const StageSlot *, int, int, int, const double *, int, \
+                                         RotCoef<T> *, size_t, void *, size_t, cudaStream_t);   \
+    template cudaError_t launch_pass<T>(const PassDesc *, const PassDesc &, int, int, void *,   \
+                                        void *, size_t, const RotCoef<T> *, size_t,             \
+                                        const void *, size_t, double *, size_t, bool, int,      \
+                                        cudaStream_t);                                          \
+    template cudaError_t launch_gate_ry<T>(void *, size_t, int, int, int, const double *, int,  \
+                                           int, cudaStream_t);                                  \
+    template cudaError_t launch_gate_rz<T>(void *, size_t, int, int, int, const double *, int,  \
+                                           int, cudaStream_t);                                  \
+    template cudaError_t launch_gate_cz<T>(void *, size_t, int, int, int, cudaStream_t);        \
+    template cudaError_t launch_init_zero_state<T>(void *, size_t, int, int, cudaStream_t);
+
+VQE_INSTANTIATE(float)
+VQE_INSTANTIATE(double)
+
+}  // namespace vqe

@@ -1,0 +1,1166 @@
+// Host side of libvqe_gb300: the C ABI of include/vqe.h, Hamiltonian
+// canonicalisation and cutoff, term grouping, the tile-pass planner, device
+// buffers and the evaluation pipelines.  All numerical work runs in the
+// kernels of k_layers.cu and k_energy.cu; this file only plans and launches.
+#include "vqe.h"
+#include "vqe_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+using namespace vqe;
+
+namespace {
+
+struct Group {        // one qubit group = the tile bits of one kind of pass
+    int k, m, a;      // tile bits, low run bits, start of the high range
+    uint32_t gated;   // tile bits that carry this group's qubits
+    int qubit_of(int j) const { return j < m ? j : a + (j - m); }
+};
+
+struct PassPlan {
+    int group;
+    std::vector<int> layers;  // one slot per layer
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+}  // namespace
+
+struct vqe_ctx {
+    int n = 0, depth = 0;
+    vqe_precision prec = VQE_C64;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+
+    // Hamiltonian (host)
+    std::vector<uint64_t> cx, cz;  // canonical terms
+    std::vector<double> cc;
+    std::vector<uint8_t> keep;
+    bool ham_set = false;
+    bool state_valid = false;
+    vqe_stats stats{};
+
+    // Hamiltonian plan (device)
+    DevBuf d_groups, d_tz, d_tc;
+    int n_groups = 0;
+
+    // ansatz plan
+    std::vector<Group> groups;
+    std::vector<PassDesc> fwd, bwd;
+    std::vector<int> pass_tiles_log2;
+    DevBuf d_fwd, d_bwd, d_stage, d_goff, d_gcnt, d_gstep;
+    int n_stage = 0;
+    size_t coef_stride = 0, dtab_stride = 0, grad_stride = 0;
+    int n_params = 0;
+
+    // workspace and scratch
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false;
+    DevBuf ws_own;
+    DevBuf d_params, d_coefs, d_dtab, d_gpart, d_epart, d_out;
+    DevBuf hb_params, hb_e, hb_n, hb_g;   // device copies for the host-buffer batch calls
+    int scratch_batch = 0;
+
+    // event timing (vqe_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Mark { int group; int launches; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    size_t ev_used = 0;
+    vqe_kernel_times times{};
+
+    size_t elem_bytes() const { return prec == VQE_C128 ? 16 : 8; }
+    size_t state_elems() const { return size_t(1) << n; }
+    size_t state_bytes() const { return state_elems() * elem_bytes(); }
+};
+
+namespace {
+
+vqe_status fail(vqe_ctx *h, vqe_status st, const std::string &msg) {
+    if (h) h->err = msg;
+    return st;
+}
+
+vqe_status cuda_fail(vqe_ctx *h, cudaError_t e, const char *where) {
+    return fail(h, VQE_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define VQE_CUDA(h, call)                                            \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);     \
+    } while (0)
+
+vqe_status ensure(vqe_ctx *h, DevBuf &b, size_t bytes, const char *what) {
+    if (b.bytes >= bytes && b.p) return VQE_OK;
+    b.release();
+    if (bytes == 0) return VQE_OK;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(h, VQE_ERR_OOM, std::string("cudaMalloc failed for ") + what);
+    }
+    b.bytes = bytes;
+    return VQE_OK;
+}
+
+template <typename V>
+vqe_status upload(vqe_ctx *h, DevBuf &b, const std::vector<V> &v, const char *what) {
+    vqe_status st = ensure(h, b, std::max<size_t>(v.size() * sizeof(V), 16), what);
+    if (st != VQE_OK) return st;
+    if (!v.empty())
+        VQE_CUDA(h, cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice,
+                                    h->stream));
+    VQE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return VQE_OK;
+}
+
+// ---------------------------------------------------------------- event timing
+
+cudaEvent_t next_event(vqe_ctx *h) {
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_used++];
+}
+
+// Opens a timed interval for kernel group g; returns the mark index or -1.
+int prof_begin(vqe_ctx *h, int g) {
+    if (!h->prof) return -1;
+    cudaEvent_t a = next_event(h), b = next_event(h);
+    if (!a || !b) return -1;
+    cudaEventRecord(a, h->stream);
+    h->marks.push_back({g, 0, a, b});
+    return int(h->marks.size()) - 1;
+}
+
+void prof_end(vqe_ctx *h, int mark, int launches) {
+    if (mark < 0) return;
+    h->marks[mark].launches = launches;
+    cudaEventRecord(h->marks[mark].b, h->stream);
+}
+
+vqe_status prof_collect(vqe_ctx *h) {
+    if (h->marks.empty()) return VQE_OK;
+    VQE_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (auto &m : h->marks) {
+        float ms = 0.f;
+        VQE_CUDA(h, cudaEventElapsedTime(&ms, m.a, m.b));
+        h->times.ms[m.group] += ms;
+        h->times.launches[m.group] += uint64_t(m.launches);
+        h->times.chunks[m.group] += 1;
+    }
+    h->marks.clear();
+    h->ev_used = 0;
+    return VQE_OK;
+}
+
+// ---------------------------------------------------------------- planner
+
+std::vector<Group> plan_groups(int n, vqe_precision prec) {
+    const int kmax = prec == VQE_C128 ? 12 : 13;
+    const int mrun = prec == VQE_C128 ? 3 : 4;   // 128-byte contiguous runs in high passes
+    std::vector<Group> gs;
+    if (n <= kmax) {
+        gs.push_back({n, n, n, (n >= 32 ? 0xffffffffu : ((1u << n) - 1u))});
+        return gs;
+    }
+    gs.push_back({kmax, kmax, kmax, (1u << kmax) - 1u});
+    const int rest = n - kmax, hmax = kmax - mrun;
+    const int ng = (rest + hmax - 1) / hmax;
+    int a = kmax;
+    for (int j = 0; j < ng; ++j) {
+        const int hj = rest / ng + (j < rest % ng ? 1 : 0);
+        const int k = mrun + hj;
+        gs.push_back({k, mrun, a, ((1u << k) - 1u) & ~((1u << mrun) - 1u)});
+        a += hj;
+    }
+    return gs;
+}
+
+struct Round {
+    int chunk;
+    std::vector<PassOp> ops;
+};
+
+struct HostPlan {
+    std::vector<Group> groups;
+    std::vector<PassDesc> fwd, bwd;
+    std::vector<int> pass_tiles_log2;
+    std::vector<StageSlot> stage;
+    std::vector<int> goff, gcnt, gstep;
+    size_t coef_stride = 0, dtab_stride = 0, grad_stride = 0;
+    int n_params = 0;
+};
+
+// Rounds of one pass: per slot, the gated tile bits are covered by register
+// chunks; chunk order alternates between slots so that consecutive slots
+// share the chunk at their boundary (the diagonal sits there).
+std::vector<Round> make_rounds(int k, int R, const std::vector<uint32_t> &slot_gated) {
+    std::vector<int> chunks;
+    for (int c = 0; c < k; c += R) chunks.push_back(std::min(c, k - R));
+    const int top = chunks.back();
+    std::vector<Round> rounds;
+    for (size_t s = 0; s < slot_gated.size(); ++s) {
+        std::vector<uint8_t> cmask(chunks.size(), 0);
+        uint32_t left = slot_gated[s];
+        for (size_t ci = 0; ci < chunks.size(); ++ci) {
+            for (int j = 0; j < R; ++j) {
+                const int bit = chunks[ci] + j;
+                if ((left >> bit) & 1u) {
+                    cmask[ci] |= uint8_t(1u << j);
+                    left &= ~(1u << bit);
+                }
+            }
+        }
+        std::vector<size_t> order;
+        for (size_t ci = 0; ci < chunks.size(); ++ci)
+            if (cmask[ci]) order.push_back(ci);
+        if (s % 2 == 0) std::reverse(order.begin(), order.end());
+        for (size_t ci : order) {
+            if (rounds.empty() || rounds.back().chunk != chunks[ci]) rounds.push_back({chunks[ci], {}});
+            rounds.back().ops.push_back({OP_BF, 0, cmask[ci], uint8_t(s)});
+        }
+        rounds.back().ops.push_back({OP_DIAG, 0, 0, uint8_t(s)});
+    }
+    if (rounds.back().chunk != top) rounds.push_back({top, {}});
+    return rounds;
+}
+
+int count_ops(const std::vector<Round> &rs) {
+    int c = 0;
+    for (auto &r : rs) c += 1 + int(r.ops.size());
+    return c;
+}
+
+void emit_forward(PassDesc &d, const std::vector<Round> &rs) {
+    int k = 0;
+    for (auto &r : rs) {
+        d.ops[k++] = {OP_ROUND, uint8_t(r.chunk), 0, 0};
+        for (auto &o : r.ops) d.ops[k++] = o;
+    }
+    d.n_ops = k;
+}
+
+void emit_backward(PassDesc &d, const std::vector<Round> &rs, int n_slots) {
+    std::vector<int> bf_left(n_slots, 0);
+    for (auto &r : rs)
+        for (auto &o : r.ops)
+            if (o.kind == OP_BF) bf_left[o.slot]++;
+    int k = 0;
+    for (auto it = rs.rbegin(); it != rs.rend(); ++it) {
+        d.ops[k++] = {OP_ROUND, uint8_t(it->chunk), 0, 0};
+        for (auto o = it->ops.rbegin(); o != it->ops.rend(); ++o) {
+            d.ops[k++] = *o;
+            if (o->kind == OP_BF && --bf_left[o->slot] == 0)
+                d.ops[k++] = {OP_FLUSH, 0, 0, o->slot};
+        }
+    }
+    d.n_ops = k;
+}
+
+bool make_plan(int n, int D, vqe_precision prec, HostPlan &hp, std::string &err) {
+    hp = HostPlan{};
+    hp.groups = plan_groups(n, prec);
+    const int ng = int(hp.groups.size());
+    const int Rdef = prec == VQE_C128 ? 3 : 4;
+
+    // Layer events in zigzag order; consecutive events of one group merge.
+    std::vector<PassPlan> plans;
+    for (int l = 0; l < D; ++l) {
+        for (int jj = 0; jj < ng; ++jj) {
+            const int g = (l % 2 == 0) ? jj : ng - 1 - jj;
+            if (!plans.empty() && plans.back().group == g) plans.back().layers.push_back(l);
+            else plans.push_back({g, {l}});
+        }
+    }
+    // Split passes whose program would not fit.
+    std::vector<PassPlan> split;
+    for (auto &p : plans) {
+        const Group &G = hp.groups[p.group];
+        const int R = std::min(Rdef, G.k);
+        PassPlan cur{p.group, {}};
+        for (int l : p.layers) {
+            cur.layers.push_back(l);
+            std::vector<uint32_t> gm(cur.layers.size(), G.gated);
+            const int nb = count_ops(make_rounds(G.k, R, gm)) + int(cur.layers.size());
+            if (int(cur.layers.size()) > kMaxSlots || nb > kMaxOps) {
+                cur.layers.pop_back();
+                split.push_back(cur);
+                cur.layers = {l};
+            }
+        }
+        split.push_back(cur);
+    }
+    plans.swap(split);
+
+    const int np = int(plans.size());
+    hp.fwd.assign(np, PassDesc{});
+    hp.bwd.assign(np, PassDesc{});
+    hp.pass_tiles_log2.assign(np, 0);
+    // slot ids in global order and where RY_l(q) lives
+    std::vector<std::vector<int>> slot_of(D, std::vector<int>(n, -1));
+    std::vector<std::pair<int, int>> slot_pos;   // global slot id -> (pass, slot)
+    for (int p = 0; p < np; ++p) {
+        const Group &G = hp.groups[plans[p].group];
+        for (size_t s = 0; s < plans[p].layers.size(); ++s) {
+            const int gid = int(slot_pos.size());
+            slot_pos.push_back({p, int(s)});
+            for (int j = 0; j < G.k; ++j)
+                if ((G.gated >> j) & 1u) slot_of[plans[p].layers[s]][G.qubit_of(j)] = gid;
+        }
+    }
+    for (int l = 0; l < D; ++l)
+        for (int q = 0; q < n; ++q)
+            if (slot_of[l][q] < 0) {
+                err = "planner left a qubit uncovered";
+                return false;
+            }
+
+    std::vector<StageSlot> stage;
+    size_t coef_off = 0, dtab_off = 0, grad_off = 0;
+    std::vector<size_t> slot_grad_off(slot_pos.size());
+    for (int p = 0; p < np; ++p) {
+        const Group &G = hp.groups[plans[p].group];
+        const int R = std::min(Rdef, G.k);
+        PassDesc &d = hp.fwd[p];
+        d.k = G.k;
+        d.m = G.m;
+        d.a = G.a;
+        d.R = R;
+        d.n_slots = int(plans[p].layers.size());
+        hp.pass_tiles_log2[p] = n - G.k;
+        std::vector<uint32_t> gm(d.n_slots, G.gated);
+        for (int s = 0; s < d.n_slots; ++s) {
+            const int l = plans[p].layers[s];
+            d.slot_layer[s] = l;
+            d.slot_gated[s] = G.gated;
+            d.slot_czmask[s] = 0;
+            if (coef_off > 0x7fffffff || dtab_off > 0x7fffffff || grad_off > 0x7fffffff) {
+                err = "plan tables exceed 2^31 entries";
+                return false;
+            }
+            d.slot_coef_off[s] = int(coef_off);
+            d.slot_dtab_off[s] = int(dtab_off);
+            d.slot_grad_off[s] = int(grad_off);
+            StageSlot ss{};
+            ss.k = G.k;
+            ss.layer = l;
+            ss.coef_off = int(coef_off);
+            ss.dtab_off = int(dtab_off);
+            for (int j = 0; j < G.k; ++j) {
+                if (!((G.gated >> j) & 1u)) continue;
+                ss.tile_bit[ss.n_gated] = uint8_t(j);
+                ss.qubit[ss.n_gated] = uint8_t(G.qubit_of(j));
+                ss.n_gated++;
+            }
+            stage.push_back(ss);
+            slot_grad_off[stage.size() - 1] = grad_off;
+            coef_off += G.k;
+            dtab_off += size_t(1) << G.k;
+            grad_off += (size_t(1) << (n - G.k)) * 2 * G.k;
+        }
+        const auto rounds = make_rounds(G.k, R, gm);
+        emit_forward(d, rounds);
+        hp.bwd[p] = d;
+        emit_backward(hp.bwd[p], rounds, d.n_slots);
+        // order in which the backward program un-rotates each slot's bits
+        std::vector<uint32_t> done(d.n_slots, 0);
+        std::vector<std::vector<uint16_t>> before(d.n_slots, std::vector<uint16_t>(G.k, 0));
+        int chunk = -1;
+        const PassDesc &bd = hp.bwd[p];
+        for (int oi = 0; oi < bd.n_ops; ++oi) {
+            const PassOp &o = bd.ops[oi];
+            if (o.kind == OP_ROUND) chunk = o.chunk;
+            if (o.kind != OP_BF) continue;
+            for (int j = 0; j < R; ++j) {
+                if (!((o.mask >> j) & 1)) continue;
+                before[o.slot][chunk + j] = uint16_t(done[o.slot]);
+                done[o.slot] |= 1u << (chunk + j);
+            }
+        }
+        const size_t first_stage = stage.size() - d.n_slots;
+        for (int s = 0; s < d.n_slots; ++s) {
+            StageSlot &ss = stage[first_stage + s];
+            for (int u = 0; u < ss.n_gated; ++u) ss.before[u] = before[s][ss.tile_bit[u]];
+        }
+    }
+    // CZ(q, q+1) of layer l goes to the later of the slots holding RY_l(q), RY_l(q+1).
+    for (int l = 0; l < D; ++l) {
+        for (int q = 0; q + 1 < n; ++q) {
+            const int gid = std::max(slot_of[l][q], slot_of[l][q + 1]);
+            const auto ps = slot_pos[gid];
+            hp.fwd[ps.first].slot_czmask[ps.second] |= (1u << q);
+            hp.bwd[ps.first].slot_czmask[ps.second] |= (1u << q);
+        }
+    }
+    // Gradient reduction map: param (l, q, comp) -> partial column.
+    const int NP = 2 * n * D;
+    std::vector<int> goff(NP), gcnt(NP), gstep(NP);
+    for (int l = 0; l < D; ++l) {
+        for (int q = 0; q < n; ++q) {
+            const int gid = slot_of[l][q];
+            const auto ps = slot_pos[gid];
+            const PassDesc &d = hp.fwd[ps.first];
+            const Group &G = hp.groups[plans[ps.first].group];
+            int j = -1;
+            for (int jj = 0; jj < G.k; ++jj)
+                if (((G.gated >> jj) & 1u) && G.qubit_of(jj) == q) j = jj;
+            for (int comp = 0; comp < 2; ++comp) {
+                const int pidx = (l * n + q) * 2 + comp;
+                goff[pidx] = int(slot_grad_off[gid]) + j * 2 + comp;
+                gcnt[pidx] = 1 << (n - d.k);
+                gstep[pidx] = 2 * d.k;
+            }
+        }
+    }
+    hp.coef_stride = coef_off;
+    hp.dtab_stride = dtab_off;
+    hp.grad_stride = grad_off;
+    hp.stage = stage;
+    hp.goff = goff;
+    hp.gcnt = gcnt;
+    hp.gstep = gstep;
+    hp.n_params = NP;
+    return true;
+}
+
+vqe_status build_plan(vqe_ctx *h) {
+    HostPlan hp;
+    std::string err;
+    if (!make_plan(h->n, h->depth, h->prec, hp, err)) return fail(h, VQE_ERR_STATE, err);
+    h->groups = hp.groups;
+    h->fwd = hp.fwd;
+    h->bwd = hp.bwd;
+    h->pass_tiles_log2 = hp.pass_tiles_log2;
+    h->coef_stride = hp.coef_stride;
+    h->dtab_stride = hp.dtab_stride;
+    h->grad_stride = hp.grad_stride;
+    h->n_stage = int(hp.stage.size());
+    h->n_params = hp.n_params;
+    vqe_status st;
+    if ((st = upload(h, h->d_fwd, h->fwd, "pass plan")) != VQE_OK) return st;
+    if ((st = upload(h, h->d_bwd, h->bwd, "pass plan")) != VQE_OK) return st;
+    if ((st = upload(h, h->d_stage, hp.stage, "stage plan")) != VQE_OK) return st;
+    if ((st = upload(h, h->d_goff, hp.goff, "grad map")) != VQE_OK) return st;
+    if ((st = upload(h, h->d_gcnt, hp.gcnt, "grad map")) != VQE_OK) return st;
+    if ((st = upload(h, h->d_gstep, hp.gstep, "grad map")) != VQE_OK) return st;
+    h->stats.ansatz_passes = uint32_t(h->fwd.size());
+    int kmax = 0;
+    for (auto &g : h->groups) kmax = std::max(kmax, g.k);
+    h->stats.tile_bits_max = uint32_t(kmax);
+    return VQE_OK;
+}
+
+// ---------------------------------------------------------------- Hamiltonian
+
+struct HamPlan {
+    std::vector<GroupDesc> groups;
+    std::vector<uint32_t> tz;
+    std::vector<double> tc;
+    uint64_t n_groups_nonempty = 0;
+};
+
+// Groups of kept terms by x mask (the x = 0 group always first, since it
+// also yields <psi|psi>); within a group A terms (kappa even) precede B
+// terms (kappa odd); the coefficient carries the sign (-1)^{floor(kappa/2)}.
+void make_ham_plan(const std::vector<uint64_t> &cx, const std::vector<uint64_t> &cz,
+                   const std::vector<double> &cc, const std::vector<uint8_t> &keep, HamPlan &hp) {
+    struct T3 { uint32_t x, z; int cls; double c; };
+    std::vector<T3> terms;
+    for (size_t t = 0; t < cc.size(); ++t) {
+        if (!keep[t]) continue;
+        const uint32_t x = uint32_t(cx[t]), z = uint32_t(cz[t]);
+        const int kappa = __builtin_popcount(x & z);
+        const double sign = ((kappa >> 1) & 1) ? -1.0 : 1.0;
+        terms.push_back({x, z, kappa & 1, cc[t] * sign});
+    }
+    std::stable_sort(terms.begin(), terms.end(), [](const T3 &p, const T3 &q) {
+        if (p.x != q.x) return p.x < q.x;
+        if (p.cls != q.cls) return p.cls < q.cls;
+        return p.z < q.z;
+    });
+    hp = HamPlan{};
+    auto open_group = [&](uint32_t x) {
+        GroupDesc g{};
+        g.x = x;
+        g.h = x ? 31 - __builtin_clz(x) : 0;
+        g.t_begin = int(hp.tz.size());
+        g.t_mid = g.t_begin;
+        g.t_end = g.t_begin;
+        hp.groups.push_back(g);
+    };
+    open_group(0);
+    for (size_t t = 0; t < terms.size(); ++t) {
+        if (terms[t].x != hp.groups.back().x) open_group(terms[t].x);
+        hp.tz.push_back(terms[t].z);
+        hp.tc.push_back(terms[t].c);
+        GroupDesc &g = hp.groups.back();
+        g.t_end = int(hp.tz.size());
+        if (terms[t].cls == 0) g.t_mid = g.t_end;
+    }
+    for (auto &g : hp.groups)
+        if (g.t_end > g.t_begin) hp.n_groups_nonempty++;
+}
+
+// Canonical form: equal strings merged (coefficients summed in input
+// order), exact zeros removed, sorted by (x, z).
+void canonicalise(const uint64_t *x, const uint64_t *z, const double *c, size_t n_terms,
+                  std::vector<uint64_t> &cx, std::vector<uint64_t> &cz, std::vector<double> &cc) {
+    std::vector<size_t> idx(n_terms);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t p, size_t q) {
+        if (x[p] != x[q]) return x[p] < x[q];
+        return z[p] < z[q];
+    });
+    cx.clear();
+    cz.clear();
+    cc.clear();
+    for (size_t i = 0; i < n_terms;) {
+        size_t j = i;
+        double s = 0.0;
+        while (j < n_terms && x[idx[j]] == x[idx[i]] && z[idx[j]] == z[idx[i]]) s += c[idx[j++]];
+        if (s != 0.0) {
+            cx.push_back(x[idx[i]]);
+            cz.push_back(z[idx[i]]);
+            cc.push_back(s);
+        }
+        i = j;
+    }
+}
+
+// Cutoff (Sec. II-D, III-D): keep |c| >= threshold; returns sum |c| dropped.
+double slim_keep(const std::vector<double> &cc, double threshold, std::vector<uint8_t> &keep,
+                 size_t &kept) {
+    keep.assign(cc.size(), 0);
+    kept = 0;
+    double dropped = 0.0;
+    for (size_t t = 0; t < cc.size(); ++t) {
+        if (std::fabs(cc[t]) >= threshold) {
+            keep[t] = 1;
+            ++kept;
+        } else {
+            dropped += std::fabs(cc[t]);
+        }
+    }
+    return dropped;
+}
+
+vqe_status build_ham_plan(vqe_ctx *h) {
+    HamPlan hp;
+    make_ham_plan(h->cx, h->cz, h->cc, h->keep, hp);
+    h->n_groups = int(hp.groups.size());
+    vqe_status st;
+    if ((st = upload(h, h->d_groups, hp.groups, "groups")) != VQE_OK) return st;
+    if ((st = upload(h, h->d_tz, hp.tz, "terms")) != VQE_OK) return st;
+    if (h->prec == VQE_C128) {
+        if ((st = upload(h, h->d_tc, hp.tc, "terms")) != VQE_OK) return st;
+    } else {
+        std::vector<float> tcf(hp.tc.begin(), hp.tc.end());
+        if ((st = upload(h, h->d_tc, tcf, "terms")) != VQE_OK) return st;
+    }
+    h->stats.n_groups = hp.n_groups_nonempty;
+    return VQE_OK;
+}
+
+// ---------------------------------------------------------------- buffers
+
+int capacity(const vqe_ctx *h, bool grad) {
+    const size_t per = h->state_bytes() * (grad ? 2 : 1);
+    if (!h->ws) return 0;
+    return int(std::min<size_t>(h->ws_bytes / per, 65535));   // grid.y limit
+}
+
+vqe_status ensure_workspace(vqe_ctx *h, int batch, bool grad) {
+    if (h->ws && !h->ws_owned) {
+        if (capacity(h, grad) < 1)
+            return fail(h, VQE_ERR_ARG, "bound workspace is smaller than one state set");
+        return VQE_OK;
+    }
+    const size_t want = h->state_bytes() * (grad ? 2 : 1) * size_t(batch);
+    if (h->ws && h->ws_bytes >= want) return VQE_OK;
+    size_t freeb = 0, total = 0;
+    VQE_CUDA(h, cudaMemGetInfo(&freeb, &total));
+    if (want > freeb) {
+        // shrink the batch to what fits (chunked runs), but at least one state set
+        const size_t one = h->state_bytes() * (grad ? 2 : 1);
+        if (one > freeb + h->ws_own.bytes)
+            return fail(h, VQE_ERR_OOM, "state workspace does not fit in device memory");
+    }
+    size_t bytes = std::min(want, std::max(h->state_bytes() * (grad ? 2 : 1),
+                                           (freeb + h->ws_own.bytes) / 10 * 9));
+    h->ws_own.release();
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    vqe_status st = ensure(h, h->ws_own, bytes, "state workspace");
+    if (st != VQE_OK) return st;
+    h->ws = h->ws_own.p;
+    h->ws_bytes = h->ws_own.bytes;
+    h->ws_owned = true;
+    return VQE_OK;
+}
+
+int blocks_per_state(const vqe_ctx *h, int batch) {
+    const uint64_t work = uint64_t(1) << std::max(0, h->n - 1);
+    int bps = (152 * 4 + batch - 1) / batch;
+    const uint64_t cap = (work + kEnergyThreads - 1) / kEnergyThreads;
+    if (uint64_t(bps) > cap) bps = int(cap);
+    return std::max(1, bps);
+}
+
+vqe_status ensure_scratch(vqe_ctx *h, int batch) {
+    const bool c128 = h->prec == VQE_C128;
+    const size_t coef_b = c128 ? sizeof(RotCoef<double>) : sizeof(RotCoef<float>);
+    vqe_status st;
+    if ((st = ensure(h, h->d_coefs, coef_b * h->coef_stride * batch + 16, "coefficients")) != VQE_OK)
+        return st;
+    if ((st = ensure(h, h->d_dtab, h->elem_bytes() * h->dtab_stride * batch + 16, "tables")) != VQE_OK)
+        return st;
+    // blocks_per_state(B) * B <= 152 * 4 + B - 1 for every chunk size B <= batch
+    if ((st = ensure(h, h->d_epart, sizeof(double) * 3 * (152 * 4 + size_t(batch)) + 16,
+                     "partials")) != VQE_OK)
+        return st;
+    if ((st = ensure(h, h->d_out, sizeof(double) * 4 * batch + 16, "results")) != VQE_OK) return st;
+    if ((st = ensure(h, h->d_params, sizeof(double) * h->n_params * batch + 16, "params")) != VQE_OK)
+        return st;
+    return VQE_OK;
+}
+
+vqe_status ensure_grad_scratch(vqe_ctx *h, int batch) {
+    return ensure(h, h->d_gpart, sizeof(double) * h->grad_stride * batch + 16, "grad partials");
+}
+
+// ---------------------------------------------------------------- pipelines
+
+template <typename T>
+vqe_status run_forward(vqe_ctx *h, const double *params_dev, int B, void *psi) {
+    cudaStream_t s = h->stream;
+    const size_t N = h->state_elems();
+    auto *coefs = static_cast<RotCoef<T> *>(h->d_coefs.p);
+    VQE_CUDA(h, launch_stage<T>(static_cast<const StageSlot *>(h->d_stage.p), h->n_stage, h->n,
+                                h->depth, params_dev, B, coefs, h->coef_stride, h->d_dtab.p,
+                                h->dtab_stride, s));
+    h->stats.kernel_launches++;
+    const PassDesc *dd = static_cast<const PassDesc *>(h->d_fwd.p);
+    const int mk = prof_begin(h, 0);
+    for (size_t p = 0; p < h->fwd.size(); ++p) {
+        VQE_CUDA(h, launch_pass<T>(dd + p, h->fwd[p], h->n, B, psi, nullptr, N, coefs,
+                                   h->coef_stride, h->d_dtab.p, h->dtab_stride, nullptr, 0, false,
+                                   p == 0 ? 1 : 0, s));
+        h->stats.kernel_launches++;
+    }
+    prof_end(h, mk, int(h->fwd.size()));
+    return VQE_OK;
+}
+
+template <typename T>
+vqe_status run_energy(vqe_ctx *h, int B, const void *psi, double *energies, double *norms,
+                      double *unnorm) {
+    const int bps = blocks_per_state(h, B);
+    const int mk = prof_begin(h, 1);
+    VQE_CUDA(h, launch_energy<T>(static_cast<const GroupDesc *>(h->d_groups.p), h->n_groups,
+                                 static_cast<const uint32_t *>(h->d_tz.p),
+                                 static_cast<const double *>(h->d_tc.p), h->n, B, psi,
+                                 h->state_elems(), static_cast<double *>(h->d_epart.p), bps,
+                                 h->stream));
+    prof_end(h, mk, 1);
+    VQE_CUDA(h, launch_energy_finish(static_cast<double *>(h->d_epart.p), bps, B, energies, norms,
+                                     unnorm, h->stream));
+    h->stats.kernel_launches += 2;
+    return VQE_OK;
+}
+
+template <typename T>
+vqe_status energy_chunk(vqe_ctx *h, const double *params_dev, int B, double *E, double *nrm) {
+    vqe_status st = run_forward<T>(h, params_dev, B, h->ws);
+    if (st != VQE_OK) return st;
+    return run_energy<T>(h, B, h->ws, E, nrm, nullptr);
+}
+
+template <typename T>
+vqe_status gradient_chunk(vqe_ctx *h, const double *params_dev, int B, double *grads,
+                          double *E) {
+    cudaStream_t s = h->stream;
+    const size_t N = h->state_elems();
+    void *psi = h->ws;
+    void *lam = static_cast<char *>(h->ws) + h->state_bytes() * size_t(B);
+    vqe_status st = run_forward<T>(h, params_dev, B, psi);
+    if (st != VQE_OK) return st;
+    const int bps = blocks_per_state(h, B);
+    const int mk_h = prof_begin(h, 2);
+    VQE_CUDA(h, launch_apply_h<T>(static_cast<const GroupDesc *>(h->d_groups.p), h->n_groups,
+                                  static_cast<const uint32_t *>(h->d_tz.p),
+                                  static_cast<const double *>(h->d_tc.p), h->n, B, psi, lam, N,
+                                  static_cast<double *>(h->d_epart.p), bps, s));
+    prof_end(h, mk_h, 1);
+    VQE_CUDA(h, launch_energy_finish(static_cast<double *>(h->d_epart.p), bps, B, E, nullptr,
+                                     nullptr, s));
+    h->stats.kernel_launches += 2;
+    auto *coefs = static_cast<RotCoef<T> *>(h->d_coefs.p);
+    const PassDesc *dd = static_cast<const PassDesc *>(h->d_bwd.p);
+    double *gpart = static_cast<double *>(h->d_gpart.p);
+    const int mk_b = prof_begin(h, 3);
+    for (int p = int(h->bwd.size()) - 1; p >= 0; --p) {
+        VQE_CUDA(h, launch_pass<T>(dd + p, h->bwd[p], h->n, B, psi, lam, N, coefs, h->coef_stride,
+                                   h->d_dtab.p, h->dtab_stride, gpart, h->grad_stride, true, 0, s));
+        h->stats.kernel_launches++;
+    }
+    prof_end(h, mk_b, int(h->bwd.size()));
+    VQE_CUDA(h, launch_grad_finish(gpart, h->grad_stride, static_cast<const int *>(h->d_goff.p),
+                                   static_cast<const int *>(h->d_gcnt.p),
+                                   static_cast<const int *>(h->d_gstep.p), h->n_params, B, grads,
+                                   s));
+    h->stats.kernel_launches++;
+    return VQE_OK;
+}
+
+template <typename T>
+vqe_status pergate_chunk(vqe_ctx *h, const double *params_dev, int B, double *E, double *nrm) {
+    cudaStream_t s = h->stream;
+    const size_t N = h->state_elems();
+    const int n = h->n, P = h->n_params;
+    VQE_CUDA(h, launch_init_zero_state<T>(h->ws, N, n, B, s));
+    h->stats.kernel_launches++;
+    for (int l = 0; l < h->depth; ++l) {
+        for (int q = 0; q < n; ++q) {
+            VQE_CUDA(h, launch_gate_ry<T>(h->ws, N, n, B, q, params_dev, (l * n + q) * 2, P, s));
+            VQE_CUDA(h, launch_gate_rz<T>(h->ws, N, n, B, q, params_dev, (l * n + q) * 2 + 1, P, s));
+            h->stats.kernel_launches += 2;
+        }
+        for (int q = 0; q + 1 < n; ++q) {
+            VQE_CUDA(h, launch_gate_cz<T>(h->ws, N, n, B, q, s));
+            h->stats.kernel_launches++;
+        }
+    }
+    return run_energy<T>(h, B, h->ws, E, nrm, nullptr);
+}
+
+enum class Job { Energy, Gradient, PerGate };
+
+vqe_status run_batch(vqe_ctx *h, Job job, const double *params_dev, int batch, double *E,
+                     double *nrm, double *grads) {
+    if (!h->ham_set) return fail(h, VQE_ERR_STATE, "no Hamiltonian set");
+    if (batch < 1) return fail(h, VQE_ERR_ARG, "batch must be >= 1");
+    if (!params_dev) return fail(h, VQE_ERR_ARG, "params is NULL");
+    const bool grad = job == Job::Gradient;
+    vqe_status st = ensure_workspace(h, batch, grad);
+    if (st != VQE_OK) return st;
+    const int cap = std::max(1, std::min(batch, capacity(h, grad)));
+    if ((st = ensure_scratch(h, cap)) != VQE_OK) return st;
+    if (grad && (st = ensure_grad_scratch(h, cap)) != VQE_OK) return st;
+    for (int b0 = 0; b0 < batch; b0 += cap) {
+        const int B = std::min(cap, batch - b0);
+        const double *pp = params_dev + size_t(b0) * h->n_params;
+        double *e = E ? E + b0 : nullptr;
+        double *nn = nrm ? nrm + b0 : nullptr;
+        const bool c128 = h->prec == VQE_C128;
+        switch (job) {
+            case Job::Energy:
+                st = c128 ? energy_chunk<double>(h, pp, B, e, nn) : energy_chunk<float>(h, pp, B, e, nn);
+                break;
+            case Job::PerGate:
+                st = c128 ? pergate_chunk<double>(h, pp, B, e, nn) : pergate_chunk<float>(h, pp, B, e, nn);
+                break;
+            case Job::Gradient: {
+                double *g = grads + size_t(b0) * h->n_params;
+                st = c128 ? gradient_chunk<double>(h, pp, B, g, e) : gradient_chunk<float>(h, pp, B, g, e);
+                break;
+            }
+        }
+        if (st != VQE_OK) return st;
+    }
+    return VQE_OK;
+}
+
+bool finite_params(const double *p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+
+extern "C" {
+
+const char *vqe_version(void) { return "vqe-gb300 0.1 (sm_103a)"; }
+
+const char *vqe_last_error(vqe_handle h) { return h ? h->err.c_str() : "NULL handle"; }
+
+vqe_status vqe_create(int n_qubits, int depth, vqe_precision precision, void *cuda_stream,
+                      vqe_handle *out) {
+    if (!out) return VQE_ERR_ARG;
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > 32 || depth < 1 || depth > 4096) return VQE_ERR_ARG;
+    if (precision != VQE_C64 && precision != VQE_C128) return VQE_ERR_ARG;
+    vqe_ctx *h = new vqe_ctx();
+    h->n = n_qubits;
+    h->depth = depth;
+    h->prec = precision;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return VQE_ERR_CUDA;
+    }
+    vqe_status st = build_plan(h);
+    if (st != VQE_OK) {
+        vqe_destroy(h);
+        return st;
+    }
+    *out = h;
+    return VQE_OK;
+}
+
+vqe_status vqe_destroy(vqe_handle h) {
+    if (!h) return VQE_ERR_ARG;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (DevBuf *b : {&h->d_groups, &h->d_tz, &h->d_tc, &h->d_fwd, &h->d_bwd, &h->d_stage,
+                      &h->d_goff, &h->d_gcnt, &h->d_gstep, &h->ws_own, &h->d_params, &h->d_coefs,
+                      &h->d_dtab, &h->d_gpart, &h->d_epart, &h->d_out, &h->hb_params,
+                      &h->hb_e, &h->hb_n, &h->hb_g})
+        b->release();
+    delete h;
+    return VQE_OK;
+}
+
+vqe_status vqe_workspace_size(vqe_handle h, int batch, int want_gradient, size_t *bytes) {
+    if (!h || !bytes || batch < 1) return fail(h, VQE_ERR_ARG, "bad argument");
+    *bytes = h->state_bytes() * (want_gradient ? 2 : 1) * size_t(batch);
+    return VQE_OK;
+}
+
+vqe_status vqe_bind_workspace(vqe_handle h, void *dev_ptr, size_t bytes) {
+    if (!h) return VQE_ERR_ARG;
+    if (dev_ptr == nullptr) {
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+        h->ws_owned = false;
+        h->state_valid = false;
+        return VQE_OK;
+    }
+    if (reinterpret_cast<uintptr_t>(dev_ptr) % 256 != 0)
+        return fail(h, VQE_ERR_ARG, "workspace must be 256-byte aligned");
+    if (bytes < h->state_bytes())
+        return fail(h, VQE_ERR_ARG, "workspace smaller than one state");
+    h->ws_own.release();
+    h->ws = dev_ptr;
+    h->ws_bytes = bytes;
+    h->ws_owned = false;
+    h->state_valid = false;
+    return VQE_OK;
+}
+
+vqe_status vqe_set_hamiltonian(vqe_handle h, const uint64_t *x_masks, const uint64_t *z_masks,
+                               const double *coeffs, size_t n_terms) {
+    if (!h) return VQE_ERR_ARG;
+    if (n_terms > 0 && (!x_masks || !z_masks || !coeffs))
+        return fail(h, VQE_ERR_ARG, "NULL term array");
+    if (n_terms > (size_t(1) << 30)) return fail(h, VQE_ERR_ARG, "too many terms");
+    const uint64_t lim = h->n >= 64 ? ~0ull : ((uint64_t(1) << h->n) - 1);
+    for (size_t t = 0; t < n_terms; ++t) {
+        if ((x_masks[t] & ~lim) || (z_masks[t] & ~lim))
+            return fail(h, VQE_ERR_ARG, "Pauli mask has a bit at or above n_qubits (term " +
+                                            std::to_string(t) + ")");
+        if (!std::isfinite(coeffs[t]))
+            return fail(h, VQE_ERR_ARG, "non-finite coefficient (term " + std::to_string(t) + ")");
+    }
+    std::vector<uint64_t> cx, cz;
+    std::vector<double> cc;
+    canonicalise(x_masks, z_masks, coeffs, n_terms, cx, cz, cc);
+    h->cx.swap(cx);
+    h->cz.swap(cz);
+    h->cc.swap(cc);
+    h->keep.assign(h->cc.size(), 1);
+    vqe_status st = build_ham_plan(h);
+    if (st != VQE_OK) {
+        h->cx.swap(cx);
+        h->cz.swap(cz);
+        h->cc.swap(cc);
+        h->keep.assign(h->cc.size(), 1);
+        return st;
+    }
+    h->ham_set = true;
+    h->stats.n_terms_input = n_terms;
+    h->stats.n_terms_canonical = h->cc.size();
+    h->stats.n_terms_kept = h->cc.size();
+    h->stats.sum_abs_dropped = 0.0;
+    h->stats.threshold = 0.0;
+    return VQE_OK;
+}
+
+vqe_status vqe_slim(vqe_handle h, double threshold, size_t *n_kept, double *sum_abs_dropped) {
+    if (!h) return VQE_ERR_ARG;
+    if (!h->ham_set) return fail(h, VQE_ERR_STATE, "no Hamiltonian set");
+    if (!(threshold >= 0.0) || !std::isfinite(threshold))
+        return fail(h, VQE_ERR_ARG, "threshold must be finite and >= 0");
+    std::vector<uint8_t> old = h->keep;
+    size_t kept = 0;
+    const double dropped = slim_keep(h->cc, threshold, h->keep, kept);
+    vqe_status st = build_ham_plan(h);
+    if (st != VQE_OK) {
+        h->keep.swap(old);
+        return st;
+    }
+    h->stats.n_terms_kept = kept;
+    h->stats.sum_abs_dropped = dropped;
+    h->stats.threshold = threshold;
+    if (n_kept) *n_kept = kept;
+    if (sum_abs_dropped) *sum_abs_dropped = dropped;
+    return VQE_OK;
+}
+
+vqe_status vqe_apply_ansatz(vqe_handle h, const double *params) {
+    if (!h) return VQE_ERR_ARG;
+    if (!params) return fail(h, VQE_ERR_ARG, "params is NULL");
+    if (!finite_params(params, h->n_params)) return fail(h, VQE_ERR_ARG, "non-finite parameter");
+    vqe_status st = ensure_workspace(h, 1, false);
+    if (st != VQE_OK) return st;
+    if ((st = ensure_scratch(h, 1)) != VQE_OK) return st;
+    VQE_CUDA(h, cudaMemcpyAsync(h->d_params.p, params, sizeof(double) * h->n_params,
+                                cudaMemcpyHostToDevice, h->stream));
+    const double *pd = static_cast<const double *>(h->d_params.p);
+    st = h->prec == VQE_C128 ? run_forward<double>(h, pd, 1, h->ws) : run_forward<float>(h, pd, 1, h->ws);
+    if (st != VQE_OK) return st;
+    VQE_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->state_valid = true;
+    return VQE_OK;
+}
+
+vqe_status vqe_energy(vqe_handle h, double *energy, double *norm) {
+    if (!h) return VQE_ERR_ARG;
+    if (!h->ham_set) return fail(h, VQE_ERR_STATE, "no Hamiltonian set");
+    if (!h->state_valid) return fail(h, VQE_ERR_STATE, "no state: call vqe_apply_ansatz first");
+    vqe_status st = ensure_scratch(h, 1);
+    if (st != VQE_OK) return st;
+    double *out = static_cast<double *>(h->d_out.p);
+    st = h->prec == VQE_C128 ? run_energy<double>(h, 1, h->ws, out, out + 1, nullptr)
+                             : run_energy<float>(h, 1, h->ws, out, out + 1, nullptr);
+    if (st != VQE_OK) return st;
+    double host[2];
+    VQE_CUDA(h, cudaMemcpyAsync(host, out, sizeof(host), cudaMemcpyDeviceToHost, h->stream));
+    VQE_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (energy) *energy = host[0];
+    if (norm) *norm = host[1];
+    return VQE_OK;
+}
+
+vqe_status vqe_get_state(vqe_handle h, void *host_out, size_t bytes) {
+    if (!h) return VQE_ERR_ARG;
+    if (!host_out || bytes != h->state_bytes()) return fail(h, VQE_ERR_ARG, "bad output buffer size");
+    if (!h->state_valid) return fail(h, VQE_ERR_STATE, "no state: call vqe_apply_ansatz first");
+    VQE_CUDA(h, cudaMemcpyAsync(host_out, h->ws, bytes, cudaMemcpyDeviceToHost, h->stream));
+    VQE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return VQE_OK;
+}
+
+vqe_status vqe_gradient(vqe_handle h, const double *params, double *grad, double *energy) {
+    if (!h) return VQE_ERR_ARG;
+    if (!params || !grad) return fail(h, VQE_ERR_ARG, "NULL argument");
+    return vqe_gradient_batch(h, params, 1, grad, energy);
+}
+
+vqe_status vqe_energy_batch_dev(vqe_handle h, const double *params_dev, int batch,
+                                double *energies_dev, double *norms_dev) {
+    if (!h) return VQE_ERR_ARG;
+    if (!energies_dev) return fail(h, VQE_ERR_ARG, "energies is NULL");
+    h->state_valid = false;
+    return run_batch(h, Job::Energy, params_dev, batch, energies_dev, norms_dev, nullptr);
+}
+
+vqe_status vqe_gradient_batch_dev(vqe_handle h, const double *params_dev, int batch,
+                                  double *grads_dev, double *energies_dev) {
+    if (!h) return VQE_ERR_ARG;
+    if (!grads_dev) return fail(h, VQE_ERR_ARG, "grads is NULL");
+    h->state_valid = false;
+    return run_batch(h, Job::Gradient, params_dev, batch, energies_dev, nullptr, grads_dev);
+}
+
+vqe_status vqe_energy_batch_pergate_dev(vqe_handle h, const double *params_dev, int batch,
+                                        double *energies_dev, double *norms_dev) {
+    if (!h) return VQE_ERR_ARG;
+    if (!energies_dev) return fail(h, VQE_ERR_ARG, "energies is NULL");
+    h->state_valid = false;
+    return run_batch(h, Job::PerGate, params_dev, batch, energies_dev, norms_dev, nullptr);
+}
+
+static vqe_status host_batch(vqe_handle h, Job job, const double *params, int batch, double *E,
+                             double *nrm, double *grads) {
+    if (!h) return VQE_ERR_ARG;
+    if (!params || batch < 1) return fail(h, VQE_ERR_ARG, "bad params/batch");
+    if (!finite_params(params, size_t(batch) * h->n_params))
+        return fail(h, VQE_ERR_ARG, "non-finite parameter");
+    const size_t P = size_t(h->n_params) * batch;
+    DevBuf &dp = h->hb_params, &de = h->hb_e, &dn = h->hb_n, &dg = h->hb_g;
+    vqe_status st = ensure(h, dp, P * sizeof(double), "params");
+    if (st == VQE_OK) st = ensure(h, de, batch * sizeof(double), "energies");
+    if (st == VQE_OK) st = ensure(h, dn, batch * sizeof(double), "norms");
+    if (st == VQE_OK && job == Job::Gradient) st = ensure(h, dg, P * sizeof(double), "grads");
+    if (st == VQE_OK) {
+        cudaError_t e = cudaMemcpyAsync(dp.p, params, P * sizeof(double), cudaMemcpyHostToDevice,
+                                        h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "cudaMemcpyAsync(params)");
+    }
+    if (st == VQE_OK) {
+        h->state_valid = false;
+        st = run_batch(h, job, static_cast<double *>(dp.p), batch, static_cast<double *>(de.p),
+                       job == Job::Gradient ? nullptr : static_cast<double *>(dn.p),
+                       static_cast<double *>(dg.p));
+    }
+    if (st == VQE_OK && E) {
+        cudaError_t e = cudaMemcpyAsync(E, de.p, batch * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "cudaMemcpyAsync(energies)");
+    }
+    if (st == VQE_OK && nrm && job != Job::Gradient) {
+        cudaError_t e = cudaMemcpyAsync(nrm, dn.p, batch * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "cudaMemcpyAsync(norms)");
+    }
+    if (st == VQE_OK && grads) {
+        cudaError_t e = cudaMemcpyAsync(grads, dg.p, P * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "cudaMemcpyAsync(grads)");
+    }
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (st == VQE_OK && e != cudaSuccess) st = cuda_fail(h, e, "cudaStreamSynchronize");
+    return st;
+}
+
+vqe_status vqe_energy_batch(vqe_handle h, const double *params, int batch, double *energies,
+                            double *norms) {
+    return host_batch(h, Job::Energy, params, batch, energies, norms, nullptr);
+}
+
+vqe_status vqe_gradient_batch(vqe_handle h, const double *params, int batch, double *grads,
+                              double *energies) {
+    if (!grads) return fail(h, VQE_ERR_ARG, "grads is NULL");
+    return host_batch(h, Job::Gradient, params, batch, energies, nullptr, grads);
+}
+
+vqe_status vqe_profile(vqe_handle h, int enable) {
+    if (!h) return VQE_ERR_ARG;
+    vqe_status st = prof_collect(h);
+    if (st != VQE_OK) return st;
+    h->prof = enable != 0;
+    h->times = vqe_kernel_times{};
+    return VQE_OK;
+}
+
+vqe_status vqe_profile_read(vqe_handle h, vqe_kernel_times *out) {
+    if (!h || !out) return VQE_ERR_ARG;
+    vqe_status st = prof_collect(h);
+    if (st != VQE_OK) return st;
+    *out = h->times;
+    return VQE_OK;
+}
+
+vqe_status vqe_get_stats(vqe_handle h, vqe_stats *out) {
+    if (!h || !out) return VQE_ERR_ARG;
+    *out = h->stats;
+    return VQE_OK;
+}
+
+}  // extern "C"
+
+// ================================================================= inspection (host only)
+
+#include "vqe_inspect.h"
+
+extern "C" {
+
+size_t vqe_inspect_sizeof(int which) {
+    switch (which) {
+        case 0: return sizeof(PassDesc);
+        case 1: return sizeof(StageSlot);
+        case 2: return sizeof(GroupDesc);
+        default: return 0;
+    }
+}
+
+int vqe_inspect_plan(int n_qubits, int depth, int precision, void *fwd, void *bwd, int max_passes,
+                     void *stage, int max_stage, int *grad_map, int max_params,
+                     uint64_t strides[3], int counts[3]) {
+    if (n_qubits < 1 || n_qubits > 32 || depth < 1 || (precision != 0 && precision != 1)) return -1;
+    HostPlan hp;
+    std::string err;
+    if (!make_plan(n_qubits, depth, vqe_precision(precision), hp, err)) return -1;
+    if (counts) {
+        counts[0] = int(hp.fwd.size());
+        counts[1] = int(hp.stage.size());
+        counts[2] = hp.n_params;
+    }
+    if (strides) {
+        strides[0] = hp.coef_stride;
+        strides[1] = hp.dtab_stride;
+        strides[2] = hp.grad_stride;
+    }
+    if (int(hp.fwd.size()) > max_passes || int(hp.stage.size()) > max_stage ||
+        hp.n_params > max_params)
+        return -1;
+    if (fwd) std::memcpy(fwd, hp.fwd.data(), hp.fwd.size() * sizeof(PassDesc));
+    if (bwd) std::memcpy(bwd, hp.bwd.data(), hp.bwd.size() * sizeof(PassDesc));
+    if (stage) std::memcpy(stage, hp.stage.data(), hp.stage.size() * sizeof(StageSlot));
+    if (grad_map)
+        for (int p = 0; p < hp.n_params; ++p) {
+            grad_map[3 * p] = hp.goff[p];
+            grad_map[3 * p + 1] = hp.gcnt[p];
+            grad_map[3 * p + 2] = hp.gstep[p];
+        }
+    return 0;
+}
+
+int vqe_inspect_hamiltonian(int n_qubits, const uint64_t *x_masks, const uint64_t *z_masks,
+                            const double *coeffs, size_t n_terms, double threshold, void *groups,
+                            int max_groups, uint32_t *tz, double *tc, int max_terms, int counts[2],
+                            double *sum_abs_dropped, uint64_t *n_canonical) {
+    if (n_qubits < 1 || n_qubits > 32) return -1;
+    if (n_terms && (!x_masks || !z_masks || !coeffs)) return -1;
+    if (!(threshold >= 0.0) || !std::isfinite(threshold)) return -1;
+    const uint64_t lim = (uint64_t(1) << n_qubits) - 1;
+    for (size_t t = 0; t < n_terms; ++t)
+        if ((x_masks[t] & ~lim) || (z_masks[t] & ~lim) || !std::isfinite(coeffs[t])) return -1;
+    std::vector<uint64_t> cx, cz;
+    std::vector<double> cc;
+    canonicalise(x_masks, z_masks, coeffs, n_terms, cx, cz, cc);
+    std::vector<uint8_t> keep;
+    size_t kept = 0;
+    const double dropped = slim_keep(cc, threshold, keep, kept);
+    HamPlan hp;
+    make_ham_plan(cx, cz, cc, keep, hp);
+    if (counts) {
+        counts[0] = int(hp.groups.size());
+        counts[1] = int(hp.tz.size());
+    }
+    if (sum_abs_dropped) *sum_abs_dropped = dropped;
+    if (n_canonical) *n_canonical = cc.size();
+    if (int(hp.groups.size()) > max_groups || int(hp.tz.size()) > max_terms) return -1;
+    if (groups) std::memcpy(groups, hp.groups.data(), hp.groups.size() * sizeof(GroupDesc));
+    if (tz) std::memcpy(tz, hp.tz.data(), hp.tz.size() * sizeof(uint32_t));
+    if (tc) std::memcpy(tc, hp.tc.data(), hp.tc.size() * sizeof(double));
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Internal declarations shared by the host planner and the CUDA kernels of
+// libvqe_gb300.  Nothing here is part of the public C ABI (include/vqe.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace vqe {
+
+// ---------------------------------------------------------------- ansatz passes
+//
+// The ansatz layer l is  CZ_chain * prod_q RZ_q(phi_{l,q}) * prod_q RY_q(theta_{l,q}).
+// Its qubits are split into groups; one "pass" stages one tile of 2^k
+// amplitudes per CTA in shared memory, where the tile spans the pass's
+// qubit group, and applies every gate of one or more layers that acts on
+// those qubits.  A pass program is a list of ops interpreted by the kernel:
+//   OP_ROUND(chunk)   move the thread's registers to a new set of R tile bits
+//                     [chunk, chunk+R) (through shared memory; the first
+//                     round loads from global memory)
+//   OP_BF(slot,mask)  RY butterflies of `slot` on register bits in `mask`
+//   OP_DIAG(slot)     RZ phases + RY scale (table) and CZ signs of `slot`
+//   OP_FLUSH(slot)    (backward only) reduce this slot's gradient partials
+// A "slot" is one layer's share of the pass.
+
+constexpr int kMaxOps = 384;
+constexpr int kMaxSlots = 40;
+constexpr int kMaxTileBits = 14;
+
+enum OpKind : uint8_t { OP_ROUND = 0, OP_BF = 1, OP_DIAG = 2, OP_FLUSH = 3 };
+
+struct PassOp {
+    uint8_t kind;
+    uint8_t chunk;  // OP_ROUND: first tile bit of the register chunk
+    uint8_t mask;   // OP_BF: register bits whose gate is applied
+    uint8_t slot;   // OP_BF / OP_DIAG / OP_FLUSH: slot index within the pass
+};
+
+struct PassDesc {
+    int k;          // tile bits (tile = 2^k amplitudes)
+    int m;          // low tile bits = global bits [0, m) (contiguous run of 2^m amplitudes)
+    int a;          // tile bits [m, k) = global bits [a, a + k - m)
+    int R;          // register bits per thread (thread holds 2^R amplitudes)
+    int n_ops;
+    int n_slots;
+    int slot_layer[kMaxSlots];
+    uint32_t slot_czmask[kMaxSlots];  // bit q: CZ(q, q+1) applied in this slot's DIAG
+    uint32_t slot_gated[kMaxSlots];   // tile bits gated (RY, RZ) in this slot
+    int slot_coef_off[kMaxSlots];     // per-state index of this slot's coefficient row (k entries)
+    int slot_dtab_off[kMaxSlots];     // per-state index (complex entries) of this slot's 2^k table
+    int slot_grad_off[kMaxSlots];     // per-state index (doubles) of this slot's gradient partials
+    PassOp ops[kMaxOps];
+};
+
+// Rotation coefficient of one gated tile bit: RY(theta) = scale * B with
+//   mode 0 ("tan"): B = [[1, -v], [v, 1]], v = tan(theta/2), scale = cos(theta/2)
+//   mode 1 ("cot"): B = [[v, -1], [1, v]], v = cot(theta/2), scale = sin(theta/2)
+// The mode keeps |v| <= 1.  The scales of a slot go into its diagonal table.
+// In the backward sweep both buffers carry, when bit j's gradient is taken,
+// the factor f_j = sigma / prod(scales of the bits un-rotated before j);
+// gs = 1 / f_j^2 undoes it in the gradient partials.
+template <typename T>
+struct RotCoef {
+    T v;
+    T gs;
+    int mode;
+};
+
+// Staging job: one slot of one pass (one row of coefficients and one table).
+struct StageSlot {
+    int k;             // tile bits of the pass
+    int layer;
+    int coef_off;      // per state
+    int dtab_off;      // per state
+    int n_gated;
+    uint8_t tile_bit[kMaxTileBits];  // gated tile bits
+    uint8_t qubit[kMaxTileBits];     // their global qubits
+    uint16_t before[kMaxTileBits];   // tile bits un-rotated before this one in the backward sweep
+};
+
+// ---------------------------------------------------------------- Hamiltonian
+//
+// Terms grouped by x mask.  For a group with mask x and top bit h, every
+// pair (i, i^x) with bit h of i clear contributes
+//     2 * [ a * FA(i) + b * FB(i) ],   a + ib = conj(psi_i) psi_{i^x},
+//     FA(i) = sum_{A terms} c' (-1)^{popc(i & z)},  FB likewise,
+// where A terms have kappa = popc(x & z) even, B terms odd, and
+// c' = c * (-1)^{floor(kappa/2)} (the phase (-i)^kappa of the Pauli string
+// folded into a sign).  The x = 0 group contributes |psi_i|^2 FA(i).
+struct GroupDesc {
+    uint32_t x;
+    int h;         // top bit of x (unused when x == 0)
+    int t_begin;   // A terms: [t_begin, t_mid); B terms: [t_mid, t_end)
+    int t_mid;
+    int t_end;
+};
+
+// Per-state reduction layout of the energy kernels.
+constexpr int kEnergyThreads = 256;
+
+// ---------------------------------------------------------------- launchers
+// Each returns cudaGetLastError() after queueing.
+
+template <typename T>
+cudaError_t launch_stage(const StageSlot *slots_dev, int n_slots, int n_qubits, int depth,
+                         const double *params, int batch, RotCoef<T> *coefs, size_t coef_stride,
+                         void *dtab, size_t dtab_stride, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_pass(const PassDesc *desc_dev, const PassDesc &desc_host, int n_qubits,
+                        int batch, void *psi, void *lam, size_t state_stride,
+                        const RotCoef<T> *coefs, size_t coef_stride, const void *dtab,
+                        size_t dtab_stride, double *grad_part, size_t grad_stride, bool backward,
+                        int init_zero, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_energy(const GroupDesc *groups, int n_groups, const uint32_t *tz,
+                          const double *tc, int n_qubits, int batch, const void *psi,
+                          size_t state_stride, double *partials, int blocks_per_state,
+                          cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_apply_h(const GroupDesc *groups, int n_groups, const uint32_t *tz,
+                           const double *tc, int n_qubits, int batch, const void *psi,
+                           void *lam, size_t state_stride, double *partials,
+                           int blocks_per_state, cudaStream_t s);
+
+cudaError_t launch_energy_finish(const double *partials, int blocks_per_state, int batch,
+                                 double *energies, double *norms, double *unnorm,
+                                 cudaStream_t s);
+
+// Gradient reduction: param p of state b sums `count` partials at
+// part[b*stride + off[p] + j*step], j = 0..count-1.
+cudaError_t launch_grad_finish(const double *part, size_t part_stride, const int *off,
+                               const int *count, const int *step, int n_params, int batch,
+                               double *grads, cudaStream_t s);
+
+// One gate per pass (reference kernel): RY/RZ on qubit q, or CZ(q, q+1).
+template <typename T>
+cudaError_t launch_gate_ry(void *psi, size_t stride, int n, int batch, int q, const double *params,
+                           int pidx, int pstride, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gate_rz(void *psi, size_t stride, int n, int batch, int q, const double *params,
+                           int pidx, int pstride, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gate_cz(void *psi, size_t stride, int n, int batch, int q, cudaStream_t s);
+template <typename T>
+cudaError_t launch_init_zero_state(void *psi, size_t stride, int n, int batch, cudaStream_t s);
+
+int pass_threads(const PassDesc &d);
+size_t pass_smem_bytes(const PassDesc &d, bool backward, size_t elem_bytes);
+
+}  // namespace vqe

@@ -1,0 +1,107 @@
+"""Host-only views of the plans libvqe_gb300 builds (include/vqe_inspect.h).
+
+The library's own planners run on the host and their records are copied
+out, so tests can check index arithmetic and plan semantics without a GPU.
+The ctypes records below mirror the library's internal layouts; their sizes
+are checked against ``vqe_inspect_sizeof`` on every call.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from .binding import load
+
+K_MAX_OPS = 384
+K_MAX_SLOTS = 40
+K_MAX_TILE_BITS = 14
+OP_ROUND, OP_BF, OP_DIAG, OP_FLUSH = 0, 1, 2, 3
+
+
+class PassOp(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint8), ("chunk", ctypes.c_uint8), ("mask", ctypes.c_uint8),
+                ("slot", ctypes.c_uint8)]
+
+
+class PassDesc(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("m", ctypes.c_int), ("a", ctypes.c_int), ("R", ctypes.c_int),
+                ("n_ops", ctypes.c_int), ("n_slots", ctypes.c_int),
+                ("slot_layer", ctypes.c_int * K_MAX_SLOTS),
+                ("slot_czmask", ctypes.c_uint32 * K_MAX_SLOTS),
+                ("slot_gated", ctypes.c_uint32 * K_MAX_SLOTS),
+                ("slot_coef_off", ctypes.c_int * K_MAX_SLOTS),
+                ("slot_dtab_off", ctypes.c_int * K_MAX_SLOTS),
+                ("slot_grad_off", ctypes.c_int * K_MAX_SLOTS),
+                ("ops", PassOp * K_MAX_OPS)]
+
+
+class StageSlot(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("layer", ctypes.c_int), ("coef_off", ctypes.c_int),
+                ("dtab_off", ctypes.c_int), ("n_gated", ctypes.c_int),
+                ("tile_bit", ctypes.c_uint8 * K_MAX_TILE_BITS),
+                ("qubit", ctypes.c_uint8 * K_MAX_TILE_BITS),
+                ("before", ctypes.c_uint16 * K_MAX_TILE_BITS)]
+
+
+class GroupDesc(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_uint32), ("h", ctypes.c_int), ("t_begin", ctypes.c_int),
+                ("t_mid", ctypes.c_int), ("t_end", ctypes.c_int)]
+
+
+def _check_layouts(lib):
+    for which, cls in enumerate((PassDesc, StageSlot, GroupDesc)):
+        got = lib.vqe_inspect_sizeof(which)
+        if got != ctypes.sizeof(cls):
+            raise RuntimeError(f"record layout mismatch for {cls.__name__}: library {got}, "
+                               f"binding {ctypes.sizeof(cls)}")
+
+
+def plan(n_qubits: int, depth: int, precision: str = "c64") -> dict:
+    """The tile-pass plan: forward/backward pass records, staging slots, gradient map."""
+    lib = load()
+    _check_layouts(lib)
+    prec = {"c64": 0, "c128": 1}[precision]
+    strides = (ctypes.c_uint64 * 3)()
+    counts = (ctypes.c_int * 3)()
+    rc = lib.vqe_inspect_plan(n_qubits, depth, prec, None, None, 0, None, 0, None, 0, strides, counts)
+    npass, nstage, nparams = counts[0], counts[1], counts[2]
+    fwd = (PassDesc * npass)()
+    bwd = (PassDesc * npass)()
+    stage = (StageSlot * nstage)()
+    gmap = np.zeros(3 * nparams, dtype=np.int32)
+    rc = lib.vqe_inspect_plan(n_qubits, depth, prec, ctypes.addressof(fwd), ctypes.addressof(bwd),
+                              npass, ctypes.addressof(stage), nstage, gmap.ctypes.data, nparams,
+                              strides, counts)
+    if rc != 0:
+        raise ValueError("vqe_inspect_plan rejected the arguments")
+    return {"fwd": list(fwd), "bwd": list(bwd), "stage": list(stage),
+            "grad_map": gmap.reshape(nparams, 3), "coef_stride": strides[0],
+            "dtab_stride": strides[1], "grad_stride": strides[2]}
+
+
+def hamiltonian(n_qubits: int, x, z, c, threshold: float = 0.0) -> dict:
+    """Canonical, cut and grouped terms as the library prepares them."""
+    lib = load()
+    _check_layouts(lib)
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    z = np.ascontiguousarray(z, dtype=np.uint64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    counts = (ctypes.c_int * 2)()
+    dropped = ctypes.c_double()
+    ncanon = ctypes.c_uint64()
+    lib.vqe_inspect_hamiltonian(n_qubits, x.ctypes.data, z.ctypes.data, c.ctypes.data, c.size,
+                                float(threshold), None, 0, None, None, 0, counts,
+                                ctypes.byref(dropped), ctypes.byref(ncanon))
+    ng, nt = counts[0], counts[1]
+    groups = (GroupDesc * max(ng, 1))()
+    tz = np.zeros(max(nt, 1), dtype=np.uint32)
+    tc = np.zeros(max(nt, 1), dtype=np.float64)
+    rc = lib.vqe_inspect_hamiltonian(n_qubits, x.ctypes.data, z.ctypes.data, c.ctypes.data, c.size,
+                                     float(threshold), ctypes.addressof(groups), ng, tz.ctypes.data,
+                                     tc.ctypes.data, nt, counts, ctypes.byref(dropped),
+                                     ctypes.byref(ncanon))
+    if rc != 0:
+        raise ValueError("vqe_inspect_hamiltonian rejected the input")
+    return {"groups": list(groups)[:ng], "tz": tz[:nt], "tc": tc[:nt],
+            "sum_abs_dropped": dropped.value, "n_canonical": ncanon.value}

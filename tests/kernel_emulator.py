@@ -1,0 +1,283 @@
+"""NumPy emulation of the library's tile-pass and energy kernels on the CPU.
+
+Test infrastructure.  It interprets the plan records the library's host
+planner produces (``paper_2402_11878_gb300.plans``) with the same index
+arithmetic as the CUDA kernels (register chunks, shared-memory swizzle,
+tile base addresses, coefficient/table/partial offsets) and checks every
+index against its buffer.  Running it against the oracle validates the
+planner and the kernels' addressing before any GPU run; it is never a
+fallback for the library.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2402_11878_gb300 import plans as P
+
+
+def popc(a):
+    return np.bitwise_count(np.asarray(a, dtype=np.uint64)).astype(np.int64)
+
+
+def elem_of(t, r, p, R):
+    lo = t & ((1 << p) - 1)
+    return lo | (r << p) | ((t >> p) << (p + R))
+
+
+def swz(e, prec):
+    if prec == "c128":
+        f = (e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12)
+        return e ^ (f & 7)
+    f = (e >> 4) ^ (e >> 8) ^ (e >> 12)
+    return e ^ (f & 15)
+
+
+class Emu:
+    def __init__(self, n, depth, prec):
+        self.n, self.depth, self.prec = n, depth, prec
+        self.plan = P.plan(n, depth, prec)
+
+    # ------------------------------------------------------------ staging
+    def stage(self, params):
+        """Coefficients and diagonal tables exactly as the staging kernel builds them."""
+        n = self.n
+        pl = self.plan
+        cv = np.zeros(pl["coef_stride"])
+        cg = np.zeros(pl["coef_stride"])
+        cm = np.full(pl["coef_stride"], -1, dtype=np.int64)
+        dt = np.full(pl["dtab_stride"], np.nan, dtype=np.complex128)
+        for S in pl["stage"]:
+            size = 1 << S.k
+            assert S.coef_off + S.k <= pl["coef_stride"]
+            assert S.dtab_off + size <= pl["dtab_stride"]
+            e = np.arange(size)
+            tab = np.ones(size, dtype=np.complex128)
+            sigma = 1.0
+            scales = {}
+            for j in range(S.n_gated):
+                q, tb = S.qubit[j], S.tile_bit[j]
+                assert 0 <= q < n and 0 <= tb < S.k
+                th = params[(S.layer * n + q) * 2]
+                ph = params[(S.layer * n + q) * 2 + 1]
+                c, s = np.cos(th / 2), np.sin(th / 2)
+                if abs(c) >= abs(s):
+                    cv[S.coef_off + tb], cm[S.coef_off + tb], sc = s / c, 0, c
+                else:
+                    cv[S.coef_off + tb], cm[S.coef_off + tb], sc = c / s, 1, s
+                sigma *= sc
+                scales[tb] = sc
+                bit = (e >> tb) & 1
+                tab *= np.where(bit == 1, np.exp(0.5j * ph), np.exp(-0.5j * ph))
+            dt[S.dtab_off:S.dtab_off + size] = sigma * tab
+            for j in range(S.n_gated):
+                tb = S.tile_bit[j]
+                pb = np.prod([scales[u] for u in scales if (S.before[j] >> u) & 1])
+                f = sigma / pb
+                cg[S.coef_off + tb] = 1.0 / (f * f)
+        self._cg = cg
+        return cv, cm, dt
+
+    # ------------------------------------------------------------ passes
+    def _run_pass(self, d, psi, lam, cv, cm, dt, init_zero, backward, gpart):
+        n, prec = self.n, self.prec
+        k, m, a, R = d.k, d.m, d.a, d.R
+        assert 1 <= R <= k <= P.K_MAX_TILE_BITS and k <= n
+        assert 0 < d.n_ops <= P.K_MAX_OPS and d.n_slots <= P.K_MAX_SLOTS
+        hbits = k - m
+        mid = a - m
+        assert mid >= 0 and a + hbits <= n
+        tiles = 1 << (n - k)
+        threads = 1 << (k - R)
+        assert threads <= 1024
+        NR = 1 << R
+        tile = np.arange(tiles, dtype=np.int64)[:, None, None]
+        t = np.arange(threads, dtype=np.int64)[None, :, None]
+        r = np.arange(NR, dtype=np.int64)[None, None, :]
+        base = ((tile & ((1 << mid) - 1)) << m) | ((tile >> mid) << (a + hbits))
+        lowmask = (1 << m) - 1
+
+        def gaddr(e):
+            return base | (e & lowmask) | ((e >> m) << a)
+
+        v = w = None
+        chunk = -1
+        warps = max(1, threads // 32)
+        written = {}
+        for oi in range(d.n_ops):
+            op = d.ops[oi]
+            if op.kind == P.OP_ROUND:
+                p = op.chunk
+                assert p + R <= k
+                e = elem_of(t, r, p, R)
+                if chunk < 0:
+                    g = gaddr(e)
+                    gf = np.broadcast_to(g, (tiles, threads, NR)).ravel()
+                    assert gf.min() >= 0 and gf.max() < (1 << n)
+                    assert np.unique(gf).size == gf.size == (1 << n), "tiles must partition the state"
+                    if init_zero:
+                        v = (g == 0).astype(np.complex128) + 0j * g
+                    else:
+                        v = psi[g]
+                    if backward:
+                        w = lam[g]
+                else:
+                    e_old = elem_of(t, r, chunk, R)
+                    s_old = swz(np.broadcast_to(e_old, (1, threads, NR)), prec)
+                    s_new = swz(np.broadcast_to(e, (1, threads, NR)), prec)
+                    for s_ in (s_old, s_new):
+                        flat = s_.ravel()
+                        assert flat.min() >= 0 and flat.max() < (1 << k)
+                        assert np.unique(flat).size == (1 << k), "smem slots must be a bijection"
+                    sm = np.empty((tiles, 1 << k), dtype=np.complex128)
+                    sm[:, s_old[0].ravel()] = v.reshape(tiles, -1)
+                    v = sm[:, s_new[0].ravel()].reshape(tiles, threads, NR)
+                    if backward:
+                        sl = np.empty((tiles, 1 << k), dtype=np.complex128)
+                        sl[:, s_old[0].ravel()] = w.reshape(tiles, -1)
+                        w = sl[:, s_new[0].ravel()].reshape(tiles, threads, NR)
+                chunk = p
+            elif op.kind == P.OP_BF:
+                s = op.slot
+                assert s < d.n_slots and chunk >= 0
+                coff = d.slot_coef_off[s]
+                for j in range(R):
+                    if not (op.mask >> j) & 1:
+                        continue
+                    bit = chunk + j
+                    assert (d.slot_gated[s] >> bit) & 1, "butterfly on a bit the slot does not gate"
+                    idx = coff + bit
+                    assert 0 <= idx < len(cv) and cm[idx] in (0, 1)
+                    c, mode = cv[idx], cm[idx]
+                    r0 = [rr for rr in range(NR) if not rr & (1 << j)]
+                    r1 = [rr | (1 << j) for rr in r0]
+                    if backward:
+                        p0, p1, l0, l1 = v[..., r0], v[..., r1], w[..., r0], w[..., r1]
+                        gs = self._cg[idx]
+                        gt = gs * (np.real(np.conj(l1) * p0) - np.real(np.conj(l0) * p1)).sum(axis=(1, 2))
+                        gp = gs * (np.imag(np.conj(l0) * p0) - np.imag(np.conj(l1) * p1)).sum(axis=(1, 2))
+                        key = (s, bit)
+                        assert key not in written, "gradient partial written twice"
+                        written[key] = (gt, gp)
+                    bufs = [v] + ([w] if backward else [])
+                    for u in bufs:
+                        x, y = u[..., r0].copy(), u[..., r1].copy()
+                        if not backward:
+                            if mode == 0:
+                                u[..., r0], u[..., r1] = x - c * y, y + c * x
+                            else:
+                                u[..., r0], u[..., r1] = c * x - y, x + c * y
+                        else:
+                            if mode == 0:
+                                u[..., r0], u[..., r1] = x + c * y, y - c * x
+                            else:
+                                u[..., r0], u[..., r1] = c * x + y, c * y - x
+            elif op.kind == P.OP_DIAG:
+                s = op.slot
+                e = elem_of(t, r, chunk, R)
+                g = gaddr(e)
+                cz = d.slot_czmask[s]
+                sgn = popc(g & (g >> 1) & cz) & 1
+                off = d.slot_dtab_off[s]
+                assert off + (1 << k) <= len(dt)
+                tab = dt[off + np.broadcast_to(e, g.shape)]
+                assert not np.isnan(tab).any(), "table entry never staged"
+                fac = np.where(sgn == 1, -1.0, 1.0)
+                if not backward:
+                    v = v * tab * fac
+                else:
+                    v = v * np.conj(tab) * fac
+                    w = w * np.conj(tab) * fac
+            elif op.kind == P.OP_FLUSH:
+                assert backward
+                s = op.slot
+                for bit in range(k):
+                    if not (d.slot_gated[s] >> bit) & 1:
+                        continue
+                    gt, gp = written.pop((s, bit))
+                    base_off = d.slot_grad_off[s] + np.arange(tiles) * (2 * k) + bit * 2
+                    assert base_off.max() + 1 < len(gpart)
+                    gpart[base_off] = gt
+                    gpart[base_off + 1] = gp
+            else:
+                raise AssertionError(f"unknown op kind {op.kind}")
+        assert not written, "gradient partials left unflushed"
+        g = gaddr(elem_of(t, r, chunk, R))
+        psi[g] = v
+        if backward:
+            lam[g] = w
+
+    def forward(self, params):
+        cv, cm, dt = self.stage(params)
+        psi = np.zeros(1 << self.n, dtype=np.complex128)
+        for i, d in enumerate(self.plan["fwd"]):
+            self._run_pass(d, psi, None, cv, cm, dt, i == 0, False, None)
+        return psi
+
+    def gradient(self, params, lam_of):
+        """Adjoint gradient; ``lam_of(psi)`` returns H psi (from the emulated apply-H)."""
+        cv, cm, dt = self.stage(params)
+        psi = self.forward(params)
+        lam = lam_of(psi)
+        energy = np.vdot(psi, lam).real
+        gpart = np.full(self.plan["grad_stride"], np.nan)
+        for d in reversed(self.plan["bwd"]):
+            self._run_pass(d, psi, lam, cv, cm, dt, False, True, gpart)
+        gm = self.plan["grad_map"]
+        grad = np.empty(len(gm))
+        for pidx, (off, cnt, step) in enumerate(gm):
+            idx = off + np.arange(cnt) * step
+            assert idx.max() < len(gpart)
+            vals = gpart[idx]
+            assert not np.isnan(vals).any(), "gradient partial never written"
+            grad[pidx] = vals.sum()
+        return grad, energy
+
+
+def energy_terms(ham, n, psi):
+    """The energy kernel's grouped formula on the CPU: (unnormalised E, norm)."""
+    N = 1 << n
+    groups, tz, tc = ham["groups"], ham["tz"], ham["tc"]
+    i = np.arange(N, dtype=np.int64)
+    acc, nrm = 0.0, 0.0
+    for G in groups:
+        if G.x == 0:
+            a = np.abs(psi) ** 2
+            f = np.zeros(N)
+            for t_ in range(G.t_begin, G.t_mid):
+                f += tc[t_] * (1 - 2 * (popc(i & int(tz[t_])) & 1))
+            assert G.t_mid == G.t_end, "x = 0 terms are all of class A"
+            acc += float((a * f).sum())
+            nrm += float(a.sum())
+        else:
+            h = G.h
+            assert (G.x >> h) == 1
+            p = np.arange(N // 2, dtype=np.int64)
+            i0 = ((p >> h) << (h + 1)) | (p & ((1 << h) - 1))
+            i1 = i0 ^ G.x
+            assert i1.max() < N and ((i0 >> h) & 1).max() == 0
+            g = np.conj(psi[i0]) * psi[i1]
+            fa = np.zeros(N // 2)
+            fb = np.zeros(N // 2)
+            for t_ in range(G.t_begin, G.t_mid):
+                fa += tc[t_] * (1 - 2 * (popc(i0 & int(tz[t_])) & 1))
+            for t_ in range(G.t_mid, G.t_end):
+                fb += tc[t_] * (1 - 2 * (popc(i0 & int(tz[t_])) & 1))
+            acc += 2.0 * float((g.real * fa + g.imag * fb).sum())
+    return acc, nrm
+
+
+def apply_h_terms(ham, n, psi):
+    """The apply-H kernel's formula on the CPU."""
+    N = 1 << n
+    i = np.arange(N, dtype=np.int64)
+    lam = np.zeros(N, dtype=np.complex128)
+    for G in ham["groups"]:
+        pj = psi[i ^ G.x]
+        fa = np.zeros(N)
+        fb = np.zeros(N)
+        for t_ in range(G.t_begin, G.t_mid):
+            fa += ham["tc"][t_] * (1 - 2 * (popc(i & int(ham["tz"][t_])) & 1))
+        for t_ in range(G.t_mid, G.t_end):
+            fb += ham["tc"][t_] * (1 - 2 * (popc(i & int(ham["tz"][t_])) & 1))
+        lam += pj * (fa - 1j * fb)
+    return lam

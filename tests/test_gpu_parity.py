@@ -1,0 +1,217 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (fixed by the accuracy targets of the two precision modes):
+  VQE_C128: |dE| <= 1e-11 * sum|c|, amplitudes max-abs <= 1e-12,
+            gradients max-abs <= 1e-10 * max(1, |g_ref|_inf)
+  VQE_C64:  |dE| <= 1e-5 * sum|c|, gradients |g - g_ref|_inf / |g_ref|_inf <= 1e-4
+"""
+import numpy as np
+import pytest
+
+import vqe_inputs as vi
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = {"c128": 1e-11, "c64": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def eng_mod(lib_built):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_2402_11878_gb300 as pkg
+    return pkg
+
+
+def make(pkg, n, depth, prec, H):
+    e = pkg.Engine(n, depth, prec)
+    e.set_hamiltonian(H.x, H.z, H.c)
+    return e
+
+
+def check_energy(E, E_ref, H, prec):
+    tol = E_TOL[prec] * max(H.sum_abs(), 1e-300)
+    assert abs(E - E_ref) <= tol, (E, E_ref, abs(E - E_ref), tol)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_config_small_hubbard_c128_state_and_energy(eng_mod, oracle_mod, seed):
+    """8 qubits, 4-site open Hubbard t=1 U=4, depth 4, FP64: state and energy."""
+    n, D = 8, 4
+    H = vi.hubbard_1d(4, 1.0, 4.0, periodic=False)
+    p = vi.ansatz_params(seed, n, D)
+    eng = make(eng_mod, n, D, "c128", H)
+    eng.apply_ansatz(p)
+    psi = eng.get_state()
+    ref = oracle_mod.ansatz_state(n, D, p)
+    assert np.max(np.abs(psi - ref)) <= 1e-12
+    E, nn = eng.energy()
+    E_ref, n_ref = oracle_mod.energy(ref, H.x, H.z, H.c)
+    check_energy(E, E_ref, H, "c128")
+    assert abs(nn - 1.0) <= 1e-13
+
+
+SIZES = [1, 2, 3, 4, 5, 7, 8, 9, 12, 13, 14, 15, 16, 17, 18]
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n", SIZES)
+def test_random_pauli_sum_all_sizes(eng_mod, oracle_mod, prec, n):
+    """Every plan shape (single tile, multi-pass, ragged groups) on random Pauli sums with Y terms."""
+    D = 2 if n > 12 else 3
+    H = vi.random_pauli_sum(n, 40, seed=100 + n, duplicates=3)
+    p = vi.ansatz_params(7 + n, n, D)
+    eng = make(eng_mod, n, D, prec, H)
+    eng.apply_ansatz(p)
+    psi = eng.get_state()
+    ref = oracle_mod.ansatz_state(n, D, p)
+    amp_tol = 1e-12 if prec == "c128" else 2e-6
+    assert np.max(np.abs(psi - ref)) <= amp_tol
+    E, nn = eng.energy()
+    E_ref, _ = oracle_mod.energy(ref, H.x, H.z, H.c)
+    check_energy(E, E_ref, H, prec)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_batched_energies(eng_mod, oracle_mod, prec):
+    n, D, B = 10, 3, 7
+    H = vi.hubbard_1d(5, 1.0, 2.5, periodic=True)
+    P = np.stack([vi.ansatz_params(50 + b, n, D) for b in range(B)])
+    eng = make(eng_mod, n, D, prec, H)
+    E, nn = eng.energy_batch(P)
+    for b in range(B):
+        ref = oracle_mod.ansatz_state(n, D, P[b])
+        E_ref, _ = oracle_mod.energy(ref, H.x, H.z, H.c)
+        check_energy(E[b], E_ref, H, prec)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n,D", [(2, 2), (3, 2), (8, 4), (13, 2), (14, 2), (16, 2), (17, 1)])
+def test_adjoint_gradient(eng_mod, oracle_mod, prec, n, D):
+    H = vi.random_pauli_sum(n, 30, seed=200 + n) if n % 2 else vi.hubbard_1d(n // 2, 1.0, 4.0)
+    H = vi.PauliSum(n, H.x, H.z, H.c)
+    p = vi.ansatz_params(300 + n, n, D)
+    eng = make(eng_mod, n, D, prec, H)
+    g, E = eng.gradient(p)
+    g_ref, E_ref = oracle_mod.gradient_adjoint(n, D, p, H.x, H.z, H.c)
+    check_energy(E, E_ref, H, prec)
+    scale = max(np.max(np.abs(g_ref)), 1e-30)
+    err = np.max(np.abs(g - g_ref))
+    if prec == "c64":
+        assert err / scale <= 1e-4, (err, scale)
+    else:
+        assert err <= 1e-10 * max(1.0, scale), (err, scale)
+
+
+def test_gradient_batch_matches_single(eng_mod, oracle_mod):
+    n, D, B = 9, 2, 3
+    H = vi.random_pauli_sum(n, 25, seed=9)
+    P = np.stack([vi.ansatz_params(400 + b, n, D) for b in range(B)])
+    eng = make(eng_mod, n, D, "c128", H)
+    G, E = eng.gradient_batch(P)
+    for b in range(B):
+        g_ref, E_ref = oracle_mod.gradient_adjoint(n, D, P[b], H.x, H.z, H.c)
+        assert np.max(np.abs(G[b] - g_ref)) <= 1e-10 * max(1.0, np.max(np.abs(g_ref)))
+        check_energy(E[b], E_ref, H, "c128")
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_slimming_against_oracle(eng_mod, oracle_mod, prec):
+    """Cutoff: kept set, sum|c_dropped|, slimmed energy, and the Sec. II-D bound."""
+    n, D = 12, 2
+    M = vi.random_pauli_sum(n, 300, seed=5, duplicates=20)
+    M.c = M.c * np.exp(-np.linspace(0, 12, len(M.c)))    # spread |c| over ~5 decades
+    p = vi.ansatz_params(11, n, D)
+    eng = make(eng_mod, n, D, prec, M)
+    ref = oracle_mod.ansatz_state(n, D, p)
+    eng.apply_ansatz(p)
+    E_full, _ = eng.energy()
+    for th in [0.0, 1e-4, 1e-3, 1e-2, 0.1, 10.0]:
+        kept, dropped = eng.slim(th)
+        xs, zs, cs, dref = oracle_mod.slim(M.x, M.z, M.c, th)
+        assert kept == len(cs)
+        assert abs(dropped - dref) <= 1e-12 * max(1.0, dref)
+        E, _ = eng.energy()
+        E_ref, _ = oracle_mod.energy(ref, xs, zs, cs) if len(cs) else (0.0, 1.0)
+        check_energy(E, E_ref, M, prec)
+        assert abs(E_full - E) <= dropped * (1 + 1e-9) + E_TOL[prec] * M.sum_abs()
+
+
+def test_pergate_reference_kernel(eng_mod, oracle_mod):
+    import torch
+    n, D, B = 14, 3, 4
+    H = vi.hubbard_1d(7, 1.0, 4.0, periodic=True)
+    P = np.stack([vi.ansatz_params(70 + b, n, D) for b in range(B)])
+    eng = make(eng_mod, n, D, "c128", H)
+    pd = torch.tensor(P, device="cuda")
+    e1 = torch.empty(B, dtype=torch.float64, device="cuda")
+    e2 = torch.empty(B, dtype=torch.float64, device="cuda")
+    eng.energy_batch_dev(pd, e1)
+    eng.energy_batch_dev(pd, e2, pergate=True)
+    torch.cuda.synchronize()
+    for b in range(B):
+        ref = oracle_mod.ansatz_state(n, D, P[b])
+        E_ref, _ = oracle_mod.energy(ref, H.x, H.z, H.c)
+        check_energy(float(e1[b]), E_ref, H, "c128")
+        check_energy(float(e2[b]), E_ref, H, "c128")
+
+
+def test_full_size_20q_fp64_hubbard(eng_mod, oracle_mod):
+    """20 qubits FP64, 10-site periodic Hubbard, depth 10: whole state and energies vs oracle."""
+    n, D = 20, 10
+    for U in (2.0, 8.0):
+        H = vi.hubbard_1d(10, 1.0, U, periodic=True)
+        p = vi.ansatz_params(int(U) * 17, n, D)
+        eng = make(eng_mod, n, D, "c128", H)
+        eng.apply_ansatz(p)
+        psi = eng.get_state()
+        ref = oracle_mod.ansatz_state(n, D, p)
+        assert np.max(np.abs(psi - ref)) <= 1e-12
+        E, _ = eng.energy()
+        E_ref, _ = oracle_mod.energy(ref, H.x, H.z, H.c)
+        check_energy(E, E_ref, H, "c128")
+
+
+def test_theta_zero_and_basis_states(eng_mod):
+    """theta = 0 leaves |0..0>: E = sum of z-only coefficients; RY(pi) on all
+    qubits prepares |1..1>, whose Hubbard energy is U * L (all sites doubly occupied)."""
+    n, D = 12, 2
+    H = vi.hubbard_1d(6, 1.0, 3.0)
+    eng = make(eng_mod, n, D, "c128", H)
+    eng.apply_ansatz(np.zeros(2 * n * D))
+    E, _ = eng.energy()
+    zonly = H.c[H.x == 0].sum()
+    assert abs(E - zonly) <= 1e-12 * H.sum_abs()
+    p = np.zeros(2 * n * D)
+    p[0:2 * n:2] = np.pi
+    eng.apply_ansatz(p)
+    E, _ = eng.energy()
+    assert abs(E - 3.0 * 6) <= 1e-11 * H.sum_abs()
+
+
+def test_bitwise_determinism(eng_mod):
+    n, D = 16, 3
+    H = vi.random_pauli_sum(n, 60, seed=3)
+    p = vi.ansatz_params(5, n, D)
+    eng = make(eng_mod, n, D, "c64", H)
+    g1, e1 = eng.gradient(p)
+    g2, e2 = eng.gradient(p)
+    assert e1 == e2 and np.array_equal(g1, g2)
+
+
+def test_argument_errors(eng_mod):
+    pkg = eng_mod
+    eng = pkg.Engine(6, 2, "c64")
+    with pytest.raises(pkg.VQEError) as ei:
+        eng.energy()
+    assert ei.value.status == 2
+    with pytest.raises(pkg.VQEError) as ei:
+        eng.set_hamiltonian([1 << 6], [0], [1.0])
+    assert ei.value.status == 1
+    with pytest.raises(pkg.VQEError):
+        eng.set_hamiltonian([1], [0], [float("nan")])
+    eng.set_hamiltonian([1], [0], [1.0])
+    with pytest.raises(pkg.VQEError):
+        eng.apply_ansatz(np.full(24, np.inf))
+    with pytest.raises(pkg.VQEError):
+        eng.slim(-1.0)

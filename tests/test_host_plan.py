@@ -1,0 +1,135 @@
+"""Host logic of the library, checked on the CPU (no GPU): the tile-pass
+planner (index arithmetic emulated exactly as the kernels execute it),
+Hamiltonian canonicalisation, cutoff and X-mask grouping."""
+import numpy as np
+import pytest
+
+import vqe_inputs as vi
+from kernel_emulator import Emu, energy_terms, apply_h_terms
+from paper_2402_11878_gb300 import plans as P
+
+SMEM_MAX = 227 * 1024
+
+
+def pass_smem(d, backward, elem):
+    threads = 1 << (d.k - d.R)
+    warps = (threads + 31) // 32
+    return (1 << d.k) * elem * (2 if backward else 1) + (warps * d.k * 16 if backward else 0)
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n", list(range(1, 33)))
+def test_plan_invariants(n, prec):
+    D = 3
+    pl = P.plan(n, D, prec)
+    elem = 16 if prec == "c128" else 8
+    covered = {}
+    cz_seen = {}
+    gid = 0
+    for d, b in zip(pl["fwd"], pl["bwd"]):
+        assert 1 <= d.R <= d.k <= 14 and d.k <= n
+        assert (1 << (d.k - d.R)) <= 512
+        assert pass_smem(b, True, elem) <= SMEM_MAX
+        assert d.n_ops <= P.K_MAX_OPS and b.n_ops <= P.K_MAX_OPS
+        assert d.n_slots == b.n_slots <= P.K_MAX_SLOTS
+        for s in range(d.n_slots):
+            l = d.slot_layer[s]
+            for j in range(d.k):
+                if (d.slot_gated[s] >> j) & 1:
+                    q = j if j < d.m else d.a + (j - d.m)
+                    assert (l, q) not in covered, "qubit gated twice in a layer"
+                    covered[(l, q)] = gid
+            for q in range(32):
+                if (d.slot_czmask[s] >> q) & 1:
+                    assert (l, q) not in cz_seen
+                    cz_seen[(l, q)] = gid
+            gid += 1
+    assert len(covered) == n * D
+    assert len(cz_seen) == (n - 1) * D
+    # every CZ comes after both of its RY gates and before the next layer's
+    for (l, q), g in cz_seen.items():
+        assert g >= covered[(l, q)] and g >= covered[(l, q + 1)]
+        if l + 1 < D:
+            assert g < covered[(l + 1, q)] and g < covered[(l + 1, q + 1)]
+
+
+CASES = [(1, 2, "c64"), (2, 3, "c128"), (3, 2, "c64"), (5, 2, "c128"), (8, 4, "c128"),
+         (8, 4, "c64"), (12, 3, "c128"), (13, 2, "c64"), (14, 2, "c64"), (14, 2, "c128"),
+         (16, 2, "c128"), (17, 2, "c64"), (13, 45, "c64")]
+
+
+@pytest.mark.parametrize("n,D,prec", CASES)
+def test_emulated_kernels_match_oracle(oracle_mod, n, D, prec):
+    """The plan, executed with the kernels' index arithmetic, reproduces the oracle."""
+    H = vi.random_pauli_sum(n, 25, seed=n + D, duplicates=2)
+    p = vi.ansatz_params(1000 + n, n, D)
+    emu = Emu(n, D, prec)
+    psi = emu.forward(p)
+    ref = oracle_mod.ansatz_state(n, D, p)
+    assert np.max(np.abs(psi - ref)) < 1e-12
+    ham = P.hamiltonian(n, H.x, H.z, H.c)
+    e, nn = energy_terms(ham, n, psi)
+    e_ref, _, n_ref = oracle_mod.expectation(ref, H.x, H.z, H.c)
+    assert abs(e - e_ref) < 1e-12 * H.sum_abs() and abs(nn - n_ref) < 1e-12
+    lam = apply_h_terms(ham, n, psi)
+    assert np.max(np.abs(lam - oracle_mod.apply_h(ref, H.x, H.z, H.c))) < 1e-12 * H.sum_abs()
+    if n <= 14:
+        g, eg = emu.gradient(p, lambda s: apply_h_terms(ham, n, s))
+        g_ref, _ = oracle_mod.gradient_adjoint(n, D, p, H.x, H.z, H.c)
+        assert np.max(np.abs(g - g_ref)) < 1e-11 * max(1.0, np.max(np.abs(g_ref)))
+
+
+def test_emulated_full_size_20q_plan(oracle_mod):
+    """The 20-qubit FP64 plan of the benchmark workload, checked end to end."""
+    n, D = 20, 10
+    H = vi.hubbard_1d(10, 1.0, 4.0, periodic=True)
+    p = vi.ansatz_params(4, n, D)
+    psi = Emu(n, D, "c128").forward(p)
+    ref = oracle_mod.ansatz_state(n, D, p)
+    assert np.max(np.abs(psi - ref)) < 1e-12
+    ham = P.hamiltonian(n, H.x, H.z, H.c)
+    e, _ = energy_terms(ham, n, psi)
+    e_ref, _, _ = oracle_mod.expectation(ref, H.x, H.z, H.c)
+    assert abs(e - e_ref) < 1e-11 * H.sum_abs()
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_canonicalise_and_slim_match_oracle(oracle_mod, seed):
+    n = 10
+    H = vi.random_pauli_sum(n, 400, seed=seed, duplicates=60)
+    H.c = H.c * np.exp(-np.linspace(0, 14, len(H.c)))
+    # add exact cancellations: they must disappear in the canonical form
+    x = np.concatenate([H.x, H.x[:5], H.x[:5]])
+    z = np.concatenate([H.z, H.z[:5], H.z[:5]])
+    c = np.concatenate([H.c, np.full(5, 2.0), np.full(5, -2.0)])
+    for th in [0.0, 1e-6, 1e-4, 1e-3, 0.05, 100.0]:
+        ham = P.hamiltonian(n, x, z, c, threshold=th)
+        xs, zs, cs, dref = oracle_mod.slim(x, z, c, th)
+        assert len(ham["tz"]) == len(cs)
+        assert abs(ham["sum_abs_dropped"] - dref) <= 1e-12 * max(1.0, dref)
+        # same kept strings (bit exact)
+        kept = set()
+        for G in ham["groups"]:
+            for t in range(G.t_begin, G.t_end):
+                kept.add((G.x, int(ham["tz"][t])))
+        assert kept == set(zip(xs.astype(int).tolist(), zs.astype(int).tolist()))
+
+
+def test_grouping_signs_match_pauli_phase(oracle_mod):
+    """Folding (-i)^kappa into class A/B signs reproduces every single Pauli string."""
+    n = 5
+    rng = np.random.default_rng(0)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    for x in range(1 << n):
+        for z in range(0, 1 << n, 3):
+            ham = P.hamiltonian(n, [x], [z], [1.0])
+            e, _ = energy_terms(ham, n, psi)
+            e_ref, _, _ = oracle_mod.expectation(psi, [x], [z], [1.0])
+            assert abs(e - e_ref) < 1e-12
+
+
+def test_inspect_rejects_bad_input():
+    with pytest.raises(ValueError):
+        P.hamiltonian(4, [1 << 4], [0], [1.0])
+    with pytest.raises(ValueError):
+        P.hamiltonian(4, [1], [0], [float("inf")])

@@ -180,6 +180,44 @@ const char *vqe_last_error(vqe_handle h);
 /* Library version string. */
 const char *vqe_version(void);
 
+/* ---- Energy without device allocation ------------------------------------
+ * The paper has no counterpart of this call; it exists for users of this
+ * library whose code may not allocate device memory: code whose device memory
+ * is owned by another allocator (a framework's caching allocator or a fixed
+ * pre-reserved pool), loops that keep other streams busy and cannot afford
+ * the device-wide synchronisation of cudaMalloc/cudaFree, and plug-ins that
+ * only receive raw device pointers from their host application.
+ *
+ * It computes, for `batch` states stored back to back at psi_dev (2^n
+ * complex64 or complex128 each, as `precision` says), the energy
+ * <psi|H|psi>/<psi|psi> of H = sum_t c_t P(x_t, z_t), taking the terms one at
+ * a time (no merging, grouping or cutoff), and writes energies_dev[batch] and,
+ * if not NULL, norms_dev[batch].  All arrays are caller-owned device memory;
+ * the call itself allocates nothing.  Its only scratch is a fixed array of
+ * 2 * VQE_NOALLOC_MAX_BATCH + 32 doubles (64 KiB) in the library's static
+ * device memory, present on every GPU that loads the library until exit.
+ *
+ * Limits and errors: batch must be 1..VQE_NOALLOC_MAX_BATCH and n_qubits
+ * 1..32, else VQE_ERR_ARG is returned before any work is queued.  Masks with
+ * bits at or above n_qubits or non-finite coefficients cannot be checked on
+ * the host (they are in device memory): such terms are skipped and every
+ * energy of the call is set to NaN.
+ *
+ * The work is queued on cuda_stream (NULL = legacy default stream) and the
+ * call returns without synchronising.  The first call on a device looks up
+ * the scratch array's device address with that device current (the device
+ * current on the calling thread); make that first call before any stream
+ * capture.  Every call uses the same scratch array and overwrites what the
+ * previous call left there; each slot a call reads is written by that call
+ * first, so nothing needs clearing, but two calls that overlap on the GPU
+ * (on different streams, or from different threads) race on the scratch and
+ * give wrong results: serialise them. */
+#define VQE_NOALLOC_MAX_BATCH 4096
+vqe_status vqe_energy_noalloc(int n_qubits, vqe_precision precision, const void *psi_dev,
+                              int batch, const uint64_t *x_masks_dev, const uint64_t *z_masks_dev,
+                              const double *coeffs_dev, size_t n_terms, double *energies_dev,
+                              double *norms_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ EXPORTED = [
     "vqe_gradient", "vqe_energy_batch_dev", "vqe_gradient_batch_dev", "vqe_energy_batch",
     "vqe_gradient_batch", "vqe_energy_batch_pergate_dev", "vqe_get_stats", "vqe_last_error",
     "vqe_version", "vqe_profile", "vqe_profile_read", "vqe_inspect_sizeof", "vqe_inspect_plan",
-    "vqe_inspect_hamiltonian",
+    "vqe_inspect_hamiltonian", "vqe_energy_noalloc",
 ]
 
 

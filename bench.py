@@ -347,8 +347,53 @@ def run_gpu(args, world, rank, local, pg):
         e.close()
 
 
+def run_case(name: str, batch: int):
+    """Small named workloads for profiler captures (no JSON line): each runs
+    its evaluation twice on cuda:0 and prints the first energies."""
+    import numpy as np
+    import torch
+    import paper_2402_11878_gb300 as pkg
+    import vqe_inputs as vi
+    cases = {  # name: (n, depth, precision, gradient)
+        "fwd20c128": (20, 10, "c128", False), "grad20c128": (20, 10, "c128", True),
+        "fwd24c64": (24, 4, "c64", False), "grad24c64": (24, 4, "c64", True),
+        "fwd26c64": (26, 4, "c64", False),
+    }
+    if name == "batch512":
+        inst = vi.batched_instances(512, seed=7)
+        b = pkg.Batch([d["n"] for d in inst], [d["depth"] for d in inst], "c64",
+                      stream=torch.cuda.current_stream())
+        for i, d in enumerate(inst):
+            b.set_hamiltonian(i, d["H"].x, d["H"].z, d["H"].c)
+        P = torch.tensor(np.concatenate([d["params"] for d in inst]), device="cuda")
+        E = torch.empty(len(inst), dtype=torch.float64, device="cuda")
+        G = torch.empty_like(P)
+        for _ in range(2):
+            b.run_dev(P, E, G)
+        torch.cuda.synchronize()
+        print("energies", E[:4].tolist())
+        return
+    n, D, prec, grad = cases[name]
+    H = vi.hubbard_1d(n // 2, 1.0, 4.0, periodic=True)
+    eng = pkg.Engine(n, D, prec)
+    eng.set_hamiltonian(H.x, H.z, H.c)
+    P = torch.tensor(np.stack([vi.ansatz_params(j, n, D) for j in range(batch)]), device="cuda")
+    E = torch.empty(batch, dtype=torch.float64, device="cuda")
+    G = torch.empty(batch, 2 * n * D, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        if grad:
+            eng.gradient_batch_dev(P, G, E)
+        else:
+            eng.energy_batch_dev(P, E)
+    torch.cuda.synchronize()
+    print("energies", E[:4].tolist())
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default=None,
+                    help="run a small named workload for profiler captures instead of the benchmark")
+    ap.add_argument("--case-batch", type=int, default=16)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -358,6 +403,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--pergate", action="store_true")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case, args.case_batch)
+        return
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     world, rank, local, pg = dist_setup(args)

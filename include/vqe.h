@@ -99,6 +99,17 @@ vqe_status vqe_workspace_size(vqe_handle h, int batch, int want_gradient, size_t
  * library-allocated workspace.  The batch capacity follows from `bytes`. */
 vqe_status vqe_bind_workspace(vqe_handle h, void *dev_ptr, size_t bytes);
 
+/* Tile plan of the ansatz passes (0 = default for each): tile_bits_max =
+ * log2 of the largest tile a pass stages in shared memory (1..14; default
+ * 12 for C128, 13 for C64), run_bits = log2 of the contiguous run of
+ * amplitudes kept in the tiles of high-qubit passes (default 3 / 4, i.e. 128
+ * bytes), reg_bits = log2 of the amplitudes each thread holds (1..4;
+ * default 3 / 4).  Rejected (VQE_ERR_ARG) if a pass would need more than 512
+ * threads or 227 KiB of shared memory.  Rebuilds the plan; the state of
+ * vqe_apply_ansatz is discarded.  Results do not depend on the plan beyond
+ * floating-point rounding order. */
+vqe_status vqe_set_plan_options(vqe_handle h, int tile_bits_max, int run_bits, int reg_bits);
+
 /* Set the Hamiltonian H = sum_t coeffs[t] * P(x_masks[t], z_masks[t])
  * (Sec. II-B, Eqs. 2-4).  Host arrays of length n_terms; masks must have no
  * bit at or above n_qubits; coefficients must be finite.  Equal strings are
@@ -179,6 +190,49 @@ const char *vqe_last_error(vqe_handle h);
 
 /* Library version string. */
 const char *vqe_version(void);
+
+/* ---- Batched driver ------------------------------------------------------
+ * Many independent problems of uneven size (the single-GPU counterpart of
+ * the paper's distributed processing of independent circuit evaluations,
+ * Sec. II-C): instance i has n_qubits[i] (1..24) qubits, depth[i] (1..64)
+ * ansatz layers and its own Hamiltonian and parameters.  One run computes,
+ * for every instance, the energy <psi|H|psi>/<psi|psi> and the adjoint
+ * gradient, in ONE persistent kernel (each CTA takes whole instances from a
+ * queue ordered largest first; states that fit one tile stay in shared
+ * memory) launched through a CUDA graph captured on first use.
+ *
+ * Parameters and gradients of all instances are concatenated: instance i
+ * owns entries [offsets[i], offsets[i+1]) (vqe_batch_param_offsets), laid
+ * out as for vqe_create.  Every instance needs a Hamiltonian before a run
+ * (VQE_ERR_STATE otherwise).  The library allocates device memory at
+ * creation and on the first run: per-CTA scratch of 2 * 2^n amplitudes for
+ * the largest instance that does not fit one tile.  cuda_stream NULL: the
+ * batch uses an internal stream and vqe_batch_run_dev synchronises. */
+typedef struct vqe_batch_ctx *vqe_batch;
+vqe_status vqe_batch_create(int count, const int *n_qubits, const int *depths,
+                            vqe_precision precision, void *cuda_stream, vqe_batch *out);
+vqe_status vqe_batch_destroy(vqe_batch b);
+vqe_status vqe_batch_set_hamiltonian(vqe_batch b, int instance, const uint64_t *x_masks,
+                                     const uint64_t *z_masks, const double *coeffs,
+                                     size_t n_terms);
+/* offsets: count + 1 entries. */
+vqe_status vqe_batch_param_offsets(vqe_batch b, size_t *offsets);
+/* Device buffers: params and grads as the offsets say, energies[count]. */
+vqe_status vqe_batch_run_dev(vqe_batch b, const double *params_dev, double *energies_dev,
+                             double *grads_dev);
+/* Host buffers (copies inside; synchronises). */
+vqe_status vqe_batch_run(vqe_batch b, const double *params, double *energies, double *grads);
+/* Tile size (log2 amplitudes, 10..13 for C64, 10..12 for C128) of the passes
+ * of instances larger than one tile. */
+vqe_status vqe_batch_set_tile_bits(vqe_batch b, int tile_bits);
+/* Autotuner: times `reps` runs for each candidate tile size on the given
+ * device buffers, keeps the fastest (reported in *tile_bits_out if not
+ * NULL) and leaves the buffers holding a run with it. */
+vqe_status vqe_batch_autotune(vqe_batch b, const double *params_dev, double *energies_dev,
+                              double *grads_dev, int reps, int *tile_bits_out);
+/* Graph launches so far (each launch runs one memset and one kernel). */
+vqe_status vqe_batch_launch_count(vqe_batch b, uint64_t *graph_launches);
+const char *vqe_batch_last_error(vqe_batch b);
 
 /* ---- Energy without device allocation ------------------------------------
  * The paper has no counterpart of this call; it exists for users of this

@@ -21,15 +21,17 @@ extern "C" {
  * 2 = term group; 0 for an unknown `which`. */
 size_t vqe_inspect_sizeof(int which);
 
-/* Tile-pass plan of the ansatz for (n, depth, precision): forward and
+/* Tile-pass plan of the ansatz for (n, depth, precision, options) -- options
+ * as vqe_set_plan_options (tile_bits_max, run_bits, reg_bits; NULL = defaults):
+ * forward and
  * backward pass descriptors (max_passes each), staging slots (max_stage),
  * and the gradient reduction map grad_map[3 * 2*n*depth] = (offset, count,
  * step) per parameter.  strides[3] = per-state coefficient, table and
  * gradient-partial sizes; counts[3] = passes, staging slots, parameters.
  * Returns 0, or -1 on invalid arguments or too-small buffers. */
-int vqe_inspect_plan(int n_qubits, int depth, int precision, void *fwd, void *bwd, int max_passes,
-                     void *stage, int max_stage, int *grad_map, int max_params,
-                     uint64_t strides[3], int counts[3]);
+int vqe_inspect_plan(int n_qubits, int depth, int precision, const int options[3], void *fwd,
+                     void *bwd, int max_passes, void *stage, int max_stage, int *grad_map,
+                     int max_params, uint64_t strides[3], int counts[3]);
 
 /* Canonicalisation, cutoff and X-mask grouping of a Pauli sum, exactly as
  * vqe_set_hamiltonian followed by vqe_slim(threshold) prepare it: term

@@ -5,9 +5,9 @@ library ``_lib/libvqe_gb300.so``); ``energy_and_grad`` exposes the adjoint
 gradient to ``torch.autograd``.  The library is loaded on first use and its
 absence raises ImportError (there is no other code path).
 """
-from .binding import Engine, VQEError, load, version, library_path  # noqa: F401
+from .binding import Batch, Engine, VQEError, load, version, library_path  # noqa: F401
 
-__all__ = ["Engine", "VQEError", "load", "version", "library_path", "EnergyFunction",
+__all__ = ["Batch", "Engine", "VQEError", "load", "version", "library_path", "EnergyFunction",
            "energy_and_grad"]
 
 

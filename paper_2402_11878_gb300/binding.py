@@ -21,12 +21,15 @@ STATUS = {0: "VQE_OK", 1: "VQE_ERR_ARG", 2: "VQE_ERR_STATE", 3: "VQE_ERR_OOM",
 
 # C ABI entry points declared in include/vqe.h and include/vqe_inspect.h
 EXPORTED = [
-    "vqe_create", "vqe_destroy", "vqe_workspace_size", "vqe_bind_workspace",
+    "vqe_create", "vqe_destroy", "vqe_workspace_size", "vqe_bind_workspace", "vqe_set_plan_options",
     "vqe_set_hamiltonian", "vqe_slim", "vqe_apply_ansatz", "vqe_energy", "vqe_get_state",
     "vqe_gradient", "vqe_energy_batch_dev", "vqe_gradient_batch_dev", "vqe_energy_batch",
     "vqe_gradient_batch", "vqe_energy_batch_pergate_dev", "vqe_get_stats", "vqe_last_error",
     "vqe_version", "vqe_profile", "vqe_profile_read", "vqe_inspect_sizeof", "vqe_inspect_plan",
-    "vqe_inspect_hamiltonian", "vqe_energy_noalloc",
+    "vqe_inspect_hamiltonian", "vqe_energy_noalloc", "vqe_batch_create", "vqe_batch_destroy",
+    "vqe_batch_set_hamiltonian", "vqe_batch_param_offsets", "vqe_batch_run_dev", "vqe_batch_run",
+    "vqe_batch_set_tile_bits", "vqe_batch_autotune", "vqe_batch_launch_count",
+    "vqe_batch_last_error",
 ]
 
 
@@ -90,7 +93,18 @@ def load() -> ctypes.CDLL:
         "vqe_profile": [vp, i],
         "vqe_profile_read": [vp, ctypes.POINTER(KernelTimes)],
         "vqe_inspect_sizeof": [i],
-        "vqe_inspect_plan": [i, i, i, vp, vp, i, vp, i, vp, i, vp, vp],
+        "vqe_batch_create": [i, vp, vp, i, vp, ctypes.POINTER(vp)],
+        "vqe_batch_destroy": [vp],
+        "vqe_batch_set_hamiltonian": [vp, i, vp, vp, vp, sz],
+        "vqe_batch_param_offsets": [vp, vp],
+        "vqe_batch_run_dev": [vp, dp, dp, dp],
+        "vqe_batch_run": [vp, dp, dp, dp],
+        "vqe_batch_set_tile_bits": [vp, i],
+        "vqe_batch_autotune": [vp, dp, dp, dp, i, ctypes.POINTER(i)],
+        "vqe_batch_launch_count": [vp, ctypes.POINTER(ctypes.c_uint64)],
+        "vqe_batch_last_error": [vp],
+        "vqe_inspect_plan": [i, i, i, vp, vp, vp, i, vp, i, vp, i, vp, vp],
+        "vqe_set_plan_options": [vp, i, i, i],
         "vqe_inspect_hamiltonian": [i, vp, vp, vp, sz, ctypes.c_double, vp, i, vp, vp, i, vp,
                                     vp, vp],
     }
@@ -99,6 +113,7 @@ def load() -> ctypes.CDLL:
         f.argtypes = args
         f.restype = ctypes.c_int
     lib.vqe_last_error.restype = ctypes.c_char_p
+    lib.vqe_batch_last_error.restype = ctypes.c_char_p
     lib.vqe_version.restype = ctypes.c_char_p
     lib.vqe_inspect_sizeof.restype = ctypes.c_size_t
     _lib = lib
@@ -240,6 +255,10 @@ class Engine:
         self._check(self._lib.vqe_gradient_batch_dev(self._h, _ptr(params_dev), b,
                                                      _ptr(grads_dev), _ptr(energies_dev)))
 
+    def set_plan_options(self, tile_bits_max: int = 0, run_bits: int = 0, reg_bits: int = 0):
+        """Choose the tile plan (0 = default); see vqe_set_plan_options."""
+        self._check(self._lib.vqe_set_plan_options(self._h, tile_bits_max, run_bits, reg_bits))
+
     def workspace_size(self, batch: int, gradient: bool = False) -> int:
         out = ctypes.c_size_t()
         self._check(self._lib.vqe_workspace_size(self._h, batch, int(gradient), ctypes.byref(out)))
@@ -268,6 +287,75 @@ class Engine:
         s = Stats()
         self._check(self._lib.vqe_get_stats(self._h, ctypes.byref(s)))
         return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+
+class Batch:
+    """Many independent problems of uneven size in one graph launch (vqe_batch_*)."""
+
+    def __init__(self, n_qubits, depths, precision: str = "c64", stream=None):
+        lib = load()
+        self._lib = lib
+        self.n = np.ascontiguousarray(n_qubits, dtype=np.int32)
+        self.depth = np.ascontiguousarray(depths, dtype=np.int32)
+        self.count = len(self.n)
+        prec = {"c64": VQE_C64, "c128": VQE_C128}[precision]
+        h = ctypes.c_void_p()
+        st = lib.vqe_batch_create(self.count, self.n.ctypes.data, self.depth.ctypes.data, prec,
+                                  _stream_ptr(stream), ctypes.byref(h))
+        if st != 0:
+            raise VQEError(st, "vqe_batch_create failed")
+        self._h = h
+        off = np.zeros(self.count + 1, dtype=np.uint64)
+        self._check(lib.vqe_batch_param_offsets(self._h, off.ctypes.data))
+        self.offsets = off.astype(np.int64)
+        self.n_params_total = int(self.offsets[-1])
+
+    def _check(self, st: int):
+        if st != 0:
+            raise VQEError(st, self._lib.vqe_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.vqe_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_hamiltonian(self, i: int, x, z, c):
+        x, z, c = _u64(x), _u64(z), _f64(c)
+        self._check(self._lib.vqe_batch_set_hamiltonian(self._h, i, x.ctypes.data, z.ctypes.data,
+                                                        c.ctypes.data, c.size))
+
+    def run(self, params):
+        """Host params (concatenated) -> (energies, grads) on the host."""
+        p = _f64(params)
+        assert p.size == self.n_params_total
+        e = np.empty(self.count)
+        g = np.empty_like(p)
+        self._check(self._lib.vqe_batch_run(self._h, p.ctypes.data, e.ctypes.data, g.ctypes.data))
+        return e, g
+
+    def run_dev(self, params_dev, energies_dev, grads_dev):
+        self._check(self._lib.vqe_batch_run_dev(self._h, _ptr(params_dev), _ptr(energies_dev),
+                                                _ptr(grads_dev)))
+
+    def set_tile_bits(self, k: int):
+        self._check(self._lib.vqe_batch_set_tile_bits(self._h, k))
+
+    def autotune(self, params_dev, energies_dev, grads_dev, reps: int = 2) -> int:
+        out = ctypes.c_int()
+        self._check(self._lib.vqe_batch_autotune(self._h, _ptr(params_dev), _ptr(energies_dev),
+                                                 _ptr(grads_dev), reps, ctypes.byref(out)))
+        return out.value
+
+    def graph_launches(self) -> int:
+        out = ctypes.c_uint64()
+        self._check(self._lib.vqe_batch_launch_count(self._h, ctypes.byref(out)))
+        return out.value
 
 
 def version() -> str:

@@ -178,18 +178,26 @@ __global__ void k_energy_finish(const double *__restrict__ partials, int bps, in
     if (unnorm) unnorm[b] = e;
 }
 
-__global__ void k_grad_finish(const double *__restrict__ part, size_t part_stride,
-                              const int *__restrict__ off, const int *__restrict__ count,
-                              const int *__restrict__ step, int n_params, int batch,
-                              double *grads) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n_params * batch) return;
-    const int b = idx / n_params, p = idx % n_params;
+// One block per (state, parameter): threads sum strided partials, then a
+// fixed-order tree over the block (bitwise reproducible).
+constexpr int kGradThreads = 128;
+__global__ void __launch_bounds__(kGradThreads)
+k_grad_finish(const double *__restrict__ part, size_t part_stride, const int *__restrict__ off,
+              const int *__restrict__ count, const int *__restrict__ step, int n_params,
+              double *grads) {
+    __shared__ double sh[kGradThreads];
+    const int p = blockIdx.x, b = blockIdx.y;
     const double *src = part + (size_t)b * part_stride + off[p];
     const int c = count[p], s = step[p];
     double acc = 0.0;
-    for (int j = 0; j < c; ++j) acc += src[(size_t)j * s];
-    grads[idx] = acc;
+    for (int j = threadIdx.x; j < c; j += kGradThreads) acc += src[(size_t)j * s];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kGradThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) grads[(size_t)b * n_params + p] = sh[0];
 }
 
 template <typename T>
@@ -228,9 +236,9 @@ cudaError_t launch_energy_finish(const double *partials, int bps, int batch, dou
 cudaError_t launch_grad_finish(const double *part, size_t part_stride, const int *off,
                                const int *count, const int *step, int n_params, int batch,
                                double *grads, cudaStream_t s) {
-    const int total = n_params * batch;
-    k_grad_finish<<<(total + 255) / 256, 256, 0, s>>>(part, part_stride, off, count, step,
-                                                      n_params, batch, grads);
+    dim3 grid(n_params, batch);
+    k_grad_finish<<<grid, kGradThreads, 0, s>>>(part, part_stride, off, count, step, n_params,
+                                                grads);
     return cudaGetLastError();
 }
 

@@ -16,53 +16,9 @@
 //     dE/dtheta = Im <lambda| Y_q |psi>,   dE/dphi = Im <lambda| Z_q |psi>
 // at a point of the sweep where both are valid (after the slot's diagonal is
 // undone and before q's own rotation is undone).
-#include "vqe_internal.h"
+#include "pass_core.cuh"
 
 namespace vqe {
-
-template <typename T> struct V2;
-template <> struct V2<float> { using type = float2; };
-template <> struct V2<double> { using type = double2; };
-
-__device__ __forceinline__ uint32_t elem_of(uint32_t t, uint32_t r, int p, int R) {
-    const uint32_t lo = t & ((1u << p) - 1u);
-    return lo | (r << p) | ((t >> p) << (p + R));
-}
-
-// Shared-memory slot of tile element e: XOR-fold of the higher bits into the
-// bank-selecting low bits, so that every register chunk of the plan reads
-// and writes conflict-free (16-byte elements: 8 per 128 B; 8-byte: 16).
-template <typename T> __device__ __forceinline__ uint32_t swz(uint32_t e);
-template <> __device__ __forceinline__ uint32_t swz<double>(uint32_t e) {
-    const uint32_t f = (e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12);
-    return e ^ (f & 7u);
-}
-template <> __device__ __forceinline__ uint32_t swz<float>(uint32_t e) {
-    const uint32_t f = (e >> 4) ^ (e >> 8) ^ (e >> 12);
-    return e ^ (f & 15u);
-}
-
-__device__ __forceinline__ double flip_sign(double v, uint32_t s) {
-    return __longlong_as_double(__double_as_longlong(v) ^ ((unsigned long long)s << 63));
-}
-__device__ __forceinline__ float flip_sign(float v, uint32_t s) {
-    return __int_as_float(__float_as_int(v) ^ (int)(s << 31));
-}
-
-template <typename C>
-__device__ __forceinline__ C cmul(C x, C d) {
-    C r;
-    r.x = fma(x.x, d.x, -x.y * d.y);
-    r.y = fma(x.x, d.y, x.y * d.x);
-    return r;
-}
-template <typename C>
-__device__ __forceinline__ C cmul_conj(C x, C d) {   // x * conj(d)
-    C r;
-    r.x = fma(x.x, d.x, x.y * d.y);
-    r.y = fma(x.y, d.x, -x.x * d.y);
-    return r;
-}
 
 // ---------------------------------------------------------------- staging
 
@@ -148,6 +104,40 @@ cudaError_t launch_stage(const StageSlot *slots_dev, int n_slots, int n_qubits, 
 // Plans keep k - R <= 9, so a pass block has at most 512 threads.
 constexpr int kPassMaxThreads = 512;
 
+template <typename T>
+struct GridEnv {
+    using C = typename V2<T>::type;
+    const PassDesc *d;          // shared-memory copy of the pass descriptor
+    const RotCoef<T> *cf;       // shared-memory copy: coefficient rows of the pass's slots
+    const C *dt;
+    double *gout;   // this state's gradient partials
+    uint64_t tile;
+    __device__ RotCoef<T> coef(int slot, int bit) const { return cf[slot * d->k + bit]; }
+    __device__ C diag(int slot, uint32_t e) const { return dt[d->slot_dtab_off[slot] + e]; }
+    __device__ void grad(int slot, int bit, int comp, double v) const {
+        gout[d->slot_grad_off[slot] + tile * (uint64_t)(2 * d->k) + bit * 2 + comp] = v;
+    }
+};
+
+// Copies the pass descriptor and the pass's coefficient rows into shared
+// memory, so the op interpreter reads them with shared-memory loads.
+template <typename T>
+__device__ __forceinline__ void stage_pass(const PassDesc *__restrict__ desc,
+                                           const RotCoef<T> *__restrict__ cf, PassDesc *sd,
+                                           RotCoef<T> *scf) {
+    static_assert(sizeof(PassDesc) % 4 == 0, "descriptor copied in words");
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(desc);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(sd);
+    for (int i = threadIdx.x; i < (int)(sizeof(PassDesc) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    const int k = sd->k;
+    for (int i = threadIdx.x; i < sd->n_slots * k; i += blockDim.x)
+        scf[i] = cf[sd->slot_coef_off[i / k] + (i % k)];
+    __syncthreads();
+}
+
+// One CTA per (tile, state): global -> shared (plain order), the pass
+// program, shared -> global.
 template <typename T, int R, bool BWD>
 __global__ void __launch_bounds__(kPassMaxThreads)
 k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *__restrict__ psi,
@@ -155,174 +145,47 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
        size_t coef_stride, const typename V2<T>::type *__restrict__ dtab, size_t dtab_stride,
        double *__restrict__ gpart, size_t grad_stride) {
     using C = typename V2<T>::type;
-    constexpr int NR = 1 << R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int k = desc->k, m = desc->m, a = desc->a;
-    const int hbits = k - m;
-    C *sp = reinterpret_cast<C *>(smem_raw);
-    C *sl = sp + (BWD ? (1u << k) : 0u);
-    double *gsh = reinterpret_cast<double *>(sp + (BWD ? (2u << k) : (1u << k)));
-    // Blocks of fewer than 32 threads (tiles of < 2^(R+5) amplitudes) form one
-    // partial warp; the shuffles below then stay inside its active lanes.
-    const int nwarps = (blockDim.x + 31) >> 5;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned wmask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
-    const int wlanes = blockDim.x >= 32 ? 32 : (int)blockDim.x;
-
-    const uint32_t t = threadIdx.x;
-    const uint64_t tile = blockIdx.x;
+    __shared__ PassDesc sd;
     const int b = blockIdx.y;
+    // dynamic shared memory: tile(s) | gradient scratch (backward) | coefficient rows
+    const int kk = desc->k;
+    const uint32_t size = 1u << kk;
+    C *sp = reinterpret_cast<C *>(smem_raw);
+    C *sl = sp + (BWD ? size : 0u);
+    double *gsh = reinterpret_cast<double *>(sp + (BWD ? 2 * size : size));
+    RotCoef<T> *scf = reinterpret_cast<RotCoef<T> *>(
+        reinterpret_cast<unsigned char *>(gsh) +
+        (BWD ? tile_grad_scratch_bytes((int)blockDim.x, kk) : 0));
+    stage_pass<T>(desc, coefs + (size_t)b * coef_stride, &sd, scf);
+    const PassDesc &d = sd;
+    const int k = d.k, m = d.m, a = d.a;
+    const uint64_t tile = blockIdx.x;
     const int mid = a - m;
-    const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + hbits));
+    const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (k - m)));
     const uint32_t lowmask = (1u << m) - 1u;
     C *P = psi + (size_t)b * stride;
     C *L = BWD ? lam + (size_t)b * stride : nullptr;
-    const RotCoef<T> *cf = coefs + (size_t)b * coef_stride;
-    const C *dt = dtab + (size_t)b * dtab_stride;
-
-    auto gaddr = [&](uint32_t e) -> uint64_t {
-        return base | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a);
-    };
-
-    C v[NR];
-    C w[NR];
-    int chunk = -1;
-    const int nops = desc->n_ops;
-    for (int oi = 0; oi < nops; ++oi) {
-        const PassOp op = desc->ops[oi];
-        if (op.kind == OP_ROUND) {
-            const int p = op.chunk;
-            if (chunk < 0) {
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const uint64_t g = gaddr(elem_of(t, r, p, R));
-                    if (init_zero) {
-                        v[r].x = (g == 0) ? T(1) : T(0);
-                        v[r].y = T(0);
-                    } else {
-                        v[r] = P[g];
-                    }
-                    if (BWD) w[r] = L[g];
-                }
-            } else {
-                __syncthreads();
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const uint32_t s = swz<T>(elem_of(t, r, chunk, R));
-                    sp[s] = v[r];
-                    if (BWD) sl[s] = w[r];
-                }
-                __syncthreads();
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const uint32_t s = swz<T>(elem_of(t, r, p, R));
-                    v[r] = sp[s];
-                    if (BWD) w[r] = sl[s];
-                }
-            }
-            chunk = p;
-        } else if (op.kind == OP_BF) {
-            const int coff = desc->slot_coef_off[op.slot];
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                if (!((op.mask >> j) & 1)) continue;
-                const RotCoef<T> rc = cf[coff + chunk + j];
-                const T cv = rc.v;
-                if (BWD) {
-                    T gt = T(0), gp = T(0);
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        if (r & (1 << j)) continue;
-                        const C p0 = v[r], p1 = v[r | (1 << j)];
-                        const C l0 = w[r], l1 = w[r | (1 << j)];
-                        // Im<l|Y|p> over the pair: Re(conj(l1) p0) - Re(conj(l0) p1)
-                        gt += fma(l1.x, p0.x, l1.y * p0.y) - fma(l0.x, p1.x, l0.y * p1.y);
-                        // Im<l|Z|p> over the pair: Im(conj(l0) p0) - Im(conj(l1) p1)
-                        gp += fma(l0.x, p0.y, -l0.y * p0.x) - fma(l1.x, p1.y, -l1.y * p1.x);
-                    }
-                    double dgt = (double)(gt * rc.gs), dgp = (double)(gp * rc.gs);
-                    for (int o = wlanes >> 1; o > 0; o >>= 1) {
-                        dgt += __shfl_xor_sync(wmask, dgt, o);
-                        dgp += __shfl_xor_sync(wmask, dgp, o);
-                    }
-                    if (lane == 0) {
-                        gsh[(warp * k + chunk + j) * 2 + 0] = dgt;
-                        gsh[(warp * k + chunk + j) * 2 + 1] = dgp;
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    if (r & (1 << j)) continue;
-                    const int r1 = r | (1 << j);
-                    if (!BWD) {
-                        const C x = v[r], y = v[r1];
-                        if (rc.mode == 0) {   // [[1,-t],[t,1]]
-                            v[r].x = fma(-cv, y.x, x.x);  v[r].y = fma(-cv, y.y, x.y);
-                            v[r1].x = fma(cv, x.x, y.x);  v[r1].y = fma(cv, x.y, y.y);
-                        } else {              // [[u,-1],[1,u]]
-                            v[r].x = fma(cv, x.x, -y.x);  v[r].y = fma(cv, x.y, -y.y);
-                            v[r1].x = fma(cv, y.x, x.x);  v[r1].y = fma(cv, y.y, x.y);
-                        }
-                    } else {
-#pragma unroll
-                        for (int bufi = 0; bufi < 2; ++bufi) {
-                            C *u = bufi ? w : v;
-                            const C x = u[r], y = u[r1];
-                            if (rc.mode == 0) {   // transpose: [[1,t],[-t,1]]
-                                u[r].x = fma(cv, y.x, x.x);    u[r].y = fma(cv, y.y, x.y);
-                                u[r1].x = fma(-cv, x.x, y.x);  u[r1].y = fma(-cv, x.y, y.y);
-                            } else {              // transpose: [[u,1],[-1,u]]
-                                u[r].x = fma(cv, x.x, y.x);    u[r].y = fma(cv, x.y, y.y);
-                                u[r1].x = fma(cv, y.x, -x.x);  u[r1].y = fma(cv, y.y, -x.y);
-                            }
-                        }
-                    }
-                }
-            }
-        } else if (op.kind == OP_DIAG) {
-            const uint32_t cz = desc->slot_czmask[op.slot];
-            const C *tab = dt + desc->slot_dtab_off[op.slot];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const uint32_t e = elem_of(t, r, chunk, R);
-                const uint32_t g32 = (uint32_t)gaddr(e);
-                const uint32_t sgn = __popc(g32 & (g32 >> 1) & cz) & 1u;
-                const C d = tab[e];
-                if (!BWD) {
-                    C y = cmul(v[r], d);
-                    y.x = flip_sign(y.x, sgn);
-                    y.y = flip_sign(y.y, sgn);
-                    v[r] = y;
-                } else {
-                    C y = cmul_conj(v[r], d);
-                    y.x = flip_sign(y.x, sgn);
-                    y.y = flip_sign(y.y, sgn);
-                    v[r] = y;
-                    C z = cmul_conj(w[r], d);
-                    z.x = flip_sign(z.x, sgn);
-                    z.y = flip_sign(z.y, sgn);
-                    w[r] = z;
-                }
-            }
-        } else if (BWD && op.kind == OP_FLUSH) {
-            __syncthreads();
-            const uint32_t gated = desc->slot_gated[op.slot];
-            double *out = gpart + (size_t)b * grad_stride + desc->slot_grad_off[op.slot] +
-                          tile * (uint64_t)(2 * k);
-            for (int idx = threadIdx.x; idx < 2 * k; idx += blockDim.x) {
-                if (!((gated >> (idx >> 1)) & 1u)) continue;
-                double s = 0.0;
-                for (int wi = 0; wi < nwarps; ++wi) s += gsh[wi * 2 * k + idx];
-                out[idx] = s;
-            }
-            __syncthreads();
+    for (uint32_t e = threadIdx.x; e < size; e += blockDim.x) {
+        const uint64_t g = base | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a);
+        if (init_zero) {
+            C z;
+            z.x = (g == 0) ? T(1) : T(0);
+            z.y = T(0);
+            sp[e] = z;
+        } else {
+            sp[e] = P[g];
         }
+        if (BWD) sl[e] = L[g];
     }
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        const uint64_t g = gaddr(elem_of(t, r, chunk, R));
-        P[g] = v[r];
-        if (BWD) L[g] = w[r];
+    __syncthreads();
+    GridEnv<T> env{&sd, scf, dtab + (size_t)b * dtab_stride,
+                   BWD ? gpart + (size_t)b * grad_stride : nullptr, tile};
+    run_tile<T, R, BWD>(d, d.ops, d.n_ops, base, sp, sl, gsh, env);
+    for (uint32_t e = threadIdx.x; e < size; e += blockDim.x) {
+        const uint64_t g = base | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a);
+        P[g] = sp[e];
+        if (BWD) L[g] = sl[e];
     }
 }
 
@@ -330,9 +193,9 @@ int pass_threads(const PassDesc &d) { return 1 << (d.k - d.R); }
 
 size_t pass_smem_bytes(const PassDesc &d, bool backward, size_t elem_bytes) {
     size_t tiles = (size_t(1) << d.k) * elem_bytes * (backward ? 2 : 1);
-    int warps = (pass_threads(d) + 31) / 32;
-    size_t gsh = backward ? size_t(warps) * d.k * 2 * sizeof(double) : 0;
-    return tiles + gsh;
+    size_t gsh = backward ? tile_grad_scratch_bytes(pass_threads(d), d.k) : 0;
+    const size_t coef = elem_bytes == 16 ? sizeof(RotCoef<double>) : sizeof(RotCoef<float>);
+    return tiles + gsh + size_t(d.n_slots) * d.k * coef;
 }
 
 template <typename T, int R, bool BWD>

@@ -1,0 +1,273 @@
+// Device core of the ansatz tile passes, shared by the grid kernel
+// (k_layers.cu) and the persistent batched kernel (k_batch.cu).
+//
+// A tile holds 2^k amplitudes of the state in shared memory.  Its tile bits
+// map to global index bits as [0, m) -> [0, m) and [m, k) -> [a, a + k - m);
+// `gbase` carries the fixed global bits of the tile.  The pass program (see
+// vqe_internal.h) moves the amplitudes between shared memory and registers in
+// "rounds": in a round, each thread holds 2^R amplitudes whose tile indices
+// differ in the R bits [chunk, chunk + R) and applies the RY butterflies of
+// those bits in registers.  Between rounds the tile goes through shared
+// memory with an XOR swizzle (bank-conflict free for every chunk of the
+// plan); the tile is in plain (linear) order on entry and on exit.
+//
+// The Env policy supplies the per-state data:
+//   RotCoef<T> coef(int slot, int tile_bit)    RY coefficient of a gated bit
+//   C diag(int slot, uint32_t e)               diagonal table entry of tile element e
+//   void grad(int slot, int tile_bit, int comp, double v)   (backward) block total of
+//        a gradient partial: comp 0 = theta (RY), 1 = phi (RZ); called by thread 0
+#pragma once
+
+#include "vqe_internal.h"
+
+namespace vqe {
+
+template <typename T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+
+__device__ __forceinline__ uint32_t elem_of(uint32_t t, uint32_t r, int p, int R) {
+    const uint32_t lo = t & ((1u << p) - 1u);
+    return lo | (r << p) | ((t >> p) << (p + R));
+}
+
+// Shared-memory slot of tile element e: XOR-fold of the higher bits into the
+// bank-selecting low bits (16-byte elements: 8 per 128 B; 8-byte: 16).
+template <typename T> __device__ __forceinline__ uint32_t swz(uint32_t e);
+template <> __device__ __forceinline__ uint32_t swz<double>(uint32_t e) {
+    const uint32_t f = (e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12);
+    return e ^ (f & 7u);
+}
+template <> __device__ __forceinline__ uint32_t swz<float>(uint32_t e) {
+    const uint32_t f = (e >> 4) ^ (e >> 8) ^ (e >> 12);
+    return e ^ (f & 15u);
+}
+
+__device__ __forceinline__ double flip_sign(double v, uint32_t s) {
+    return __longlong_as_double(__double_as_longlong(v) ^ ((unsigned long long)s << 63));
+}
+__device__ __forceinline__ float flip_sign(float v, uint32_t s) {
+    return __int_as_float(__float_as_int(v) ^ (int)(s << 31));
+}
+
+template <typename C>
+__device__ __forceinline__ C cmul(C x, C d) {
+    C r;
+    r.x = fma(x.x, d.x, -x.y * d.y);
+    r.y = fma(x.x, d.y, x.y * d.x);
+    return r;
+}
+template <typename C>
+__device__ __forceinline__ C cmul_conj(C x, C d) {   // x * conj(d)
+    C r;
+    r.x = fma(x.x, d.x, x.y * d.y);
+    r.y = fma(x.y, d.x, -x.x * d.y);
+    return r;
+}
+
+// Scratch a backward tile program needs besides the tile buffers:
+// nwarps * k * 2 doubles.
+__host__ __device__ inline size_t tile_grad_scratch_bytes(int threads, int k) {
+    return size_t((threads + 31) / 32) * k * 2 * sizeof(double);
+}
+
+// Runs the program `ops[0..n_ops)` of pass `d` on the tile in `buf` (and
+// `lbuf` when backward).  All threads of the block must call it; threads
+// t >= 2^(k-R) take part only in the barriers.  `gsh` is the backward
+// scratch of tile_grad_scratch_bytes(blockDim.x, k) bytes.
+template <typename T, int R, bool BWD, class Env>
+__device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, int n_ops,
+                                         uint64_t gbase, typename V2<T>::type *buf,
+                                         typename V2<T>::type *lbuf, double *gsh, Env &env) {
+    using C = typename V2<T>::type;
+    constexpr int NR = 1 << R;
+    const int k = d.k, m = d.m, a = d.a;
+    const uint32_t nthr = 1u << (k - R);
+    const uint32_t t = threadIdx.x;
+    const bool active = t < nthr;
+    const int nwarps = (int)((blockDim.x + 31) >> 5);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned wmask = nthr >= 32 ? 0xffffffffu : ((1u << nthr) - 1u);
+    const int wlanes = nthr >= 32 ? 32 : (int)nthr;
+    const uint32_t lowmask = (1u << m) - 1u;
+    auto g32 = [&](uint32_t e) -> uint32_t {
+        return (uint32_t)(gbase | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a));
+    };
+
+    C v[NR];
+    C w[NR];
+    int chunk = -1;
+    for (int oi = 0; oi < n_ops; ++oi) {
+        const PassOp op = ops[oi];
+        if (op.kind == OP_ROUND) {
+            const int p = op.chunk;
+            if (chunk < 0) {
+                if (active) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const uint32_t e = elem_of(t, r, p, R);
+                        v[r] = buf[e];
+                        if (BWD) w[r] = lbuf[e];
+                    }
+                }
+            } else {
+                __syncthreads();
+                if (active) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const uint32_t s = swz<T>(elem_of(t, r, chunk, R));
+                        buf[s] = v[r];
+                        if (BWD) lbuf[s] = w[r];
+                    }
+                }
+                __syncthreads();
+                if (active) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const uint32_t s = swz<T>(elem_of(t, r, p, R));
+                        v[r] = buf[s];
+                        if (BWD) w[r] = lbuf[s];
+                    }
+                }
+            }
+            chunk = p;
+        } else if (op.kind == OP_BF) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (!((op.mask >> j) & 1)) continue;
+                const RotCoef<T> rc = env.coef(op.slot, chunk + j);
+                const T cv = rc.v;
+                if (BWD) {
+                    // dE/dtheta = Im<l|Y|p>; per pair Re(conj(l1) p0) - Re(conj(l0) p1)
+                    T gt = T(0);
+                    if (active) {
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            if (r & (1 << j)) continue;
+                            const C p0 = v[r], p1 = v[r | (1 << j)];
+                            const C l0 = w[r], l1 = w[r | (1 << j)];
+                            gt = fma(l1.x, p0.x, gt);
+                            gt = fma(l1.y, p0.y, gt);
+                            gt = fma(-l0.x, p1.x, gt);
+                            gt = fma(-l0.y, p1.y, gt);
+                        }
+                        double dgt = (double)(gt * rc.gs);
+                        for (int o = wlanes >> 1; o > 0; o >>= 1)
+                            dgt += __shfl_xor_sync(wmask, dgt, o);
+                        if (lane == 0) gsh[(warp * k + chunk + j) * 2 + 0] = dgt;
+                    }
+                }
+                if (!active) continue;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (r & (1 << j)) continue;
+                    const int r1 = r | (1 << j);
+                    if (!BWD) {
+                        const C x = v[r], y = v[r1];
+                        if (rc.mode == 0) {   // [[1,-t],[t,1]]
+                            v[r].x = fma(-cv, y.x, x.x);  v[r].y = fma(-cv, y.y, x.y);
+                            v[r1].x = fma(cv, x.x, y.x);  v[r1].y = fma(cv, x.y, y.y);
+                        } else {              // [[u,-1],[1,u]]
+                            v[r].x = fma(cv, x.x, -y.x);  v[r].y = fma(cv, x.y, -y.y);
+                            v[r1].x = fma(cv, y.x, x.x);  v[r1].y = fma(cv, y.y, x.y);
+                        }
+                    } else {
+#pragma unroll
+                        for (int bufi = 0; bufi < 2; ++bufi) {
+                            C *u = bufi ? w : v;
+                            const C x = u[r], y = u[r1];
+                            if (rc.mode == 0) {   // transpose: [[1,t],[-t,1]]
+                                u[r].x = fma(cv, y.x, x.x);    u[r].y = fma(cv, y.y, x.y);
+                                u[r1].x = fma(-cv, x.x, y.x);  u[r1].y = fma(-cv, x.y, y.y);
+                            } else {              // transpose: [[u,1],[-1,u]]
+                                u[r].x = fma(cv, x.x, y.x);    u[r].y = fma(cv, x.y, y.y);
+                                u[r1].x = fma(cv, y.x, -x.x);  u[r1].y = fma(cv, y.y, -x.y);
+                            }
+                        }
+                    }
+                }
+            }
+        } else if (op.kind == OP_DIAG) {
+            const uint32_t cz = d.slot_czmask[op.slot];
+            if (BWD && active) {
+                // dE/dphi_q = Im<l|Z_q|p> = sum_i u_i (-1)^{bit_q(i)}, u = Im(conj(l) p),
+                // for every gated bit q of the slot, taken before the diagonal is
+                // undone (where the buffers hold the exact states).
+                T u[NR];
+                T tot = T(0);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    u[r] = fma(w[r].x, v[r].y, -w[r].y * v[r].x);
+                    tot += u[r];
+                }
+                const uint32_t gated = d.slot_gated[op.slot];
+                const uint32_t e0 = elem_of(t, 0, chunk, R);
+                for (int q = 0; q < k; ++q) {
+                    if (!((gated >> q) & 1u)) continue;
+                    T gq;
+                    if (q >= chunk && q < chunk + R) {
+                        gq = T(0);
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) gq += ((r >> (q - chunk)) & 1) ? -u[r] : u[r];
+                    } else {
+                        gq = ((e0 >> q) & 1u) ? -tot : tot;
+                    }
+                    double dg = (double)gq;
+                    for (int o = wlanes >> 1; o > 0; o >>= 1) dg += __shfl_xor_sync(wmask, dg, o);
+                    if (lane == 0) gsh[(warp * k + q) * 2 + 1] = dg;
+                }
+            }
+            if (active) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t e = elem_of(t, r, chunk, R);
+                    const uint32_t g = g32(e);
+                    const uint32_t sgn = __popc(g & (g >> 1) & cz) & 1u;
+                    const C dv = env.diag(op.slot, e);
+                    if (!BWD) {
+                        C y = cmul(v[r], dv);
+                        y.x = flip_sign(y.x, sgn);
+                        y.y = flip_sign(y.y, sgn);
+                        v[r] = y;
+                    } else {
+                        C y = cmul_conj(v[r], dv);
+                        y.x = flip_sign(y.x, sgn);
+                        y.y = flip_sign(y.y, sgn);
+                        v[r] = y;
+                        C z = cmul_conj(w[r], dv);
+                        z.x = flip_sign(z.x, sgn);
+                        z.y = flip_sign(z.y, sgn);
+                        w[r] = z;
+                    }
+                }
+            }
+        } else if (BWD && op.kind == OP_FLUSH) {
+            __syncthreads();
+            const uint32_t gated = d.slot_gated[op.slot];
+            const int used_warps = (int)((nthr + 31) >> 5);
+            if (threadIdx.x == 0) {
+                for (int idx = 0; idx < 2 * k; ++idx) {
+                    if (!((gated >> (idx >> 1)) & 1u)) continue;
+                    double s = 0.0;
+                    for (int wi = 0; wi < used_warps; ++wi) s += gsh[wi * 2 * k + idx];
+                    env.grad(op.slot, idx >> 1, idx & 1, s);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // back to plain order in shared memory
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const uint32_t e = elem_of(t, r, chunk, R);
+            buf[e] = v[r];
+            if (BWD) lbuf[e] = w[r];
+        }
+    }
+    __syncthreads();
+    (void)nwarps;
+}
+
+}  // namespace vqe

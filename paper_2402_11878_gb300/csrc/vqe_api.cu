@@ -23,6 +23,12 @@ struct Group {        // one qubit group = the tile bits of one kind of pass
     int qubit_of(int j) const { return j < m ? j : a + (j - m); }
 };
 
+struct PlanOptions {
+    int tile_bits_max = 0;  // 0: default (12 for C128, 13 for C64)
+    int run_bits = 0;       // 0: default (3 for C128, 4 for C64: 128-byte runs)
+    int reg_bits = 0;       // 0: default (3 for C128, 4 for C64)
+};
+
 struct PassPlan {
     int group;
     std::vector<int> layers;  // one slot per layer
@@ -60,6 +66,7 @@ struct vqe_ctx {
     int n_groups = 0;
 
     // ansatz plan
+    PlanOptions plan_opts;
     std::vector<Group> groups;
     std::vector<PassDesc> fwd, bwd;
     std::vector<int> pass_tiles_log2;
@@ -179,9 +186,7 @@ vqe_status prof_collect(vqe_ctx *h) {
 
 // ---------------------------------------------------------------- planner
 
-std::vector<Group> plan_groups(int n, vqe_precision prec) {
-    const int kmax = prec == VQE_C128 ? 12 : 13;
-    const int mrun = prec == VQE_C128 ? 3 : 4;   // 128-byte contiguous runs in high passes
+std::vector<Group> plan_groups(int n, int kmax, int mrun) {
     std::vector<Group> gs;
     if (n <= kmax) {
         gs.push_back({n, n, n, (n >= 32 ? 0xffffffffu : ((1u << n) - 1u))});
@@ -204,6 +209,29 @@ struct Round {
     int chunk;
     std::vector<PassOp> ops;
 };
+
+PlanOptions resolve(const PlanOptions &o, vqe_precision prec) {
+    PlanOptions r;
+    r.tile_bits_max = o.tile_bits_max ? o.tile_bits_max : (prec == VQE_C128 ? 12 : 13);
+    r.run_bits = o.run_bits ? o.run_bits : (prec == VQE_C128 ? 3 : 4);
+    r.reg_bits = o.reg_bits ? o.reg_bits : (prec == VQE_C128 ? 3 : 4);
+    return r;
+}
+
+bool options_valid(const PlanOptions &o, vqe_precision prec, std::string &err) {
+    const PlanOptions r = resolve(o, prec);
+    if (r.tile_bits_max < 1 || r.tile_bits_max > kMaxTileBits) err = "tile_bits_max out of 1..14";
+    else if (r.reg_bits < 1 || r.reg_bits > 4) err = "reg_bits out of 1..4";
+    else if (r.tile_bits_max - r.reg_bits > 9) err = "tile_bits_max - reg_bits must be <= 9 (512 threads)";
+    else if (r.run_bits < 1 || r.run_bits >= r.tile_bits_max) err = "run_bits out of 1..tile_bits_max-1";
+    else {
+        const size_t elem = prec == VQE_C128 ? 16 : 8;
+        const size_t warps = ((size_t(1) << (r.tile_bits_max - std::min(r.reg_bits, r.tile_bits_max))) + 31) / 32;
+        const size_t smem = (size_t(2) << r.tile_bits_max) * elem + warps * r.tile_bits_max * 16;
+        if (smem > 227 * 1024) err = "tile does not fit in shared memory";
+    }
+    return err.empty();
+}
 
 struct HostPlan {
     std::vector<Group> groups;
@@ -281,11 +309,14 @@ void emit_backward(PassDesc &d, const std::vector<Round> &rs, int n_slots) {
     d.n_ops = k;
 }
 
-bool make_plan(int n, int D, vqe_precision prec, HostPlan &hp, std::string &err) {
+bool make_plan(int n, int D, vqe_precision prec, const PlanOptions &opt, HostPlan &hp,
+               std::string &err) {
     hp = HostPlan{};
-    hp.groups = plan_groups(n, prec);
+    if (!options_valid(opt, prec, err)) return false;
+    const PlanOptions o = resolve(opt, prec);
+    hp.groups = plan_groups(n, o.tile_bits_max, o.run_bits);
     const int ng = int(hp.groups.size());
-    const int Rdef = prec == VQE_C128 ? 3 : 4;
+    const int Rdef = o.reg_bits;
 
     // Layer events in zigzag order; consecutive events of one group merge.
     std::vector<PassPlan> plans;
@@ -450,7 +481,7 @@ bool make_plan(int n, int D, vqe_precision prec, HostPlan &hp, std::string &err)
 vqe_status build_plan(vqe_ctx *h) {
     HostPlan hp;
     std::string err;
-    if (!make_plan(h->n, h->depth, h->prec, hp, err)) return fail(h, VQE_ERR_STATE, err);
+    if (!make_plan(h->n, h->depth, h->prec, h->plan_opts, hp, err)) return fail(h, VQE_ERR_ARG, err);
     h->groups = hp.groups;
     h->fwd = hp.fwd;
     h->bwd = hp.bwd;
@@ -849,6 +880,28 @@ vqe_status vqe_destroy(vqe_handle h) {
     return VQE_OK;
 }
 
+vqe_status vqe_set_plan_options(vqe_handle h, int tile_bits_max, int run_bits, int reg_bits) {
+    if (!h) return VQE_ERR_ARG;
+    PlanOptions o;
+    o.tile_bits_max = tile_bits_max;
+    o.run_bits = run_bits;
+    o.reg_bits = reg_bits;
+    std::string err;
+    if (!options_valid(o, h->prec, err)) return fail(h, VQE_ERR_ARG, err);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    const PlanOptions old = h->plan_opts;
+    h->plan_opts = o;
+    vqe_status st = build_plan(h);
+    if (st != VQE_OK) {
+        h->plan_opts = old;
+        build_plan(h);
+        return st;
+    }
+    h->state_valid = false;
+    return VQE_OK;
+}
+
 vqe_status vqe_workspace_size(vqe_handle h, int batch, int want_gradient, size_t *bytes) {
     if (!h || !bytes || batch < 1) return fail(h, VQE_ERR_ARG, "bad argument");
     *bytes = h->state_bytes() * (want_gradient ? 2 : 1) * size_t(batch);
@@ -1100,13 +1153,19 @@ size_t vqe_inspect_sizeof(int which) {
     }
 }
 
-int vqe_inspect_plan(int n_qubits, int depth, int precision, void *fwd, void *bwd, int max_passes,
-                     void *stage, int max_stage, int *grad_map, int max_params,
-                     uint64_t strides[3], int counts[3]) {
+int vqe_inspect_plan(int n_qubits, int depth, int precision, const int options[3], void *fwd,
+                     void *bwd, int max_passes, void *stage, int max_stage, int *grad_map,
+                     int max_params, uint64_t strides[3], int counts[3]) {
     if (n_qubits < 1 || n_qubits > 32 || depth < 1 || (precision != 0 && precision != 1)) return -1;
     HostPlan hp;
     std::string err;
-    if (!make_plan(n_qubits, depth, vqe_precision(precision), hp, err)) return -1;
+    PlanOptions opt;
+    if (options) {
+        opt.tile_bits_max = options[0];
+        opt.run_bits = options[1];
+        opt.reg_bits = options[2];
+    }
+    if (!make_plan(n_qubits, depth, vqe_precision(precision), opt, hp, err)) return -1;
     if (counts) {
         counts[0] = int(hp.fwd.size());
         counts[1] = int(hp.stage.size());
@@ -1161,6 +1220,485 @@ int vqe_inspect_hamiltonian(int n_qubits, const uint64_t *x_masks, const uint64_
     if (tz) std::memcpy(tz, hp.tz.data(), hp.tz.size() * sizeof(uint32_t));
     if (tc) std::memcpy(tc, hp.tc.data(), hp.tc.size() * sizeof(double));
     return 0;
+}
+
+}  // extern "C"
+
+// ================================================================= batched driver
+
+#include "batch_internal.h"
+
+struct vqe_batch_ctx {
+    int count = 0;
+    vqe_precision prec = VQE_C64;
+    cudaStream_t stream = nullptr;     // caller's stream (or an internal one)
+    bool own_stream = false;
+    int device = 0;
+    int tile_bits = 0;                 // plan tile size for instances larger than one tile
+    std::string err;
+    std::vector<int> n, depth;
+    std::vector<size_t> poff;          // parameter offsets (count + 1)
+    std::vector<std::vector<uint64_t>> hx, hz;
+    std::vector<std::vector<double>> hc;
+    std::vector<uint8_t> ham_ok;
+    bool ham_dirty = true, plan_dirty = true;
+    // device
+    DevBuf d_inst, d_order, d_counter, d_plans, d_fwd, d_bwd, d_stage, d_groups, d_tz, d_tc,
+        d_scratch;
+    DevBuf hb_p, hb_e, hb_g;   // device copies for vqe_batch_run (host buffers)
+    BatchLayout layout{};
+    int grid = 0;
+    size_t scratch_elems = 0;
+    std::vector<BatchInst> inst;
+    // captured graph for the last pointer triple
+    cudaGraphExec_t gexec = nullptr;
+    const void *g_params = nullptr, *g_e = nullptr, *g_g = nullptr;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+vqe_status bfail(vqe_batch_ctx *b, vqe_status st, const std::string &msg) {
+    if (b) b->err = msg;
+    return st;
+}
+
+#define VQE_BCUDA(b, call)                                                                      \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return bfail((b), VQE_ERR_CUDA, std::string(#call) + ": " +       \
+                                                                  cudaGetErrorString(e_));      \
+    } while (0)
+
+vqe_status bensure(vqe_batch_ctx *b, DevBuf &buf, size_t bytes, const char *what) {
+    if (buf.bytes >= bytes && buf.p) return VQE_OK;
+    buf.release();
+    if (bytes == 0) return VQE_OK;
+    if (cudaMalloc(&buf.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        buf.p = nullptr;
+        return bfail(b, VQE_ERR_OOM, std::string("cudaMalloc failed for ") + what);
+    }
+    buf.bytes = bytes;
+    return VQE_OK;
+}
+
+template <typename V>
+vqe_status bupload(vqe_batch_ctx *b, DevBuf &buf, const std::vector<V> &v, const char *what) {
+    vqe_status st = bensure(b, buf, std::max<size_t>(v.size() * sizeof(V), 16), what);
+    if (st != VQE_OK) return st;
+    if (!v.empty())
+        VQE_BCUDA(b, cudaMemcpyAsync(buf.p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice,
+                                     b->stream));
+    VQE_BCUDA(b, cudaStreamSynchronize(b->stream));
+    return VQE_OK;
+}
+
+// Options that give every pass of an n-qubit instance exactly kBatchThreads
+// threads: one tile for n <= tile bits, else a low group and one high group
+// of equal tile size.
+bool batch_options(int n, vqe_precision prec, int tile_bits, PlanOptions &o) {
+    const int kmax = tile_bits;
+    const int lg = 9;   // log2(kBatchThreads)
+    if (n <= kmax) {
+        o.tile_bits_max = std::max(n, 2);
+        o.reg_bits = std::min(4, std::max(1, n - lg));
+        o.run_bits = 1;
+    } else {
+        const int run = 2 * kmax - n;
+        if (run < 1) return false;
+        o.tile_bits_max = kmax;
+        o.run_bits = run;
+        o.reg_bits = kmax - lg;
+    }
+    (void)prec;
+    return true;
+}
+
+vqe_status batch_build(vqe_batch_ctx *b) {
+    const bool c128 = b->prec == VQE_C128;
+    const size_t elem = c128 ? 16 : 8;
+    const size_t coef_sz = c128 ? sizeof(RotCoef<double>) : sizeof(RotCoef<float>);
+    std::vector<BatchPlan> plans;
+    std::vector<PassDesc> fwd, bwd;
+    std::vector<StageSlot> stage;
+    std::vector<std::pair<int, int>> keys;   // (n, depth) -> plan index
+    b->inst.assign(b->count, BatchInst{});
+    size_t max_tile = 0, max_coef = 0, max_lo = 0, max_hi = 0, max_np = 0, max_stage = 0;
+    int max_multi_n = 0;
+    for (int i = 0; i < b->count; ++i) {
+        const std::pair<int, int> key{b->n[i], b->depth[i]};
+        int pi = -1;
+        for (size_t j = 0; j < keys.size(); ++j)
+            if (keys[j] == key) pi = int(j);
+        if (pi < 0) {
+            PlanOptions o;
+            if (!batch_options(key.first, b->prec, b->tile_bits, o))
+                return bfail(b, VQE_ERR_ARG, "instance too large for the batched driver");
+            HostPlan hp;
+            std::string err;
+            if (!make_plan(key.first, key.second, b->prec, o, hp, err))
+                return bfail(b, VQE_ERR_ARG, "batch plan: " + err);
+            if (int(hp.fwd.size()) > kBatchMaxPasses || int(hp.stage.size()) > kBatchMaxSlots)
+                return bfail(b, VQE_ERR_ARG, "instance plan too deep for the batched driver");
+            BatchPlan P{};
+            P.n = key.first;
+            P.depth = key.second;
+            P.pass_off = int(fwd.size());
+            P.n_passes = int(hp.fwd.size());
+            P.stage_off = int(stage.size());
+            P.n_stage = int(hp.stage.size());
+            int slot = 0;
+            int kk = 0;
+            P.whole_tile = 1;
+            for (int p = 0; p < P.n_passes; ++p) {
+                P.slot_first[p] = slot;
+                slot += hp.fwd[p].n_slots;
+                kk = std::max(kk, hp.fwd[p].k);
+                if (hp.fwd[p].k != key.first) P.whole_tile = 0;
+            }
+            P.coef_entries = int(hp.coef_stride);
+            P.kl = (kk + 1) / 2;
+            P.lo_stride = 1 << P.kl;
+            P.hi_stride = 1 << (kk - P.kl);
+            fwd.insert(fwd.end(), hp.fwd.begin(), hp.fwd.end());
+            bwd.insert(bwd.end(), hp.bwd.begin(), hp.bwd.end());
+            stage.insert(stage.end(), hp.stage.begin(), hp.stage.end());
+            max_tile = std::max(max_tile, size_t(1) << kk);
+            max_coef = std::max(max_coef, hp.coef_stride);
+            max_lo = std::max(max_lo, size_t(P.n_stage) * P.lo_stride);
+            max_hi = std::max(max_hi, size_t(P.n_stage) * P.hi_stride);
+            max_stage = std::max(max_stage, size_t(P.n_stage));
+            if (!P.whole_tile) max_multi_n = std::max(max_multi_n, key.first);
+            pi = int(plans.size());
+            plans.push_back(P);
+            keys.push_back(key);
+        }
+        BatchInst &I = b->inst[i];
+        I.index = i;
+        I.n = b->n[i];
+        I.depth = b->depth[i];
+        I.plan = pi;
+        I.params_off = b->poff[i];
+        max_np = std::max(max_np, size_t(2 * b->n[i] * b->depth[i]));
+    }
+    // shared-memory layout (16-byte aligned pieces)
+    auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+    BatchLayout L{};
+    size_t o = 0;
+    L.off_psi = o; o = al(o + max_tile * elem);
+    L.off_lam = o; o = al(o + max_tile * elem);
+    L.off_gsh = o; o = al(o + size_t((kBatchThreads + 31) / 32) * kMaxTileBits * 2 * sizeof(double));
+    L.off_coef = o; o = al(o + max_coef * coef_sz);
+    L.off_lo = o; o = al(o + max_lo * elem);
+    L.off_hi = o; o = al(o + max_hi * elem);
+    L.off_gacc = o; o = al(o + max_np * sizeof(double));
+    L.off_red = o; o = al(o + 2 * (kBatchThreads / 32) * sizeof(double));
+    L.off_slotbase = o; o = al(o + kMaxSlots * sizeof(int));
+    L.off_phc = o; o = al(o + max_stage * kMaxTileBits * sizeof(double));
+    L.off_phs = o; o = al(o + max_stage * kMaxTileBits * sizeof(double));
+    L.off_scl = o; o = al(o + max_stage * kMaxTileBits * sizeof(double));
+    L.off_sigma = o; o = al(o + max_stage * sizeof(double));
+    L.total = o;
+    if (L.total > 227 * 1024) return bfail(b, VQE_ERR_ARG, "batched instance needs more than 227 KiB of shared memory");
+    b->layout = L;
+    vqe_status st;
+    if ((st = bupload(b, b->d_plans, plans, "batch plans")) != VQE_OK) return st;
+    if ((st = bupload(b, b->d_fwd, fwd, "batch passes")) != VQE_OK) return st;
+    if ((st = bupload(b, b->d_bwd, bwd, "batch passes")) != VQE_OK) return st;
+    if ((st = bupload(b, b->d_stage, stage, "batch stage")) != VQE_OK) return st;
+    // largest first
+    std::vector<int> order(b->count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+        const double cp = double(size_t(1) << b->n[p]) * b->depth[p];
+        const double cq = double(size_t(1) << b->n[q]) * b->depth[q];
+        return cp > cq;
+    });
+    if ((st = bupload(b, b->d_order, order, "batch order")) != VQE_OK) return st;
+    int sms = 0;
+    VQE_BCUDA(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    b->grid = std::max(1, std::min(sms, b->count));
+    b->scratch_elems = max_multi_n ? (size_t(1) << max_multi_n) : 0;
+    if ((st = bensure(b, b->d_scratch, std::max<size_t>(16, size_t(b->grid) * 2 * b->scratch_elems * elem),
+                      "batch scratch")) != VQE_OK)
+        return st;
+    if ((st = bensure(b, b->d_counter, 16, "batch counter")) != VQE_OK) return st;
+    b->plan_dirty = false;
+    b->ham_dirty = true;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    return VQE_OK;
+}
+
+vqe_status batch_upload_hams(vqe_batch_ctx *b) {
+    std::vector<GroupDesc> groups;
+    std::vector<uint32_t> tz;
+    std::vector<double> tc;
+    for (int i = 0; i < b->count; ++i) {
+        if (!b->ham_ok[i]) return bfail(b, VQE_ERR_STATE, "instance " + std::to_string(i) + " has no Hamiltonian");
+        std::vector<uint64_t> cx, cz;
+        std::vector<double> cc;
+        canonicalise(b->hx[i].data(), b->hz[i].data(), b->hc[i].data(), b->hc[i].size(), cx, cz, cc);
+        std::vector<uint8_t> keep(cc.size(), 1);
+        HamPlan hp;
+        make_ham_plan(cx, cz, cc, keep, hp);
+        BatchInst &I = b->inst[i];
+        I.groups_off = int(groups.size());
+        I.n_groups = int(hp.groups.size());
+        I.terms_off = int(tz.size());
+        for (auto g : hp.groups) {
+            groups.push_back(g);
+        }
+        tz.insert(tz.end(), hp.tz.begin(), hp.tz.end());
+        tc.insert(tc.end(), hp.tc.begin(), hp.tc.end());
+    }
+    vqe_status st;
+    if ((st = bupload(b, b->d_inst, b->inst, "batch instances")) != VQE_OK) return st;
+    if ((st = bupload(b, b->d_groups, groups, "batch groups")) != VQE_OK) return st;
+    if ((st = bupload(b, b->d_tz, tz, "batch terms")) != VQE_OK) return st;
+    if (b->prec == VQE_C128) {
+        if ((st = bupload(b, b->d_tc, tc, "batch terms")) != VQE_OK) return st;
+    } else {
+        std::vector<float> tf(tc.begin(), tc.end());
+        if ((st = bupload(b, b->d_tc, tf, "batch terms")) != VQE_OK) return st;
+    }
+    b->ham_dirty = false;
+    return VQE_OK;
+}
+
+vqe_status batch_launch(vqe_batch_ctx *b, const double *params, double *energies, double *grads,
+                        cudaStream_t s) {
+    VQE_BCUDA(b, cudaMemsetAsync(b->d_counter.p, 0, sizeof(int), s));
+    BatchArgs a{};
+    a.inst = static_cast<const BatchInst *>(b->d_inst.p);
+    a.order = static_cast<const int *>(b->d_order.p);
+    a.count = b->count;
+    a.counter = static_cast<int *>(b->d_counter.p);
+    a.plans = static_cast<const BatchPlan *>(b->d_plans.p);
+    a.fwd = static_cast<const PassDesc *>(b->d_fwd.p);
+    a.bwd = static_cast<const PassDesc *>(b->d_bwd.p);
+    a.stage = static_cast<const StageSlot *>(b->d_stage.p);
+    a.groups = static_cast<const GroupDesc *>(b->d_groups.p);
+    a.tz = static_cast<const uint32_t *>(b->d_tz.p);
+    a.tc = b->d_tc.p;
+    a.params = params;
+    a.energies = energies;
+    a.grads = grads;
+    a.scratch = b->d_scratch.p;
+    a.scratch_elems = b->scratch_elems;
+    a.layout = b->layout;
+    cudaError_t e = b->prec == VQE_C128 ? launch_batch<double>(a, b->grid, b->layout.total, s)
+                                        : launch_batch<float>(a, b->grid, b->layout.total, s);
+    if (e != cudaSuccess) return bfail(b, VQE_ERR_CUDA, std::string("k_batch: ") + cudaGetErrorString(e));
+    return VQE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vqe_status vqe_batch_create(int count, const int *n_qubits, const int *depths,
+                            vqe_precision precision, void *cuda_stream, vqe_batch *out) {
+    if (!out) return VQE_ERR_ARG;
+    *out = nullptr;
+    if (count < 1 || count > (1 << 24) || !n_qubits || !depths) return VQE_ERR_ARG;
+    if (precision != VQE_C64 && precision != VQE_C128) return VQE_ERR_ARG;
+    for (int i = 0; i < count; ++i)
+        if (n_qubits[i] < 1 || n_qubits[i] > 24 || depths[i] < 1 || depths[i] > 64) return VQE_ERR_ARG;
+    vqe_batch_ctx *b = new vqe_batch_ctx();
+    b->count = count;
+    b->prec = precision;
+    b->tile_bits = precision == VQE_C128 ? 12 : 13;
+    b->n.assign(n_qubits, n_qubits + count);
+    b->depth.assign(depths, depths + count);
+    b->poff.assign(count + 1, 0);
+    for (int i = 0; i < count; ++i) b->poff[i + 1] = b->poff[i] + size_t(2 * b->n[i] * b->depth[i]);
+    b->hx.resize(count);
+    b->hz.resize(count);
+    b->hc.resize(count);
+    b->ham_ok.assign(count, 0);
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return VQE_ERR_CUDA;
+    }
+    if (cuda_stream) {
+        b->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return VQE_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    vqe_status st = batch_build(b);
+    if (st != VQE_OK) {
+        vqe_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return VQE_OK;
+}
+
+vqe_status vqe_batch_destroy(vqe_batch b) {
+    if (!b) return VQE_ERR_ARG;
+    cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (DevBuf *d : {&b->d_inst, &b->d_order, &b->d_counter, &b->d_plans, &b->d_fwd, &b->d_bwd,
+                      &b->d_stage, &b->d_groups, &b->d_tz, &b->d_tc, &b->d_scratch, &b->hb_p,
+                      &b->hb_e, &b->hb_g})
+        d->release();
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return VQE_OK;
+}
+
+const char *vqe_batch_last_error(vqe_batch b) { return b ? b->err.c_str() : "NULL batch"; }
+
+vqe_status vqe_batch_param_offsets(vqe_batch b, size_t *offsets) {
+    if (!b || !offsets) return VQE_ERR_ARG;
+    std::memcpy(offsets, b->poff.data(), sizeof(size_t) * (b->count + 1));
+    return VQE_OK;
+}
+
+vqe_status vqe_batch_set_hamiltonian(vqe_batch b, int instance, const uint64_t *x_masks,
+                                     const uint64_t *z_masks, const double *coeffs,
+                                     size_t n_terms) {
+    if (!b) return VQE_ERR_ARG;
+    if (instance < 0 || instance >= b->count) return bfail(b, VQE_ERR_ARG, "instance out of range");
+    if (n_terms && (!x_masks || !z_masks || !coeffs)) return bfail(b, VQE_ERR_ARG, "NULL term array");
+    const uint64_t lim = (uint64_t(1) << b->n[instance]) - 1;
+    for (size_t t = 0; t < n_terms; ++t) {
+        if ((x_masks[t] & ~lim) || (z_masks[t] & ~lim))
+            return bfail(b, VQE_ERR_ARG, "Pauli mask has a bit at or above the instance's qubits");
+        if (!std::isfinite(coeffs[t])) return bfail(b, VQE_ERR_ARG, "non-finite coefficient");
+    }
+    b->hx[instance].assign(x_masks, x_masks + n_terms);
+    b->hz[instance].assign(z_masks, z_masks + n_terms);
+    b->hc[instance].assign(coeffs, coeffs + n_terms);
+    b->ham_ok[instance] = 1;
+    b->ham_dirty = true;
+    return VQE_OK;
+}
+
+vqe_status vqe_batch_run_dev(vqe_batch b, const double *params_dev, double *energies_dev,
+                             double *grads_dev) {
+    if (!b) return VQE_ERR_ARG;
+    if (!params_dev || !energies_dev || !grads_dev) return bfail(b, VQE_ERR_ARG, "NULL buffer");
+    vqe_status st;
+    if (b->plan_dirty && (st = batch_build(b)) != VQE_OK) return st;
+    if (b->ham_dirty) {
+        if ((st = batch_upload_hams(b)) != VQE_OK) return st;
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+    }
+    if (!b->gexec || b->g_params != params_dev || b->g_e != energies_dev || b->g_g != grads_dev) {
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        VQE_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        st = batch_launch(b, params_dev, energies_dev, grads_dev, b->stream);
+        cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+        if (st != VQE_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ec != cudaSuccess) return bfail(b, VQE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+        ec = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ec != cudaSuccess) {
+            b->gexec = nullptr;
+            return bfail(b, VQE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
+        }
+        b->g_params = params_dev;
+        b->g_e = energies_dev;
+        b->g_g = grads_dev;
+    }
+    VQE_BCUDA(b, cudaGraphLaunch(b->gexec, b->stream));
+    b->launches += 1;
+    if (b->own_stream) VQE_BCUDA(b, cudaStreamSynchronize(b->stream));
+    return VQE_OK;
+}
+
+vqe_status vqe_batch_run(vqe_batch b, const double *params, double *energies, double *grads) {
+    if (!b) return VQE_ERR_ARG;
+    if (!params || !energies || !grads) return bfail(b, VQE_ERR_ARG, "NULL buffer");
+    const size_t P = b->poff[b->count];
+    for (size_t i = 0; i < P; ++i)
+        if (!std::isfinite(params[i])) return bfail(b, VQE_ERR_ARG, "non-finite parameter");
+    DevBuf &dp = b->hb_p, &de = b->hb_e, &dg = b->hb_g;
+    vqe_status st = bensure(b, dp, P * sizeof(double), "params");
+    if (st == VQE_OK) st = bensure(b, de, b->count * sizeof(double), "energies");
+    if (st == VQE_OK) st = bensure(b, dg, P * sizeof(double), "grads");
+    if (st == VQE_OK && cudaMemcpyAsync(dp.p, params, P * sizeof(double), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        st = bfail(b, VQE_ERR_CUDA, "params upload failed");
+    if (st == VQE_OK) st = vqe_batch_run_dev(b, static_cast<double *>(dp.p), static_cast<double *>(de.p), static_cast<double *>(dg.p));
+    if (st == VQE_OK && cudaMemcpyAsync(energies, de.p, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+        st = bfail(b, VQE_ERR_CUDA, "energies download failed");
+    if (st == VQE_OK && cudaMemcpyAsync(grads, dg.p, P * sizeof(double), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+        st = bfail(b, VQE_ERR_CUDA, "grads download failed");
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess && st == VQE_OK)
+        st = bfail(b, VQE_ERR_CUDA, "stream synchronise failed");
+    return st;
+}
+
+vqe_status vqe_batch_autotune(vqe_batch b, const double *params_dev, double *energies_dev,
+                              double *grads_dev, int reps, int *tile_bits_out) {
+    if (!b) return VQE_ERR_ARG;
+    if (reps < 1) reps = 1;
+    std::vector<int> cands = b->prec == VQE_C128 ? std::vector<int>{12, 11, 10}
+                                                 : std::vector<int>{13, 12, 11};
+    float best = 0.f;
+    int best_k = b->tile_bits;
+    cudaEvent_t e0, e1;
+    VQE_BCUDA(b, cudaEventCreate(&e0));
+    VQE_BCUDA(b, cudaEventCreate(&e1));
+    for (int kb : cands) {
+        b->tile_bits = kb;
+        b->plan_dirty = true;
+        vqe_status st = vqe_batch_run_dev(b, params_dev, energies_dev, grads_dev);   // builds + warms up
+        if (st != VQE_OK) continue;
+        cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps && st == VQE_OK; ++r) st = vqe_batch_run_dev(b, params_dev, energies_dev, grads_dev);
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st == VQE_OK && (best == 0.f || ms < best)) {
+            best = ms;
+            best_k = kb;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tile_bits = best_k;
+    b->plan_dirty = true;
+    vqe_status st = vqe_batch_run_dev(b, params_dev, energies_dev, grads_dev);
+    if (tile_bits_out) *tile_bits_out = best_k;
+    return st;
+}
+
+vqe_status vqe_batch_set_tile_bits(vqe_batch b, int tile_bits) {
+    if (!b) return VQE_ERR_ARG;
+    const int kmax = b->prec == VQE_C128 ? 12 : 13;
+    if (tile_bits < 10 || tile_bits > kmax) return bfail(b, VQE_ERR_ARG, "tile_bits out of range");
+    b->tile_bits = tile_bits;
+    b->plan_dirty = true;
+    return VQE_OK;
+}
+
+vqe_status vqe_batch_launch_count(vqe_batch b, uint64_t *graph_launches) {
+    if (!b || !graph_launches) return VQE_ERR_ARG;
+    *graph_launches = b->launches;
+    return VQE_OK;
 }
 
 }  // extern "C"

@@ -57,22 +57,28 @@ def _check_layouts(lib):
                                f"binding {ctypes.sizeof(cls)}")
 
 
-def plan(n_qubits: int, depth: int, precision: str = "c64") -> dict:
-    """The tile-pass plan: forward/backward pass records, staging slots, gradient map."""
+def plan(n_qubits: int, depth: int, precision: str = "c64", options=(0, 0, 0)) -> dict:
+    """The tile-pass plan: forward/backward pass records, staging slots, gradient map.
+
+    ``options`` = (tile_bits_max, run_bits, reg_bits), 0 = default."""
     lib = load()
     _check_layouts(lib)
     prec = {"c64": 0, "c128": 1}[precision]
     strides = (ctypes.c_uint64 * 3)()
     counts = (ctypes.c_int * 3)()
-    rc = lib.vqe_inspect_plan(n_qubits, depth, prec, None, None, 0, None, 0, None, 0, strides, counts)
+    opts = (ctypes.c_int * 3)(*options)
+    rc = lib.vqe_inspect_plan(n_qubits, depth, prec, opts, None, None, 0, None, 0, None, 0,
+                              strides, counts)
+    if rc != 0 and counts[0] == 0:
+        raise ValueError("vqe_inspect_plan rejected the arguments")
     npass, nstage, nparams = counts[0], counts[1], counts[2]
     fwd = (PassDesc * npass)()
     bwd = (PassDesc * npass)()
     stage = (StageSlot * nstage)()
     gmap = np.zeros(3 * nparams, dtype=np.int32)
-    rc = lib.vqe_inspect_plan(n_qubits, depth, prec, ctypes.addressof(fwd), ctypes.addressof(bwd),
-                              npass, ctypes.addressof(stage), nstage, gmap.ctypes.data, nparams,
-                              strides, counts)
+    rc = lib.vqe_inspect_plan(n_qubits, depth, prec, opts, ctypes.addressof(fwd),
+                              ctypes.addressof(bwd), npass, ctypes.addressof(stage), nstage,
+                              gmap.ctypes.data, nparams, strides, counts)
     if rc != 0:
         raise ValueError("vqe_inspect_plan rejected the arguments")
     return {"fwd": list(fwd), "bwd": list(bwd), "stage": list(stage),

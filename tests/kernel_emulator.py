@@ -154,10 +154,9 @@ class Emu:
                         p0, p1, l0, l1 = v[..., r0], v[..., r1], w[..., r0], w[..., r1]
                         gs = self._cg[idx]
                         gt = gs * (np.real(np.conj(l1) * p0) - np.real(np.conj(l0) * p1)).sum(axis=(1, 2))
-                        gp = gs * (np.imag(np.conj(l0) * p0) - np.imag(np.conj(l1) * p1)).sum(axis=(1, 2))
                         key = (s, bit)
-                        assert key not in written, "gradient partial written twice"
-                        written[key] = (gt, gp)
+                        assert key not in written, "theta partial written twice"
+                        written[key] = gt
                     bufs = [v] + ([w] if backward else [])
                     for u in bufs:
                         x, y = u[..., r0].copy(), u[..., r1].copy()
@@ -175,6 +174,16 @@ class Emu:
                 s = op.slot
                 e = elem_of(t, r, chunk, R)
                 g = gaddr(e)
+                if backward:
+                    # phi partials for every gated bit, before the diagonal is undone
+                    u = np.imag(np.conj(w) * v)
+                    eb = np.broadcast_to(e, u.shape)
+                    for bit in range(k):
+                        if (d.slot_gated[s] >> bit) & 1:
+                            sg = np.where((eb >> bit) & 1, -1.0, 1.0)
+                            key = ("phi", s, bit)
+                            assert key not in written
+                            written[key] = (sg * u).sum(axis=(1, 2))
                 cz = d.slot_czmask[s]
                 sgn = popc(g & (g >> 1) & cz) & 1
                 off = d.slot_dtab_off[s]
@@ -193,7 +202,8 @@ class Emu:
                 for bit in range(k):
                     if not (d.slot_gated[s] >> bit) & 1:
                         continue
-                    gt, gp = written.pop((s, bit))
+                    gt = written.pop((s, bit))
+                    gp = written.pop(("phi", s, bit))
                     base_off = d.slot_grad_off[s] + np.arange(tiles) * (2 * k) + bit * 2
                     assert base_off.max() + 1 < len(gpart)
                     gpart[base_off] = gt

@@ -14,7 +14,9 @@ SMEM_MAX = 227 * 1024
 def pass_smem(d, backward, elem):
     threads = 1 << (d.k - d.R)
     warps = (threads + 31) // 32
-    return (1 << d.k) * elem * (2 if backward else 1) + (warps * d.k * 16 if backward else 0)
+    coef = 24 if elem == 16 else 12
+    return ((1 << d.k) * elem * (2 if backward else 1) + (warps * d.k * 16 if backward else 0)
+            + d.n_slots * d.k * coef + 2528)
 
 
 @pytest.mark.parametrize("prec", ["c64", "c128"])
@@ -133,3 +135,38 @@ def test_inspect_rejects_bad_input():
         P.hamiltonian(4, [1 << 4], [0], [1.0])
     with pytest.raises(ValueError):
         P.hamiltonian(4, [1], [0], [float("inf")])
+
+
+OPTION_CASES = [((10, 1, 3), "c128"), ((11, 2, 3), "c128"), ((12, 2, 4), "c128"), ((12, 3, 4), "c128"),
+                ((13, 2, 4), "c64"), ((12, 2, 4), "c64"), ((11, 4, 3), "c64"),
+                ((9, 1, 2), "c64")]
+
+
+@pytest.mark.parametrize("opts,prec", OPTION_CASES)
+@pytest.mark.parametrize("n", [7, 16, 21])
+def test_plan_options_emulated(oracle_mod, opts, prec, n):
+    """Alternative tile plans (as the autotuner may pick) stay exact."""
+    D = 2
+    pl = P.plan(n, D, prec, opts)
+    elem = 16 if prec == "c128" else 8
+    for d in pl["bwd"]:
+        assert (1 << (d.k - d.R)) <= 512 and pass_smem(d, True, elem) <= SMEM_MAX
+    if n > 16:
+        return
+    emu = Emu(n, D, prec)
+    emu.plan = pl
+    p = vi.ansatz_params(77 + n, n, D)
+    psi = emu.forward(p)
+    assert np.max(np.abs(psi - oracle_mod.ansatz_state(n, D, p))) < 1e-12
+    H = vi.random_pauli_sum(n, 10, seed=n)
+    ham = P.hamiltonian(n, H.x, H.z, H.c)
+    g, _ = emu.gradient(p, lambda s: apply_h_terms(ham, n, s))
+    g_ref, _ = oracle_mod.gradient_adjoint(n, D, p, H.x, H.z, H.c)
+    assert np.max(np.abs(g - g_ref)) < 1e-11 * max(1.0, np.max(np.abs(g_ref)))
+
+
+def test_plan_options_rejected():
+    with pytest.raises(ValueError):
+        P.plan(20, 2, "c128", (14, 3, 3))   # 2^11 threads
+    with pytest.raises(ValueError):
+        P.plan(20, 2, "c128", (12, 12, 3))  # run bits >= tile bits

@@ -347,6 +347,103 @@ def run_gpu(args, world, rank, local, pg):
         e.close()
 
 
+def _timed(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_workload(name: str, args):
+    """Secondary workloads (one JSON line each, same keys as the default line
+    where they apply): the other configurations of the evaluation set."""
+    import numpy as np
+    import torch
+    import paper_2402_11878_gb300 as pkg
+    import vqe_inputs as vi
+    dev = torch.device("cuda", 0)
+    line = {"metric": METRIC, "unit": "evals/s", "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic", "scaling": "weak", "vs_baseline": None}
+    if name == "molecular24":
+        # 24 qubits complex64: synthetic molecular-style Pauli sum, cutoff sweep
+        H = vi.synthetic_molecular(12, seed=2024)
+        n, D, B = 24, 12, 2
+        eng = pkg.Engine(n, D, "c64")
+        eng.set_hamiltonian(H.x, H.z, H.c)
+        P = torch.tensor(np.stack([vi.ansatz_params(9000 + j, n, D) for j in range(B)]), device=dev)
+        E = torch.empty(B, dtype=torch.float64, device=dev)
+        G = torch.empty(B, 2 * n * D, dtype=torch.float64, device=dev)
+        rows = []
+        for th in (0.0, 1e-6, 1e-4, 1e-3):
+            kept, dropped = eng.slim(th)
+            eng.profile(True)
+            ms_e = _timed(lambda: eng.energy_batch_dev(P, E), 2) / B
+            pe = eng.profile_read()
+            ms_g = _timed(lambda: eng.gradient_batch_dev(P, G, E), 1) / B
+            eng.profile(False)
+            rows.append({"threshold": th, "terms_kept": kept, "sum_abs_dropped": dropped,
+                         "groups": eng.stats()["n_groups"], "energy_ms": ms_e,
+                         "energy_kernel_ms": pe["energy"]["ms"] / 3 / B,
+                         "forward_ms": pe["forward_passes"]["ms"] / 3 / B,
+                         "energy_gradient_ms": ms_g})
+        line.update({"value": 1e3 / rows[0]["energy_gradient_ms"], "dtype": "c64",
+                     "config": {"workload": "24q complex64 synthetic molecular (12 spatial orbitals, "
+                                "JW), HEA depth 12, energy + adjoint gradient, cutoff sweep",
+                                "terms": len(H), "groups": H.n_groups},
+                     "cutoff_sweep": rows})
+    elif name == "batch512":
+        inst = vi.batched_instances(512, seed=7)
+        b = pkg.Batch([d["n"] for d in inst], [d["depth"] for d in inst], "c64",
+                      stream=torch.cuda.current_stream())
+        for i, d in enumerate(inst):
+            b.set_hamiltonian(i, d["H"].x, d["H"].z, d["H"].c)
+        P = torch.tensor(np.concatenate([d["params"] for d in inst]), device=dev)
+        E = torch.empty(len(inst), dtype=torch.float64, device=dev)
+        G = torch.empty_like(P)
+        kb = b.autotune(P, E, G, reps=2)
+        ms = _timed(lambda: b.run_dev(P, E, G), max(3, args.steps))
+        # plain baseline: one-by-one FP64 handles on the first 32 instances
+        engs = []
+        for d in inst[:32]:
+            e = pkg.Engine(d["n"], d["depth"], "c128")
+            e.set_hamiltonian(d["H"].x, d["H"].z, d["H"].c)
+            engs.append(e)
+        for e, d in zip(engs, inst[:32]):
+            e.gradient(d["params"])
+        t0 = time.perf_counter()
+        for e, d in zip(engs, inst[:32]):
+            e.gradient(d["params"])
+        per_inst = (time.perf_counter() - t0) / 32
+        line.update({"value": len(inst) / (ms / 1e3), "unit": "instance energy+gradient evals/s",
+                     "ms_per_step": ms, "dtype": "c64",
+                     "config": {"workload": "512 instances, 12-18 qubits (uniform), open Hubbard "
+                                "sites n/2, U~U[1,8], depth n/2, complex64 energy + adjoint gradient, "
+                                "one persistent launch under a CUDA graph",
+                                "autotuned_tile_bits": kb},
+                     "fp64_one_by_one_baseline": {"value": 1.0 / per_inst,
+                                                   "unit": "instance evals/s",
+                                                   "sample": "first 32 instances, warm handles"}})
+    elif name == "small8":
+        H = vi.hubbard_1d(4, 1.0, 4.0, periodic=False)
+        n, D, B = 8, 4, 1024
+        eng = pkg.Engine(n, D, "c128")
+        eng.set_hamiltonian(H.x, H.z, H.c)
+        P = torch.tensor(np.stack([vi.ansatz_params(j, n, D) for j in range(B)]), device=dev)
+        E = torch.empty(B, dtype=torch.float64, device=dev)
+        G = torch.empty(B, 2 * n * D, dtype=torch.float64, device=dev)
+        ms = _timed(lambda: eng.gradient_batch_dev(P, G, E), 5)
+        line.update({"value": B / (ms / 1e3), "dtype": "f64", "ms_per_step": ms,
+                     "config": {"workload": "8q FP64 4-site open Hubbard, depth 4, energy + "
+                                "adjoint gradient, 1024 parameter vectors per step"}})
+    print(json.dumps(line), flush=True)
+
+
 def run_case(name: str, batch: int):
     """Small named workloads for profiler captures (no JSON line): each runs
     its evaluation twice on cuda:0 and prints the first energies."""
@@ -394,6 +491,10 @@ def main():
     ap.add_argument("--case", default=None,
                     help="run a small named workload for profiler captures instead of the benchmark")
     ap.add_argument("--case-batch", type=int, default=16)
+    ap.add_argument("--workload", default="hubbard20",
+                    choices=["hubbard20", "molecular24", "batch512", "small8"],
+                    help="hubbard20 (default) is the benchmark line; the others report the "
+                         "remaining configurations")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -405,6 +506,9 @@ def main():
     args = ap.parse_args()
     if args.case:
         run_case(args.case, args.case_batch)
+        return
+    if args.workload != "hubbard20" and args.impl != "reference":
+        run_workload(args.workload, args)
         return
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

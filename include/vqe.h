@@ -64,7 +64,7 @@ typedef enum {
     VQE_ERR_STATE = 2,    /* call out of order (e.g. energy before any ansatz) */
     VQE_ERR_OOM = 3,      /* device memory could not be allocated */
     VQE_ERR_CUDA = 4,     /* a CUDA runtime call or kernel launch failed */
-    VQE_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+    VQE_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up (reported at the next synchronising call) */
     VQE_ERR_DEVICE = 6    /* a kernel reported an internal error through its error word */
 } vqe_status;
 
@@ -103,12 +103,21 @@ vqe_status vqe_bind_workspace(vqe_handle h, void *dev_ptr, size_t bytes);
  * log2 of the largest tile a pass stages in shared memory (1..14; default
  * 12 for C128, 13 for C64), run_bits = log2 of the contiguous run of
  * amplitudes kept in the tiles of high-qubit passes (default 3 / 4, i.e. 128
- * bytes), reg_bits = log2 of the amplitudes each thread holds (1..4;
- * default 3 / 4).  Rejected (VQE_ERR_ARG) if a pass would need more than 512
- * threads or 227 KiB of shared memory.  Rebuilds the plan; the state of
+ * bytes), reg_bits = log2 of the amplitudes each thread holds (1..5;
+ * default 3 for C128; for C64 5 in energy evaluations and 4 in gradients).
+ * reg_bits 5 applies to energy evaluations only; gradients use at most 4.
+ * Rejected (VQE_ERR_ARG) if a pass would need more than 512 threads or
+ * 227 KiB of shared memory.  Rebuilds the plans; the state of
  * vqe_apply_ansatz is discarded.  Results do not depend on the plan beyond
  * floating-point rounding order. */
 vqe_status vqe_set_plan_options(vqe_handle h, int tile_bits_max, int run_bits, int reg_bits);
+
+/* Kernel used for the ansatz passes: 0 (default) = one CTA per tile, first
+ * and last register round straight from/to global memory; 1 = persistent
+ * CTAs that pipeline tiles through shared memory with bulk copies (a pass
+ * whose double-buffered tiles exceed shared memory, or that uses 32
+ * amplitudes per thread, still runs with kind 0).  Results are identical. */
+vqe_status vqe_set_pass_kernel(vqe_handle h, int kind);
 
 /* Set the Hamiltonian H = sum_t coeffs[t] * P(x_masks[t], z_masks[t])
  * (Sec. II-B, Eqs. 2-4).  Host arrays of length n_terms; masks must have no

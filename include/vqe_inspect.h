@@ -18,7 +18,7 @@ extern "C" {
 #endif
 
 /* sizeof of internal record `which`: 0 = pass descriptor, 1 = staging slot,
- * 2 = term group; 0 for an unknown `which`. */
+ * 2 = term group, 3 = energy window; 0 for an unknown `which`. */
 size_t vqe_inspect_sizeof(int which);
 
 /* Tile-pass plan of the ansatz for (n, depth, precision, options) -- options
@@ -44,6 +44,16 @@ int vqe_inspect_hamiltonian(int n_qubits, const uint64_t *x_masks, const uint64_
                             const double *coeffs, size_t n_terms, double threshold, void *groups,
                             int max_groups, uint32_t *tz, double *tc, int max_terms, int counts[2],
                             double *sum_abs_dropped, uint64_t *n_canonical);
+
+/* Windows of the windowed expectation kernel for the same prepared terms:
+ * window records (max_windows), the group indices of each window (into the
+ * groups of vqe_inspect_hamiltonian; max_wgroups), and the groups swept over
+ * the whole state instead (max_wide).  counts[3] = windows, window groups,
+ * wide groups.  Returns 0, or -1 on invalid input or too-small buffers. */
+int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
+                        const uint64_t *z_masks, const double *coeffs, size_t n_terms,
+                        double threshold, void *windows, int max_windows, int *wgroups,
+                        int max_wgroups, void *wide, int max_wide, int counts[3]);
 
 #ifdef __cplusplus
 }

@@ -22,11 +22,12 @@ STATUS = {0: "VQE_OK", 1: "VQE_ERR_ARG", 2: "VQE_ERR_STATE", 3: "VQE_ERR_OOM",
 # C ABI entry points declared in include/vqe.h and include/vqe_inspect.h
 EXPORTED = [
     "vqe_create", "vqe_destroy", "vqe_workspace_size", "vqe_bind_workspace", "vqe_set_plan_options",
+    "vqe_set_pass_kernel",
     "vqe_set_hamiltonian", "vqe_slim", "vqe_apply_ansatz", "vqe_energy", "vqe_get_state",
     "vqe_gradient", "vqe_energy_batch_dev", "vqe_gradient_batch_dev", "vqe_energy_batch",
     "vqe_gradient_batch", "vqe_energy_batch_pergate_dev", "vqe_get_stats", "vqe_last_error",
     "vqe_version", "vqe_profile", "vqe_profile_read", "vqe_inspect_sizeof", "vqe_inspect_plan",
-    "vqe_inspect_hamiltonian", "vqe_energy_noalloc", "vqe_batch_create", "vqe_batch_destroy",
+    "vqe_inspect_hamiltonian", "vqe_inspect_windows", "vqe_energy_noalloc", "vqe_batch_create", "vqe_batch_destroy",
     "vqe_batch_set_hamiltonian", "vqe_batch_param_offsets", "vqe_batch_run_dev", "vqe_batch_run",
     "vqe_batch_set_tile_bits", "vqe_batch_autotune", "vqe_batch_launch_count",
     "vqe_batch_last_error",
@@ -105,8 +106,10 @@ def load() -> ctypes.CDLL:
         "vqe_batch_last_error": [vp],
         "vqe_inspect_plan": [i, i, i, vp, vp, vp, i, vp, i, vp, i, vp, vp],
         "vqe_set_plan_options": [vp, i, i, i],
+        "vqe_set_pass_kernel": [vp, i],
         "vqe_inspect_hamiltonian": [i, vp, vp, vp, sz, ctypes.c_double, vp, i, vp, vp, i, vp,
                                     vp, vp],
+        "vqe_inspect_windows": [i, i, vp, vp, vp, sz, ctypes.c_double, vp, i, vp, i, vp, i, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -258,6 +261,10 @@ class Engine:
     def set_plan_options(self, tile_bits_max: int = 0, run_bits: int = 0, reg_bits: int = 0):
         """Choose the tile plan (0 = default); see vqe_set_plan_options."""
         self._check(self._lib.vqe_set_plan_options(self._h, tile_bits_max, run_bits, reg_bits))
+
+    def set_pass_kernel(self, kind: int):
+        """0: one CTA per tile (default), 1: pipelined persistent pass kernel."""
+        self._check(self._lib.vqe_set_pass_kernel(self._h, kind))
 
     def workspace_size(self, batch: int, gradient: bool = False) -> int:
         out = ctypes.c_size_t()

@@ -20,6 +20,9 @@ namespace {
 template <typename T>
 struct BatchEnv {
     using C = typename V2<T>::type;
+    static constexpr bool kDirect = false;   // the tile is in shared memory
+    __device__ void load(uint32_t, C &, C &) const {}
+    __device__ void store(uint32_t, const C &, const C &) const {}
     const PassDesc *d;
     const RotCoef<T> *coef_s;   // shared: all slots of the instance (plan's coef offsets)
     const C *lo_s;              // shared: per plan slot, 2^kl low half-table entries

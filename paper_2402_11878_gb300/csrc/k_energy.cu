@@ -39,6 +39,20 @@ __device__ __forceinline__ T sign_sum(uint32_t i, const uint32_t *__restrict__ t
     return f;
 }
 
+// f[j] += sum over terms [t0, t1) of c_t (-1)^{popc(i[j] & z_t)}, one load of
+// each term for all J indices.
+template <typename T, int J>
+__device__ __forceinline__ void sign_sums(const uint32_t (&i)[J], T (&f)[J],
+                                          const uint32_t *__restrict__ tz,
+                                          const T *__restrict__ tc, int t0, int t1) {
+    for (int t = t0; t < t1; ++t) {
+        const uint32_t z = __ldg(tz + t);
+        const T c = __ldg(tc + t);
+#pragma unroll
+        for (int j = 0; j < J; ++j) f[j] += sgn_flip(c, __popc(i[j] & z) & 1u);
+    }
+}
+
 __device__ __forceinline__ void block_reduce2(double &a, double &b, double *sh) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -65,10 +79,11 @@ __device__ __forceinline__ void block_reduce2(double &a, double &b, double *sh) 
 
 template <typename T>
 __global__ void __launch_bounds__(kEnergyThreads)
-k_energy(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__restrict__ tz,
-         const T *__restrict__ tc, int n, const typename EV2<T>::type *__restrict__ psi,
-         size_t stride, double *__restrict__ partials) {
+k_energy_cols(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__restrict__ tz,
+              const T *__restrict__ tc, int n, const typename EV2<T>::type *__restrict__ psi,
+              size_t stride, double *__restrict__ partials, int block_off, int bps_total) {
     using C = typename EV2<T>::type;
+    constexpr int J = 4;   // pairs per thread and iteration: one load of each term serves J pairs
     __shared__ double sh[2 * (kEnergyThreads / 32)];
     const int b = blockIdx.y;
     const C *P = psi + (size_t)b * stride;
@@ -79,39 +94,66 @@ k_energy(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__r
     for (int g = 0; g < n_groups; ++g) {
         const GroupDesc G = groups[g];
         T part = T(0), pn = T(0);
-        if (G.x == 0u) {
-            for (uint64_t p = tid; p < npairs; p += nthr) {
-                const uint32_t i0 = (uint32_t)(2 * p), i1 = i0 | 1u;
-                const C x0 = P[i0], x1 = P[i1];
-                const T a0 = fma(x0.x, x0.x, x0.y * x0.y);
-                const T a1 = fma(x1.x, x1.x, x1.y * x1.y);
-                const T f0 = sign_sum<T>(i0, tz, tc, G.t_begin, G.t_mid);
-                const T f1 = sign_sum<T>(i1, tz, tc, G.t_begin, G.t_mid);
-                part = fma(a0, f0, fma(a1, f1, part));
-                pn += a0 + a1;
+        const int h = G.x ? G.h : 0;
+        const uint64_t lowm = (1ull << h) - 1ull;
+        const bool has_b = G.t_end > G.t_mid;
+        for (uint64_t p0 = tid; p0 < npairs; p0 += nthr * J) {
+            uint32_t i0[J], i1[J];
+            bool ok[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const uint64_t p = p0 + (uint64_t)j * nthr;
+                ok[j] = p < npairs;
+                const uint64_t pp = ok[j] ? p : p0;
+                if (G.x == 0u) {
+                    i0[j] = (uint32_t)(2 * pp);
+                    i1[j] = i0[j] | 1u;
+                } else {
+                    i0[j] = (uint32_t)(((pp >> h) << (h + 1)) | (pp & lowm));
+                    i1[j] = i0[j] ^ G.x;
+                }
             }
-            nrm += (double)pn;
-        } else {
-            const int h = G.h;
-            const uint64_t lowm = (1ull << h) - 1ull;
-            for (uint64_t p = tid; p < npairs; p += nthr) {
-                const uint32_t i0 = (uint32_t)(((p >> h) << (h + 1)) | (p & lowm));
-                const uint32_t i1 = i0 ^ G.x;
-                const C x0 = P[i0], x1 = P[i1];
-                // conj(x0) * x1 = ar + i ai
-                const T ar = fma(x0.x, x1.x, x0.y * x1.y);
-                const T ai = fma(x0.x, x1.y, -x0.y * x1.x);
-                const T fa = sign_sum<T>(i0, tz, tc, G.t_begin, G.t_mid);
-                const T fb = sign_sum<T>(i0, tz, tc, G.t_mid, G.t_end);
-                part = fma(ar, fa, fma(ai, fb, part));
+            if (G.x == 0u) {
+                T a0[J], a1[J], f0[J], f1[J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const C x0 = P[i0[j]], x1 = P[i1[j]];
+                    a0[j] = ok[j] ? fma(x0.x, x0.x, x0.y * x0.y) : T(0);
+                    a1[j] = ok[j] ? fma(x1.x, x1.x, x1.y * x1.y) : T(0);
+                    f0[j] = T(0);
+                    f1[j] = T(0);
+                }
+                sign_sums<T, J>(i0, f0, tz, tc, G.t_begin, G.t_mid);
+                sign_sums<T, J>(i1, f1, tz, tc, G.t_begin, G.t_mid);
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    part = fma(a0[j], f0[j], fma(a1[j], f1[j], part));
+                    pn += a0[j] + a1[j];
+                }
+            } else {
+                T ar[J], ai[J], fa[J], fb[J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const C x0 = P[i0[j]], x1 = P[i1[j]];
+                    // conj(x0) * x1 = ar + i ai; the imaginary part only matters for B terms
+                    ar[j] = ok[j] ? fma(x0.x, x1.x, x0.y * x1.y) : T(0);
+                    ai[j] = ok[j] ? fma(x0.x, x1.y, -x0.y * x1.x) : T(0);
+                    fa[j] = T(0);
+                    fb[j] = T(0);
+                }
+                sign_sums<T, J>(i0, fa, tz, tc, G.t_begin, G.t_mid);
+                if (has_b) sign_sums<T, J>(i0, fb, tz, tc, G.t_mid, G.t_end);
+#pragma unroll
+                for (int j = 0; j < J; ++j) part = fma(ar[j], fa[j], has_b ? fma(ai[j], fb[j], part) : part);
             }
-            part *= T(2);
         }
+        if (G.x == 0u) nrm += (double)pn;
+        else part *= T(2);
         acc += (double)part;
     }
     block_reduce2(acc, nrm, sh);
     if (threadIdx.x == 0) {
-        double *o = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
+        double *o = partials + ((size_t)b * bps_total + block_off + blockIdx.x) * 3;
         o[0] = acc;
         o[1] = nrm;
         o[2] = 0.0;
@@ -125,6 +167,7 @@ k_apply_h(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__
           const T *__restrict__ tc, int n, const typename EV2<T>::type *__restrict__ psi,
           typename EV2<T>::type *__restrict__ lam, size_t stride, double *__restrict__ partials) {
     using C = typename EV2<T>::type;
+    constexpr int J = 4;
     __shared__ double sh[2 * (kEnergyThreads / 32)];
     const int b = blockIdx.y;
     const C *P = psi + (size_t)b * stride;
@@ -133,25 +176,48 @@ k_apply_h(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
     double acc = 0.0, nrm = 0.0;
-    for (uint64_t ii = tid; ii < dim; ii += nthr) {
-        const uint32_t i = (uint32_t)ii;
-        T lr = T(0), li = T(0);
+    for (uint64_t i00 = tid; i00 < dim; i00 += nthr * J) {
+        uint32_t i[J];
+        bool ok[J];
+        T lr[J], li[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const uint64_t ii = i00 + (uint64_t)j * nthr;
+            ok[j] = ii < dim;
+            i[j] = (uint32_t)(ok[j] ? ii : i00);
+            lr[j] = T(0);
+            li[j] = T(0);
+        }
         for (int g = 0; g < n_groups; ++g) {
             const GroupDesc G = groups[g];
-            const C pj = P[i ^ G.x];
-            const T fa = sign_sum<T>(i, tz, tc, G.t_begin, G.t_mid);
-            const T fb = sign_sum<T>(i, tz, tc, G.t_mid, G.t_end);
-            // (pr + i pi)(fa - i fb)
-            lr = fma(pj.x, fa, fma(pj.y, fb, lr));
-            li = fma(pj.y, fa, fma(-pj.x, fb, li));
+            T fa[J], fb[J];
+            C pj[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                pj[j] = P[i[j] ^ G.x];
+                fa[j] = T(0);
+                fb[j] = T(0);
+            }
+            sign_sums<T, J>(i, fa, tz, tc, G.t_begin, G.t_mid);
+            if (G.t_end > G.t_mid) sign_sums<T, J>(i, fb, tz, tc, G.t_mid, G.t_end);
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                // (pr + i pi)(fa - i fb)
+                lr[j] = fma(pj[j].x, fa[j], fma(pj[j].y, fb[j], lr[j]));
+                li[j] = fma(pj[j].y, fa[j], fma(-pj[j].x, fb[j], li[j]));
+            }
         }
-        C out;
-        out.x = lr;
-        out.y = li;
-        L[i] = out;
-        const C x = P[i];
-        acc += (double)fma(x.x, lr, x.y * li);
-        nrm += (double)fma(x.x, x.x, x.y * x.y);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            if (!ok[j]) continue;
+            C out;
+            out.x = lr[j];
+            out.y = li[j];
+            L[i[j]] = out;
+            const C x = P[i[j]];
+            acc += (double)fma(x.x, lr[j], x.y * li[j]);
+            nrm += (double)fma(x.x, x.x, x.y * x.y);
+        }
     }
     block_reduce2(acc, nrm, sh);
     if (threadIdx.x == 0) {
@@ -206,10 +272,10 @@ cudaError_t launch_energy(const GroupDesc *groups, int n_groups, const uint32_t 
                           size_t state_stride, double *partials, int bps, cudaStream_t s) {
     using C = typename EV2<T>::type;
     dim3 grid(bps, batch);
-    k_energy<T><<<grid, kEnergyThreads, 0, s>>>(groups, n_groups, tz,
-                                                reinterpret_cast<const T *>(tc), n_qubits,
-                                                static_cast<const C *>(psi), state_stride,
-                                                partials);
+    k_energy_cols<T><<<grid, kEnergyThreads, 0, s>>>(groups, n_groups, tz,
+                                                     reinterpret_cast<const T *>(tc), n_qubits,
+                                                     static_cast<const C *>(psi), state_stride,
+                                                     partials, 0, bps);
     return cudaGetLastError();
 }
 
@@ -254,5 +320,155 @@ template cudaError_t launch_apply_h<float>(const GroupDesc *, int, const uint32_
 template cudaError_t launch_apply_h<double>(const GroupDesc *, int, const uint32_t *,
                                             const double *, int, int, const void *, void *,
                                             size_t, double *, int, cudaStream_t);
+
+}  // namespace vqe
+
+// ---------------------------------------------------------------- windowed expectation
+//
+// Groups whose X mask fits one tile "window" (tile bits [0, m) plus the
+// window [a, a + k - m)) are evaluated from a tile staged in shared memory:
+// the state is read once per window instead of once per group.  Window 0 is
+// the low contiguous tile and also yields <psi|psi>.
+
+namespace vqe {
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kEnergyWinThreads)
+k_energy_win(WinDesc W, const GroupDesc *__restrict__ groups, const int *__restrict__ wgroups,
+             const uint32_t *__restrict__ tz, const T *__restrict__ tc, int n,
+             const typename EV2<T>::type *__restrict__ psi, size_t stride,
+             double *__restrict__ partials, int bps_total) {
+    using C = typename EV2<T>::type;
+    constexpr uint32_t size = 1u << K;
+    constexpr int EPT = size / kEnergyWinThreads;   // tile elements per thread
+    constexpr int PPT = EPT / 2;                    // pairs per thread and group
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *sp = reinterpret_cast<C *>(smem_raw);
+    __shared__ double sh[2 * (kEnergyWinThreads / 32)];
+    const int m = W.m, a = W.a, mid = a - m;
+    const uint64_t tile = blockIdx.x;
+    const int b = blockIdx.y;
+    const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (K - m)));
+    const uint32_t lowmask = (1u << m) - 1u;
+    const C *P = psi + (size_t)b * stride;
+    auto g32 = [&](uint32_t e) -> uint32_t {
+        return (uint32_t)(base | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a));
+    };
+    for (uint32_t e = threadIdx.x; e < size; e += blockDim.x) sp[e] = P[g32(e)];
+    __syncthreads();
+    double acc = 0.0, nrm = 0.0;
+    if (W.with_norm) {
+        T pn = T(0);
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) {
+            const C x = sp[threadIdx.x + j * kEnergyWinThreads];
+            pn += fma(x.x, x.x, x.y * x.y);
+        }
+        nrm = (double)pn;
+    }
+    for (int gi = W.g_begin; gi < W.g_end; ++gi) {
+        const GroupDesc G = groups[wgroups[gi]];
+        T part = T(0);
+        if (G.x == 0u) {
+            uint32_t ge[EPT];
+            T f[EPT];
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                ge[j] = g32(threadIdx.x + j * kEnergyWinThreads);
+                f[j] = T(0);
+            }
+            sign_sums<T, EPT>(ge, f, tz, tc, G.t_begin, G.t_mid);
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                const C x = sp[threadIdx.x + j * kEnergyWinThreads];
+                part = fma(fma(x.x, x.x, x.y * x.y), f[j], part);
+            }
+        } else {
+            // X mask in tile coordinates
+            const uint32_t xl = (G.x & lowmask) | ((G.x >> a) << m);
+            const int hl = 31 - __clz(xl);
+            const uint32_t lm = (1u << hl) - 1u;
+            uint32_t il[PPT], gi0[PPT];
+            T fa[PPT], fb[PPT];
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const uint32_t p = threadIdx.x + j * kEnergyWinThreads;
+                il[j] = ((p >> hl) << (hl + 1)) | (p & lm);
+                gi0[j] = g32(il[j]);
+                fa[j] = T(0);
+                fb[j] = T(0);
+            }
+            sign_sums<T, PPT>(gi0, fa, tz, tc, G.t_begin, G.t_mid);
+            const bool has_b = G.t_end > G.t_mid;
+            if (has_b) sign_sums<T, PPT>(gi0, fb, tz, tc, G.t_mid, G.t_end);
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const C x0 = sp[il[j]], x1 = sp[il[j] ^ xl];
+                const T ar = fma(x0.x, x1.x, x0.y * x1.y);
+                part = fma(ar, fa[j], part);
+                if (has_b) part = fma(fma(x0.x, x1.y, -x0.y * x1.x), fb[j], part);
+            }
+            part *= T(2);
+        }
+        acc += (double)part;
+    }
+    block_reduce2(acc, nrm, sh);
+    if (threadIdx.x == 0) {
+        double *o = partials + ((size_t)b * bps_total + W.block_off + blockIdx.x) * 3;
+        o[0] = acc;
+        o[1] = nrm;
+        o[2] = 0.0;
+    }
+}
+
+template <typename T>
+cudaError_t launch_energy_win(const WinDesc &W, const GroupDesc *groups, const int *wgroups,
+                              const uint32_t *tz, const double *tc, int n_qubits, int batch,
+                              const void *psi, size_t state_stride, double *partials,
+                              int bps_total, cudaStream_t s) {
+    using C = typename EV2<T>::type;
+    const size_t smem = (size_t(1) << W.k) * sizeof(C);
+    auto kern = W.k == 13 ? k_energy_win<T, 13> : (W.k == 12 ? k_energy_win<T, 12> : nullptr);
+    if (!kern) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)(1ull << (n_qubits - W.k)), batch);
+    kern<<<grid, kEnergyWinThreads, smem, s>>>(W, groups, wgroups, tz,
+                                               reinterpret_cast<const T *>(tc), n_qubits,
+                                               static_cast<const C *>(psi), state_stride, partials,
+                                               bps_total);
+    return cudaGetLastError();
+}
+
+// Global-sweep expectation for a subset of groups, writing its block partials
+// at column `block_off` of a layout with `bps_total` columns per state.
+template <typename T>
+cudaError_t launch_energy_sub(const GroupDesc *groups, int n_groups, const uint32_t *tz,
+                              const double *tc, int n_qubits, int batch, const void *psi,
+                              size_t state_stride, double *partials, int bps, int block_off,
+                              int bps_total, cudaStream_t s) {
+    using C = typename EV2<T>::type;
+    dim3 grid(bps, batch);
+    k_energy_cols<T><<<grid, kEnergyThreads, 0, s>>>(groups, n_groups, tz,
+                                                     reinterpret_cast<const T *>(tc), n_qubits,
+                                                     static_cast<const C *>(psi), state_stride,
+                                                     partials, block_off, bps_total);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_energy_win<float>(const WinDesc &, const GroupDesc *, const int *,
+                                              const uint32_t *, const double *, int, int,
+                                              const void *, size_t, double *, int, cudaStream_t);
+template cudaError_t launch_energy_win<double>(const WinDesc &, const GroupDesc *, const int *,
+                                               const uint32_t *, const double *, int, int,
+                                               const void *, size_t, double *, int, cudaStream_t);
+template cudaError_t launch_energy_sub<float>(const GroupDesc *, int, const uint32_t *,
+                                              const double *, int, int, const void *, size_t,
+                                              double *, int, int, int, cudaStream_t);
+template cudaError_t launch_energy_sub<double>(const GroupDesc *, int, const uint32_t *,
+                                               const double *, int, int, const void *, size_t,
+                                               double *, int, int, int, cudaStream_t);
 
 }  // namespace vqe

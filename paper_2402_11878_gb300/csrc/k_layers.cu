@@ -107,11 +107,35 @@ constexpr int kPassMaxThreads = 512;
 template <typename T>
 struct GridEnv {
     using C = typename V2<T>::type;
+    static constexpr bool kDirect = true;   // first/last round straight from/to global memory
     const PassDesc *d;          // shared-memory copy of the pass descriptor
     const RotCoef<T> *cf;       // shared-memory copy: coefficient rows of the pass's slots
     const C *dt;
     double *gout;   // this state's gradient partials
     uint64_t tile;
+    C *P, *L;
+    uint64_t base;
+    uint32_t lowmask;
+    int m, a;
+    int init_zero;
+    __device__ uint64_t g(uint32_t e) const {
+        return base | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a);
+    }
+    __device__ void load(uint32_t e, C &v, C &w) const {
+        const uint64_t gi = g(e);
+        if (init_zero) {
+            v.x = (gi == 0) ? T(1) : T(0);
+            v.y = T(0);
+        } else {
+            v = P[gi];
+        }
+        if (L) w = L[gi];
+    }
+    __device__ void store(uint32_t e, const C &v, const C &w) const {
+        const uint64_t gi = g(e);
+        P[gi] = v;
+        if (L) L[gi] = w;
+    }
     __device__ RotCoef<T> coef(int slot, int bit) const { return cf[slot * d->k + bit]; }
     __device__ C diag(int slot, uint32_t e) const { return dt[d->slot_dtab_off[slot] + e]; }
     __device__ void grad(int slot, int bit, int comp, double v) const {
@@ -138,8 +162,10 @@ __device__ __forceinline__ void stage_pass(const PassDesc *__restrict__ desc,
 
 // One CTA per (tile, state): global -> shared (plain order), the pass
 // program, shared -> global.
+// Forward passes hold one buffer per thread: two blocks of 512 threads fit an
+// SM (<= 64 registers); backward passes hold two.
 template <typename T, int R, bool BWD>
-__global__ void __launch_bounds__(kPassMaxThreads)
+__global__ void __launch_bounds__(kPassMaxThreads, (BWD || R > 4) ? 1 : 2)
 k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *__restrict__ psi,
        typename V2<T>::type *__restrict__ lam, size_t stride, const RotCoef<T> *__restrict__ coefs,
        size_t coef_stride, const typename V2<T>::type *__restrict__ dtab, size_t dtab_stride,
@@ -166,27 +192,10 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
     const uint32_t lowmask = (1u << m) - 1u;
     C *P = psi + (size_t)b * stride;
     C *L = BWD ? lam + (size_t)b * stride : nullptr;
-    for (uint32_t e = threadIdx.x; e < size; e += blockDim.x) {
-        const uint64_t g = base | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a);
-        if (init_zero) {
-            C z;
-            z.x = (g == 0) ? T(1) : T(0);
-            z.y = T(0);
-            sp[e] = z;
-        } else {
-            sp[e] = P[g];
-        }
-        if (BWD) sl[e] = L[g];
-    }
-    __syncthreads();
     GridEnv<T> env{&sd, scf, dtab + (size_t)b * dtab_stride,
-                   BWD ? gpart + (size_t)b * grad_stride : nullptr, tile};
+                   BWD ? gpart + (size_t)b * grad_stride : nullptr, tile, P, L, base, lowmask,
+                   m, a, init_zero};
     run_tile<T, R, BWD>(d, d.ops, d.n_ops, base, sp, sl, gsh, env);
-    for (uint32_t e = threadIdx.x; e < size; e += blockDim.x) {
-        const uint64_t g = base | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a);
-        P[g] = sp[e];
-        if (BWD) L[g] = sl[e];
-    }
 }
 
 int pass_threads(const PassDesc &d) { return 1 << (d.k - d.R); }
@@ -241,6 +250,11 @@ cudaError_t launch_pass(const PassDesc *desc_dev, const PassDesc &dh, int n_qubi
         VQE_PASS_CASE(2)
         VQE_PASS_CASE(3)
         VQE_PASS_CASE(4)
+        case 5:   // forward only (the backward buffers would not fit in registers)
+            if (backward) return cudaErrorInvalidValue;
+            return launch_pass_r<T, 5, false>(desc_dev, dh, n_qubits, batch, psi, nullptr, stride,
+                                             coefs, coef_stride, dtab, dtab_stride, gpart,
+                                             grad_stride, init_zero, s);
         default:
             return cudaErrorInvalidValue;
     }

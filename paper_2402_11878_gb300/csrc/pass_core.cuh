@@ -16,6 +16,10 @@
 //   C diag(int slot, uint32_t e)               diagonal table entry of tile element e
 //   void grad(int slot, int tile_bit, int comp, double v)   (backward) block total of
 //        a gradient partial: comp 0 = theta (RY), 1 = phi (RZ); called by thread 0
+//   static constexpr bool kDirect                 true: the first round loads and the
+//        last round stores tile elements through load/store below instead of
+//        reading/writing `buf`/`lbuf` in plain order
+//   void load(uint32_t e, C &v, C &w) / void store(uint32_t e, const C &v, const C &w)
 #pragma once
 
 #include "vqe_internal.h"
@@ -25,6 +29,8 @@ namespace vqe {
 template <typename T> struct V2;
 template <> struct V2<float> { using type = float2; };
 template <> struct V2<double> { using type = double2; };
+
+template <int P> struct ChunkC { static constexpr int value = P; };
 
 __device__ __forceinline__ uint32_t elem_of(uint32_t t, uint32_t r, int p, int R) {
     const uint32_t lo = t & ((1u << p) - 1u);
@@ -41,6 +47,36 @@ template <> __device__ __forceinline__ uint32_t swz<double>(uint32_t e) {
 template <> __device__ __forceinline__ uint32_t swz<float>(uint32_t e) {
     const uint32_t f = (e >> 4) ^ (e >> 8) ^ (e >> 12);
     return e ^ (f & 15u);
+}
+
+// The swizzle is XOR-linear: swz(a ^ b) = swz(a) ^ swz(b).  Element indices
+// of a round are (thread part) | (r << chunk) with disjoint bits, so the
+// slot of register r is swz(thread part) ^ swz(r << chunk), and the second
+// term is a compile-time constant once the chunk is.
+template <typename T> __host__ __device__ constexpr uint32_t swz_c(uint32_t e);
+template <> __host__ __device__ constexpr uint32_t swz_c<double>(uint32_t e) {
+    return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12)) & 7u);
+}
+template <> __host__ __device__ constexpr uint32_t swz_c<float>(uint32_t e) {
+    return e ^ (((e >> 4) ^ (e >> 8) ^ (e >> 12)) & 15u);
+}
+
+// Calls f(std::integral_constant<int, P>) for the runtime chunk p, P in [0, 14 - R].
+template <int R, class F>
+__device__ __forceinline__ void with_chunk(int p, F &&f) {
+    switch (p) {
+#define VQE_CHUNK_CASE(PP) \
+    case PP:               \
+        if constexpr (PP + R <= kMaxTileBits) f(ChunkC<PP>{}); \
+        break;
+        VQE_CHUNK_CASE(0) VQE_CHUNK_CASE(1) VQE_CHUNK_CASE(2) VQE_CHUNK_CASE(3)
+        VQE_CHUNK_CASE(4) VQE_CHUNK_CASE(5) VQE_CHUNK_CASE(6) VQE_CHUNK_CASE(7)
+        VQE_CHUNK_CASE(8) VQE_CHUNK_CASE(9) VQE_CHUNK_CASE(10) VQE_CHUNK_CASE(11)
+        VQE_CHUNK_CASE(12) VQE_CHUNK_CASE(13)
+#undef VQE_CHUNK_CASE
+        default:
+            break;
+    }
 }
 
 __device__ __forceinline__ double flip_sign(double v, uint32_t s) {
@@ -106,28 +142,40 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
 #pragma unroll
                     for (int r = 0; r < NR; ++r) {
                         const uint32_t e = elem_of(t, r, p, R);
-                        v[r] = buf[e];
-                        if (BWD) w[r] = lbuf[e];
+                        if (Env::kDirect) {
+                            env.load(e, v[r], w[r]);
+                        } else {
+                            v[r] = buf[e];
+                            if (BWD) w[r] = lbuf[e];
+                        }
                     }
                 }
             } else {
                 __syncthreads();
                 if (active) {
+                    with_chunk<R>(chunk, [&](auto pc) {
+                        constexpr int P = decltype(pc)::value;
+                        const uint32_t sb = swz<T>(elem_of(t, 0, P, R));
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        const uint32_t s = swz<T>(elem_of(t, r, chunk, R));
-                        buf[s] = v[r];
-                        if (BWD) lbuf[s] = w[r];
-                    }
+                        for (int r = 0; r < NR; ++r) {
+                            const uint32_t s = sb ^ swz_c<T>((uint32_t)r << P);
+                            buf[s] = v[r];
+                            if (BWD) lbuf[s] = w[r];
+                        }
+                    });
                 }
                 __syncthreads();
                 if (active) {
+                    with_chunk<R>(p, [&](auto pc) {
+                        constexpr int P = decltype(pc)::value;
+                        const uint32_t sb = swz<T>(elem_of(t, 0, P, R));
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        const uint32_t s = swz<T>(elem_of(t, r, p, R));
-                        v[r] = buf[s];
-                        if (BWD) w[r] = lbuf[s];
-                    }
+                        for (int r = 0; r < NR; ++r) {
+                            const uint32_t s = sb ^ swz_c<T>((uint32_t)r << P);
+                            v[r] = buf[s];
+                            if (BWD) w[r] = lbuf[s];
+                        }
+                    });
                 }
             }
             chunk = p;
@@ -218,10 +266,17 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                 }
             }
             if (active) {
+                const uint32_t e0 = elem_of(t, 0, chunk, R);
+                const uint32_t g0 = g32(e0);
+                // g32 is XOR-linear over disjoint tile bits: g32(e0 | r<<chunk) = g0 ^ lin(r<<chunk)
+                auto lin = [&](uint32_t e) -> uint32_t {
+                    return (e & lowmask) | ((e >> m) << a);
+                };
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
-                    const uint32_t e = elem_of(t, r, chunk, R);
-                    const uint32_t g = g32(e);
+                    const uint32_t er = (uint32_t)r << chunk;
+                    const uint32_t e = e0 | er;
+                    const uint32_t g = g0 ^ lin(er);
                     const uint32_t sgn = __popc(g & (g >> 1) & cz) & 1u;
                     const C dv = env.diag(op.slot, e);
                     if (!BWD) {
@@ -256,17 +311,24 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
             __syncthreads();
         }
     }
-    // back to plain order in shared memory
-    __syncthreads();
-    if (active) {
+    if (Env::kDirect) {
+        if (active) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            const uint32_t e = elem_of(t, r, chunk, R);
-            buf[e] = v[r];
-            if (BWD) lbuf[e] = w[r];
+            for (int r = 0; r < NR; ++r) env.store(elem_of(t, r, chunk, R), v[r], w[r]);
         }
+    } else {
+        // back to plain order in shared memory
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const uint32_t e = elem_of(t, r, chunk, R);
+                buf[e] = v[r];
+                if (BWD) lbuf[e] = w[r];
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
     (void)nwarps;
 }
 

@@ -64,15 +64,24 @@ struct vqe_ctx {
     // Hamiltonian plan (device)
     DevBuf d_groups, d_tz, d_tc;
     int n_groups = 0;
+    // windowed expectation: tile windows, their group lists, groups too wide for any window
+    std::vector<WinDesc> wins;
+    DevBuf d_wgroups, d_wide;
+    int n_wide = 0;
+    int win_tiles = 0;   // columns of all windows per state
 
-    // ansatz plan
-    PlanOptions plan_opts;
-    std::vector<Group> groups;
-    std::vector<PassDesc> fwd, bwd;
-    std::vector<int> pass_tiles_log2;
-    DevBuf d_fwd, d_bwd, d_stage, d_goff, d_gcnt, d_gstep;
-    int n_stage = 0;
-    size_t coef_stride = 0, dtab_stride = 0, grad_stride = 0;
+    // ansatz plans: [0] energy evaluations (forward only), [1] gradients (forward + backward)
+    struct DevPlan {
+        PlanOptions opts;
+        std::vector<Group> groups;
+        std::vector<PassDesc> fwd, bwd;
+        DevBuf d_fwd, d_bwd, d_stage, d_goff, d_gcnt, d_gstep;
+        int n_stage = 0;
+        size_t coef_stride = 0, dtab_stride = 0, grad_stride = 0;
+        void release() {
+            for (DevBuf *b : {&d_fwd, &d_bwd, &d_stage, &d_goff, &d_gcnt, &d_gstep}) b->release();
+        }
+    } plan[2];
     int n_params = 0;
 
     // workspace and scratch
@@ -83,6 +92,11 @@ struct vqe_ctx {
     DevBuf d_params, d_coefs, d_dtab, d_gpart, d_epart, d_out;
     DevBuf hb_params, hb_e, hb_n, hb_g;   // device copies for the host-buffer batch calls
     int scratch_batch = 0;
+
+    // pass kernel choice and the device error word of bounded waits
+    int pass_kernel = 0;          // 0: one CTA per tile, 1: pipelined persistent where it fits
+    int sms = 0;
+    DevBuf d_err;
 
     // event timing (vqe_profile)
     bool prof = false;
@@ -221,7 +235,7 @@ PlanOptions resolve(const PlanOptions &o, vqe_precision prec) {
 bool options_valid(const PlanOptions &o, vqe_precision prec, std::string &err) {
     const PlanOptions r = resolve(o, prec);
     if (r.tile_bits_max < 1 || r.tile_bits_max > kMaxTileBits) err = "tile_bits_max out of 1..14";
-    else if (r.reg_bits < 1 || r.reg_bits > 4) err = "reg_bits out of 1..4";
+    else if (r.reg_bits < 1 || r.reg_bits > 5) err = "reg_bits out of 1..5";
     else if (r.tile_bits_max - r.reg_bits > 9) err = "tile_bits_max - reg_bits must be <= 9 (512 threads)";
     else if (r.run_bits < 1 || r.run_bits >= r.tile_bits_max) err = "run_bits out of 1..tile_bits_max-1";
     else {
@@ -478,29 +492,51 @@ bool make_plan(int n, int D, vqe_precision prec, const PlanOptions &opt, HostPla
     return true;
 }
 
-vqe_status build_plan(vqe_ctx *h) {
+// Default plan options: the energy plan may use 32 amplitudes per thread
+// (forward only); the gradient plan keeps at most 16 (both buffers in registers).
+PlanOptions plan_defaults(vqe_precision prec, int which) {
+    PlanOptions o;
+    if (which == 0 && prec == VQE_C64) {
+        o.tile_bits_max = 13;
+        o.run_bits = 4;
+        o.reg_bits = 5;
+    }
+    return o;
+}
+
+vqe_status build_one_plan(vqe_ctx *h, int which) {
+    vqe_ctx::DevPlan &P = h->plan[which];
     HostPlan hp;
     std::string err;
-    if (!make_plan(h->n, h->depth, h->prec, h->plan_opts, hp, err)) return fail(h, VQE_ERR_ARG, err);
-    h->groups = hp.groups;
-    h->fwd = hp.fwd;
-    h->bwd = hp.bwd;
-    h->pass_tiles_log2 = hp.pass_tiles_log2;
-    h->coef_stride = hp.coef_stride;
-    h->dtab_stride = hp.dtab_stride;
-    h->grad_stride = hp.grad_stride;
-    h->n_stage = int(hp.stage.size());
+    if (!make_plan(h->n, h->depth, h->prec, P.opts, hp, err)) return fail(h, VQE_ERR_ARG, err);
+    P.groups = hp.groups;
+    P.fwd = hp.fwd;
+    P.bwd = hp.bwd;
+    P.coef_stride = hp.coef_stride;
+    P.dtab_stride = hp.dtab_stride;
+    P.grad_stride = hp.grad_stride;
+    P.n_stage = int(hp.stage.size());
     h->n_params = hp.n_params;
     vqe_status st;
-    if ((st = upload(h, h->d_fwd, h->fwd, "pass plan")) != VQE_OK) return st;
-    if ((st = upload(h, h->d_bwd, h->bwd, "pass plan")) != VQE_OK) return st;
-    if ((st = upload(h, h->d_stage, hp.stage, "stage plan")) != VQE_OK) return st;
-    if ((st = upload(h, h->d_goff, hp.goff, "grad map")) != VQE_OK) return st;
-    if ((st = upload(h, h->d_gcnt, hp.gcnt, "grad map")) != VQE_OK) return st;
-    if ((st = upload(h, h->d_gstep, hp.gstep, "grad map")) != VQE_OK) return st;
-    h->stats.ansatz_passes = uint32_t(h->fwd.size());
+    if ((st = upload(h, P.d_fwd, P.fwd, "pass plan")) != VQE_OK) return st;
+    if (which == 1) {
+        if ((st = upload(h, P.d_bwd, P.bwd, "pass plan")) != VQE_OK) return st;
+        if ((st = upload(h, P.d_goff, hp.goff, "grad map")) != VQE_OK) return st;
+        if ((st = upload(h, P.d_gcnt, hp.gcnt, "grad map")) != VQE_OK) return st;
+        if ((st = upload(h, P.d_gstep, hp.gstep, "grad map")) != VQE_OK) return st;
+    }
+    if ((st = upload(h, P.d_stage, hp.stage, "stage plan")) != VQE_OK) return st;
+    return VQE_OK;
+}
+
+vqe_status build_plan(vqe_ctx *h) {
+    for (int w = 0; w < 2; ++w) {
+        vqe_status st = build_one_plan(h, w);
+        if (st != VQE_OK) return st;
+    }
+    h->stats.ansatz_passes = uint32_t(h->plan[0].fwd.size());
     int kmax = 0;
-    for (auto &g : h->groups) kmax = std::max(kmax, g.k);
+    for (auto &g : h->plan[0].groups) kmax = std::max(kmax, g.k);
     h->stats.tile_bits_max = uint32_t(kmax);
     return VQE_OK;
 }
@@ -599,9 +635,71 @@ double slim_keep(const std::vector<double> &cc, double threshold, std::vector<ui
     return dropped;
 }
 
+// Energy windows (see k_energy_win): window 0 = the low kE bits (and the
+// x = 0 group); a group whose X mask above the low `mrun` bits spans at most
+// kE - mrun bits joins (or opens) a window [0, mrun) + [a, a + kE - mrun);
+// wider groups are swept over the whole state.
+void plan_windows(int n, vqe_precision prec, const HamPlan &hp, std::vector<WinDesc> &wins,
+                  std::vector<int> &wgroups, std::vector<GroupDesc> &wide, int &win_tiles) {
+    wins.clear();
+    wgroups.clear();
+    wide.clear();
+    win_tiles = 0;
+    const int kE = prec == VQE_C128 ? 12 : 13;
+    const int mrun = prec == VQE_C128 ? 3 : 4;
+    if (n <= kE) return;
+    const int hw = kE - mrun;
+    std::vector<std::vector<int>> lists(1);
+    std::vector<int> win_a(1, kE);
+    for (size_t g = 0; g < hp.groups.size(); ++g) {
+        const uint32_t x = hp.groups[g].x;
+        if (x < (1u << kE)) {
+            lists[0].push_back(int(g));
+            continue;
+        }
+        const uint32_t xm = x & ~((1u << mrun) - 1u);
+        const int lo = __builtin_ctz(xm), hi = 31 - __builtin_clz(x);
+        if (hi - lo + 1 > hw) {
+            wide.push_back(hp.groups[g]);
+            continue;
+        }
+        int w = -1;
+        for (size_t j = 1; j < win_a.size(); ++j)
+            if (win_a[j] <= lo && hi < win_a[j] + hw) w = int(j);
+        if (w < 0) {
+            win_a.push_back(std::min(lo, n - hw));
+            lists.emplace_back();
+            w = int(win_a.size()) - 1;
+        }
+        lists[w].push_back(int(g));
+    }
+    for (size_t j = 0; j < lists.size(); ++j) {
+        WinDesc W{};
+        W.k = kE;
+        W.m = j == 0 ? kE : mrun;
+        W.a = j == 0 ? kE : win_a[j];
+        W.g_begin = int(wgroups.size());
+        wgroups.insert(wgroups.end(), lists[j].begin(), lists[j].end());
+        W.g_end = int(wgroups.size());
+        W.block_off = win_tiles;
+        W.with_norm = j == 0 ? 1 : 0;
+        win_tiles += 1 << (n - kE);
+        wins.push_back(W);
+    }
+}
+
 vqe_status build_ham_plan(vqe_ctx *h) {
     HamPlan hp;
     make_ham_plan(h->cx, h->cz, h->cc, h->keep, hp);
+    {
+        std::vector<int> wg;
+        std::vector<GroupDesc> wide;
+        plan_windows(h->n, h->prec, hp, h->wins, wg, wide, h->win_tiles);
+        h->n_wide = int(wide.size());
+        vqe_status st;
+        if ((st = upload(h, h->d_wgroups, wg, "window groups")) != VQE_OK) return st;
+        if ((st = upload(h, h->d_wide, wide, "wide groups")) != VQE_OK) return st;
+    }
     h->n_groups = int(hp.groups.size());
     vqe_status st;
     if ((st = upload(h, h->d_groups, hp.groups, "groups")) != VQE_OK) return st;
@@ -665,9 +763,11 @@ vqe_status ensure_scratch(vqe_ctx *h, int batch) {
     const bool c128 = h->prec == VQE_C128;
     const size_t coef_b = c128 ? sizeof(RotCoef<double>) : sizeof(RotCoef<float>);
     vqe_status st;
-    if ((st = ensure(h, h->d_coefs, coef_b * h->coef_stride * batch + 16, "coefficients")) != VQE_OK)
+    const size_t cs = std::max(h->plan[0].coef_stride, h->plan[1].coef_stride);
+    const size_t ds = std::max(h->plan[0].dtab_stride, h->plan[1].dtab_stride);
+    if ((st = ensure(h, h->d_coefs, coef_b * cs * batch + 16, "coefficients")) != VQE_OK)
         return st;
-    if ((st = ensure(h, h->d_dtab, h->elem_bytes() * h->dtab_stride * batch + 16, "tables")) != VQE_OK)
+    if ((st = ensure(h, h->d_dtab, h->elem_bytes() * ds * batch + 16, "tables")) != VQE_OK)
         return st;
     // blocks_per_state(B) * B <= 152 * 4 + B - 1 for every chunk size B <= batch
     if ((st = ensure(h, h->d_epart, sizeof(double) * 3 * (152 * 4 + size_t(batch)) + 16,
@@ -680,35 +780,87 @@ vqe_status ensure_scratch(vqe_ctx *h, int batch) {
 }
 
 vqe_status ensure_grad_scratch(vqe_ctx *h, int batch) {
-    return ensure(h, h->d_gpart, sizeof(double) * h->grad_stride * batch + 16, "grad partials");
+    return ensure(h, h->d_gpart, sizeof(double) * h->plan[1].grad_stride * batch + 16, "grad partials");
 }
 
 // ---------------------------------------------------------------- pipelines
 
 template <typename T>
-vqe_status run_forward(vqe_ctx *h, const double *params_dev, int B, void *psi) {
-    cudaStream_t s = h->stream;
+cudaError_t launch_any_pass(vqe_ctx *h, const vqe_ctx::DevPlan &P, const PassDesc *dd,
+                            const PassDesc &dh, int B, void *psi, void *lam, RotCoef<T> *coefs,
+                            double *gpart, bool backward, int init_zero) {
     const size_t N = h->state_elems();
+    const size_t elem = sizeof(T) * 2;
+    if (h->pass_kernel == 1 && dh.R <= 4 && pipe_smem_bytes(dh, backward, elem) <= 227 * 1024)
+        return launch_pass_pipe<T>(dd, dh, h->n, B, psi, lam, N, coefs, P.coef_stride, h->d_dtab.p,
+                                   P.dtab_stride, gpart, P.grad_stride, backward, init_zero,
+                                   static_cast<int *>(h->d_err.p), h->sms, h->stream);
+    return launch_pass<T>(dd, dh, h->n, B, psi, lam, N, coefs, P.coef_stride, h->d_dtab.p,
+                          P.dtab_stride, gpart, P.grad_stride, backward, init_zero, h->stream);
+}
+
+// Reads (and clears) the device error word; call after a synchronisation.
+vqe_status check_device_error(vqe_ctx *h) {
+    int e = 0;
+    VQE_CUDA(h, cudaMemcpy(&e, h->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        VQE_CUDA(h, cudaMemset(h->d_err.p, 0, sizeof(int)));
+        return fail(h, VQE_ERR_TIMEOUT, "a bounded wait in a pass kernel gave up");
+    }
+    return VQE_OK;
+}
+
+template <typename T>
+vqe_status run_forward(vqe_ctx *h, int which, const double *params_dev, int B, void *psi) {
+    cudaStream_t s = h->stream;
+    const vqe_ctx::DevPlan &P = h->plan[which];
     auto *coefs = static_cast<RotCoef<T> *>(h->d_coefs.p);
-    VQE_CUDA(h, launch_stage<T>(static_cast<const StageSlot *>(h->d_stage.p), h->n_stage, h->n,
-                                h->depth, params_dev, B, coefs, h->coef_stride, h->d_dtab.p,
-                                h->dtab_stride, s));
+    VQE_CUDA(h, launch_stage<T>(static_cast<const StageSlot *>(P.d_stage.p), P.n_stage, h->n,
+                                h->depth, params_dev, B, coefs, P.coef_stride, h->d_dtab.p,
+                                P.dtab_stride, s));
     h->stats.kernel_launches++;
-    const PassDesc *dd = static_cast<const PassDesc *>(h->d_fwd.p);
+    const PassDesc *dd = static_cast<const PassDesc *>(P.d_fwd.p);
     const int mk = prof_begin(h, 0);
-    for (size_t p = 0; p < h->fwd.size(); ++p) {
-        VQE_CUDA(h, launch_pass<T>(dd + p, h->fwd[p], h->n, B, psi, nullptr, N, coefs,
-                                   h->coef_stride, h->d_dtab.p, h->dtab_stride, nullptr, 0, false,
-                                   p == 0 ? 1 : 0, s));
+    for (size_t p = 0; p < P.fwd.size(); ++p) {
+        VQE_CUDA(h, launch_any_pass<T>(h, P, dd + p, P.fwd[p], B, psi, nullptr, coefs, nullptr,
+                                       false, p == 0 ? 1 : 0));
         h->stats.kernel_launches++;
     }
-    prof_end(h, mk, int(h->fwd.size()));
+    prof_end(h, mk, int(P.fwd.size()));
     return VQE_OK;
 }
 
 template <typename T>
 vqe_status run_energy(vqe_ctx *h, int B, const void *psi, double *energies, double *norms,
                       double *unnorm) {
+    if (!h->wins.empty() && uint64_t(h->win_tiles / int(h->wins.size())) * B >= uint64_t(2 * h->sms)) {
+        const int bps_wide = h->n_wide ? blocks_per_state(h, B) : 0;
+        const int bps_total = h->win_tiles + bps_wide;
+        vqe_status st = ensure(h, h->d_epart, sizeof(double) * 3 * size_t(bps_total) * B + 16, "partials");
+        if (st != VQE_OK) return st;
+        double *part = static_cast<double *>(h->d_epart.p);
+        const int mk = prof_begin(h, 1);
+        for (const WinDesc &W : h->wins) {
+            VQE_CUDA(h, launch_energy_win<T>(W, static_cast<const GroupDesc *>(h->d_groups.p),
+                                             static_cast<const int *>(h->d_wgroups.p),
+                                             static_cast<const uint32_t *>(h->d_tz.p),
+                                             static_cast<const double *>(h->d_tc.p), h->n, B, psi,
+                                             h->state_elems(), part, bps_total, h->stream));
+            h->stats.kernel_launches++;
+        }
+        if (h->n_wide) {
+            VQE_CUDA(h, launch_energy_sub<T>(static_cast<const GroupDesc *>(h->d_wide.p), h->n_wide,
+                                             static_cast<const uint32_t *>(h->d_tz.p),
+                                             static_cast<const double *>(h->d_tc.p), h->n, B, psi,
+                                             h->state_elems(), part, bps_wide, h->win_tiles,
+                                             bps_total, h->stream));
+            h->stats.kernel_launches++;
+        }
+        prof_end(h, mk, int(h->wins.size()) + (h->n_wide ? 1 : 0));
+        VQE_CUDA(h, launch_energy_finish(part, bps_total, B, energies, norms, unnorm, h->stream));
+        h->stats.kernel_launches++;
+        return VQE_OK;
+    }
     const int bps = blocks_per_state(h, B);
     const int mk = prof_begin(h, 1);
     VQE_CUDA(h, launch_energy<T>(static_cast<const GroupDesc *>(h->d_groups.p), h->n_groups,
@@ -725,7 +877,7 @@ vqe_status run_energy(vqe_ctx *h, int B, const void *psi, double *energies, doub
 
 template <typename T>
 vqe_status energy_chunk(vqe_ctx *h, const double *params_dev, int B, double *E, double *nrm) {
-    vqe_status st = run_forward<T>(h, params_dev, B, h->ws);
+    vqe_status st = run_forward<T>(h, 0, params_dev, B, h->ws);
     if (st != VQE_OK) return st;
     return run_energy<T>(h, B, h->ws, E, nrm, nullptr);
 }
@@ -737,8 +889,9 @@ vqe_status gradient_chunk(vqe_ctx *h, const double *params_dev, int B, double *g
     const size_t N = h->state_elems();
     void *psi = h->ws;
     void *lam = static_cast<char *>(h->ws) + h->state_bytes() * size_t(B);
-    vqe_status st = run_forward<T>(h, params_dev, B, psi);
+    vqe_status st = run_forward<T>(h, 1, params_dev, B, psi);
     if (st != VQE_OK) return st;
+    const vqe_ctx::DevPlan &P = h->plan[1];
     const int bps = blocks_per_state(h, B);
     const int mk_h = prof_begin(h, 2);
     VQE_CUDA(h, launch_apply_h<T>(static_cast<const GroupDesc *>(h->d_groups.p), h->n_groups,
@@ -750,18 +903,17 @@ vqe_status gradient_chunk(vqe_ctx *h, const double *params_dev, int B, double *g
                                      nullptr, s));
     h->stats.kernel_launches += 2;
     auto *coefs = static_cast<RotCoef<T> *>(h->d_coefs.p);
-    const PassDesc *dd = static_cast<const PassDesc *>(h->d_bwd.p);
+    const PassDesc *dd = static_cast<const PassDesc *>(P.d_bwd.p);
     double *gpart = static_cast<double *>(h->d_gpart.p);
     const int mk_b = prof_begin(h, 3);
-    for (int p = int(h->bwd.size()) - 1; p >= 0; --p) {
-        VQE_CUDA(h, launch_pass<T>(dd + p, h->bwd[p], h->n, B, psi, lam, N, coefs, h->coef_stride,
-                                   h->d_dtab.p, h->dtab_stride, gpart, h->grad_stride, true, 0, s));
+    for (int p = int(P.bwd.size()) - 1; p >= 0; --p) {
+        VQE_CUDA(h, launch_any_pass<T>(h, P, dd + p, P.bwd[p], B, psi, lam, coefs, gpart, true, 0));
         h->stats.kernel_launches++;
     }
-    prof_end(h, mk_b, int(h->bwd.size()));
-    VQE_CUDA(h, launch_grad_finish(gpart, h->grad_stride, static_cast<const int *>(h->d_goff.p),
-                                   static_cast<const int *>(h->d_gcnt.p),
-                                   static_cast<const int *>(h->d_gstep.p), h->n_params, B, grads,
+    prof_end(h, mk_b, int(P.bwd.size()));
+    VQE_CUDA(h, launch_grad_finish(gpart, P.grad_stride, static_cast<const int *>(P.d_goff.p),
+                                   static_cast<const int *>(P.d_gcnt.p),
+                                   static_cast<const int *>(P.d_gstep.p), h->n_params, B, grads,
                                    s));
     h->stats.kernel_launches++;
     return VQE_OK;
@@ -857,7 +1009,16 @@ vqe_status vqe_create(int n_qubits, int depth, vqe_precision precision, void *cu
         delete h;
         return VQE_ERR_CUDA;
     }
-    vqe_status st = build_plan(h);
+    if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return VQE_ERR_CUDA;
+    }
+    h->plan[0].opts = plan_defaults(precision, 0);
+    h->plan[1].opts = plan_defaults(precision, 1);
+    vqe_status st = ensure(h, h->d_err, 16, "error word");
+    if (st == VQE_OK && cudaMemset(h->d_err.p, 0, 16) != cudaSuccess) st = VQE_ERR_CUDA;
+    if (st == VQE_OK) st = build_plan(h);
     if (st != VQE_OK) {
         vqe_destroy(h);
         return st;
@@ -866,15 +1027,23 @@ vqe_status vqe_create(int n_qubits, int depth, vqe_precision precision, void *cu
     return VQE_OK;
 }
 
+vqe_status vqe_set_pass_kernel(vqe_handle h, int kind) {
+    if (!h) return VQE_ERR_ARG;
+    if (kind != 0 && kind != 1) return fail(h, VQE_ERR_ARG, "pass kernel kind must be 0 or 1");
+    h->pass_kernel = kind;
+    return VQE_OK;
+}
+
 vqe_status vqe_destroy(vqe_handle h) {
     if (!h) return VQE_ERR_ARG;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    for (DevBuf *b : {&h->d_groups, &h->d_tz, &h->d_tc, &h->d_fwd, &h->d_bwd, &h->d_stage,
-                      &h->d_goff, &h->d_gcnt, &h->d_gstep, &h->ws_own, &h->d_params, &h->d_coefs,
+    h->plan[0].release();
+    h->plan[1].release();
+    for (DevBuf *b : {&h->d_groups, &h->d_tz, &h->d_tc, &h->d_wgroups, &h->d_wide, &h->ws_own, &h->d_params, &h->d_coefs,
                       &h->d_dtab, &h->d_gpart, &h->d_epart, &h->d_out, &h->hb_params,
-                      &h->hb_e, &h->hb_n, &h->hb_g})
+                      &h->hb_e, &h->hb_n, &h->hb_g, &h->d_err})
         b->release();
     delete h;
     return VQE_OK;
@@ -890,11 +1059,17 @@ vqe_status vqe_set_plan_options(vqe_handle h, int tile_bits_max, int run_bits, i
     if (!options_valid(o, h->prec, err)) return fail(h, VQE_ERR_ARG, err);
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
-    const PlanOptions old = h->plan_opts;
-    h->plan_opts = o;
+    // reg_bits 5 applies to the energy plan; the gradient plan holds two buffers per thread
+    PlanOptions og = o;
+    if (og.reg_bits > 4) og.reg_bits = 4;
+    if (!options_valid(og, h->prec, err)) return fail(h, VQE_ERR_ARG, err);
+    const PlanOptions old0 = h->plan[0].opts, old1 = h->plan[1].opts;
+    h->plan[0].opts = o;
+    h->plan[1].opts = og;
     vqe_status st = build_plan(h);
     if (st != VQE_OK) {
-        h->plan_opts = old;
+        h->plan[0].opts = old0;
+        h->plan[1].opts = old1;
         build_plan(h);
         return st;
     }
@@ -998,9 +1173,11 @@ vqe_status vqe_apply_ansatz(vqe_handle h, const double *params) {
     VQE_CUDA(h, cudaMemcpyAsync(h->d_params.p, params, sizeof(double) * h->n_params,
                                 cudaMemcpyHostToDevice, h->stream));
     const double *pd = static_cast<const double *>(h->d_params.p);
-    st = h->prec == VQE_C128 ? run_forward<double>(h, pd, 1, h->ws) : run_forward<float>(h, pd, 1, h->ws);
+    st = h->prec == VQE_C128 ? run_forward<double>(h, 0, pd, 1, h->ws)
+                             : run_forward<float>(h, 0, pd, 1, h->ws);
     if (st != VQE_OK) return st;
     VQE_CUDA(h, cudaStreamSynchronize(h->stream));
+    if ((st = check_device_error(h)) != VQE_OK) return st;
     h->state_valid = true;
     return VQE_OK;
 }
@@ -1099,6 +1276,7 @@ static vqe_status host_batch(vqe_handle h, Job job, const double *params, int ba
     }
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (st == VQE_OK && e != cudaSuccess) st = cuda_fail(h, e, "cudaStreamSynchronize");
+    if (st == VQE_OK) st = check_device_error(h);
     return st;
 }
 
@@ -1126,6 +1304,7 @@ vqe_status vqe_profile_read(vqe_handle h, vqe_kernel_times *out) {
     if (!h || !out) return VQE_ERR_ARG;
     vqe_status st = prof_collect(h);
     if (st != VQE_OK) return st;
+    if ((st = check_device_error(h)) != VQE_OK) return st;
     *out = h->times;
     return VQE_OK;
 }
@@ -1149,6 +1328,7 @@ size_t vqe_inspect_sizeof(int which) {
         case 0: return sizeof(PassDesc);
         case 1: return sizeof(StageSlot);
         case 2: return sizeof(GroupDesc);
+        case 3: return sizeof(WinDesc);
         default: return 0;
     }
 }
@@ -1219,6 +1399,41 @@ int vqe_inspect_hamiltonian(int n_qubits, const uint64_t *x_masks, const uint64_
     if (groups) std::memcpy(groups, hp.groups.data(), hp.groups.size() * sizeof(GroupDesc));
     if (tz) std::memcpy(tz, hp.tz.data(), hp.tz.size() * sizeof(uint32_t));
     if (tc) std::memcpy(tc, hp.tc.data(), hp.tc.size() * sizeof(double));
+    return 0;
+}
+
+int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
+                        const uint64_t *z_masks, const double *coeffs, size_t n_terms,
+                        double threshold, void *windows, int max_windows, int *wgroups,
+                        int max_wgroups, void *wide, int max_wide, int counts[3]) {
+    if (n_qubits < 1 || n_qubits > 32 || (precision != 0 && precision != 1)) return -1;
+    if (n_terms && (!x_masks || !z_masks || !coeffs)) return -1;
+    const uint64_t lim = (uint64_t(1) << n_qubits) - 1;
+    for (size_t t = 0; t < n_terms; ++t)
+        if ((x_masks[t] & ~lim) || (z_masks[t] & ~lim) || !std::isfinite(coeffs[t])) return -1;
+    std::vector<uint64_t> cx, cz;
+    std::vector<double> cc;
+    canonicalise(x_masks, z_masks, coeffs, n_terms, cx, cz, cc);
+    std::vector<uint8_t> keep;
+    size_t kept = 0;
+    slim_keep(cc, threshold, keep, kept);
+    HamPlan hp;
+    make_ham_plan(cx, cz, cc, keep, hp);
+    std::vector<WinDesc> wins;
+    std::vector<int> wg;
+    std::vector<GroupDesc> wd;
+    int tiles = 0;
+    plan_windows(n_qubits, vqe_precision(precision), hp, wins, wg, wd, tiles);
+    if (counts) {
+        counts[0] = int(wins.size());
+        counts[1] = int(wg.size());
+        counts[2] = int(wd.size());
+    }
+    if (int(wins.size()) > max_windows || int(wg.size()) > max_wgroups || int(wd.size()) > max_wide)
+        return -1;
+    if (windows) std::memcpy(windows, wins.data(), wins.size() * sizeof(WinDesc));
+    if (wgroups) std::memcpy(wgroups, wg.data(), wg.size() * sizeof(int));
+    if (wide) std::memcpy(wide, wd.data(), wd.size() * sizeof(GroupDesc));
     return 0;
 }
 

@@ -98,6 +98,17 @@ struct GroupDesc {
 
 // Per-state reduction layout of the energy kernels.
 constexpr int kEnergyThreads = 256;
+constexpr int kEnergyWinThreads = 512;
+
+// One energy window: tile bits [0, m) and [m, k) -> global [a, a + k - m);
+// groups wgroups[g_begin, g_end) are evaluated from the staged tile; block
+// partials go to columns [block_off, block_off + 2^(n-k)).
+struct WinDesc {
+    int k, m, a;
+    int g_begin, g_end;
+    int block_off;
+    int with_norm;
+};
 
 // ---------------------------------------------------------------- launchers
 // Each returns cudaGetLastError() after queueing.
@@ -126,6 +137,17 @@ cudaError_t launch_apply_h(const GroupDesc *groups, int n_groups, const uint32_t
                            void *lam, size_t state_stride, double *partials,
                            int blocks_per_state, cudaStream_t s);
 
+template <typename T>
+cudaError_t launch_energy_win(const WinDesc &W, const GroupDesc *groups, const int *wgroups,
+                              const uint32_t *tz, const double *tc, int n_qubits, int batch,
+                              const void *psi, size_t state_stride, double *partials,
+                              int bps_total, cudaStream_t s);
+template <typename T>
+cudaError_t launch_energy_sub(const GroupDesc *groups, int n_groups, const uint32_t *tz,
+                              const double *tc, int n_qubits, int batch, const void *psi,
+                              size_t state_stride, double *partials, int bps, int block_off,
+                              int bps_total, cudaStream_t s);
+
 cudaError_t launch_energy_finish(const double *partials, int blocks_per_state, int batch,
                                  double *energies, double *norms, double *unnorm,
                                  cudaStream_t s);
@@ -150,5 +172,15 @@ cudaError_t launch_init_zero_state(void *psi, size_t stride, int n, int batch, c
 
 int pass_threads(const PassDesc &d);
 size_t pass_smem_bytes(const PassDesc &d, bool backward, size_t elem_bytes);
+
+// Persistent, bulk-copy pipelined variant of launch_pass (k_pipe.cu): two
+// tile buffers per CTA; *err is set to 1 if a bounded wait gives up.
+template <typename T>
+cudaError_t launch_pass_pipe(const PassDesc *desc_dev, const PassDesc &desc_host, int n_qubits,
+                             int batch, void *psi, void *lam, size_t state_stride,
+                             const RotCoef<T> *coefs, size_t coef_stride, const void *dtab,
+                             size_t dtab_stride, double *grad_part, size_t grad_stride,
+                             bool backward, int init_zero, int *err, int sms, cudaStream_t s);
+size_t pipe_smem_bytes(const PassDesc &d, bool backward, size_t elem_bytes);
 
 }  // namespace vqe

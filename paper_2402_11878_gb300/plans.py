@@ -49,8 +49,14 @@ class GroupDesc(ctypes.Structure):
                 ("t_mid", ctypes.c_int), ("t_end", ctypes.c_int)]
 
 
+class WinDesc(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("m", ctypes.c_int), ("a", ctypes.c_int),
+                ("g_begin", ctypes.c_int), ("g_end", ctypes.c_int), ("block_off", ctypes.c_int),
+                ("with_norm", ctypes.c_int)]
+
+
 def _check_layouts(lib):
-    for which, cls in enumerate((PassDesc, StageSlot, GroupDesc)):
+    for which, cls in enumerate((PassDesc, StageSlot, GroupDesc, WinDesc)):
         got = lib.vqe_inspect_sizeof(which)
         if got != ctypes.sizeof(cls):
             raise RuntimeError(f"record layout mismatch for {cls.__name__}: library {got}, "
@@ -111,3 +117,26 @@ def hamiltonian(n_qubits: int, x, z, c, threshold: float = 0.0) -> dict:
         raise ValueError("vqe_inspect_hamiltonian rejected the input")
     return {"groups": list(groups)[:ng], "tz": tz[:nt], "tc": tc[:nt],
             "sum_abs_dropped": dropped.value, "n_canonical": ncanon.value}
+
+
+def windows(n_qubits: int, precision: str, x, z, c, threshold: float = 0.0) -> dict:
+    """Windows of the windowed expectation kernel, as the library plans them."""
+    lib = load()
+    _check_layouts(lib)
+    prec = {"c64": 0, "c128": 1}[precision]
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    z = np.ascontiguousarray(z, dtype=np.uint64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    counts = (ctypes.c_int * 3)()
+    lib.vqe_inspect_windows(n_qubits, prec, x.ctypes.data, z.ctypes.data, c.ctypes.data, c.size,
+                            float(threshold), None, 0, None, 0, None, 0, counts)
+    nw, ng, nd = counts[0], counts[1], counts[2]
+    wins = (WinDesc * max(nw, 1))()
+    wg = np.zeros(max(ng, 1), dtype=np.int32)
+    wide = (GroupDesc * max(nd, 1))()
+    rc = lib.vqe_inspect_windows(n_qubits, prec, x.ctypes.data, z.ctypes.data, c.ctypes.data,
+                                 c.size, float(threshold), ctypes.addressof(wins), nw,
+                                 wg.ctypes.data, ng, ctypes.addressof(wide), nd, counts)
+    if rc != 0:
+        raise ValueError("vqe_inspect_windows rejected the input")
+    return {"windows": list(wins)[:nw], "wgroups": wg[:ng], "wide": list(wide)[:nd]}

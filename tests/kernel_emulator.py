@@ -291,3 +291,59 @@ def apply_h_terms(ham, n, psi):
             fb += ham["tc"][t_] * (1 - 2 * (popc(i & int(ham["tz"][t_])) & 1))
         lam += pj * (fa - 1j * fb)
     return lam
+
+
+def energy_windows(ham, win, n, psi):
+    """The windowed expectation kernel on the CPU: each window's tiles staged,
+    its groups evaluated from the tile, wide groups swept; (E, norm)."""
+    groups, tz, tc = ham["groups"], ham["tz"], ham["tc"]
+    acc, nrm = 0.0, 0.0
+    covered = 0
+    for W in win["windows"]:
+        k, m, a = W.k, W.m, W.a
+        mid = a - m
+        assert 0 <= mid and a + (k - m) <= n and k <= 14
+        tiles = 1 << (n - k)
+        tile = np.arange(tiles, dtype=np.int64)[:, None]
+        e = np.arange(1 << k, dtype=np.int64)[None, :]
+        base = ((tile & ((1 << mid) - 1)) << m) | ((tile >> mid) << (a + (k - m)))
+        g = base | (e & ((1 << m) - 1)) | ((e >> m) << a)
+        flat = g.ravel()
+        assert np.unique(flat).size == flat.size == (1 << n)
+        sp = psi[g]
+        if W.with_norm:
+            nrm += float((np.abs(sp) ** 2).sum())
+            covered += 1
+        for gi in win["wgroups"][W.g_begin:W.g_end]:
+            G = groups[gi]
+            if G.x == 0:
+                f = np.zeros(g.shape)
+                for t_ in range(G.t_begin, G.t_mid):
+                    f += tc[t_] * (1 - 2 * (popc(g & int(tz[t_])) & 1))
+                acc += float((np.abs(sp) ** 2 * f).sum())
+                continue
+            xl = (G.x & ((1 << m) - 1)) | ((G.x >> a) << m)
+            assert xl < (1 << k), "group outside its window"
+            # the window must hold every bit of x
+            assert ((xl & ((1 << m) - 1)) | ((xl >> m) << a)) == G.x
+            hl = int(xl).bit_length() - 1
+            p = np.arange(1 << (k - 1), dtype=np.int64)[None, :]
+            i0 = ((p >> hl) << (hl + 1)) | (p & ((1 << hl) - 1))
+            i1 = i0 ^ xl
+            x0 = np.take_along_axis(sp, np.broadcast_to(i0, (tiles, i0.shape[1])), axis=1)
+            x1 = np.take_along_axis(sp, np.broadcast_to(i1, (tiles, i1.shape[1])), axis=1)
+            gi0 = base | (i0 & ((1 << m) - 1)) | ((i0 >> m) << a)
+            prod = np.conj(x0) * x1
+            fa = np.zeros(gi0.shape)
+            fb = np.zeros(gi0.shape)
+            for t_ in range(G.t_begin, G.t_mid):
+                fa += tc[t_] * (1 - 2 * (popc(gi0 & int(tz[t_])) & 1))
+            for t_ in range(G.t_mid, G.t_end):
+                fb += tc[t_] * (1 - 2 * (popc(gi0 & int(tz[t_])) & 1))
+            acc += 2.0 * float((prod.real * fa + prod.imag * fb).sum())
+    if win["wide"]:
+        sub = {"groups": win["wide"], "tz": tz, "tc": tc}
+        e_w, _ = energy_terms(sub, n, psi)
+        acc += e_w
+    assert covered == 1
+    return acc, nrm

@@ -54,14 +54,17 @@ def test_config_small_hubbard_c128_state_and_energy(eng_mod, oracle_mod, seed):
 SIZES = [1, 2, 3, 4, 5, 7, 8, 9, 12, 13, 14, 15, 16, 17, 18]
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("n", SIZES)
-def test_random_pauli_sum_all_sizes(eng_mod, oracle_mod, prec, n):
-    """Every plan shape (single tile, multi-pass, ragged groups) on random Pauli sums with Y terms."""
+def test_random_pauli_sum_all_sizes(eng_mod, oracle_mod, prec, n, kernel):
+    """Every plan shape (single tile, multi-pass, ragged groups) on random Pauli sums with Y
+    terms, with the one-CTA-per-tile kernel (0) and the pipelined persistent kernel (1)."""
     D = 2 if n > 12 else 3
     H = vi.random_pauli_sum(n, 40, seed=100 + n, duplicates=3)
     p = vi.ansatz_params(7 + n, n, D)
     eng = make(eng_mod, n, D, prec, H)
+    eng.set_pass_kernel(kernel)
     eng.apply_ansatz(p)
     psi = eng.get_state()
     ref = oracle_mod.ansatz_state(n, D, p)
@@ -85,13 +88,17 @@ def test_batched_energies(eng_mod, oracle_mod, prec):
         check_energy(E[b], E_ref, H, prec)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("n,D", [(2, 2), (3, 2), (8, 4), (13, 2), (14, 2), (16, 2), (17, 1)])
-def test_adjoint_gradient(eng_mod, oracle_mod, prec, n, D):
+def test_adjoint_gradient(eng_mod, oracle_mod, prec, n, D, kernel):
     H = vi.random_pauli_sum(n, 30, seed=200 + n) if n % 2 else vi.hubbard_1d(n // 2, 1.0, 4.0)
     H = vi.PauliSum(n, H.x, H.z, H.c)
     p = vi.ansatz_params(300 + n, n, D)
     eng = make(eng_mod, n, D, prec, H)
+    eng.set_pass_kernel(kernel)
+    if kernel == 1 and n > 12:
+        eng.set_plan_options(11 if prec == "c128" else 12, 0, 0)   # backward tiles fit twice
     g, E = eng.gradient(p)
     g_ref, E_ref = oracle_mod.gradient_adjoint(n, D, p, H.x, H.z, H.c)
     check_energy(E, E_ref, H, prec)
@@ -215,3 +222,23 @@ def test_argument_errors(eng_mod):
         eng.apply_ansatz(np.full(24, np.inf))
     with pytest.raises(pkg.VQEError):
         eng.slim(-1.0)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("case", ["hubbard", "random", "molecular"])
+def test_windowed_energy_batch(eng_mod, oracle_mod, prec, case):
+    """Batches large enough for the windowed expectation kernel (tile windows + wide groups)."""
+    if case == "hubbard":
+        H = vi.hubbard_1d(9, 1.0, 2.0, periodic=True)
+    elif case == "random":
+        H = vi.random_pauli_sum(18, 80, seed=77, duplicates=5)
+    else:
+        H = vi.synthetic_molecular(9, seed=3)
+    n, D, B = H.n, 2, 16
+    P = np.stack([vi.ansatz_params(800 + b, n, D) for b in range(B)])
+    eng = make(eng_mod, n, D, prec, H)
+    E, nn = eng.energy_batch(P)
+    for b in (0, 7, 15):
+        ref = oracle_mod.ansatz_state(n, D, P[b])
+        E_ref, _ = oracle_mod.energy(ref, H.x, H.z, H.c)
+        check_energy(E[b], E_ref, H, prec)

@@ -137,7 +137,7 @@ def test_inspect_rejects_bad_input():
         P.hamiltonian(4, [1], [0], [float("inf")])
 
 
-OPTION_CASES = [((10, 1, 3), "c128"), ((11, 2, 3), "c128"), ((12, 2, 4), "c128"), ((12, 3, 4), "c128"),
+OPTION_CASES = [((13, 4, 5), "c64"), ((12, 3, 5), "c128"), ((10, 1, 3), "c128"), ((11, 2, 3), "c128"), ((12, 2, 4), "c128"), ((12, 3, 4), "c128"),
                 ((13, 2, 4), "c64"), ((12, 2, 4), "c64"), ((11, 4, 3), "c64"),
                 ((9, 1, 2), "c64")]
 
@@ -150,7 +150,8 @@ def test_plan_options_emulated(oracle_mod, opts, prec, n):
     pl = P.plan(n, D, prec, opts)
     elem = 16 if prec == "c128" else 8
     for d in pl["bwd"]:
-        assert (1 << (d.k - d.R)) <= 512 and pass_smem(d, True, elem) <= SMEM_MAX
+        assert (1 << (d.k - d.R)) <= 512
+        assert pass_smem(d, opts[2] <= 4, elem) <= SMEM_MAX
     if n > 16:
         return
     emu = Emu(n, D, prec)
@@ -158,6 +159,8 @@ def test_plan_options_emulated(oracle_mod, opts, prec, n):
     p = vi.ansatz_params(77 + n, n, D)
     psi = emu.forward(p)
     assert np.max(np.abs(psi - oracle_mod.ansatz_state(n, D, p))) < 1e-12
+    if opts[2] == 5:
+        return      # 32 amplitudes per thread: forward (energy) plans only
     H = vi.random_pauli_sum(n, 10, seed=n)
     ham = P.hamiltonian(n, H.x, H.z, H.c)
     g, _ = emu.gradient(p, lambda s: apply_h_terms(ham, n, s))
@@ -170,3 +173,28 @@ def test_plan_options_rejected():
         P.plan(20, 2, "c128", (14, 3, 3))   # 2^11 threads
     with pytest.raises(ValueError):
         P.plan(20, 2, "c128", (12, 12, 3))  # run bits >= tile bits
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("case", ["hubbard", "random", "molecular"])
+def test_energy_windows_emulated(oracle_mod, prec, case):
+    """The windowed expectation plan covers every group exactly once and reproduces the oracle."""
+    from kernel_emulator import energy_windows
+    if case == "hubbard":
+        H = vi.hubbard_1d(8, 1.0, 3.0, periodic=True)
+    elif case == "random":
+        H = vi.random_pauli_sum(16, 60, seed=21, duplicates=4)
+    else:
+        H = vi.synthetic_molecular(8, seed=5)
+    n = H.n
+    p = vi.ansatz_params(31, n, 1)
+    psi = oracle_mod.ansatz_state(n, 1, p)
+    ham = P.hamiltonian(n, H.x, H.z, H.c)
+    win = P.windows(n, prec, H.x, H.z, H.c)
+    assert win["windows"], "expected windows above the tile size"
+    n_in = len(win["wgroups"]) + len(win["wide"])
+    assert n_in == len(ham["groups"])
+    assert sorted(win["wgroups"].tolist()) == sorted(set(win["wgroups"].tolist()))
+    e, nn = energy_windows(ham, win, n, psi)
+    e_ref, _, n_ref = oracle_mod.expectation(psi, H.x, H.z, H.c)
+    assert abs(e - e_ref) < 1e-11 * H.sum_abs() and abs(nn - n_ref) < 1e-12

@@ -101,11 +101,11 @@ vqe_status vqe_bind_workspace(vqe_handle h, void *dev_ptr, size_t bytes);
 
 /* Tile plan of the ansatz passes (0 = default for each): tile_bits_max =
  * log2 of the largest tile a pass stages in shared memory (1..14; default
- * 12 for C128, 13 for C64), run_bits = log2 of the contiguous run of
- * amplitudes kept in the tiles of high-qubit passes (default 3 / 4, i.e. 128
- * bytes), reg_bits = log2 of the amplitudes each thread holds (1..5;
- * default 3 for C128; for C64 5 in energy evaluations and 4 in gradients).
- * reg_bits 5 applies to energy evaluations only; gradients use at most 4.
+ * 11 for C128, 12 for C64), run_bits = log2 of the contiguous run of
+ * amplitudes at least kept in the tiles of high-qubit passes (default 2 for
+ * C128, 4 for C64: 64 bytes), reg_bits = log2 of the amplitudes each thread
+ * holds (1..5; default 3 for C128, 4 for C64).  reg_bits 5 applies to energy
+ * evaluations only; gradients use at most 4.
  * Rejected (VQE_ERR_ARG) if a pass would need more than 512 threads or
  * 227 KiB of shared memory.  Rebuilds the plans; the state of
  * vqe_apply_ansatz is discarded.  Results do not depend on the plan beyond

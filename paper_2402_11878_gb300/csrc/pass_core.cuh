@@ -206,31 +206,37 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                     }
                 }
                 if (!active) continue;
+                // Both butterfly forms share one shape once the operands are
+                // chosen by the mode: with (P, Q) = (x, y) in tan mode and
+                // (y, x) in cot mode,
+                //   forward  [[1,-t],[t,1]] / [[u,-1],[1,u]]:
+                //     y' = fma(c, P, Q),  x' = s * fma(-c, Q, P)
+                //   backward (transposes):
+                //     x' = fma(c, Q, P),  y' = s * fma(-c, P, Q)
+                // with s = -1 in cot mode (an integer sign flip).  Selecting
+                // operands instead of branching keeps every DFMA useful.
+                const uint32_t md = (uint32_t)rc.mode;
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     if (r & (1 << j)) continue;
                     const int r1 = r | (1 << j);
-                    if (!BWD) {
-                        const C x = v[r], y = v[r1];
-                        if (rc.mode == 0) {   // [[1,-t],[t,1]]
-                            v[r].x = fma(-cv, y.x, x.x);  v[r].y = fma(-cv, y.y, x.y);
-                            v[r1].x = fma(cv, x.x, y.x);  v[r1].y = fma(cv, x.y, y.y);
-                        } else {              // [[u,-1],[1,u]]
-                            v[r].x = fma(cv, x.x, -y.x);  v[r].y = fma(cv, x.y, -y.y);
-                            v[r1].x = fma(cv, y.x, x.x);  v[r1].y = fma(cv, y.y, x.y);
-                        }
-                    } else {
 #pragma unroll
-                        for (int bufi = 0; bufi < 2; ++bufi) {
-                            C *u = bufi ? w : v;
-                            const C x = u[r], y = u[r1];
-                            if (rc.mode == 0) {   // transpose: [[1,t],[-t,1]]
-                                u[r].x = fma(cv, y.x, x.x);    u[r].y = fma(cv, y.y, x.y);
-                                u[r1].x = fma(-cv, x.x, y.x);  u[r1].y = fma(-cv, x.y, y.y);
-                            } else {              // transpose: [[u,1],[-1,u]]
-                                u[r].x = fma(cv, x.x, y.x);    u[r].y = fma(cv, x.y, y.y);
-                                u[r1].x = fma(cv, y.x, -x.x);  u[r1].y = fma(cv, y.y, -x.y);
-                            }
+                    for (int bufi = 0; bufi < (BWD ? 2 : 1); ++bufi) {
+                        C *u = bufi ? w : v;
+                        const C x = u[r], y = u[r1];
+                        C P, Q;
+                        P.x = md ? y.x : x.x;  P.y = md ? y.y : x.y;
+                        Q.x = md ? x.x : y.x;  Q.y = md ? x.y : y.y;
+                        if (!BWD) {
+                            u[r1].x = fma(cv, P.x, Q.x);
+                            u[r1].y = fma(cv, P.y, Q.y);
+                            u[r].x = flip_sign(fma(-cv, Q.x, P.x), md);
+                            u[r].y = flip_sign(fma(-cv, Q.y, P.y), md);
+                        } else {
+                            u[r].x = fma(cv, Q.x, P.x);
+                            u[r].y = fma(cv, Q.y, P.y);
+                            u[r1].x = flip_sign(fma(-cv, P.x, Q.x), md);
+                            u[r1].y = flip_sign(fma(-cv, P.y, Q.y), md);
                         }
                     }
                 }

@@ -24,8 +24,8 @@ struct Group {        // one qubit group = the tile bits of one kind of pass
 };
 
 struct PlanOptions {
-    int tile_bits_max = 0;  // 0: default (12 for C128, 13 for C64)
-    int run_bits = 0;       // 0: default (3 for C128, 4 for C64: 128-byte runs)
+    int tile_bits_max = 0;  // 0: default (11 for C128, 12 for C64)
+    int run_bits = 0;       // 0: default (2 for C128, 4 for C64: 64-byte runs)
     int reg_bits = 0;       // 0: default (3 for C128, 4 for C64)
 };
 
@@ -200,6 +200,9 @@ vqe_status prof_collect(vqe_ctx *h) {
 
 // ---------------------------------------------------------------- planner
 
+// Qubit groups: the low kmax qubits, then high groups of at most kmax - mrun
+// qubits (balanced).  Every high tile is filled up to kmax bits with low
+// qubits, so its contiguous runs hold 2^(kmax - h) >= 2^mrun amplitudes.
 std::vector<Group> plan_groups(int n, int kmax, int mrun) {
     std::vector<Group> gs;
     if (n <= kmax) {
@@ -212,22 +215,28 @@ std::vector<Group> plan_groups(int n, int kmax, int mrun) {
     int a = kmax;
     for (int j = 0; j < ng; ++j) {
         const int hj = rest / ng + (j < rest % ng ? 1 : 0);
-        const int k = mrun + hj;
-        gs.push_back({k, mrun, a, ((1u << k) - 1u) & ~((1u << mrun) - 1u)});
+        const int m = kmax - hj;
+        gs.push_back({kmax, m, a, ((1u << kmax) - 1u) & ~((1u << m) - 1u)});
         a += hj;
     }
     return gs;
 }
+
 
 struct Round {
     int chunk;
     std::vector<PassOp> ops;
 };
 
+// Zero fields take the defaults, the fastest plans measured on GB300 for the
+// forward and the adjoint passes: FP64 tiles of 2^11 amplitudes with 4-amplitude
+// runs and 8 amplitudes per thread; FP32 tiles of 2^12 with 16-amplitude runs
+// and 16 per thread (256 threads each).  Plans with fewer passes (larger
+// tiles, or 32 amplitudes per thread) measured slower.
 PlanOptions resolve(const PlanOptions &o, vqe_precision prec) {
     PlanOptions r;
-    r.tile_bits_max = o.tile_bits_max ? o.tile_bits_max : (prec == VQE_C128 ? 12 : 13);
-    r.run_bits = o.run_bits ? o.run_bits : (prec == VQE_C128 ? 3 : 4);
+    r.tile_bits_max = o.tile_bits_max ? o.tile_bits_max : (prec == VQE_C128 ? 11 : 12);
+    r.run_bits = o.run_bits ? o.run_bits : (prec == VQE_C128 ? 2 : 4);
     r.reg_bits = o.reg_bits ? o.reg_bits : (prec == VQE_C128 ? 3 : 4);
     return r;
 }
@@ -241,7 +250,8 @@ bool options_valid(const PlanOptions &o, vqe_precision prec, std::string &err) {
     else {
         const size_t elem = prec == VQE_C128 ? 16 : 8;
         const size_t warps = ((size_t(1) << (r.tile_bits_max - std::min(r.reg_bits, r.tile_bits_max))) + 31) / 32;
-        const size_t smem = (size_t(2) << r.tile_bits_max) * elem + warps * r.tile_bits_max * 16;
+        const size_t bufs = r.reg_bits > 4 ? 1 : 2;   // 32-amplitude plans are forward only
+        const size_t smem = (bufs << r.tile_bits_max) * elem + warps * r.tile_bits_max * 16;
         if (smem > 227 * 1024) err = "tile does not fit in shared memory";
     }
     return err.empty();
@@ -494,15 +504,6 @@ bool make_plan(int n, int D, vqe_precision prec, const PlanOptions &opt, HostPla
 
 // Default plan options: the energy plan may use 32 amplitudes per thread
 // (forward only); the gradient plan keeps at most 16 (both buffers in registers).
-PlanOptions plan_defaults(vqe_precision prec, int which) {
-    PlanOptions o;
-    if (which == 0 && prec == VQE_C64) {
-        o.tile_bits_max = 13;
-        o.run_bits = 4;
-        o.reg_bits = 5;
-    }
-    return o;
-}
 
 vqe_status build_one_plan(vqe_ctx *h, int which) {
     vqe_ctx::DevPlan &P = h->plan[which];
@@ -1014,8 +1015,6 @@ vqe_status vqe_create(int n_qubits, int depth, vqe_precision precision, void *cu
         delete h;
         return VQE_ERR_CUDA;
     }
-    h->plan[0].opts = plan_defaults(precision, 0);
-    h->plan[1].opts = plan_defaults(precision, 1);
     vqe_status st = ensure(h, h->d_err, 16, "error word");
     if (st == VQE_OK && cudaMemset(h->d_err.p, 0, 16) != cudaSuccess) st = VQE_ERR_CUDA;
     if (st == VQE_OK) st = build_plan(h);

@@ -101,9 +101,9 @@ vqe_status vqe_bind_workspace(vqe_handle h, void *dev_ptr, size_t bytes);
 
 /* Tile plan of the ansatz passes (0 = default for each): tile_bits_max =
  * log2 of the largest tile a pass stages in shared memory (1..14; default
- * 11 for C128, 12 for C64), run_bits = log2 of the contiguous run of
- * amplitudes at least kept in the tiles of high-qubit passes (default 2 for
- * C128, 4 for C64: 64 bytes), reg_bits = log2 of the amplitudes each thread
+ * 11), run_bits = log2 of the contiguous run of amplitudes at least kept in
+ * the tiles of high-qubit passes (default 2 for C128, 3 for C64: 64 bytes),
+ * reg_bits = log2 of the amplitudes each thread
  * holds (1..5; default 3 for C128, 4 for C64).  reg_bits 5 applies to energy
  * evaluations only; gradients use at most 4.
  * Rejected (VQE_ERR_ARG) if a pass would need more than 512 threads or

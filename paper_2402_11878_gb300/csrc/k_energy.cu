@@ -228,20 +228,35 @@ k_apply_h(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__
     }
 }
 
-// One thread per state; partials summed in block order.
-__global__ void k_energy_finish(const double *__restrict__ partials, int bps, int batch,
-                                double *energies, double *norms, double *unnorm) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= batch) return;
+// One block per state: each thread sums a strided subset of the block
+// partials, then a fixed-order tree over the block (bitwise reproducible).
+constexpr int kFinishThreads = 256;
+__global__ void __launch_bounds__(kFinishThreads)
+k_energy_finish(const double *__restrict__ partials, int bps, int batch, double *energies,
+                double *norms, double *unnorm) {
+    __shared__ double se[kFinishThreads], sn[kFinishThreads];
+    const int b = blockIdx.x;
     const double *p = partials + (size_t)b * bps * 3;
     double e = 0.0, nn = 0.0;
-    for (int i = 0; i < bps; ++i) {
-        e += p[3 * i];
-        nn += p[3 * i + 1];
+    for (int i = threadIdx.x; i < bps; i += kFinishThreads) {
+        e += p[3 * (size_t)i];
+        nn += p[3 * (size_t)i + 1];
     }
-    if (energies) energies[b] = e / nn;
-    if (norms) norms[b] = nn;
-    if (unnorm) unnorm[b] = e;
+    se[threadIdx.x] = e;
+    sn[threadIdx.x] = nn;
+    __syncthreads();
+    for (int w = kFinishThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            se[threadIdx.x] += se[threadIdx.x + w];
+            sn[threadIdx.x] += sn[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (energies) energies[b] = se[0] / sn[0];
+        if (norms) norms[b] = sn[0];
+        if (unnorm) unnorm[b] = se[0];
+    }
 }
 
 // One block per (state, parameter): threads sum strided partials, then a
@@ -294,8 +309,9 @@ cudaError_t launch_apply_h(const GroupDesc *groups, int n_groups, const uint32_t
 
 cudaError_t launch_energy_finish(const double *partials, int bps, int batch, double *energies,
                                  double *norms, double *unnorm, cudaStream_t s) {
-    k_energy_finish<<<(batch + 127) / 128, 128, 0, s>>>(partials, bps, batch, energies, norms,
-                                                        unnorm);
+    if (batch <= 0) return cudaSuccess;
+    k_energy_finish<<<batch, kFinishThreads, 0, s>>>(partials, bps, batch, energies, norms,
+                                                     unnorm);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,13 @@ __device__ __forceinline__ float flip_sign(float v, uint32_t s) {
     return __int_as_float(__float_as_int(v) ^ (int)(s << 31));
 }
 
+// Truth table of bit j of the register index r over r = 0..31 (bit r of the
+// result is bit j of r).
+__host__ __device__ constexpr uint32_t reg_bit_table(int j) {
+    return j == 0 ? 0xAAAAAAAAu : j == 1 ? 0xCCCCCCCCu : j == 2 ? 0xF0F0F0F0u
+         : j == 3 ? 0xFF00FF00u : 0xFFFF0000u;
+}
+
 template <typename C>
 __device__ __forceinline__ C cmul(C x, C d) {
     C r;
@@ -206,37 +213,77 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                     }
                 }
                 if (!active) continue;
-                // Both butterfly forms share one shape once the operands are
-                // chosen by the mode: with (P, Q) = (x, y) in tan mode and
+                // FP64: both butterfly forms share one shape once the operands
+                // are chosen by the mode: with (P, Q) = (x, y) in tan mode and
                 // (y, x) in cot mode,
                 //   forward  [[1,-t],[t,1]] / [[u,-1],[1,u]]:
                 //     y' = fma(c, P, Q),  x' = s * fma(-c, Q, P)
                 //   backward (transposes):
                 //     x' = fma(c, Q, P),  y' = s * fma(-c, P, Q)
                 // with s = -1 in cot mode (an integer sign flip).  Selecting
-                // operands instead of branching keeps every DFMA useful.
+                // operands keeps every DFMA useful on the slow FP64 pipe.  FP32
+                // branches on the (block-uniform) mode around the whole register
+                // loop instead: no selects on the busier integer pipe.
                 const uint32_t md = (uint32_t)rc.mode;
+                if constexpr (sizeof(T) == 8) {
 #pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    if (r & (1 << j)) continue;
-                    const int r1 = r | (1 << j);
+                    for (int r = 0; r < NR; ++r) {
+                        if (r & (1 << j)) continue;
+                        const int r1 = r | (1 << j);
 #pragma unroll
-                    for (int bufi = 0; bufi < (BWD ? 2 : 1); ++bufi) {
-                        C *u = bufi ? w : v;
-                        const C x = u[r], y = u[r1];
-                        C P, Q;
-                        P.x = md ? y.x : x.x;  P.y = md ? y.y : x.y;
-                        Q.x = md ? x.x : y.x;  Q.y = md ? x.y : y.y;
-                        if (!BWD) {
-                            u[r1].x = fma(cv, P.x, Q.x);
-                            u[r1].y = fma(cv, P.y, Q.y);
-                            u[r].x = flip_sign(fma(-cv, Q.x, P.x), md);
-                            u[r].y = flip_sign(fma(-cv, Q.y, P.y), md);
-                        } else {
-                            u[r].x = fma(cv, Q.x, P.x);
-                            u[r].y = fma(cv, Q.y, P.y);
-                            u[r1].x = flip_sign(fma(-cv, P.x, Q.x), md);
-                            u[r1].y = flip_sign(fma(-cv, P.y, Q.y), md);
+                        for (int bufi = 0; bufi < (BWD ? 2 : 1); ++bufi) {
+                            C *u = bufi ? w : v;
+                            const C x = u[r], y = u[r1];
+                            C P, Q;
+                            P.x = md ? y.x : x.x;  P.y = md ? y.y : x.y;
+                            Q.x = md ? x.x : y.x;  Q.y = md ? x.y : y.y;
+                            if (!BWD) {
+                                u[r1].x = fma(cv, P.x, Q.x);
+                                u[r1].y = fma(cv, P.y, Q.y);
+                                u[r].x = flip_sign(fma(-cv, Q.x, P.x), md);
+                                u[r].y = flip_sign(fma(-cv, Q.y, P.y), md);
+                            } else {
+                                u[r].x = fma(cv, Q.x, P.x);
+                                u[r].y = fma(cv, Q.y, P.y);
+                                u[r1].x = flip_sign(fma(-cv, P.x, Q.x), md);
+                                u[r1].y = flip_sign(fma(-cv, P.y, Q.y), md);
+                            }
+                        }
+                    }
+                } else if (md == 0) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        if (r & (1 << j)) continue;
+                        const int r1 = r | (1 << j);
+#pragma unroll
+                        for (int bufi = 0; bufi < (BWD ? 2 : 1); ++bufi) {
+                            C *u = bufi ? w : v;
+                            const C x = u[r], y = u[r1];
+                            if (!BWD) {   // [[1,-t],[t,1]]
+                                u[r].x = fma(-cv, y.x, x.x);  u[r].y = fma(-cv, y.y, x.y);
+                                u[r1].x = fma(cv, x.x, y.x);  u[r1].y = fma(cv, x.y, y.y);
+                            } else {      // transpose: [[1,t],[-t,1]]
+                                u[r].x = fma(cv, y.x, x.x);    u[r].y = fma(cv, y.y, x.y);
+                                u[r1].x = fma(-cv, x.x, y.x);  u[r1].y = fma(-cv, x.y, y.y);
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        if (r & (1 << j)) continue;
+                        const int r1 = r | (1 << j);
+#pragma unroll
+                        for (int bufi = 0; bufi < (BWD ? 2 : 1); ++bufi) {
+                            C *u = bufi ? w : v;
+                            const C x = u[r], y = u[r1];
+                            if (!BWD) {   // [[u,-1],[1,u]]
+                                u[r].x = fma(cv, x.x, -y.x);  u[r].y = fma(cv, x.y, -y.y);
+                                u[r1].x = fma(cv, y.x, x.x);  u[r1].y = fma(cv, y.y, x.y);
+                            } else {      // transpose: [[u,1],[-1,u]]
+                                u[r].x = fma(cv, x.x, y.x);    u[r].y = fma(cv, x.y, y.y);
+                                u[r1].x = fma(cv, y.x, -x.x);  u[r1].y = fma(cv, y.y, -x.y);
+                            }
                         }
                     }
                 }
@@ -274,16 +321,43 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
             if (active) {
                 const uint32_t e0 = elem_of(t, 0, chunk, R);
                 const uint32_t g0 = g32(e0);
-                // g32 is XOR-linear over disjoint tile bits: g32(e0 | r<<chunk) = g0 ^ lin(r<<chunk)
-                auto lin = [&](uint32_t e) -> uint32_t {
-                    return (e & lowmask) | ((e >> m) << a);
-                };
+                // CZ signs of all NR registers as one mask (bit r = register r).
+                // Register r holds global index g = g0 ^ L_r, L_r the global
+                // image of r << chunk, and the CZ chain sign is Q(g) =
+                // parity(g & (g >> 1) & cz).  Q is quadratic over GF(2):
+                //   Q(g0 ^ L) = Q(g0) ^ Q(L) ^ parity(L & W),
+                //   W = ((g0 & cz) << 1) ^ ((g0 >> 1) & cz),
+                // where parity(L_r & W) is linear in the bits of r (the bits of
+                // W at the chunk's global positions) and Q(L_r) comes from the
+                // CZ pairs that join two adjacent bits of the chunk.
+                uint32_t sm;
+                {
+                    constexpr uint32_t kFull = NR >= 32 ? 0xffffffffu : ((1u << NR) - 1u);
+                    const uint32_t W = ((g0 & cz) << 1) ^ ((g0 >> 1) & cz);
+                    const int lo_cnt = min(max(m - chunk, 0), R);
+                    uint32_t wv = (W >> chunk) & ((1u << lo_cnt) - 1u);
+                    if (lo_cnt < R)
+                        wv |= ((W >> (a + max(chunk - m, 0))) & ((1u << (R - lo_cnt)) - 1u)) << lo_cnt;
+                    // tile bits b whose qubits b, b+1 are adjacent and CZ-coupled
+                    uint32_t czt = 0u;
+                    if (m >= 1) {
+                        czt = cz & ((1u << (m - 1)) - 1u);
+                        if (a == m && k > m) czt |= cz & (1u << (m - 1));
+                    }
+                    if (k - m >= 2) czt |= ((cz >> a) & ((1u << (k - m - 1)) - 1u)) << m;
+                    const uint32_t adj = czt >> chunk;
+                    sm = (__popc(g0 & (g0 >> 1) & cz) & 1u) ? kFull : 0u;
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        if ((wv >> j) & 1u) sm ^= reg_bit_table(j);
+                        if (j + 1 < R && ((adj >> j) & 1u)) sm ^= reg_bit_table(j) & reg_bit_table(j + 1);
+                    }
+                    sm &= kFull;
+                }
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
-                    const uint32_t er = (uint32_t)r << chunk;
-                    const uint32_t e = e0 | er;
-                    const uint32_t g = g0 ^ lin(er);
-                    const uint32_t sgn = __popc(g & (g >> 1) & cz) & 1u;
+                    const uint32_t e = e0 + ((uint32_t)r << chunk);   // disjoint bits
+                    const uint32_t sgn = (sm >> r) & 1u;
                     const C dv = env.diag(op.slot, e);
                     if (!BWD) {
                         C y = cmul(v[r], dv);

@@ -24,8 +24,8 @@ struct Group {        // one qubit group = the tile bits of one kind of pass
 };
 
 struct PlanOptions {
-    int tile_bits_max = 0;  // 0: default (11 for C128, 12 for C64)
-    int run_bits = 0;       // 0: default (2 for C128, 4 for C64: 64-byte runs)
+    int tile_bits_max = 0;  // 0: default (11 for C128 and C64)
+    int run_bits = 0;       // 0: default (2 for C128, 3 for C64)
     int reg_bits = 0;       // 0: default (3 for C128, 4 for C64)
 };
 
@@ -229,14 +229,14 @@ struct Round {
 };
 
 // Zero fields take the defaults, the fastest plans measured on GB300 for the
-// forward and the adjoint passes: FP64 tiles of 2^11 amplitudes with 4-amplitude
-// runs and 8 amplitudes per thread; FP32 tiles of 2^12 with 16-amplitude runs
-// and 16 per thread (256 threads each).  Plans with fewer passes (larger
-// tiles, or 32 amplitudes per thread) measured slower.
+// forward and the adjoint passes: tiles of 2^11 amplitudes; FP64 with runs of
+// at least 4 amplitudes and 8 amplitudes per thread (256 threads), FP32 with
+// runs of at least 8 and 16 per thread (128 threads).  Plans with fewer
+// passes (larger tiles, or 32 amplitudes per thread) measured slower.
 PlanOptions resolve(const PlanOptions &o, vqe_precision prec) {
     PlanOptions r;
-    r.tile_bits_max = o.tile_bits_max ? o.tile_bits_max : (prec == VQE_C128 ? 11 : 12);
-    r.run_bits = o.run_bits ? o.run_bits : (prec == VQE_C128 ? 2 : 4);
+    r.tile_bits_max = o.tile_bits_max ? o.tile_bits_max : 11;
+    r.run_bits = o.run_bits ? o.run_bits : (prec == VQE_C128 ? 2 : 3);
     r.reg_bits = o.reg_bits ? o.reg_bits : (prec == VQE_C128 ? 3 : 4);
     return r;
 }

@@ -28,6 +28,10 @@ N_QUBITS, DEPTH, SITES, N_VEC = 20, 10, 10, 1000
 U_VALUES = (2.0, 4.0, 8.0)
 CHUNK = 64                      # states per workspace chunk (64 x 16 MiB = 1 GiB > L2)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
+# DRAM read+write bytes per state of one forward-pass launch (k_pass<double,3,fwd>,
+# 20 qubits, default plan): 478.7 MB for a 16-state launch in the ncu capture
+# of profiles/k_pass_c128_fwd_20q.md.  None once the kernel changes.
+PASS_DRAM_BYTES_PER_STATE = 478.712832e6 / 16
 METRIC = "energy+gradient evals/s at 8-32 qubits; achieved HBM GB/s vs GB300 peak"
 WORKLOAD = ("20q FP64 (complex128) 10-site periodic 1D Hubbard t=1 U in {2,4,8}, "
             "HEA depth 10, 1000 param vectors per U, energy only")
@@ -253,14 +257,11 @@ def run_gpu(args, world, rank, local, pg):
     bytes_fwd = len(U_VALUES) * N_VEC * args.steps * n_pass * 2 * 16 * (1 << N_QUBITS)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            with open(tfile) as f:
-                traffic = json.load(f).get("k_pass_fwd_c128_20q")
-        except (OSError, ValueError):
-            traffic = None
+    # DRAM bytes (read + write) of one launch of this kernel, from the ncu
+    # capture summarised in profiles/k_pass_c128_fwd_20q.md (dram__bytes_read.sum +
+    # dram__bytes_write.sum per state, times the states of one bench launch).
+    # Set to None whenever the kernel changes until it is captured again.
+    traffic = PASS_DRAM_BYTES_PER_STATE * CHUNK if PASS_DRAM_BYTES_PER_STATE else None
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                 "traffic": traffic, "kernel": "k_pass<double,3,fwd>",

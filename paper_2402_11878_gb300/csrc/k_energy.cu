@@ -12,6 +12,8 @@
 // two orientations contribute equal real parts.  Accumulation is FP64 per
 // thread; reductions go through fixed-order warp shuffles, a block partial
 // per CTA, and a fixed-order final sum, so results are bitwise reproducible.
+#include <algorithm>
+
 #include "vqe_internal.h"
 
 namespace vqe {
@@ -80,8 +82,9 @@ __device__ __forceinline__ void block_reduce2(double &a, double &b, double *sh) 
 template <typename T>
 __global__ void __launch_bounds__(kEnergyThreads)
 k_energy_cols(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__restrict__ tz,
-              const T *__restrict__ tc, int n, const typename EV2<T>::type *__restrict__ psi,
-              size_t stride, double *__restrict__ partials, int block_off, int bps_total) {
+              const T *__restrict__ tc, const T *__restrict__ hdiag, int n,
+              const typename EV2<T>::type *__restrict__ psi, size_t stride,
+              double *__restrict__ partials, int block_off, int bps_total) {
     using C = typename EV2<T>::type;
     constexpr int J = 4;   // pairs per thread and iteration: one load of each term serves J pairs
     __shared__ double sh[2 * (kEnergyThreads / 32)];
@@ -123,8 +126,16 @@ k_energy_cols(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t
                     f0[j] = T(0);
                     f1[j] = T(0);
                 }
-                sign_sums<T, J>(i0, f0, tz, tc, G.t_begin, G.t_mid);
-                sign_sums<T, J>(i1, f1, tz, tc, G.t_begin, G.t_mid);
+                if (hdiag) {
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        f0[j] = __ldg(hdiag + i0[j]);
+                        f1[j] = __ldg(hdiag + i1[j]);
+                    }
+                } else {
+                    sign_sums<T, J>(i0, f0, tz, tc, G.t_begin, G.t_mid);
+                    sign_sums<T, J>(i1, f1, tz, tc, G.t_begin, G.t_mid);
+                }
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
                     part = fma(a0[j], f0[j], fma(a1[j], f1[j], part));
@@ -164,8 +175,9 @@ k_energy_cols(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t
 template <typename T>
 __global__ void __launch_bounds__(kEnergyThreads)
 k_apply_h(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__restrict__ tz,
-          const T *__restrict__ tc, int n, const typename EV2<T>::type *__restrict__ psi,
-          typename EV2<T>::type *__restrict__ lam, size_t stride, double *__restrict__ partials) {
+          const T *__restrict__ tc, const T *__restrict__ hdiag, int n,
+          const typename EV2<T>::type *__restrict__ psi, typename EV2<T>::type *__restrict__ lam,
+          size_t stride, double *__restrict__ partials) {
     using C = typename EV2<T>::type;
     constexpr int J = 4;
     __shared__ double sh[2 * (kEnergyThreads / 32)];
@@ -198,7 +210,12 @@ k_apply_h(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__
                 fa[j] = T(0);
                 fb[j] = T(0);
             }
-            sign_sums<T, J>(i, fa, tz, tc, G.t_begin, G.t_mid);
+            if (G.x == 0u && hdiag) {
+#pragma unroll
+                for (int j = 0; j < J; ++j) fa[j] = __ldg(hdiag + i[j]);
+            } else {
+                sign_sums<T, J>(i, fa, tz, tc, G.t_begin, G.t_mid);
+            }
             if (G.t_end > G.t_mid) sign_sums<T, J>(i, fb, tz, tc, G.t_mid, G.t_end);
 #pragma unroll
             for (int j = 0; j < J; ++j) {
@@ -227,6 +244,37 @@ k_apply_h(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__
         o[2] = 0.0;
     }
 }
+
+// Diagonal of H: D_i = sum over the terms of the x = 0 group of
+// c_t (-1)^{popc(i & z_t)}, summed in FP64 in term order and stored in T.
+// Built once per Hamiltonian (and cutoff); the expectation and apply-H
+// kernels then read D_i instead of evaluating every Z string per amplitude.
+template <typename T>
+__global__ void k_build_hdiag(const uint32_t *__restrict__ z, const double *__restrict__ c,
+                              int n_terms, int n, T *__restrict__ D) {
+    const uint64_t dim = 1ull << n;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+        double f = 0.0;
+        for (int t = 0; t < n_terms; ++t)
+            f += sgn_flip(__ldg(c + t), __popc((uint32_t)i & __ldg(z + t)) & 1u);
+        D[i] = (T)f;
+    }
+}
+
+template <typename T>
+cudaError_t launch_build_hdiag(const uint32_t *z, const double *c, int n_terms, int n_qubits,
+                               void *D, int sms, cudaStream_t s) {
+    const uint64_t dim = 1ull << n_qubits;
+    const uint64_t want = (dim + 255) / 256;
+    const unsigned blocks = (unsigned)std::min<uint64_t>(want, (uint64_t)sms * 16);
+    k_build_hdiag<T><<<blocks, 256, 0, s>>>(z, c, n_terms, n_qubits, static_cast<T *>(D));
+    return cudaGetLastError();
+}
+template cudaError_t launch_build_hdiag<float>(const uint32_t *, const double *, int, int, void *,
+                                               int, cudaStream_t);
+template cudaError_t launch_build_hdiag<double>(const uint32_t *, const double *, int, int,
+                                                void *, int, cudaStream_t);
 
 // One block per state: each thread sums a strided subset of the block
 // partials, then a fixed-order tree over the block (bitwise reproducible).
@@ -283,12 +331,14 @@ k_grad_finish(const double *__restrict__ part, size_t part_stride, const int *__
 
 template <typename T>
 cudaError_t launch_energy(const GroupDesc *groups, int n_groups, const uint32_t *tz,
-                          const double *tc, int n_qubits, int batch, const void *psi,
-                          size_t state_stride, double *partials, int bps, cudaStream_t s) {
+                          const double *tc, const void *hdiag, int n_qubits, int batch,
+                          const void *psi, size_t state_stride, double *partials, int bps,
+                          cudaStream_t s) {
     using C = typename EV2<T>::type;
     dim3 grid(bps, batch);
     k_energy_cols<T><<<grid, kEnergyThreads, 0, s>>>(groups, n_groups, tz,
-                                                     reinterpret_cast<const T *>(tc), n_qubits,
+                                                     reinterpret_cast<const T *>(tc),
+                                                     static_cast<const T *>(hdiag), n_qubits,
                                                      static_cast<const C *>(psi), state_stride,
                                                      partials, 0, bps);
     return cudaGetLastError();
@@ -296,12 +346,14 @@ cudaError_t launch_energy(const GroupDesc *groups, int n_groups, const uint32_t 
 
 template <typename T>
 cudaError_t launch_apply_h(const GroupDesc *groups, int n_groups, const uint32_t *tz,
-                           const double *tc, int n_qubits, int batch, const void *psi, void *lam,
-                           size_t state_stride, double *partials, int bps, cudaStream_t s) {
+                           const double *tc, const void *hdiag, int n_qubits, int batch,
+                           const void *psi, void *lam, size_t state_stride, double *partials,
+                           int bps, cudaStream_t s) {
     using C = typename EV2<T>::type;
     dim3 grid(bps, batch);
     k_apply_h<T><<<grid, kEnergyThreads, 0, s>>>(groups, n_groups, tz,
-                                                 reinterpret_cast<const T *>(tc), n_qubits,
+                                                 reinterpret_cast<const T *>(tc),
+                                                 static_cast<const T *>(hdiag), n_qubits,
                                                  static_cast<const C *>(psi),
                                                  static_cast<C *>(lam), state_stride, partials);
     return cudaGetLastError();
@@ -325,17 +377,17 @@ cudaError_t launch_grad_finish(const double *part, size_t part_stride, const int
 }
 
 template cudaError_t launch_energy<float>(const GroupDesc *, int, const uint32_t *, const double *,
-                                          int, int, const void *, size_t, double *, int,
-                                          cudaStream_t);
+                                          const void *, int, int, const void *, size_t, double *,
+                                          int, cudaStream_t);
 template cudaError_t launch_energy<double>(const GroupDesc *, int, const uint32_t *,
-                                           const double *, int, int, const void *, size_t,
-                                           double *, int, cudaStream_t);
+                                           const double *, const void *, int, int, const void *,
+                                           size_t, double *, int, cudaStream_t);
 template cudaError_t launch_apply_h<float>(const GroupDesc *, int, const uint32_t *,
-                                           const double *, int, int, const void *, void *, size_t,
-                                           double *, int, cudaStream_t);
+                                           const double *, const void *, int, int, const void *,
+                                           void *, size_t, double *, int, cudaStream_t);
 template cudaError_t launch_apply_h<double>(const GroupDesc *, int, const uint32_t *,
-                                            const double *, int, int, const void *, void *,
-                                            size_t, double *, int, cudaStream_t);
+                                            const double *, const void *, int, int, const void *,
+                                            void *, size_t, double *, int, cudaStream_t);
 
 }  // namespace vqe
 
@@ -349,11 +401,11 @@ template cudaError_t launch_apply_h<double>(const GroupDesc *, int, const uint32
 namespace vqe {
 
 template <typename T, int K>
-__global__ void __launch_bounds__(kEnergyWinThreads)
+__global__ void __launch_bounds__(kEnergyWinThreads, 2)
 k_energy_win(WinDesc W, const GroupDesc *__restrict__ groups, const int *__restrict__ wgroups,
-             const uint32_t *__restrict__ tz, const T *__restrict__ tc, int n,
-             const typename EV2<T>::type *__restrict__ psi, size_t stride,
-             double *__restrict__ partials, int bps_total) {
+             const uint32_t *__restrict__ tz, const T *__restrict__ tc,
+             const T *__restrict__ hdiag, int n, const typename EV2<T>::type *__restrict__ psi,
+             size_t stride, double *__restrict__ partials, int bps_total) {
     using C = typename EV2<T>::type;
     constexpr uint32_t size = 1u << K;
     constexpr int EPT = size / kEnergyWinThreads;   // tile elements per thread
@@ -382,10 +434,22 @@ k_energy_win(WinDesc W, const GroupDesc *__restrict__ groups, const int *__restr
         }
         nrm = (double)pn;
     }
+    // FP32: group totals are summed in FP32 over runs of kRun groups and each
+    // run is folded into the FP64 accumulator (FP64 adds are scarce).
+    constexpr int kRun = 8;
+    T run = T(0);
+    int in_run = 0;
     for (int gi = W.g_begin; gi < W.g_end; ++gi) {
         const GroupDesc G = groups[wgroups[gi]];
         T part = T(0);
-        if (G.x == 0u) {
+        if (G.x == 0u && hdiag) {
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                const uint32_t e = threadIdx.x + j * kEnergyWinThreads;
+                const C x = sp[e];
+                part = fma(fma(x.x, x.x, x.y * x.y), __ldg(hdiag + g32(e)), part);
+            }
+        } else if (G.x == 0u) {
             uint32_t ge[EPT];
             T f[EPT];
 #pragma unroll
@@ -426,8 +490,18 @@ k_energy_win(WinDesc W, const GroupDesc *__restrict__ groups, const int *__restr
             }
             part *= T(2);
         }
-        acc += (double)part;
+        if constexpr (sizeof(T) == 4) {
+            run += part;
+            if (++in_run == kRun) {
+                acc += (double)run;
+                run = T(0);
+                in_run = 0;
+            }
+        } else {
+            acc += (double)part;
+        }
     }
+    if constexpr (sizeof(T) == 4) acc += (double)run;
     block_reduce2(acc, nrm, sh);
     if (threadIdx.x == 0) {
         double *o = partials + ((size_t)b * bps_total + W.block_off + blockIdx.x) * 3;
@@ -439,9 +513,9 @@ k_energy_win(WinDesc W, const GroupDesc *__restrict__ groups, const int *__restr
 
 template <typename T>
 cudaError_t launch_energy_win(const WinDesc &W, const GroupDesc *groups, const int *wgroups,
-                              const uint32_t *tz, const double *tc, int n_qubits, int batch,
-                              const void *psi, size_t state_stride, double *partials,
-                              int bps_total, cudaStream_t s) {
+                              const uint32_t *tz, const double *tc, const void *hdiag,
+                              int n_qubits, int batch, const void *psi, size_t state_stride,
+                              double *partials, int bps_total, cudaStream_t s) {
     using C = typename EV2<T>::type;
     const size_t smem = (size_t(1) << W.k) * sizeof(C);
     auto kern = W.k == 13 ? k_energy_win<T, 13> : (W.k == 12 ? k_energy_win<T, 12> : nullptr);
@@ -452,7 +526,8 @@ cudaError_t launch_energy_win(const WinDesc &W, const GroupDesc *groups, const i
     }
     dim3 grid((unsigned)(1ull << (n_qubits - W.k)), batch);
     kern<<<grid, kEnergyWinThreads, smem, s>>>(W, groups, wgroups, tz,
-                                               reinterpret_cast<const T *>(tc), n_qubits,
+                                               reinterpret_cast<const T *>(tc),
+                                               static_cast<const T *>(hdiag), n_qubits,
                                                static_cast<const C *>(psi), state_stride, partials,
                                                bps_total);
     return cudaGetLastError();
@@ -468,18 +543,20 @@ cudaError_t launch_energy_sub(const GroupDesc *groups, int n_groups, const uint3
     using C = typename EV2<T>::type;
     dim3 grid(bps, batch);
     k_energy_cols<T><<<grid, kEnergyThreads, 0, s>>>(groups, n_groups, tz,
-                                                     reinterpret_cast<const T *>(tc), n_qubits,
-                                                     static_cast<const C *>(psi), state_stride,
-                                                     partials, block_off, bps_total);
+                                                     reinterpret_cast<const T *>(tc), nullptr,
+                                                     n_qubits, static_cast<const C *>(psi),
+                                                     state_stride, partials, block_off, bps_total);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_energy_win<float>(const WinDesc &, const GroupDesc *, const int *,
-                                              const uint32_t *, const double *, int, int,
-                                              const void *, size_t, double *, int, cudaStream_t);
+                                              const uint32_t *, const double *, const void *, int,
+                                              int, const void *, size_t, double *, int,
+                                              cudaStream_t);
 template cudaError_t launch_energy_win<double>(const WinDesc &, const GroupDesc *, const int *,
-                                               const uint32_t *, const double *, int, int,
-                                               const void *, size_t, double *, int, cudaStream_t);
+                                               const uint32_t *, const double *, const void *, int,
+                                               int, const void *, size_t, double *, int,
+                                               cudaStream_t);
 template cudaError_t launch_energy_sub<float>(const GroupDesc *, int, const uint32_t *,
                                               const double *, int, int, const void *, size_t,
                                               double *, int, int, int, cudaStream_t);

@@ -69,6 +69,11 @@ struct vqe_ctx {
     DevBuf d_wgroups, d_wide;
     int n_wide = 0;
     int win_tiles = 0;   // columns of all windows per state
+    // diagonal of H (one T per basis state), built when it fits in a quarter
+    // of the free device memory; null: the x = 0 terms are evaluated inline
+    DevBuf d_hdiag, d_hdiag_z, d_hdiag_c;
+    bool hdiag_ok = false;
+    const void *hdiag() const { return hdiag_ok ? d_hdiag.p : nullptr; }
 
     // ansatz plans: [0] energy evaluations (forward only), [1] gradients (forward + backward)
     struct DevPlan {
@@ -703,6 +708,30 @@ vqe_status build_ham_plan(vqe_ctx *h) {
     }
     h->n_groups = int(hp.groups.size());
     vqe_status st;
+    h->hdiag_ok = false;
+    if (!hp.groups.empty() && hp.groups[0].x == 0u && hp.groups[0].t_mid > hp.groups[0].t_begin) {
+        const size_t bytes = h->state_elems() * (h->prec == VQE_C128 ? sizeof(double) : sizeof(float));
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        if (bytes <= free_b / 4 + h->d_hdiag.bytes) {
+            const GroupDesc &G0 = hp.groups[0];
+            std::vector<uint32_t> z0(hp.tz.begin() + G0.t_begin, hp.tz.begin() + G0.t_mid);
+            std::vector<double> c0(hp.tc.begin() + G0.t_begin, hp.tc.begin() + G0.t_mid);
+            if ((st = ensure(h, h->d_hdiag, bytes, "diagonal of H")) != VQE_OK) return st;
+            if ((st = upload(h, h->d_hdiag_z, z0, "diagonal terms")) != VQE_OK) return st;
+            if ((st = upload(h, h->d_hdiag_c, c0, "diagonal terms")) != VQE_OK) return st;
+            cudaError_t e = h->prec == VQE_C128
+                ? launch_build_hdiag<double>(static_cast<const uint32_t *>(h->d_hdiag_z.p),
+                                             static_cast<const double *>(h->d_hdiag_c.p),
+                                             int(z0.size()), h->n, h->d_hdiag.p, h->sms, h->stream)
+                : launch_build_hdiag<float>(static_cast<const uint32_t *>(h->d_hdiag_z.p),
+                                            static_cast<const double *>(h->d_hdiag_c.p),
+                                            int(z0.size()), h->n, h->d_hdiag.p, h->sms, h->stream);
+            if (e != cudaSuccess) return fail(h, VQE_ERR_CUDA, cudaGetErrorString(e));
+            h->stats.kernel_launches++;
+            h->hdiag_ok = true;
+        }
+    }
     if ((st = upload(h, h->d_groups, hp.groups, "groups")) != VQE_OK) return st;
     if ((st = upload(h, h->d_tz, hp.tz, "terms")) != VQE_OK) return st;
     if (h->prec == VQE_C128) {
@@ -845,8 +874,9 @@ vqe_status run_energy(vqe_ctx *h, int B, const void *psi, double *energies, doub
             VQE_CUDA(h, launch_energy_win<T>(W, static_cast<const GroupDesc *>(h->d_groups.p),
                                              static_cast<const int *>(h->d_wgroups.p),
                                              static_cast<const uint32_t *>(h->d_tz.p),
-                                             static_cast<const double *>(h->d_tc.p), h->n, B, psi,
-                                             h->state_elems(), part, bps_total, h->stream));
+                                             static_cast<const double *>(h->d_tc.p), h->hdiag(),
+                                             h->n, B, psi, h->state_elems(), part, bps_total,
+                                             h->stream));
             h->stats.kernel_launches++;
         }
         if (h->n_wide) {
@@ -866,7 +896,7 @@ vqe_status run_energy(vqe_ctx *h, int B, const void *psi, double *energies, doub
     const int mk = prof_begin(h, 1);
     VQE_CUDA(h, launch_energy<T>(static_cast<const GroupDesc *>(h->d_groups.p), h->n_groups,
                                  static_cast<const uint32_t *>(h->d_tz.p),
-                                 static_cast<const double *>(h->d_tc.p), h->n, B, psi,
+                                 static_cast<const double *>(h->d_tc.p), h->hdiag(), h->n, B, psi,
                                  h->state_elems(), static_cast<double *>(h->d_epart.p), bps,
                                  h->stream));
     prof_end(h, mk, 1);
@@ -897,7 +927,8 @@ vqe_status gradient_chunk(vqe_ctx *h, const double *params_dev, int B, double *g
     const int mk_h = prof_begin(h, 2);
     VQE_CUDA(h, launch_apply_h<T>(static_cast<const GroupDesc *>(h->d_groups.p), h->n_groups,
                                   static_cast<const uint32_t *>(h->d_tz.p),
-                                  static_cast<const double *>(h->d_tc.p), h->n, B, psi, lam, N,
+                                  static_cast<const double *>(h->d_tc.p), h->hdiag(), h->n, B, psi,
+                                  lam, N,
                                   static_cast<double *>(h->d_epart.p), bps, s));
     prof_end(h, mk_h, 1);
     VQE_CUDA(h, launch_energy_finish(static_cast<double *>(h->d_epart.p), bps, B, E, nullptr,
@@ -1040,7 +1071,8 @@ vqe_status vqe_destroy(vqe_handle h) {
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->plan[0].release();
     h->plan[1].release();
-    for (DevBuf *b : {&h->d_groups, &h->d_tz, &h->d_tc, &h->d_wgroups, &h->d_wide, &h->ws_own, &h->d_params, &h->d_coefs,
+    for (DevBuf *b : {&h->d_groups, &h->d_tz, &h->d_tc, &h->d_wgroups, &h->d_wide, &h->d_hdiag,
+                      &h->d_hdiag_z, &h->d_hdiag_c, &h->ws_own, &h->d_params, &h->d_coefs,
                       &h->d_dtab, &h->d_gpart, &h->d_epart, &h->d_out, &h->hb_params,
                       &h->hb_e, &h->hb_n, &h->hb_g, &h->d_err})
         b->release();

@@ -127,21 +127,28 @@ cudaError_t launch_pass(const PassDesc *desc_dev, const PassDesc &desc_host, int
 
 template <typename T>
 cudaError_t launch_energy(const GroupDesc *groups, int n_groups, const uint32_t *tz,
-                          const double *tc, int n_qubits, int batch, const void *psi,
-                          size_t state_stride, double *partials, int blocks_per_state,
-                          cudaStream_t s);
+                          const double *tc, const void *hdiag, int n_qubits, int batch,
+                          const void *psi, size_t state_stride, double *partials,
+                          int blocks_per_state, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_apply_h(const GroupDesc *groups, int n_groups, const uint32_t *tz,
-                           const double *tc, int n_qubits, int batch, const void *psi,
-                           void *lam, size_t state_stride, double *partials,
+                           const double *tc, const void *hdiag, int n_qubits, int batch,
+                           const void *psi, void *lam, size_t state_stride, double *partials,
                            int blocks_per_state, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_energy_win(const WinDesc &W, const GroupDesc *groups, const int *wgroups,
-                              const uint32_t *tz, const double *tc, int n_qubits, int batch,
-                              const void *psi, size_t state_stride, double *partials,
-                              int bps_total, cudaStream_t s);
+                              const uint32_t *tz, const double *tc, const void *hdiag,
+                              int n_qubits, int batch, const void *psi, size_t state_stride,
+                              double *partials, int bps_total, cudaStream_t s);
+
+// Diagonal of H from the x = 0 group's terms (z masks, FP64 coefficients with
+// the Pauli phase folded): D[i] for i < 2^n_qubits, stored as T.  `hdiag`
+// arguments of the expectation kernels may be null (terms evaluated inline).
+template <typename T>
+cudaError_t launch_build_hdiag(const uint32_t *z, const double *c, int n_terms, int n_qubits,
+                               void *D, int sms, cudaStream_t s);
 template <typename T>
 cudaError_t launch_energy_sub(const GroupDesc *groups, int n_groups, const uint32_t *tz,
                               const double *tc, int n_qubits, int batch, const void *psi,

@@ -198,3 +198,52 @@ def test_energy_windows_emulated(oracle_mod, prec, case):
     e, nn = energy_windows(ham, win, n, psi)
     e_ref, _, n_ref = oracle_mod.expectation(psi, H.x, H.z, H.c)
     assert abs(e - e_ref) < 1e-11 * H.sum_abs() and abs(nn - n_ref) < 1e-12
+
+
+def _tile_map_ok(n, k, m, a):
+    """Tile bits [0, m) and [a, a + k - m) (global positions), the other n - k
+    bits from the tile number: the map (tile, e) -> global index must be a
+    bijection onto [0, 2^n) (checked structurally, as the kernels compute it)."""
+    assert 0 <= m <= k <= n
+    assert a >= m and a + (k - m) <= n
+    if k == m:
+        assert a == m   # the low tile: base bits are [k, n)
+    mid = a - m
+    tiles = 1 << (n - k)
+    # the largest tile number maps to the largest base; with every tile bit set
+    # the global index is 2^n - 1, never beyond
+    t = tiles - 1
+    base = ((t & ((1 << mid) - 1)) << m) | ((t >> mid) << (a + (k - m)))
+    e = (1 << k) - 1
+    g = base | (e & ((1 << m) - 1)) | ((e >> m) << a)
+    assert g == (1 << n) - 1
+    # tile and in-tile bits are disjoint
+    tile_bits = ((1 << m) - 1) | (((1 << (k - m)) - 1) << a)
+    assert base & tile_bits == 0
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n,D", [(24, 12), (26, 4), (28, 4), (32, 8)])
+def test_full_size_index_ranges(n, D, prec):
+    """At the full sizes the GPU runs (up to 32 qubits), every pass's tile map
+    stays inside [0, 2^n) and every table offset fits the 31-bit fields."""
+    pl = P.plan(n, D, prec)
+    for d in pl["fwd"] + pl["bwd"]:
+        _tile_map_ok(n, d.k, d.m, d.a)
+        for s in range(d.n_slots):
+            assert 0 <= d.slot_grad_off[s] < 2 ** 31
+            assert 0 <= d.slot_dtab_off[s] < 2 ** 31
+            assert (d.slot_czmask[s] >> (n - 1)) == 0
+    tiles_max = max(1 << (n - d.k) for d in pl["fwd"])
+    assert pl["grad_stride"] < 2 ** 31
+    assert tiles_max <= 2 ** 31 - 1   # grid.x
+    H = vi.hubbard_2d_snake(4, 4, 1.0, 4.0) if n == 32 else vi.hubbard_1d(n // 2, 1.0, 4.0, periodic=True)
+    w = P.windows(n, prec, H.x, H.z, H.c)
+    for W in w["windows"]:
+        _tile_map_ok(n, W.k, W.m, W.a)
+        assert (1 << (n - W.k)) <= 2 ** 31 - 1
+    hp = P.hamiltonian(n, H.x, H.z, H.c)
+    for W in w["windows"]:
+        win_bits = ((1 << W.m) - 1) | (((1 << (W.k - W.m)) - 1) << W.a)
+        for gi in w["wgroups"][W.g_begin:W.g_end]:
+            assert hp["groups"][gi].x & ~win_bits == 0, "group X mask outside its window"

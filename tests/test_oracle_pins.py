@@ -233,3 +233,49 @@ def test_gradient_against_dense_derivative(oracle_mod):
         up, um = dn.ansatz_unitary(n, depth, pp)[:, 0], dn.ansatz_unitary(n, depth, pm)[:, 0]
         fd = (np.vdot(up, Hd @ up).real - np.vdot(um, Hd @ um).real) / (2 * h)
         assert abs(fd - g[j]) < 1e-7
+
+
+# ---------------------------------------------------------------- path-sum amplitudes
+
+from oracle import pathsum as _pathsum
+from dense import ansatz_unitary as _ansatz_unitary
+
+
+@pytest.mark.parametrize("n,D", [(1, 1), (2, 2), (3, 1), (4, 3), (6, 2)])
+def test_pathsum_matches_dense_unitary(n, D):
+    """Single amplitudes by the path sum equal column 0 of the Kronecker-built
+    circuit unitary (an independent construction of Eq. 6's ansatz)."""
+    p = vi.ansatz_params(100 + 7 * n + D, n, D)
+    col = _ansatz_unitary(n, D, p)[:, 0]
+    a = _pathsum.amplitudes(n, D, p, range(1 << n))
+    assert np.max(np.abs(a - col)) <= 1e-13
+
+
+@pytest.mark.parametrize("n,D", [(9, 4), (10, 6), (12, 3)])
+def test_pathsum_matches_full_state_oracle(oracle_mod, n, D):
+    p = vi.ansatz_params(200 + n + D, n, D)
+    psi = oracle_mod.ansatz_state(n, D, p)
+    idx = np.random.default_rng(n).integers(0, 1 << n, 48)
+    assert np.max(np.abs(_pathsum.amplitudes(n, D, p, idx) - psi[idx])) <= 1e-13
+
+
+def test_pathsum_closed_forms():
+    """theta = 0: |0..0>.  Depth 1 product state with the CZ chain:
+    <i|U|0> = prod_q (cos or sin)(theta_q/2) e^{-+i phi_q/2} * (-1)^{popc(i & i>>1)}."""
+    n, D = 7, 2
+    z = np.zeros(2 * n * D)
+    assert abs(_pathsum.amplitude(n, D, z, 0) - 1.0) <= 1e-15
+    assert abs(_pathsum.amplitude(n, D, z, 5)) <= 1e-15
+    n = 6
+    p = vi.ansatz_params(17, n, 1)
+    for i in (0, 1, 6, 45, 63):
+        want = 1.0 + 0j
+        for q in range(n):
+            th, ph = p[2 * q], p[2 * q + 1]
+            if (i >> q) & 1:
+                want *= np.sin(th / 2) * np.exp(0.5j * ph)
+            else:
+                want *= np.cos(th / 2) * np.exp(-0.5j * ph)
+        if bin(i & (i >> 1)).count("1") % 2:
+            want = -want
+        assert abs(_pathsum.amplitude(n, 1, p, i) - want) <= 1e-15

@@ -430,6 +430,58 @@ def run_workload(name: str, args):
                      "fp64_one_by_one_baseline": {"value": 1.0 / per_inst,
                                                    "unit": "instance evals/s",
                                                    "sample": "first 32 instances, warm handles"}})
+    elif name == "hubbard32":
+        # 32 qubits: 4x4 periodic Hubbard (snake order), depth 8.  FP64 energy on
+        # one 64 GiB caller-owned state, unslimmed and slimmed (th = 0.6 drops
+        # every hopping term); complex64 energy + adjoint gradient on psi and
+        # lambda (2 x 32 GiB).
+        H = vi.hubbard_2d_snake(4, 4, 1.0, 4.0)
+        n, D = 32, 8
+        P = torch.tensor(vi.ansatz_params(3232, n, D)[None, :], device=dev)
+        E = torch.empty(1, dtype=torch.float64, device=dev)
+        G = torch.empty(1, 2 * n * D, dtype=torch.float64, device=dev)
+        eng = pkg.Engine(n, D, "c128")
+        eng.set_hamiltonian(H.x, H.z, H.c)
+        ws = torch.empty(1 << n, dtype=torch.complex128, device=dev)
+        eng.bind_workspace(ws)
+        eng.profile(True)
+        ms128 = _timed(lambda: eng.energy_batch_dev(P, E), 1)
+        pr = eng.profile_read()
+        e_full = float(E[0])
+        kept, dropped = eng.slim(0.6)
+        ms128s = _timed(lambda: eng.energy_batch_dev(P, E), 1)
+        e_slim = float(E[0])
+        passes128 = eng.stats()["ansatz_passes"]
+        eng.close()
+        del ws
+        torch.cuda.empty_cache()
+        e64 = pkg.Engine(n, D, "c64")
+        e64.set_hamiltonian(H.x, H.z, H.c)
+        e64.profile(True)
+        ms64 = _timed(lambda: e64.gradient_batch_dev(P, G, E), 1)
+        pg = e64.profile_read()
+        e64.close()
+        torch.cuda.empty_cache()
+        flops_fwd = D * (4 * n + 6) * float(1 << n)
+        fwd128_ms = pr["forward_passes"]["ms"] / 2
+        fwd64_ms = pg["forward_passes"]["ms"] / 2
+        bwd64_ms = pg["backward_passes"]["ms"] / 2
+        npass64 = pg["forward_passes"]["launches"] // 2
+        line.update({"value": 1e3 / ms64, "dtype": "c64", "ms_per_step": ms64,
+                     "config": {"workload": "32q 4x4 periodic Hubbard (snake order, t=1, U=4), "
+                                "HEA depth 8: complex64 energy + adjoint gradient (psi, lambda: "
+                                "2 x 32 GiB); FP64 energy on a 64 GiB state"},
+                     "fp64_energy": {"s_per_eval": ms128 / 1e3, "slimmed_s_per_eval": ms128s / 1e3,
+                                     "energy": e_full, "energy_slimmed": e_slim,
+                                     "terms_kept_slimmed": kept, "sum_abs_dropped": dropped,
+                                     "forward_tflops": flops_fwd / (fwd128_ms / 1e3) / 1e12,
+                                     "forward_passes": passes128},
+                     "c64_gradient": {"forward_ms": fwd64_ms, "backward_ms": bwd64_ms,
+                                      "apply_h_ms": pg["apply_h"]["ms"] / 2,
+                                      "forward_passes": npass64,
+                                      "forward_hbm_gbs": npass64 * 2 * 8 * float(1 << n) / (fwd64_ms / 1e3) / 1e9,
+                                      "backward_hbm_gbs": npass64 * 4 * 8 * float(1 << n) / (bwd64_ms / 1e3) / 1e9,
+                                      "hbm_peak_gbs": measured_peaks().get("hbm_gbs")}})
     elif name == "small8":
         H = vi.hubbard_1d(4, 1.0, 4.0, periodic=False)
         n, D, B = 8, 4, 1024
@@ -493,7 +545,7 @@ def main():
                     help="run a small named workload for profiler captures instead of the benchmark")
     ap.add_argument("--case-batch", type=int, default=16)
     ap.add_argument("--workload", default="hubbard20",
-                    choices=["hubbard20", "molecular24", "batch512", "small8"],
+                    choices=["hubbard20", "molecular24", "batch512", "small8", "hubbard32"],
                     help="hubbard20 (default) is the benchmark line; the others report the "
                          "remaining configurations")
     ap.add_argument("--gpus", type=int, default=1)

@@ -107,7 +107,9 @@ constexpr int kPassMaxThreads = 512;
 template <typename T>
 struct GridEnv {
     using C = typename V2<T>::type;
-    static constexpr bool kDirect = true;   // first/last round straight from/to global memory
+    // first/last round straight from/to global memory: run_tile reads P, L
+    // (this state's psi and lambda) and init_zero (start from |0...0>)
+    static constexpr bool kDirect = true;
     const PassDesc *d;          // shared-memory copy of the pass descriptor
     const RotCoef<T> *cf;       // shared-memory copy: coefficient rows of the pass's slots
     const C *dt;
@@ -118,24 +120,6 @@ struct GridEnv {
     uint32_t lowmask;
     int m, a;
     int init_zero;
-    __device__ uint64_t g(uint32_t e) const {
-        return base | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a);
-    }
-    __device__ void load(uint32_t e, C &v, C &w) const {
-        const uint64_t gi = g(e);
-        if (init_zero) {
-            v.x = (gi == 0) ? T(1) : T(0);
-            v.y = T(0);
-        } else {
-            v = P[gi];
-        }
-        if (L) w = L[gi];
-    }
-    __device__ void store(uint32_t e, const C &v, const C &w) const {
-        const uint64_t gi = g(e);
-        P[gi] = v;
-        if (L) L[gi] = w;
-    }
     __device__ RotCoef<T> coef(int slot, int bit) const { return cf[slot * d->k + bit]; }
     __device__ C diag(int slot, uint32_t e) const { return dt[d->slot_dtab_off[slot] + e]; }
     __device__ void grad(int slot, int bit, int comp, double v) const {
@@ -176,7 +160,7 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
     const int b = blockIdx.y;
     // dynamic shared memory: tile(s) | gradient scratch (backward) | coefficient rows
     const int kk = desc->k;
-    const uint32_t size = 1u << kk;
+    const uint32_t size = tile_buf_elems(kk, (int)sizeof(C));   // padded tile buffer
     C *sp = reinterpret_cast<C *>(smem_raw);
     C *sl = sp + (BWD ? size : 0u);
     double *gsh = reinterpret_cast<double *>(sp + (BWD ? 2 * size : size));
@@ -201,7 +185,7 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
 int pass_threads(const PassDesc &d) { return 1 << (d.k - d.R); }
 
 size_t pass_smem_bytes(const PassDesc &d, bool backward, size_t elem_bytes) {
-    size_t tiles = (size_t(1) << d.k) * elem_bytes * (backward ? 2 : 1);
+    size_t tiles = size_t(tile_buf_elems(d.k, (int)elem_bytes)) * elem_bytes * (backward ? 2 : 1);
     size_t gsh = backward ? tile_grad_scratch_bytes(pass_threads(d), d.k) : 0;
     const size_t coef = elem_bytes == 16 ? sizeof(RotCoef<double>) : sizeof(RotCoef<float>);
     return tiles + gsh + size_t(d.n_slots) * d.k * coef;

@@ -110,9 +110,10 @@ k_pass_pipe(const PassDesc *__restrict__ desc, int init_zero, int n_qubits, int 
     const PassDesc &d = sd;
     const int k = d.k, m = d.m, a = d.a, mid = a - m;
     const uint32_t size = 1u << k;
+    const uint32_t bstride = tile_buf_elems(k, (int)sizeof(C));   // padded buffer stride
     const int nbuf = BWD ? 4 : 2;   // psi[0], psi[1] (, lam[0], lam[1])
     C *tiles = reinterpret_cast<C *>(smem_raw);
-    double *gsh = reinterpret_cast<double *>(tiles + (size_t)nbuf * size);
+    double *gsh = reinterpret_cast<double *>(tiles + (size_t)nbuf * bstride);
     RotCoef<T> *scf = reinterpret_cast<RotCoef<T> *>(
         reinterpret_cast<unsigned char *>(gsh) + (BWD ? tile_grad_scratch_bytes((int)blockDim.x, k) : 0));
 
@@ -138,8 +139,8 @@ k_pass_pipe(const PassDesc *__restrict__ desc, int init_zero, int n_qubits, int 
         __syncwarp(w0mask);
         if (threadIdx.x == 0) mbar_expect_tx(&mbar[s], tile_bytes * (BWD ? 2u : 1u));
         __syncwarp(w0mask);
-        C *dp = tiles + (size_t)s * size;
-        C *dl = tiles + (size_t)(2 + s) * size;
+        C *dp = tiles + (size_t)s * bstride;
+        C *dl = tiles + (size_t)(2 + s) * bstride;
         const C *P = psi + b * stride;
         const C *L = BWD ? lam + b * stride : nullptr;
         for (uint32_t r = threadIdx.x; r < runs; r += 32) {
@@ -151,8 +152,8 @@ k_pass_pipe(const PassDesc *__restrict__ desc, int init_zero, int n_qubits, int 
     auto issue_store = [&](uint64_t it, int s) {
         if (threadIdx.x >= 32) return;
         const uint64_t b = it / n_tiles, tile = it % n_tiles, base = tile_base(tile);
-        C *dp = tiles + (size_t)s * size;
-        C *dl = tiles + (size_t)(2 + s) * size;
+        C *dp = tiles + (size_t)s * bstride;
+        C *dl = tiles + (size_t)(2 + s) * bstride;
         C *P = psi + b * stride;
         C *L = BWD ? lam + b * stride : nullptr;
         for (uint32_t r = threadIdx.x; r < runs; r += 32) {
@@ -170,8 +171,8 @@ k_pass_pipe(const PassDesc *__restrict__ desc, int init_zero, int n_qubits, int 
     for (uint64_t it = it0; it < it1; ++it) {
         const int s = (int)((it - it0) & 1);
         if (!init_zero && it + 1 < it1) issue_load(it + 1, s ^ 1);
-        C *sp = tiles + (size_t)s * size;
-        C *sl = tiles + (size_t)(2 + s) * size;
+        C *sp = tiles + (size_t)s * bstride;
+        C *sl = tiles + (size_t)(2 + s) * bstride;
         const uint64_t b = it / n_tiles, tile = it % n_tiles, base = tile_base(tile);
         if (init_zero) {
             // the first pass starts from |0...0>: no load
@@ -221,7 +222,7 @@ k_pass_pipe(const PassDesc *__restrict__ desc, int init_zero, int n_qubits, int 
 }
 
 size_t pipe_smem_bytes(const PassDesc &d, bool backward, size_t elem_bytes) {
-    const size_t tiles = (size_t(1) << d.k) * elem_bytes * (backward ? 4 : 2);
+    const size_t tiles = size_t(tile_buf_elems(d.k, (int)elem_bytes)) * elem_bytes * (backward ? 4 : 2);
     const size_t gsh = backward ? tile_grad_scratch_bytes(1 << (d.k - d.R), d.k) : 0;
     const size_t coef = elem_bytes == 16 ? sizeof(RotCoef<double>) : sizeof(RotCoef<float>);
     return tiles + gsh + size_t(d.n_slots) * d.k * coef;

@@ -37,28 +37,20 @@ __device__ __forceinline__ uint32_t elem_of(uint32_t t, uint32_t r, int p, int R
     return lo | (r << p) | ((t >> p) << (p + R));
 }
 
-// Shared-memory slot of tile element e: XOR-fold of the higher bits into the
-// bank-selecting low bits (16-byte elements: 8 per 128 B; 8-byte: 16).
-template <typename T> __device__ __forceinline__ uint32_t swz(uint32_t e);
-template <> __device__ __forceinline__ uint32_t swz<double>(uint32_t e) {
-    const uint32_t f = (e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12);
-    return e ^ (f & 7u);
-}
-template <> __device__ __forceinline__ uint32_t swz<float>(uint32_t e) {
-    const uint32_t f = (e >> 4) ^ (e >> 8) ^ (e >> 12);
-    return e ^ (f & 15u);
-}
-
-// The swizzle is XOR-linear: swz(a ^ b) = swz(a) ^ swz(b).  Element indices
-// of a round are (thread part) | (r << chunk) with disjoint bits, so the
-// slot of register r is swz(thread part) ^ swz(r << chunk), and the second
-// term is a compile-time constant once the chunk is.
-template <typename T> __host__ __device__ constexpr uint32_t swz_c(uint32_t e);
-template <> __host__ __device__ constexpr uint32_t swz_c<double>(uint32_t e) {
-    return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12)) & 7u);
-}
-template <> __host__ __device__ constexpr uint32_t swz_c<float>(uint32_t e) {
-    return e ^ (((e >> 4) ^ (e >> 8) ^ (e >> 12)) & 15u);
+// Shared-memory slot of tile element e between register rounds: one pad
+// element after every bank row of 128 bytes (2^S elements, S = 4 for 8-byte
+// and 3 for 16-byte elements).  A round at chunk P accesses elements
+// e0 + (r << P) with disjoint bits, and since the low S bits of e0 and of
+// r << P are disjoint, pad(e0 + (r << P)) = pad(e0) + pad(r << P): the
+// register part is a compile-time offset.  For the register counts of the
+// default plans (16 amplitudes per thread in FP32, 8 in FP64) the 16 (FP32) or
+// 8 (FP64) lanes of one shared-memory wavefront fall on distinct bank groups
+// at every chunk position.
+template <typename T> struct PadShift;
+template <> struct PadShift<float> { static constexpr int value = 4; };
+template <> struct PadShift<double> { static constexpr int value = 3; };
+template <typename T> __host__ __device__ constexpr uint32_t pad_of(uint32_t e) {
+    return e + (e >> PadShift<T>::value);
 }
 
 // Calls f(std::integral_constant<int, P>) for the runtime chunk p, P in [0, 14 - R].
@@ -139,6 +131,48 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
 
     C v[NR];
     C w[NR];
+
+    // Global loads (first round) and stores (last round) of an environment
+    // that reads and writes the state directly, at compile-time chunk P:
+    // register r holds global index g0 + off_r, off_r the sum of the global
+    // strides of the set bits of r (tile bit b sits at global position b below
+    // m and a + b - m above).  When the chunk lies in the low contiguous part
+    // the offsets are compile-time constants.
+    auto direct_io = [&](auto pc, bool store) {
+        if constexpr (Env::kDirect) {
+            constexpr int P = decltype(pc)::value;
+            const uint32_t g0 = g32(elem_of(t, 0, P, R));
+            uint32_t gst[R];
+            const bool low = P + R <= m;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const int bt = P + j;
+                gst[j] = low ? (1u << bt) : (bt < m ? (1u << bt) : (1u << (a + bt - m)));
+            }
+            C *Pb = env.P + g0;
+            C *Lb = BWD ? env.L + g0 : nullptr;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                uint32_t off = 0;
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if ((r >> j) & 1) off += low ? (1u << (P + j)) : gst[j];
+                if (store) {
+                    Pb[off] = v[r];
+                    if (BWD) Lb[off] = w[r];
+                } else {
+                    if (env.init_zero) {
+                        v[r].x = (g0 + off == 0u) ? T(1) : T(0);
+                        v[r].y = T(0);
+                    } else {
+                        v[r] = Pb[off];
+                    }
+                    if (BWD) w[r] = Lb[off];
+                }
+            }
+        }
+    };
+
     int chunk = -1;
     for (int oi = 0; oi < n_ops; ++oi) {
         const PassOp op = ops[oi];
@@ -146,28 +180,32 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
             const int p = op.chunk;
             if (chunk < 0) {
                 if (active) {
-#pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        const uint32_t e = elem_of(t, r, p, R);
-                        if (Env::kDirect) {
-                            env.load(e, v[r], w[r]);
+                    with_chunk<R>(p, [&](auto pc) {
+                        constexpr int P = decltype(pc)::value;
+                        if constexpr (Env::kDirect) {
+                            direct_io(pc, false);
                         } else {
-                            v[r] = buf[e];
-                            if (BWD) w[r] = lbuf[e];
+                            const uint32_t e0 = elem_of(t, 0, P, R);
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) {
+                                v[r] = buf[e0 + ((uint32_t)r << P)];
+                                if (BWD) w[r] = lbuf[e0 + ((uint32_t)r << P)];
+                            }
                         }
-                    }
+                    });
                 }
             } else {
                 __syncthreads();
                 if (active) {
                     with_chunk<R>(chunk, [&](auto pc) {
                         constexpr int P = decltype(pc)::value;
-                        const uint32_t sb = swz<T>(elem_of(t, 0, P, R));
+                        const uint32_t sb = pad_of<T>(elem_of(t, 0, P, R));
+                        C *bp = buf + sb;
+                        C *lp = BWD ? lbuf + sb : nullptr;
 #pragma unroll
                         for (int r = 0; r < NR; ++r) {
-                            const uint32_t s = sb ^ swz_c<T>((uint32_t)r << P);
-                            buf[s] = v[r];
-                            if (BWD) lbuf[s] = w[r];
+                            bp[pad_of<T>((uint32_t)r << P)] = v[r];
+                            if (BWD) lp[pad_of<T>((uint32_t)r << P)] = w[r];
                         }
                     });
                 }
@@ -175,12 +213,13 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                 if (active) {
                     with_chunk<R>(p, [&](auto pc) {
                         constexpr int P = decltype(pc)::value;
-                        const uint32_t sb = swz<T>(elem_of(t, 0, P, R));
+                        const uint32_t sb = pad_of<T>(elem_of(t, 0, P, R));
+                        const C *bp = buf + sb;
+                        const C *lp = BWD ? lbuf + sb : nullptr;
 #pragma unroll
                         for (int r = 0; r < NR; ++r) {
-                            const uint32_t s = sb ^ swz_c<T>((uint32_t)r << P);
-                            v[r] = buf[s];
-                            if (BWD) w[r] = lbuf[s];
+                            v[r] = bp[pad_of<T>((uint32_t)r << P)];
+                            if (BWD) w[r] = lp[pad_of<T>((uint32_t)r << P)];
                         }
                     });
                 }
@@ -206,9 +245,12 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                             gt = fma(-l0.x, p1.x, gt);
                             gt = fma(-l0.y, p1.y, gt);
                         }
-                        double dgt = (double)(gt * rc.gs);
+                        // warp sum in T (FP32 partials stay FP32 until the warp
+                        // total: FP64 adds are scarce), then FP64 per warp
+                        T wgt = gt * rc.gs;
                         for (int o = wlanes >> 1; o > 0; o >>= 1)
-                            dgt += __shfl_xor_sync(wmask, dgt, o);
+                            wgt += __shfl_xor_sync(wmask, wgt, o);
+                        const double dgt = (double)wgt;
                         if (lane == 0) gsh[(warp * k + chunk + j) * 2 + 0] = dgt;
                     }
                 }
@@ -313,68 +355,71 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                     } else {
                         gq = ((e0 >> q) & 1u) ? -tot : tot;
                     }
-                    double dg = (double)gq;
-                    for (int o = wlanes >> 1; o > 0; o >>= 1) dg += __shfl_xor_sync(wmask, dg, o);
+                    for (int o = wlanes >> 1; o > 0; o >>= 1) gq += __shfl_xor_sync(wmask, gq, o);
+                    const double dg = (double)gq;
                     if (lane == 0) gsh[(warp * k + q) * 2 + 1] = dg;
                 }
             }
             if (active) {
-                const uint32_t e0 = elem_of(t, 0, chunk, R);
-                const uint32_t g0 = g32(e0);
-                // CZ signs of all NR registers as one mask (bit r = register r).
-                // Register r holds global index g = g0 ^ L_r, L_r the global
-                // image of r << chunk, and the CZ chain sign is Q(g) =
-                // parity(g & (g >> 1) & cz).  Q is quadratic over GF(2):
-                //   Q(g0 ^ L) = Q(g0) ^ Q(L) ^ parity(L & W),
-                //   W = ((g0 & cz) << 1) ^ ((g0 >> 1) & cz),
-                // where parity(L_r & W) is linear in the bits of r (the bits of
-                // W at the chunk's global positions) and Q(L_r) comes from the
-                // CZ pairs that join two adjacent bits of the chunk.
-                uint32_t sm;
-                {
-                    constexpr uint32_t kFull = NR >= 32 ? 0xffffffffu : ((1u << NR) - 1u);
-                    const uint32_t W = ((g0 & cz) << 1) ^ ((g0 >> 1) & cz);
-                    const int lo_cnt = min(max(m - chunk, 0), R);
-                    uint32_t wv = (W >> chunk) & ((1u << lo_cnt) - 1u);
-                    if (lo_cnt < R)
-                        wv |= ((W >> (a + max(chunk - m, 0))) & ((1u << (R - lo_cnt)) - 1u)) << lo_cnt;
-                    // tile bits b whose qubits b, b+1 are adjacent and CZ-coupled
-                    uint32_t czt = 0u;
-                    if (m >= 1) {
-                        czt = cz & ((1u << (m - 1)) - 1u);
-                        if (a == m && k > m) czt |= cz & (1u << (m - 1));
+                with_chunk<R>(chunk, [&](auto pc) {
+                    constexpr int P = decltype(pc)::value;
+                    const uint32_t e0 = elem_of(t, 0, P, R);
+                    const uint32_t g0 = g32(e0);
+                    // CZ signs of all NR registers as one mask (bit r = register r).
+                    // Register r holds global index g = g0 ^ L_r, L_r the global
+                    // image of r << P, and the CZ chain sign is Q(g) =
+                    // parity(g & (g >> 1) & cz).  Q is quadratic over GF(2):
+                    //   Q(g0 ^ L) = Q(g0) ^ Q(L) ^ parity(L & W),
+                    //   W = ((g0 & cz) << 1) ^ ((g0 >> 1) & cz),
+                    // where parity(L_r & W) is linear in the bits of r (the bits of
+                    // W at the chunk's global positions) and Q(L_r) comes from the
+                    // CZ pairs that join two adjacent bits of the chunk.
+                    uint32_t sm;
+                    {
+                        constexpr uint32_t kFull = NR >= 32 ? 0xffffffffu : ((1u << NR) - 1u);
+                        const uint32_t W = ((g0 & cz) << 1) ^ ((g0 >> 1) & cz);
+                        const int lo_cnt = min(max(m - P, 0), R);
+                        uint32_t wv = (W >> P) & ((1u << lo_cnt) - 1u);
+                        if (lo_cnt < R)
+                            wv |= ((W >> (a + max(P - m, 0))) & ((1u << (R - lo_cnt)) - 1u)) << lo_cnt;
+                        // tile bits b whose qubits b, b+1 are adjacent and CZ-coupled
+                        uint32_t czt = 0u;
+                        if (m >= 1) {
+                            czt = cz & ((1u << (m - 1)) - 1u);
+                            if (a == m && k > m) czt |= cz & (1u << (m - 1));
+                        }
+                        if (k - m >= 2) czt |= ((cz >> a) & ((1u << (k - m - 1)) - 1u)) << m;
+                        const uint32_t adj = czt >> P;
+                        sm = (__popc(g0 & (g0 >> 1) & cz) & 1u) ? kFull : 0u;
+    #pragma unroll
+                        for (int j = 0; j < R; ++j) {
+                            if ((wv >> j) & 1u) sm ^= reg_bit_table(j);
+                            if (j + 1 < R && ((adj >> j) & 1u)) sm ^= reg_bit_table(j) & reg_bit_table(j + 1);
+                        }
+                        sm &= kFull;
                     }
-                    if (k - m >= 2) czt |= ((cz >> a) & ((1u << (k - m - 1)) - 1u)) << m;
-                    const uint32_t adj = czt >> chunk;
-                    sm = (__popc(g0 & (g0 >> 1) & cz) & 1u) ? kFull : 0u;
-#pragma unroll
-                    for (int j = 0; j < R; ++j) {
-                        if ((wv >> j) & 1u) sm ^= reg_bit_table(j);
-                        if (j + 1 < R && ((adj >> j) & 1u)) sm ^= reg_bit_table(j) & reg_bit_table(j + 1);
+    #pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const uint32_t e = e0 + ((uint32_t)r << P);   // disjoint bits: a constant offset
+                        const uint32_t sgn = (sm >> r) & 1u;
+                        const C dv = env.diag(op.slot, e);
+                        if (!BWD) {
+                            C y = cmul(v[r], dv);
+                            y.x = flip_sign(y.x, sgn);
+                            y.y = flip_sign(y.y, sgn);
+                            v[r] = y;
+                        } else {
+                            C y = cmul_conj(v[r], dv);
+                            y.x = flip_sign(y.x, sgn);
+                            y.y = flip_sign(y.y, sgn);
+                            v[r] = y;
+                            C z = cmul_conj(w[r], dv);
+                            z.x = flip_sign(z.x, sgn);
+                            z.y = flip_sign(z.y, sgn);
+                            w[r] = z;
+                        }
                     }
-                    sm &= kFull;
-                }
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const uint32_t e = e0 + ((uint32_t)r << chunk);   // disjoint bits
-                    const uint32_t sgn = (sm >> r) & 1u;
-                    const C dv = env.diag(op.slot, e);
-                    if (!BWD) {
-                        C y = cmul(v[r], dv);
-                        y.x = flip_sign(y.x, sgn);
-                        y.y = flip_sign(y.y, sgn);
-                        v[r] = y;
-                    } else {
-                        C y = cmul_conj(v[r], dv);
-                        y.x = flip_sign(y.x, sgn);
-                        y.y = flip_sign(y.y, sgn);
-                        v[r] = y;
-                        C z = cmul_conj(w[r], dv);
-                        z.x = flip_sign(z.x, sgn);
-                        z.y = flip_sign(z.y, sgn);
-                        w[r] = z;
-                    }
-                }
+                });
             }
         } else if (BWD && op.kind == OP_FLUSH) {
             __syncthreads();
@@ -391,21 +436,21 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
             __syncthreads();
         }
     }
-    if (Env::kDirect) {
-        if (active) {
-#pragma unroll
-            for (int r = 0; r < NR; ++r) env.store(elem_of(t, r, chunk, R), v[r], w[r]);
-        }
+    if constexpr (Env::kDirect) {
+        if (active) with_chunk<R>(chunk, [&](auto pc) { direct_io(pc, true); });
     } else {
         // back to plain order in shared memory
         __syncthreads();
         if (active) {
+            with_chunk<R>(chunk, [&](auto pc) {
+                constexpr int P = decltype(pc)::value;
+                const uint32_t e0 = elem_of(t, 0, P, R);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const uint32_t e = elem_of(t, r, chunk, R);
-                buf[e] = v[r];
-                if (BWD) lbuf[e] = w[r];
-            }
+                for (int r = 0; r < NR; ++r) {
+                    buf[e0 + ((uint32_t)r << P)] = v[r];
+                    if (BWD) lbuf[e0 + ((uint32_t)r << P)] = w[r];
+                }
+            });
         }
         __syncthreads();
     }

@@ -256,7 +256,8 @@ bool options_valid(const PlanOptions &o, vqe_precision prec, std::string &err) {
         const size_t elem = prec == VQE_C128 ? 16 : 8;
         const size_t warps = ((size_t(1) << (r.tile_bits_max - std::min(r.reg_bits, r.tile_bits_max))) + 31) / 32;
         const size_t bufs = r.reg_bits > 4 ? 1 : 2;   // 32-amplitude plans are forward only
-        const size_t smem = (bufs << r.tile_bits_max) * elem + warps * r.tile_bits_max * 16;
+        const size_t smem = bufs * tile_buf_elems(r.tile_bits_max, int(elem)) * elem +
+                            warps * r.tile_bits_max * 16;
         if (smem > 227 * 1024) err = "tile does not fit in shared memory";
     }
     return err.empty();
@@ -1610,7 +1611,7 @@ vqe_status batch_build(vqe_batch_ctx *b) {
             fwd.insert(fwd.end(), hp.fwd.begin(), hp.fwd.end());
             bwd.insert(bwd.end(), hp.bwd.begin(), hp.bwd.end());
             stage.insert(stage.end(), hp.stage.begin(), hp.stage.end());
-            max_tile = std::max(max_tile, size_t(1) << kk);
+            max_tile = std::max(max_tile, size_t(tile_buf_elems(kk, int(elem))));   // padded
             max_coef = std::max(max_coef, hp.coef_stride);
             max_lo = std::max(max_lo, size_t(P.n_stage) * P.lo_stride);
             max_hi = std::max(max_hi, size_t(P.n_stage) * P.hi_stride);

@@ -67,6 +67,13 @@ struct RotCoef {
     int mode;
 };
 
+// Elements of one shared-memory tile buffer of 2^k amplitudes of elem_bytes
+// each, including the padding of the layout between register rounds (one
+// pad element per 128-byte row).
+inline __host__ __device__ constexpr uint32_t tile_buf_elems(int k, int elem_bytes) {
+    return (1u << k) + ((1u << k) >> (elem_bytes == 16 ? 3 : 4));
+}
+
 // Staging job: one slot of one pass (one row of coefficients and one table).
 struct StageSlot {
     int k;             // tile bits of the pass

@@ -24,12 +24,14 @@ def elem_of(t, r, p, R):
     return lo | (r << p) | ((t >> p) << (p + R))
 
 
-def swz(e, prec):
-    if prec == "c128":
-        f = (e >> 3) ^ (e >> 6) ^ (e >> 9) ^ (e >> 12)
-        return e ^ (f & 7)
-    f = (e >> 4) ^ (e >> 8) ^ (e >> 12)
-    return e ^ (f & 15)
+def pad(e, prec):
+    """Shared-memory slot of tile element e between register rounds: one pad
+    element per 128-byte row (8 complex128 or 16 complex64 elements)."""
+    return e + (e >> (3 if prec == "c128" else 4))
+
+
+def tile_buf_elems(k, prec):
+    return (1 << k) + ((1 << k) >> (3 if prec == "c128" else 4))
 
 
 class Emu:
@@ -122,17 +124,18 @@ class Emu:
                         w = lam[g]
                 else:
                     e_old = elem_of(t, r, chunk, R)
-                    s_old = swz(np.broadcast_to(e_old, (1, threads, NR)), prec)
-                    s_new = swz(np.broadcast_to(e, (1, threads, NR)), prec)
+                    s_old = pad(np.broadcast_to(e_old, (1, threads, NR)), prec)
+                    s_new = pad(np.broadcast_to(e, (1, threads, NR)), prec)
+                    nbuf = tile_buf_elems(k, prec)
                     for s_ in (s_old, s_new):
                         flat = s_.ravel()
-                        assert flat.min() >= 0 and flat.max() < (1 << k)
-                        assert np.unique(flat).size == (1 << k), "smem slots must be a bijection"
-                    sm = np.empty((tiles, 1 << k), dtype=np.complex128)
+                        assert flat.min() >= 0 and flat.max() < nbuf
+                        assert np.unique(flat).size == (1 << k), "smem slots must be distinct"
+                    sm = np.empty((tiles, nbuf), dtype=np.complex128)
                     sm[:, s_old[0].ravel()] = v.reshape(tiles, -1)
                     v = sm[:, s_new[0].ravel()].reshape(tiles, threads, NR)
                     if backward:
-                        sl = np.empty((tiles, 1 << k), dtype=np.complex128)
+                        sl = np.empty((tiles, nbuf), dtype=np.complex128)
                         sl[:, s_old[0].ravel()] = w.reshape(tiles, -1)
                         w = sl[:, s_new[0].ravel()].reshape(tiles, threads, NR)
                 chunk = p

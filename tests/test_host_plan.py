@@ -15,7 +15,8 @@ def pass_smem(d, backward, elem):
     threads = 1 << (d.k - d.R)
     warps = (threads + 31) // 32
     coef = 24 if elem == 16 else 12
-    return ((1 << d.k) * elem * (2 if backward else 1) + (warps * d.k * 16 if backward else 0)
+    buf = (1 << d.k) + ((1 << d.k) >> (3 if elem == 16 else 4))   # padded tile buffer
+    return (buf * elem * (2 if backward else 1) + (warps * d.k * 16 if backward else 0)
             + d.n_slots * d.k * coef + 2528)
 
 
@@ -247,3 +248,26 @@ def test_full_size_index_ranges(n, D, prec):
         win_bits = ((1 << W.m) - 1) | (((1 << (W.k - W.m)) - 1) << W.a)
         for gi in w["wgroups"][W.g_begin:W.g_end]:
             assert hp["groups"][gi].x & ~win_bits == 0, "group X mask outside its window"
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n", [11, 20, 24, 32])
+def test_padded_layout_conflict_free_for_default_plans(n, prec):
+    """Every register-round access of the default plans hits distinct bank
+    groups within a shared-memory wavefront: 16 lanes of 8-byte elements, or
+    8 lanes of 16-byte elements, must fall on distinct slots modulo 16 / 8."""
+    from kernel_emulator import elem_of, pad
+    pl = P.plan(n, 2, prec)
+    lanes_per_wave = 8 if prec == "c128" else 16
+    for d in pl["fwd"] + pl["bwd"]:
+        R = d.R
+        threads = 1 << (d.k - R)
+        chunks = {op.chunk for op in d.ops[:d.n_ops] if op.kind == P.OP_ROUND}
+        for p in chunks:
+            for w0 in range(0, threads, 32):
+                lanes = np.arange(w0, min(w0 + 32, threads))
+                for r in range(1 << R):
+                    slots = pad(elem_of(lanes, r, p, R), prec)
+                    for h in range(0, lanes.size, lanes_per_wave):
+                        part = slots[h:h + lanes_per_wave] % lanes_per_wave
+                        assert np.unique(part).size == part.size, (d.k, R, p, r)

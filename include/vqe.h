@@ -114,9 +114,12 @@ vqe_status vqe_set_plan_options(vqe_handle h, int tile_bits_max, int run_bits, i
 
 /* Kernel used for the ansatz passes: 0 (default) = one CTA per tile, first
  * and last register round straight from/to global memory; 1 = persistent
- * CTAs that pipeline tiles through shared memory with bulk copies (a pass
- * whose double-buffered tiles exceed shared memory, or that uses 32
- * amplitudes per thread, still runs with kind 0).  Results are identical. */
+ * CTAs that pipeline tiles through shared memory with bulk copies; 2 =
+ * persistent CTAs that prefetch their next tile into shared memory with
+ * cp.async while running the current one (not for the first pass of a forward
+ * sweep, which loads nothing).  A pass whose double-buffered tiles exceed
+ * shared memory, or that uses 32 amplitudes per thread, runs with kind 0.
+ * Results are identical. */
 vqe_status vqe_set_pass_kernel(vqe_handle h, int kind);
 
 /* Set the Hamiltonian H = sum_t coeffs[t] * P(x_masks[t], z_masks[t])

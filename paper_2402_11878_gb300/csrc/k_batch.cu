@@ -20,9 +20,7 @@ namespace {
 template <typename T>
 struct BatchEnv {
     using C = typename V2<T>::type;
-    static constexpr bool kDirect = false;   // the tile is in shared memory
-    __device__ void load(uint32_t, C &, C &) const {}
-    __device__ void store(uint32_t, const C &, const C &) const {}
+    static constexpr int kLoad = 0, kStore = 0;   // the tile is in shared memory, plain order
     const PassDesc *d;
     const RotCoef<T> *coef_s;   // shared: all slots of the instance (plan's coef offsets)
     const C *lo_s;              // shared: per plan slot, 2^kl low half-table entries
@@ -39,6 +37,7 @@ struct BatchEnv {
         const C h = hi_s[ps * hi_stride + (e >> kl)];
         return cmul(l, h);
     }
+    static constexpr bool kDiagRow = false;   // half tables
     __device__ void grad(int slot, int bit, int comp, double v) const {
         const int q = bit < m ? bit : a + (bit - m);
         gacc[(d->slot_layer[slot] * n + q) * 2 + comp] += v;

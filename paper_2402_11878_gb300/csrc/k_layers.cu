@@ -16,6 +16,8 @@
 //     dE/dtheta = Im <lambda| Y_q |psi>,   dE/dphi = Im <lambda| Z_q |psi>
 // at a point of the sweep where both are valid (after the slot's diagonal is
 // undone and before q's own rotation is undone).
+#include <algorithm>
+
 #include "pass_core.cuh"
 
 namespace vqe {
@@ -109,7 +111,7 @@ struct GridEnv {
     using C = typename V2<T>::type;
     // first/last round straight from/to global memory: run_tile reads P, L
     // (this state's psi and lambda) and init_zero (start from |0...0>)
-    static constexpr bool kDirect = true;
+    static constexpr int kLoad = 1, kStore = 1;
     const PassDesc *d;          // shared-memory copy of the pass descriptor
     const RotCoef<T> *cf;       // shared-memory copy: coefficient rows of the pass's slots
     const C *dt;
@@ -122,6 +124,8 @@ struct GridEnv {
     int init_zero;
     __device__ RotCoef<T> coef(int slot, int bit) const { return cf[slot * d->k + bit]; }
     __device__ C diag(int slot, uint32_t e) const { return dt[d->slot_dtab_off[slot] + e]; }
+    static constexpr bool kDiagRow = true;
+    __device__ const C *diag_row(int slot, uint32_t e0) const { return dt + d->slot_dtab_off[slot] + e0; }
     __device__ void grad(int slot, int bit, int comp, double v) const {
         gout[d->slot_grad_off[slot] + tile * (uint64_t)(2 * d->k) + bit * 2 + comp] = v;
     }
@@ -170,12 +174,12 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
     stage_pass<T>(desc, coefs + (size_t)b * coef_stride, &sd, scf);
     const PassDesc &d = sd;
     const int k = d.k, m = d.m, a = d.a;
-    const uint64_t tile = blockIdx.x;
     const int mid = a - m;
-    const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (k - m)));
     const uint32_t lowmask = (1u << m) - 1u;
     C *P = psi + (size_t)b * stride;
     C *L = BWD ? lam + (size_t)b * stride : nullptr;
+    const uint64_t tile = blockIdx.x;
+    const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (k - m)));
     GridEnv<T> env{&sd, scf, dtab + (size_t)b * dtab_stride,
                    BWD ? gpart + (size_t)b * grad_stride : nullptr, tile, P, L, base, lowmask,
                    m, a, init_zero};

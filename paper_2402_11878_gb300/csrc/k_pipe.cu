@@ -65,9 +65,7 @@ constexpr uint32_t kMaxPolls = 1u << 22;
 template <typename T>
 struct PipeEnv {
     using C = typename V2<T>::type;
-    static constexpr bool kDirect = false;   // the tile is in shared memory
-    __device__ void load(uint32_t, C &, C &) const {}
-    __device__ void store(uint32_t, const C &, const C &) const {}
+    static constexpr int kLoad = 0, kStore = 0;   // the tile is in shared memory, plain order
     const PassDesc *d;
     const RotCoef<T> *cf;
     const C *dt;
@@ -75,6 +73,8 @@ struct PipeEnv {
     uint64_t tile;
     __device__ RotCoef<T> coef(int slot, int bit) const { return cf[slot * d->k + bit]; }
     __device__ C diag(int slot, uint32_t e) const { return dt[d->slot_dtab_off[slot] + e]; }
+    static constexpr bool kDiagRow = true;
+    __device__ const C *diag_row(int slot, uint32_t e0) const { return dt + d->slot_dtab_off[slot] + e0; }
     __device__ void grad(int slot, int bit, int comp, double v) const {
         gout[d->slot_grad_off[slot] + tile * (uint64_t)(2 * d->k) + bit * 2 + comp] = v;
     }

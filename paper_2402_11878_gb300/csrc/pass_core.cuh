@@ -1,25 +1,29 @@
-// Device core of the ansatz tile passes, shared by the grid kernel
-// (k_layers.cu) and the persistent batched kernel (k_batch.cu).
+// Device core of the ansatz tile passes, shared by the grid kernels
+// (k_layers.cu), the bulk-copy pipelined kernel (k_pipe.cu) and the
+// persistent batched kernel (k_batch.cu).
 //
-// A tile holds 2^k amplitudes of the state in shared memory.  Its tile bits
-// map to global index bits as [0, m) -> [0, m) and [m, k) -> [a, a + k - m);
-// `gbase` carries the fixed global bits of the tile.  The pass program (see
-// vqe_internal.h) moves the amplitudes between shared memory and registers in
-// "rounds": in a round, each thread holds 2^R amplitudes whose tile indices
-// differ in the R bits [chunk, chunk + R) and applies the RY butterflies of
-// those bits in registers.  Between rounds the tile goes through shared
-// memory with an XOR swizzle (bank-conflict free for every chunk of the
-// plan); the tile is in plain (linear) order on entry and on exit.
+// A tile holds 2^k amplitudes of the state.  Its tile bits map to global
+// index bits as [0, m) -> [0, m) and [m, k) -> [a, a + k - m); `gbase` carries
+// the fixed global bits of the tile.  The pass program (see vqe_internal.h)
+// moves the amplitudes between shared memory and registers in "rounds": in a
+// round, each thread holds 2^R amplitudes whose tile indices differ in the R
+// bits [chunk, chunk + R) and applies the RY butterflies of those bits in
+// registers.  Between rounds the tile goes through shared memory in a padded
+// layout (pad_of below).
 //
 // The Env policy supplies the per-state data:
 //   RotCoef<T> coef(int slot, int tile_bit)    RY coefficient of a gated bit
 //   C diag(int slot, uint32_t e)               diagonal table entry of tile element e
+//   static constexpr bool kDiagRow  true: the slot's table is stored in full and
+//        const C *diag_row(int slot, uint32_t e0) points at entry e0 (entry e0 + j at [j])
 //   void grad(int slot, int tile_bit, int comp, double v)   (backward) block total of
 //        a gradient partial: comp 0 = theta (RY), 1 = phi (RZ); called by thread 0
-//   static constexpr bool kDirect                 true: the first round loads and the
-//        last round stores tile elements through load/store below instead of
-//        reading/writing `buf`/`lbuf` in plain order
-//   void load(uint32_t e, C &v, C &w) / void store(uint32_t e, const C &v, const C &w)
+//   static constexpr int kLoad    where the first round reads the tile:
+//        0 = `buf`/`lbuf` in plain order, 1 = the state in global memory
+//        (members P, L and init_zero: start from |0...0>), 2 = `buf`/`lbuf` in
+//        the padded layout of the first round's chunk (a prefetched tile)
+//   static constexpr int kStore   where the last round writes the tile:
+//        0 = `buf`/`lbuf` in plain order, 1 = the state in global memory (P, L)
 #pragma once
 
 #include "vqe_internal.h"
@@ -132,43 +136,61 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
     C v[NR];
     C w[NR];
 
-    // Global loads (first round) and stores (last round) of an environment
-    // that reads and writes the state directly, at compile-time chunk P:
-    // register r holds global index g0 + off_r, off_r the sum of the global
-    // strides of the set bits of r (tile bit b sits at global position b below
-    // m and a + b - m above).  When the chunk lies in the low contiguous part
-    // the offsets are compile-time constants.
-    auto direct_io = [&](auto pc, bool store) {
-        if constexpr (Env::kDirect) {
+    // Global loads (first round) and stores (last round) at compile-time
+    // chunk P: register r holds global index g0 + off_r, off_r the sum of the
+    // global strides of the set bits of r (tile bit b sits at global position
+    // b below m and a + b - m above).  When the chunk lies in the low
+    // contiguous part the offsets are compile-time constants.
+    auto reg_offset = [&](auto pc, int r, const uint32_t (&gst)[R]) -> uint32_t {
+        constexpr int P = decltype(pc)::value;
+        uint32_t off = 0;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            if ((r >> j) & 1) off += (P + R <= m) ? (1u << (P + j)) : gst[j];
+        return off;
+    };
+    auto global_strides = [&](auto pc, uint32_t (&gst)[R]) {
+        constexpr int P = decltype(pc)::value;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int bt = P + j;
+            gst[j] = bt < m ? (1u << bt) : (1u << (a + bt - m));
+        }
+    };
+    auto direct_load = [&](auto pc) {
+        if constexpr (Env::kLoad == 1) {
             constexpr int P = decltype(pc)::value;
             const uint32_t g0 = g32(elem_of(t, 0, P, R));
             uint32_t gst[R];
-            const bool low = P + R <= m;
+            global_strides(pc, gst);
+            const C *Pb = env.P + g0;
+            const C *Lb = BWD ? env.L + g0 : nullptr;
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const int bt = P + j;
-                gst[j] = low ? (1u << bt) : (bt < m ? (1u << bt) : (1u << (a + bt - m)));
+            for (int r = 0; r < NR; ++r) {
+                const uint32_t off = reg_offset(pc, r, gst);
+                if (env.init_zero) {
+                    v[r].x = (g0 + off == 0u) ? T(1) : T(0);
+                    v[r].y = T(0);
+                } else {
+                    v[r] = Pb[off];
+                }
+                if (BWD) w[r] = Lb[off];
             }
+        }
+    };
+    auto direct_store = [&](auto pc) {
+        if constexpr (Env::kStore == 1) {
+            constexpr int P = decltype(pc)::value;
+            const uint32_t g0 = g32(elem_of(t, 0, P, R));
+            uint32_t gst[R];
+            global_strides(pc, gst);
             C *Pb = env.P + g0;
             C *Lb = BWD ? env.L + g0 : nullptr;
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                uint32_t off = 0;
-#pragma unroll
-                for (int j = 0; j < R; ++j)
-                    if ((r >> j) & 1) off += low ? (1u << (P + j)) : gst[j];
-                if (store) {
-                    Pb[off] = v[r];
-                    if (BWD) Lb[off] = w[r];
-                } else {
-                    if (env.init_zero) {
-                        v[r].x = (g0 + off == 0u) ? T(1) : T(0);
-                        v[r].y = T(0);
-                    } else {
-                        v[r] = Pb[off];
-                    }
-                    if (BWD) w[r] = Lb[off];
-                }
+                const uint32_t off = reg_offset(pc, r, gst);
+                Pb[off] = v[r];
+                if (BWD) Lb[off] = w[r];
             }
         }
     };
@@ -182,8 +204,15 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                 if (active) {
                     with_chunk<R>(p, [&](auto pc) {
                         constexpr int P = decltype(pc)::value;
-                        if constexpr (Env::kDirect) {
-                            direct_io(pc, false);
+                        if constexpr (Env::kLoad == 1) {
+                            direct_load(pc);
+                        } else if constexpr (Env::kLoad == 2) {
+                            const uint32_t sb = pad_of<T>(elem_of(t, 0, P, R));
+#pragma unroll
+                            for (int r = 0; r < NR; ++r) {
+                                v[r] = buf[sb + pad_of<T>((uint32_t)r << P)];
+                                if (BWD) w[r] = lbuf[sb + pad_of<T>((uint32_t)r << P)];
+                            }
                         } else {
                             const uint32_t e0 = elem_of(t, 0, P, R);
 #pragma unroll
@@ -398,11 +427,14 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                         }
                         sm &= kFull;
                     }
-    #pragma unroll
+                        // diagonal entries e0 + (r << P): with a full table, one row
+                    // pointer and constant offsets
+#pragma unroll
                     for (int r = 0; r < NR; ++r) {
-                        const uint32_t e = e0 + ((uint32_t)r << P);   // disjoint bits: a constant offset
                         const uint32_t sgn = (sm >> r) & 1u;
-                        const C dv = env.diag(op.slot, e);
+                        C dv;
+                        if constexpr (Env::kDiagRow) dv = env.diag_row(op.slot, e0)[(uint32_t)r << P];
+                        else dv = env.diag(op.slot, e0 + ((uint32_t)r << P));
                         if (!BWD) {
                             C y = cmul(v[r], dv);
                             y.x = flip_sign(y.x, sgn);
@@ -436,8 +468,8 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
             __syncthreads();
         }
     }
-    if constexpr (Env::kDirect) {
-        if (active) with_chunk<R>(chunk, [&](auto pc) { direct_io(pc, true); });
+    if constexpr (Env::kStore == 1) {
+        if (active) with_chunk<R>(chunk, [&](auto pc) { direct_store(pc); });
     } else {
         // back to plain order in shared memory
         __syncthreads();

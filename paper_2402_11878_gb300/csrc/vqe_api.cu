@@ -99,7 +99,7 @@ struct vqe_ctx {
     int scratch_batch = 0;
 
     // pass kernel choice and the device error word of bounded waits
-    int pass_kernel = 0;          // 0: one CTA per tile, 1: pipelined persistent where it fits
+    int pass_kernel = 0;          // 0: one CTA per tile, 1: bulk-copy pipelined, 2: cp.async prefetch (where they fit)
     int sms = 0;
     DevBuf d_err;
 
@@ -822,6 +822,9 @@ cudaError_t launch_any_pass(vqe_ctx *h, const vqe_ctx::DevPlan &P, const PassDes
                             double *gpart, bool backward, int init_zero) {
     const size_t N = h->state_elems();
     const size_t elem = sizeof(T) * 2;
+    if (h->pass_kernel == 2 && !init_zero && dh.R <= 4 && sp_smem_bytes(dh, backward, elem) <= 227 * 1024)
+        return launch_pass_sp<T>(dd, dh, h->n, B, psi, lam, N, coefs, P.coef_stride, h->d_dtab.p,
+                                 P.dtab_stride, gpart, P.grad_stride, backward, h->sms, h->stream);
     if (h->pass_kernel == 1 && dh.R <= 4 && pipe_smem_bytes(dh, backward, elem) <= 227 * 1024)
         return launch_pass_pipe<T>(dd, dh, h->n, B, psi, lam, N, coefs, P.coef_stride, h->d_dtab.p,
                                    P.dtab_stride, gpart, P.grad_stride, backward, init_zero,
@@ -1060,7 +1063,7 @@ vqe_status vqe_create(int n_qubits, int depth, vqe_precision precision, void *cu
 
 vqe_status vqe_set_pass_kernel(vqe_handle h, int kind) {
     if (!h) return VQE_ERR_ARG;
-    if (kind != 0 && kind != 1) return fail(h, VQE_ERR_ARG, "pass kernel kind must be 0 or 1");
+    if (kind < 0 || kind > 2) return fail(h, VQE_ERR_ARG, "pass kernel kind must be 0, 1 or 2");
     h->pass_kernel = kind;
     return VQE_OK;
 }

@@ -54,7 +54,7 @@ def test_config_small_hubbard_c128_state_and_energy(eng_mod, oracle_mod, seed):
 SIZES = [1, 2, 3, 4, 5, 7, 8, 9, 12, 13, 14, 15, 16, 17, 18]
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("n", SIZES)
 def test_random_pauli_sum_all_sizes(eng_mod, oracle_mod, prec, n, kernel):
@@ -88,7 +88,7 @@ def test_batched_energies(eng_mod, oracle_mod, prec):
         check_energy(E[b], E_ref, H, prec)
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("n,D", [(2, 2), (3, 2), (8, 4), (13, 2), (14, 2), (16, 2), (17, 1)])
 def test_adjoint_gradient(eng_mod, oracle_mod, prec, n, D, kernel):

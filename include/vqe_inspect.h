@@ -18,7 +18,8 @@ extern "C" {
 #endif
 
 /* sizeof of internal record `which`: 0 = pass descriptor, 1 = staging slot,
- * 2 = term group, 3 = energy window; 0 for an unknown `which`. */
+ * 2 = term group, 3 = energy window, 4 = window group, 5 = window term; 0 for
+ * an unknown `which`. */
 size_t vqe_inspect_sizeof(int which);
 
 /* Tile-pass plan of the ansatz for (n, depth, precision, options) -- options
@@ -45,15 +46,21 @@ int vqe_inspect_hamiltonian(int n_qubits, const uint64_t *x_masks, const uint64_
                             int max_groups, uint32_t *tz, double *tc, int max_terms, int counts[2],
                             double *sum_abs_dropped, uint64_t *n_canonical);
 
-/* Windows of the windowed expectation kernel for the same prepared terms:
- * window records (max_windows), the group indices of each window (into the
- * groups of vqe_inspect_hamiltonian; max_wgroups), and the groups swept over
- * the whole state instead (max_wide).  counts[3] = windows, window groups,
- * wide groups.  Returns 0, or -1 on invalid input or too-small buffers. */
+/* Windows of the windowed expectation kernel for the same prepared terms
+ * (Sec. II-B Eq. 7 evaluated per X-mask group): window records
+ * (max_windows), window groups with their register-pattern runs
+ * (max_wgroups), window terms (tile-coordinate Z bits, tile-number Z bits,
+ * coefficient; max_wterms), the windows' high-part offset tables (max_hoff),
+ * and the groups swept over the whole state instead (max_wide).  diag_terms:
+ * 1 = keep the diagonal group's terms in the low window, 0 = leave them out
+ * (the library does so when it precomputes the diagonal of H).
+ * counts[5] = windows, window groups, window terms, offsets, wide groups.
+ * Returns 0, or -1 on invalid input or too-small buffers. */
 int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
                         const uint64_t *z_masks, const double *coeffs, size_t n_terms,
-                        double threshold, void *windows, int max_windows, int *wgroups,
-                        int max_wgroups, void *wide, int max_wide, int counts[3]);
+                        double threshold, int diag_terms, void *windows, int max_windows,
+                        void *wgroups, int max_wgroups, void *wterms, int max_wterms,
+                        uint32_t *hoff, int max_hoff, void *wide, int max_wide, int counts[5]);
 
 #ifdef __cplusplus
 }

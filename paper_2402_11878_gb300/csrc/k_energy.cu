@@ -393,43 +393,111 @@ template cudaError_t launch_apply_h<double>(const GroupDesc *, int, const uint32
 
 // ---------------------------------------------------------------- windowed expectation
 //
-// Groups whose X mask fits one tile "window" (tile bits [0, m) plus the
-// window [a, a + k - m)) are evaluated from a tile staged in shared memory:
-// the state is read once per window instead of once per group.  Window 0 is
-// the low contiguous tile and also yields <psi|psi>.
+// Groups whose X mask lies inside one tile "window" are evaluated from the
+// window's tile staged in shared memory: the state is read once per window
+// instead of once per group.  A window is the low run of m global bits plus
+// k - m further global bits at any positions (a per-window offset table places
+// them); the low window (m = k) also yields <psi|psi>.
+//
+// Signs.  For a term with Z mask z and a tile with global base `base`,
+// (-1)^{popc(g & z)} = (-1)^{popc(base & zout)} * (-1)^{popc(e & zt)}: the
+// first factor is folded into the coefficient once per tile, the second uses
+// the element's tile index e.  A thread handles the pairs p = tid + j * 512
+// (zero inserted at the group's top bit hl), i.e. e_j = e_0 | D_j with D_j
+// linear in the bits of j, so (-1)^{popc(e_j & zt)} = (-1)^{popc(e_0 & zt)} *
+// (-1)^{parity(j & v)} with v the term's "register pattern".  The host sorts a
+// group's terms by v; the thread sums each run once with the sign of e_0,
+//     F[v] = sum_{t in run v} c_t (-1)^{popc(e_0 & zt_t)},
+// and a Walsh-Hadamard transform over v gives the sign sums of all its pairs,
+//     f(j) = sum_v F[v] (-1)^{parity(j & v)},
+// so a term costs one sign evaluation per thread instead of one per pair.
 
 namespace vqe {
 
-template <typename T, int K>
+template <int N, typename T>
+__device__ __forceinline__ void wht_inplace(T (&F)[N]) {
+#pragma unroll
+    for (int h = 1; h < N; h <<= 1) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            if (i & h) continue;
+            const T x = F[i], y = F[i | h];
+            F[i] = x + y;
+            F[i | h] = x - y;
+        }
+    }
+}
+
+// F[v] += sum over the terms of run v of sc_t (-1)^{popc(e0 & zt_t)}.
+template <int NV, typename T>
+__device__ __forceinline__ void run_sums(T (&F)[NV], const uint16_t *run, int begin,
+                                         const T *sc, const uint32_t *szt, uint32_t e0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        T f = T(0);
+        const int t1 = begin + run[v + 1];
+        for (int t = begin + run[v]; t < t1; ++t) f += sgn_flip(sc[t], __popc(e0 & szt[t]) & 1u);
+        F[v] = f;
+    }
+}
+
+template <typename T, int K, bool RUNS>
 __global__ void __launch_bounds__(kEnergyWinThreads, 2)
-k_energy_win(WinDesc W, const GroupDesc *__restrict__ groups, const int *__restrict__ wgroups,
-             const uint32_t *__restrict__ tz, const T *__restrict__ tc,
-             const T *__restrict__ hdiag, int n, const typename EV2<T>::type *__restrict__ psi,
-             size_t stride, double *__restrict__ partials, int bps_total) {
+k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__restrict__ wterms,
+             const uint32_t *__restrict__ hoff, const T *__restrict__ hdiag,
+             const typename EV2<T>::type *__restrict__ psi, size_t stride,
+             double *__restrict__ partials, int bps_total) {
     using C = typename EV2<T>::type;
+    static_assert(kEnergyWinThreads == 512, "pair layout assumes 512 threads");
     constexpr uint32_t size = 1u << K;
     constexpr int EPT = size / kEnergyWinThreads;   // tile elements per thread
     constexpr int PPT = EPT / 2;                    // pairs per thread and group
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *sp = reinterpret_cast<C *>(smem_raw);
+    C *sp = reinterpret_cast<C *>(smem_raw);                      // [size] the tile
+    T *sc = reinterpret_cast<T *>(sp + size);                     // [t_count] coefficients, base sign folded
+    uint32_t *szt = reinterpret_cast<uint32_t *>(sc + W.t_count); // [t_count] tile Z bits
+    uint32_t *soff = szt + W.t_count;                             // [2^(K-m)] high-part offsets
     __shared__ double sh[2 * (kEnergyWinThreads / 32)];
-    const int m = W.m, a = W.a, mid = a - m;
-    const uint64_t tile = blockIdx.x;
+    __shared__ WinGroup sg[kWinMaxGroups];                         // the window's groups
+    const int m = W.m;
     const int b = blockIdx.y;
-    const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (K - m)));
-    const uint32_t lowmask = (1u << m) - 1u;
     const C *P = psi + (size_t)b * stride;
-    auto g32 = [&](uint32_t e) -> uint32_t {
-        return (uint32_t)(base | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a));
-    };
-    for (uint32_t e = threadIdx.x; e < size; e += blockDim.x) sp[e] = P[g32(e)];
+    const uint32_t tid = threadIdx.x;
+    // tile number -> the global bits of bmask, in increasing order
+    uint32_t base = 0;
+    {
+        uint32_t bm = W.bmask, tn = blockIdx.x;
+        while (bm) {
+            const int bit = __ffs(bm) - 1;
+            base |= (tn & 1u) << bit;
+            tn >>= 1;
+            bm &= bm - 1u;
+        }
+    }
+    const uint32_t nh = 1u << (K - m);
+    for (uint32_t i = tid; i < nh; i += blockDim.x) soff[i] = hoff[W.hoff + i];
+    {
+        const int ng = W.g_end - W.g_begin;
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(wgroups + W.g_begin);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(sg);
+        for (int i = tid; i < ng * (int)(sizeof(WinGroup) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    for (int t = tid; t < W.t_count; t += blockDim.x) {
+        const WinTerm wt = wterms[W.t_begin + t];
+        sc[t] = (T)sgn_flip(wt.c, __popc(base & wt.zout) & 1u);
+        szt[t] = wt.zt;
+    }
+    __syncthreads();
+    const uint32_t lowmask = (1u << m) - 1u;
+    for (uint32_t e = tid; e < size; e += blockDim.x)
+        sp[e] = P[(size_t)(base | (e & lowmask) | soff[e >> m])];
     __syncthreads();
     double acc = 0.0, nrm = 0.0;
     if (W.with_norm) {
         T pn = T(0);
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
-            const C x = sp[threadIdx.x + j * kEnergyWinThreads];
+            const C x = sp[tid + j * kEnergyWinThreads];
             pn += fma(x.x, x.x, x.y * x.y);
         }
         nrm = (double)pn;
@@ -439,54 +507,85 @@ k_energy_win(WinDesc W, const GroupDesc *__restrict__ groups, const int *__restr
     constexpr int kRun = 8;
     T run = T(0);
     int in_run = 0;
-    for (int gi = W.g_begin; gi < W.g_end; ++gi) {
-        const GroupDesc G = groups[wgroups[gi]];
+    for (int gi = 0; gi < W.g_end - W.g_begin; ++gi) {
+        const WinGroup &G = sg[gi];
         T part = T(0);
-        if (G.x == 0u && hdiag) {
+        if (G.xl == 0u) {
+            if (!RUNS || hdiag) {   // the low window: global index = base | e
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                const uint32_t e = threadIdx.x + j * kEnergyWinThreads;
-                const C x = sp[e];
-                part = fma(fma(x.x, x.x, x.y * x.y), __ldg(hdiag + g32(e)), part);
-            }
-        } else if (G.x == 0u) {
-            uint32_t ge[EPT];
-            T f[EPT];
+                for (int j = 0; j < EPT; ++j) {
+                    const uint32_t e = tid + j * kEnergyWinThreads;
+                    const C x = sp[e];
+                    part = fma(fma(x.x, x.x, x.y * x.y), __ldg(hdiag + (size_t)(base | e)), part);
+                }
+            } else {
+                if constexpr (RUNS) {
+                T F[EPT];
+                run_sums<EPT>(F, G.arun, G.a_begin, sc, szt, tid);
+                wht_inplace<EPT>(F);
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                ge[j] = g32(threadIdx.x + j * kEnergyWinThreads);
-                f[j] = T(0);
-            }
-            sign_sums<T, EPT>(ge, f, tz, tc, G.t_begin, G.t_mid);
-#pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                const C x = sp[threadIdx.x + j * kEnergyWinThreads];
-                part = fma(fma(x.x, x.x, x.y * x.y), f[j], part);
+                for (int j = 0; j < EPT; ++j) {
+                    const C x = sp[tid + j * kEnergyWinThreads];
+                    part = fma(fma(x.x, x.x, x.y * x.y), F[j], part);
+                }
+                }
             }
         } else {
-            // X mask in tile coordinates
-            const uint32_t xl = (G.x & lowmask) | ((G.x >> a) << m);
-            const int hl = 31 - __clz(xl);
+            const uint32_t xl = G.xl;
+            const int hl = G.hl;
             const uint32_t lm = (1u << hl) - 1u;
-            uint32_t il[PPT], gi0[PPT];
-            T fa[PPT], fb[PPT];
+            const uint32_t il0 = ((tid >> hl) << (hl + 1)) | (tid & lm);
+            const bool has_b = G.b_end > G.b_begin;
+            if (!RUNS || G.direct) {
+                // few terms (at most kWinDirectMax per class): the terms sit in
+                // registers and each pair adds c * sign * conj(x0) x1 directly
+                T ca[kWinDirectMax], cb[kWinDirectMax];
+                uint32_t za[kWinDirectMax], zb[kWinDirectMax];
+                const int na = G.b_begin - G.a_begin, nb = G.b_end - G.b_begin;
 #pragma unroll
-            for (int j = 0; j < PPT; ++j) {
-                const uint32_t p = threadIdx.x + j * kEnergyWinThreads;
-                il[j] = ((p >> hl) << (hl + 1)) | (p & lm);
-                gi0[j] = g32(il[j]);
-                fa[j] = T(0);
-                fb[j] = T(0);
-            }
-            sign_sums<T, PPT>(gi0, fa, tz, tc, G.t_begin, G.t_mid);
-            const bool has_b = G.t_end > G.t_mid;
-            if (has_b) sign_sums<T, PPT>(gi0, fb, tz, tc, G.t_mid, G.t_end);
+                for (int u = 0; u < kWinDirectMax; ++u) {
+                    ca[u] = u < na ? sc[G.a_begin + u] : T(0);
+                    za[u] = u < na ? szt[G.a_begin + u] : 0u;
+                    cb[u] = u < nb ? sc[G.b_begin + u] : T(0);
+                    zb[u] = u < nb ? szt[G.b_begin + u] : 0u;
+                }
 #pragma unroll
-            for (int j = 0; j < PPT; ++j) {
-                const C x0 = sp[il[j]], x1 = sp[il[j] ^ xl];
-                const T ar = fma(x0.x, x1.x, x0.y * x1.y);
-                part = fma(ar, fa[j], part);
-                if (has_b) part = fma(fma(x0.x, x1.y, -x0.y * x1.x), fb[j], part);
+                for (int j = 0; j < PPT; ++j) {
+                    const uint32_t p = tid + j * kEnergyWinThreads;
+                    const uint32_t il = ((p >> hl) << (hl + 1)) | (p & lm);
+                    const C x0 = sp[il], x1 = sp[il ^ xl];
+                    const T ar = fma(x0.x, x1.x, x0.y * x1.y);   // Re conj(x0) x1
+#pragma unroll
+                    for (int u = 0; u < kWinDirectMax; ++u)
+                        if (u < na) part = fma(ar, sgn_flip(ca[u], __popc(il & za[u]) & 1u), part);
+                    if (has_b) {
+                        const T ai = fma(x0.x, x1.y, -x0.y * x1.x);   // Im conj(x0) x1
+#pragma unroll
+                        for (int u = 0; u < kWinDirectMax; ++u)
+                            if (u < nb) part = fma(ai, sgn_flip(cb[u], __popc(il & zb[u]) & 1u), part);
+                    }
+                }
+            } else if constexpr (RUNS) {
+                T ar[PPT], ai[PPT];
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    const uint32_t p = tid + j * kEnergyWinThreads;
+                    const uint32_t il = ((p >> hl) << (hl + 1)) | (p & lm);
+                    const C x0 = sp[il], x1 = sp[il ^ xl];
+                    ar[j] = fma(x0.x, x1.x, x0.y * x1.y);
+                    ai[j] = fma(x0.x, x1.y, -x0.y * x1.x);
+                }
+                T F[PPT];
+                run_sums<PPT>(F, G.arun, G.a_begin, sc, szt, il0);
+                wht_inplace<PPT>(F);
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) part = fma(ar[j], F[j], part);
+                if (has_b) {
+                    run_sums<PPT>(F, G.brun, G.b_begin, sc, szt, il0);
+                    wht_inplace<PPT>(F);
+#pragma unroll
+                    for (int j = 0; j < PPT; ++j) part = fma(ai[j], F[j], part);
+                }
             }
             part *= T(2);
         }
@@ -511,25 +610,33 @@ k_energy_win(WinDesc W, const GroupDesc *__restrict__ groups, const int *__restr
     }
 }
 
+size_t win_smem_bytes(const WinDesc &W, size_t elem_bytes) {
+    const size_t real = elem_bytes / 2;
+    return (size_t(1) << W.k) * elem_bytes + size_t(W.t_count) * (real + 4) +
+           (size_t(1) << (W.k - W.m)) * 4;
+}
+
 template <typename T>
-cudaError_t launch_energy_win(const WinDesc &W, const GroupDesc *groups, const int *wgroups,
-                              const uint32_t *tz, const double *tc, const void *hdiag,
-                              int n_qubits, int batch, const void *psi, size_t state_stride,
-                              double *partials, int bps_total, cudaStream_t s) {
+cudaError_t launch_energy_win(const WinDesc &W, const WinGroup *wgroups, const WinTerm *wterms,
+                              const uint32_t *hoff, const void *hdiag, int n_qubits, int batch,
+                              const void *psi, size_t state_stride, double *partials,
+                              int bps_total, cudaStream_t s) {
     using C = typename EV2<T>::type;
-    const size_t smem = (size_t(1) << W.k) * sizeof(C);
-    auto kern = W.k == 13 ? k_energy_win<T, 13> : (W.k == 12 ? k_energy_win<T, 12> : nullptr);
-    if (!kern) return cudaErrorInvalidValue;
+    const size_t smem = win_smem_bytes(W, sizeof(C));
+    auto kern = W.any_runs
+        ? (W.k == 13 ? k_energy_win<T, 13, true> : (W.k == 12 ? k_energy_win<T, 12, true> : nullptr))
+        : (W.k == 13 ? k_energy_win<T, 13, false> : (W.k == 12 ? k_energy_win<T, 12, false> : nullptr));
+    if (!kern || W.t_count > kWinMaxTerms || W.g_end - W.g_begin > kWinMaxGroups)
+        return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)(1ull << (n_qubits - W.k)), batch);
-    kern<<<grid, kEnergyWinThreads, smem, s>>>(W, groups, wgroups, tz,
-                                               reinterpret_cast<const T *>(tc),
-                                               static_cast<const T *>(hdiag), n_qubits,
-                                               static_cast<const C *>(psi), state_stride, partials,
-                                               bps_total);
+    kern<<<grid, kEnergyWinThreads, smem, s>>>(W, wgroups, wterms, hoff,
+                                               static_cast<const T *>(hdiag),
+                                               static_cast<const C *>(psi), state_stride,
+                                               partials, bps_total);
     return cudaGetLastError();
 }
 
@@ -549,14 +656,12 @@ cudaError_t launch_energy_sub(const GroupDesc *groups, int n_groups, const uint3
     return cudaGetLastError();
 }
 
-template cudaError_t launch_energy_win<float>(const WinDesc &, const GroupDesc *, const int *,
-                                              const uint32_t *, const double *, const void *, int,
-                                              int, const void *, size_t, double *, int,
-                                              cudaStream_t);
-template cudaError_t launch_energy_win<double>(const WinDesc &, const GroupDesc *, const int *,
-                                               const uint32_t *, const double *, const void *, int,
-                                               int, const void *, size_t, double *, int,
-                                               cudaStream_t);
+template cudaError_t launch_energy_win<float>(const WinDesc &, const WinGroup *, const WinTerm *,
+                                              const uint32_t *, const void *, int, int,
+                                              const void *, size_t, double *, int, cudaStream_t);
+template cudaError_t launch_energy_win<double>(const WinDesc &, const WinGroup *, const WinTerm *,
+                                               const uint32_t *, const void *, int, int,
+                                               const void *, size_t, double *, int, cudaStream_t);
 template cudaError_t launch_energy_sub<float>(const GroupDesc *, int, const uint32_t *,
                                               const double *, int, int, const void *, size_t,
                                               double *, int, int, int, cudaStream_t);

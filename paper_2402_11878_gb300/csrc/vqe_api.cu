@@ -66,7 +66,7 @@ struct vqe_ctx {
     int n_groups = 0;
     // windowed expectation: tile windows, their group lists, groups too wide for any window
     std::vector<WinDesc> wins;
-    DevBuf d_wgroups, d_wide;
+    DevBuf d_wgroups, d_wterms, d_whoff, d_wide;
     int n_wide = 0;
     int win_tiles = 0;   // columns of all windows per state
     // diagonal of H (one T per basis state), built when it fits in a quarter
@@ -646,67 +646,202 @@ double slim_keep(const std::vector<double> &cc, double threshold, std::vector<ui
 // x = 0 group); a group whose X mask above the low `mrun` bits spans at most
 // kE - mrun bits joins (or opens) a window [0, mrun) + [a, a + kE - mrun);
 // wider groups are swept over the whole state.
-void plan_windows(int n, vqe_precision prec, const HamPlan &hp, std::vector<WinDesc> &wins,
-                  std::vector<int> &wgroups, std::vector<GroupDesc> &wide, int &win_tiles) {
-    wins.clear();
-    wgroups.clear();
-    wide.clear();
-    win_tiles = 0;
-    const int kE = prec == VQE_C128 ? 12 : 13;
-    const int mrun = prec == VQE_C128 ? 3 : 4;
+struct WinPlan {
+    std::vector<WinDesc> wins;
+    std::vector<WinGroup> groups;
+    std::vector<WinTerm> terms;
+    std::vector<uint32_t> hoff;
+    std::vector<GroupDesc> wide;   // groups that fit no window: global sweeps
+    int win_tiles = 0;
+};
+
+// Tile coordinates of global mask g for a window with low run m and high
+// positions pos (increasing): bits [0, m) stay, bit pos[j] -> tile bit m + j.
+uint32_t win_gather(uint32_t g, int m, const std::vector<int> &pos) {
+    uint32_t t = g & ((1u << m) - 1u);
+    for (size_t j = 0; j < pos.size(); ++j)
+        if ((g >> pos[j]) & 1u) t |= 1u << (m + int(j));
+    return t;
+}
+
+// Windows of the windowed expectation (Sec. II-B Eq. 7 evaluated per X-mask
+// group): the low tile (with <psi|psi> and the diagonal group), then windows
+// of mrun low bits plus kE - mrun further bits chosen greedily so that every
+// group's X mask lies inside one window (a greedy cover of the groups' high
+// bits), each window holding at most kWinMaxTerms terms.  Groups with more
+// high bits than a window has go to the global sweep.  `diag_terms`: store
+// the diagonal group's terms (false when the diagonal of H is precomputed).
+void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms, WinPlan &wp) {
+    wp = WinPlan{};
+    const bool c128 = prec == VQE_C128;
+    const int kE = win_tile_bits(c128);
+    const int mrun = c128 ? 3 : 4;
     if (n <= kE) return;
     const int hw = kE - mrun;
-    std::vector<std::vector<int>> lists(1);
-    std::vector<int> win_a(1, kE);
+    const int lt = 9;                      // log2 of the kernel's 512 threads
+    const int EPT = 1 << (kE - lt), PPT = EPT / 2;
+
+    struct Cand {
+        int m;
+        uint32_t S;                        // high positions (bits >= m) of the window
+        std::vector<int> groups;
+        int terms = 0;
+        bool norm = false;
+    };
+    std::vector<Cand> cands;
+    auto group_terms = [&](int g) {
+        const GroupDesc &G = hp.groups[g];
+        if (G.x == 0u && !diag_terms) return 0;
+        return G.t_end - G.t_begin;
+    };
+    // the low tile: every group whose X mask lies in bits [0, kE); split when
+    // the term cap is reached (only the first part yields the norm)
+    cands.push_back({kE, 0u, {}, 0, true});
+    std::vector<int> rest;
     for (size_t g = 0; g < hp.groups.size(); ++g) {
         const uint32_t x = hp.groups[g].x;
         if (x < (1u << kE)) {
-            lists[0].push_back(int(g));
-            continue;
+            const int tg = group_terms(int(g));
+            if (tg > kWinMaxTerms) {                 // too many terms for any window
+                wp.wide.push_back(hp.groups[g]);
+                if (x == 0u) cands[0].norm = false;  // the sweep of the diagonal group yields the norm
+                continue;
+            }
+            if (cands.back().m != kE || cands.back().terms + tg > kWinMaxTerms ||
+                int(cands.back().groups.size()) >= kWinMaxGroups)
+                cands.push_back({kE, 0u, {}, 0, false});
+            cands.back().groups.push_back(int(g));
+            cands.back().terms += tg;
+        } else {
+            rest.push_back(int(g));
         }
-        const uint32_t xm = x & ~((1u << mrun) - 1u);
-        const int lo = __builtin_ctz(xm), hi = 31 - __builtin_clz(x);
-        if (hi - lo + 1 > hw) {
-            wide.push_back(hp.groups[g]);
-            continue;
-        }
-        int w = -1;
-        for (size_t j = 1; j < win_a.size(); ++j)
-            if (win_a[j] <= lo && hi < win_a[j] + hw) w = int(j);
-        if (w < 0) {
-            win_a.push_back(std::min(lo, n - hw));
-            lists.emplace_back();
-            w = int(win_a.size()) - 1;
-        }
-        lists[w].push_back(int(g));
     }
-    for (size_t j = 0; j < lists.size(); ++j) {
+    // other groups: greedy cover, groups with more high bits first
+    const uint32_t lowm = (1u << mrun) - 1u;
+    std::stable_sort(rest.begin(), rest.end(), [&](int p, int q) {
+        return __builtin_popcount(hp.groups[p].x & ~lowm) > __builtin_popcount(hp.groups[q].x & ~lowm);
+    });
+    const size_t first_free = cands.size();
+    for (int g : rest) {
+        const uint32_t H = hp.groups[g].x & ~lowm;
+        const int tg = group_terms(g);
+        if (__builtin_popcount(H) > hw || tg > kWinMaxTerms) {
+            wp.wide.push_back(hp.groups[g]);
+            continue;
+        }
+        int best = -1, best_add = 1 << 30;
+        for (size_t c = first_free; c < cands.size(); ++c) {
+            const uint32_t U = cands[c].S | H;
+            const int sz = __builtin_popcount(U);
+            if (sz > hw || cands[c].terms + tg > kWinMaxTerms ||
+                int(cands[c].groups.size()) >= kWinMaxGroups)
+                continue;
+            const int add = sz - __builtin_popcount(cands[c].S);
+            if (add < best_add) {
+                best_add = add;
+                best = int(c);
+            }
+        }
+        if (best < 0) {
+            cands.push_back({mrun, H, {}, 0, false});
+            best = int(cands.size()) - 1;
+        }
+        cands[best].S |= H;
+        cands[best].groups.push_back(g);
+        cands[best].terms += tg;
+    }
+    const uint32_t nmask = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+    for (Cand &c : cands) {
+        if (c.groups.empty() && !c.norm) continue;
+        // fill the high positions up to kE - m with the lowest free bits
+        for (int b = c.m; __builtin_popcount(c.S) < kE - c.m && b < n; ++b) c.S |= 1u << b;
+        std::vector<int> pos;
+        for (int b = 0; b < n; ++b)
+            if ((c.S >> b) & 1u) pos.push_back(b);
         WinDesc W{};
         W.k = kE;
-        W.m = j == 0 ? kE : mrun;
-        W.a = j == 0 ? kE : win_a[j];
-        W.g_begin = int(wgroups.size());
-        wgroups.insert(wgroups.end(), lists[j].begin(), lists[j].end());
-        W.g_end = int(wgroups.size());
-        W.block_off = win_tiles;
-        W.with_norm = j == 0 ? 1 : 0;
-        win_tiles += 1 << (n - kE);
-        wins.push_back(W);
+        W.m = c.m;
+        W.bmask = nmask & ~((1u << c.m) - 1u) & ~c.S;
+        W.hoff = int(wp.hoff.size());
+        for (uint32_t hh = 0; hh < (1u << (kE - c.m)); ++hh) {
+            uint32_t off = 0;
+            for (size_t j = 0; j < pos.size(); ++j)
+                if ((hh >> j) & 1u) off |= 1u << pos[j];
+            wp.hoff.push_back(off);
+        }
+        W.g_begin = int(wp.groups.size());
+        W.t_begin = int(wp.terms.size());
+        for (int g : c.groups) {
+            const GroupDesc &G = hp.groups[g];
+            WinGroup wg{};
+            wg.xl = win_gather(G.x, c.m, pos);
+            wg.hl = wg.xl ? 31 - __builtin_clz(wg.xl) : 0;
+            const int NV = wg.xl ? PPT : EPT;
+            // few terms: per-pair sign sums beat the transform over the
+            // register patterns and its per-run loop (FP64: up to 3 terms,
+            // FP32: up to 2)
+            const int n_t = (G.x != 0u || diag_terms) ? G.t_end - G.t_begin : 0;
+            wg.direct = (wg.xl != 0u && n_t <= std::min(kWinDirectMax, c128 ? 3 : 2)) ? 1 : 0;
+            // tile bit of register-pattern bit b: element bit lt + b of a
+            // thread's elements, or of its pairs after the zero inserted at hl
+            auto pattern = [&](uint32_t zt) {
+                uint32_t v = 0;
+                for (int bb = 0; (1 << bb) < NV; ++bb) {
+                    int q = lt + bb;
+                    if (wg.xl && q >= wg.hl) q += 1;
+                    v |= ((zt >> q) & 1u) << bb;
+                }
+                return v;
+            };
+            auto emit = [&](int t0, int t1, uint16_t *run, int &begin) {
+                begin = int(wp.terms.size()) - W.t_begin;
+                std::vector<std::pair<uint32_t, WinTerm>> ts;
+                for (int t = t0; t < t1; ++t) {
+                    WinTerm wt{};
+                    wt.zt = win_gather(hp.tz[t], c.m, pos);
+                    wt.zout = hp.tz[t] & W.bmask;
+                    wt.c = hp.tc[t];
+                    ts.push_back({pattern(wt.zt), wt});
+                }
+                if (!wg.direct)
+                    std::stable_sort(ts.begin(), ts.end(),
+                                     [](const auto &p, const auto &q) { return p.first < q.first; });
+                else
+                    for (auto &p : ts) p.first = 0;   // one run
+                int at = 0;
+                for (int v = 0; v <= NV; ++v) {
+                    while (at < int(ts.size()) && int(ts[at].first) < v) ++at;
+                    run[v] = uint16_t(at);
+                }
+                for (auto &p : ts) wp.terms.push_back(p.second);
+            };
+            const bool keep = G.x != 0u || diag_terms;
+            int bdummy = 0;
+            emit(G.t_begin, keep ? G.t_mid : G.t_begin, wg.arun, wg.a_begin);
+            emit(G.t_mid, keep ? G.t_end : G.t_mid, wg.brun, wg.b_begin);
+            (void)bdummy;
+            wg.b_end = int(wp.terms.size()) - W.t_begin;
+            wp.groups.push_back(wg);
+        }
+        W.g_end = int(wp.groups.size());
+        W.t_count = int(wp.terms.size()) - W.t_begin;
+        W.any_runs = 0;
+        for (int gi = W.g_begin; gi < W.g_end; ++gi) {
+            const WinGroup &wg = wp.groups[gi];
+            // transform path: a pair group that is not direct, or the diagonal
+            // group with its terms (no precomputed diagonal)
+            if ((wg.xl != 0u && !wg.direct) || (wg.xl == 0u && wg.b_end > wg.a_begin)) W.any_runs = 1;
+        }
+        W.block_off = wp.win_tiles;
+        W.with_norm = c.norm ? 1 : 0;
+        wp.win_tiles += 1 << (n - kE);
+        wp.wins.push_back(W);
     }
 }
 
 vqe_status build_ham_plan(vqe_ctx *h) {
     HamPlan hp;
     make_ham_plan(h->cx, h->cz, h->cc, h->keep, hp);
-    {
-        std::vector<int> wg;
-        std::vector<GroupDesc> wide;
-        plan_windows(h->n, h->prec, hp, h->wins, wg, wide, h->win_tiles);
-        h->n_wide = int(wide.size());
-        vqe_status st;
-        if ((st = upload(h, h->d_wgroups, wg, "window groups")) != VQE_OK) return st;
-        if ((st = upload(h, h->d_wide, wide, "wide groups")) != VQE_OK) return st;
-    }
     h->n_groups = int(hp.groups.size());
     vqe_status st;
     h->hdiag_ok = false;
@@ -732,6 +867,17 @@ vqe_status build_ham_plan(vqe_ctx *h) {
             h->stats.kernel_launches++;
             h->hdiag_ok = true;
         }
+    }
+    {
+        WinPlan wp;
+        plan_windows(h->n, h->prec, hp, !h->hdiag_ok, wp);
+        h->wins = wp.wins;
+        h->win_tiles = wp.win_tiles;
+        h->n_wide = int(wp.wide.size());
+        if ((st = upload(h, h->d_wgroups, wp.groups, "window groups")) != VQE_OK) return st;
+        if ((st = upload(h, h->d_wterms, wp.terms, "window terms")) != VQE_OK) return st;
+        if ((st = upload(h, h->d_whoff, wp.hoff, "window offsets")) != VQE_OK) return st;
+        if ((st = upload(h, h->d_wide, wp.wide, "wide groups")) != VQE_OK) return st;
     }
     if ((st = upload(h, h->d_groups, hp.groups, "groups")) != VQE_OK) return st;
     if ((st = upload(h, h->d_tz, hp.tz, "terms")) != VQE_OK) return st;
@@ -875,12 +1021,11 @@ vqe_status run_energy(vqe_ctx *h, int B, const void *psi, double *energies, doub
         double *part = static_cast<double *>(h->d_epart.p);
         const int mk = prof_begin(h, 1);
         for (const WinDesc &W : h->wins) {
-            VQE_CUDA(h, launch_energy_win<T>(W, static_cast<const GroupDesc *>(h->d_groups.p),
-                                             static_cast<const int *>(h->d_wgroups.p),
-                                             static_cast<const uint32_t *>(h->d_tz.p),
-                                             static_cast<const double *>(h->d_tc.p), h->hdiag(),
-                                             h->n, B, psi, h->state_elems(), part, bps_total,
-                                             h->stream));
+            VQE_CUDA(h, launch_energy_win<T>(W, static_cast<const WinGroup *>(h->d_wgroups.p),
+                                             static_cast<const WinTerm *>(h->d_wterms.p),
+                                             static_cast<const uint32_t *>(h->d_whoff.p),
+                                             h->hdiag(), h->n, B, psi, h->state_elems(), part,
+                                             bps_total, h->stream));
             h->stats.kernel_launches++;
         }
         if (h->n_wide) {
@@ -1075,7 +1220,8 @@ vqe_status vqe_destroy(vqe_handle h) {
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->plan[0].release();
     h->plan[1].release();
-    for (DevBuf *b : {&h->d_groups, &h->d_tz, &h->d_tc, &h->d_wgroups, &h->d_wide, &h->d_hdiag,
+    for (DevBuf *b : {&h->d_groups, &h->d_tz, &h->d_tc, &h->d_wgroups, &h->d_wterms, &h->d_whoff,
+                      &h->d_wide, &h->d_hdiag,
                       &h->d_hdiag_z, &h->d_hdiag_c, &h->ws_own, &h->d_params, &h->d_coefs,
                       &h->d_dtab, &h->d_gpart, &h->d_epart, &h->d_out, &h->hb_params,
                       &h->hb_e, &h->hb_n, &h->hb_g, &h->d_err})
@@ -1364,6 +1510,8 @@ size_t vqe_inspect_sizeof(int which) {
         case 1: return sizeof(StageSlot);
         case 2: return sizeof(GroupDesc);
         case 3: return sizeof(WinDesc);
+        case 4: return sizeof(WinGroup);
+        case 5: return sizeof(WinTerm);
         default: return 0;
     }
 }
@@ -1439,8 +1587,9 @@ int vqe_inspect_hamiltonian(int n_qubits, const uint64_t *x_masks, const uint64_
 
 int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
                         const uint64_t *z_masks, const double *coeffs, size_t n_terms,
-                        double threshold, void *windows, int max_windows, int *wgroups,
-                        int max_wgroups, void *wide, int max_wide, int counts[3]) {
+                        double threshold, int diag_terms, void *windows, int max_windows,
+                        void *wgroups, int max_wgroups, void *wterms, int max_wterms,
+                        uint32_t *hoff, int max_hoff, void *wide, int max_wide, int counts[5]) {
     if (n_qubits < 1 || n_qubits > 32 || (precision != 0 && precision != 1)) return -1;
     if (n_terms && (!x_masks || !z_masks || !coeffs)) return -1;
     const uint64_t lim = (uint64_t(1) << n_qubits) - 1;
@@ -1454,21 +1603,24 @@ int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
     slim_keep(cc, threshold, keep, kept);
     HamPlan hp;
     make_ham_plan(cx, cz, cc, keep, hp);
-    std::vector<WinDesc> wins;
-    std::vector<int> wg;
-    std::vector<GroupDesc> wd;
-    int tiles = 0;
-    plan_windows(n_qubits, vqe_precision(precision), hp, wins, wg, wd, tiles);
+    WinPlan wp;
+    plan_windows(n_qubits, vqe_precision(precision), hp, diag_terms != 0, wp);
     if (counts) {
-        counts[0] = int(wins.size());
-        counts[1] = int(wg.size());
-        counts[2] = int(wd.size());
+        counts[0] = int(wp.wins.size());
+        counts[1] = int(wp.groups.size());
+        counts[2] = int(wp.terms.size());
+        counts[3] = int(wp.hoff.size());
+        counts[4] = int(wp.wide.size());
     }
-    if (int(wins.size()) > max_windows || int(wg.size()) > max_wgroups || int(wd.size()) > max_wide)
+    if (int(wp.wins.size()) > max_windows || int(wp.groups.size()) > max_wgroups ||
+        int(wp.terms.size()) > max_wterms || int(wp.hoff.size()) > max_hoff ||
+        int(wp.wide.size()) > max_wide)
         return -1;
-    if (windows) std::memcpy(windows, wins.data(), wins.size() * sizeof(WinDesc));
-    if (wgroups) std::memcpy(wgroups, wg.data(), wg.size() * sizeof(int));
-    if (wide) std::memcpy(wide, wd.data(), wd.size() * sizeof(GroupDesc));
+    if (windows) std::memcpy(windows, wp.wins.data(), wp.wins.size() * sizeof(WinDesc));
+    if (wgroups) std::memcpy(wgroups, wp.groups.data(), wp.groups.size() * sizeof(WinGroup));
+    if (wterms) std::memcpy(wterms, wp.terms.data(), wp.terms.size() * sizeof(WinTerm));
+    if (hoff) std::memcpy(hoff, wp.hoff.data(), wp.hoff.size() * sizeof(uint32_t));
+    if (wide) std::memcpy(wide, wp.wide.data(), wp.wide.size() * sizeof(GroupDesc));
     return 0;
 }
 

@@ -110,11 +110,49 @@ constexpr int kEnergyWinThreads = 512;
 // One energy window: tile bits [0, m) and [m, k) -> global [a, a + k - m);
 // groups wgroups[g_begin, g_end) are evaluated from the staged tile; block
 // partials go to columns [block_off, block_off + 2^(n-k)).
+// Window of the windowed expectation kernel.  Tile bits [0, m) are global
+// bits [0, m); tile bits [m, k) are k - m further global bits in increasing
+// order (any positions), placed through the window's table of 2^(k-m) high-part
+// offsets; the tile number fills the remaining global bits `bmask` in
+// increasing order.
 struct WinDesc {
-    int k, m, a;
-    int g_begin, g_end;
-    int block_off;
-    int with_norm;
+    int k, m;
+    int g_begin, g_end;     // window groups [g_begin, g_end) (WinGroup array)
+    int t_begin, t_count;   // window terms [t_begin, t_begin + t_count) (WinTerm array)
+    int hoff;               // first of the window's 2^(k-m) high-part offsets
+    uint32_t bmask;         // global bits taken from the tile number
+    int block_off;          // first block-partial column of the window
+    int with_norm;          // also yields <psi|psi> (the low window)
+    int any_runs;           // some group uses the register-pattern transform
+};
+
+// Largest numbers of terms and groups of one window (staged in shared memory
+// per tile) and of register patterns of a window group's terms.
+constexpr int kWinMaxTerms = 2048;
+constexpr int kWinMaxGroups = 96;
+constexpr int kWinMaxRuns = 16;
+constexpr int kWinDirectMax = 3;   // terms per class of a window group in direct mode
+
+// A group inside a window.  Its terms are window-relative: A terms
+// [a_begin, b_begin), B terms [b_begin, b_end), each class sorted by its
+// register pattern v (the term's Z bits at the tile bits that distinguish a
+// thread's pairs, or a thread's elements for the diagonal group xl == 0);
+// arun[v] / brun[v] are the run starts relative to the class start and
+// arun[NV] / brun[NV] the class length.
+struct WinGroup {
+    uint32_t xl;            // X mask in tile coordinates (0: the diagonal group)
+    int hl;                 // top bit of xl
+    int direct;             // 1: terms unsorted, sign sums per pair (groups of few terms)
+    int a_begin, b_begin, b_end;
+    uint16_t arun[kWinMaxRuns + 1];
+    uint16_t brun[kWinMaxRuns + 1];
+};
+
+// A term inside a window: its Z bits at tile positions (zt), its Z bits at
+// tile-number positions (zout), and its sign-folded coefficient.
+struct WinTerm {
+    uint32_t zt, zout;
+    double c;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -145,10 +183,13 @@ cudaError_t launch_apply_h(const GroupDesc *groups, int n_groups, const uint32_t
                            int blocks_per_state, cudaStream_t s);
 
 template <typename T>
-cudaError_t launch_energy_win(const WinDesc &W, const GroupDesc *groups, const int *wgroups,
-                              const uint32_t *tz, const double *tc, const void *hdiag,
-                              int n_qubits, int batch, const void *psi, size_t state_stride,
-                              double *partials, int bps_total, cudaStream_t s);
+cudaError_t launch_energy_win(const WinDesc &W, const WinGroup *wgroups, const WinTerm *wterms,
+                              const uint32_t *hoff, const void *hdiag, int n_qubits, int batch,
+                              const void *psi, size_t state_stride, double *partials,
+                              int bps_total, cudaStream_t s);
+// Tile bits (log2 of elements) of the windowed expectation for a precision:
+// 512 threads hold 2^(kWinBits - 9) elements each.
+constexpr int win_tile_bits(bool c128) { return c128 ? 12 : 13; }
 
 // Diagonal of H from the x = 0 group's terms (z masks, FP64 coefficients with
 // the Pauli phase folded): D[i] for i < 2^n_qubits, stored as T.  `hdiag`

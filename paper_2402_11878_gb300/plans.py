@@ -49,14 +49,32 @@ class GroupDesc(ctypes.Structure):
                 ("t_mid", ctypes.c_int), ("t_end", ctypes.c_int)]
 
 
+K_WIN_MAX_RUNS = 16
+K_WIN_MAX_TERMS = 2048
+K_WIN_MAX_GROUPS = 96
+
+
 class WinDesc(ctypes.Structure):
-    _fields_ = [("k", ctypes.c_int), ("m", ctypes.c_int), ("a", ctypes.c_int),
-                ("g_begin", ctypes.c_int), ("g_end", ctypes.c_int), ("block_off", ctypes.c_int),
-                ("with_norm", ctypes.c_int)]
+    _fields_ = [("k", ctypes.c_int), ("m", ctypes.c_int), ("g_begin", ctypes.c_int),
+                ("g_end", ctypes.c_int), ("t_begin", ctypes.c_int), ("t_count", ctypes.c_int),
+                ("hoff", ctypes.c_int), ("bmask", ctypes.c_uint32), ("block_off", ctypes.c_int),
+                ("with_norm", ctypes.c_int), ("any_runs", ctypes.c_int)]
+
+
+class WinGroup(ctypes.Structure):
+    _fields_ = [("xl", ctypes.c_uint32), ("hl", ctypes.c_int), ("direct", ctypes.c_int),
+                ("a_begin", ctypes.c_int),
+                ("b_begin", ctypes.c_int), ("b_end", ctypes.c_int),
+                ("arun", ctypes.c_uint16 * (K_WIN_MAX_RUNS + 1)),
+                ("brun", ctypes.c_uint16 * (K_WIN_MAX_RUNS + 1))]
+
+
+class WinTerm(ctypes.Structure):
+    _fields_ = [("zt", ctypes.c_uint32), ("zout", ctypes.c_uint32), ("c", ctypes.c_double)]
 
 
 def _check_layouts(lib):
-    for which, cls in enumerate((PassDesc, StageSlot, GroupDesc, WinDesc)):
+    for which, cls in enumerate((PassDesc, StageSlot, GroupDesc, WinDesc, WinGroup, WinTerm)):
         got = lib.vqe_inspect_sizeof(which)
         if got != ctypes.sizeof(cls):
             raise RuntimeError(f"record layout mismatch for {cls.__name__}: library {got}, "
@@ -119,24 +137,31 @@ def hamiltonian(n_qubits: int, x, z, c, threshold: float = 0.0) -> dict:
             "sum_abs_dropped": dropped.value, "n_canonical": ncanon.value}
 
 
-def windows(n_qubits: int, precision: str, x, z, c, threshold: float = 0.0) -> dict:
-    """Windows of the windowed expectation kernel, as the library plans them."""
+def windows(n_qubits: int, precision: str, x, z, c, threshold: float = 0.0,
+            diag_terms: bool = True) -> dict:
+    """Windows of the windowed expectation kernel, as the library plans them:
+    window records, window groups, window terms, high-part offsets, wide groups."""
     lib = load()
     _check_layouts(lib)
     prec = {"c64": 0, "c128": 1}[precision]
     x = np.ascontiguousarray(x, dtype=np.uint64)
     z = np.ascontiguousarray(z, dtype=np.uint64)
     c = np.ascontiguousarray(c, dtype=np.float64)
-    counts = (ctypes.c_int * 3)()
+    counts = (ctypes.c_int * 5)()
     lib.vqe_inspect_windows(n_qubits, prec, x.ctypes.data, z.ctypes.data, c.ctypes.data, c.size,
-                            float(threshold), None, 0, None, 0, None, 0, counts)
-    nw, ng, nd = counts[0], counts[1], counts[2]
+                            float(threshold), int(diag_terms), None, 0, None, 0, None, 0, None, 0,
+                            None, 0, counts)
+    nw, ng, nt, nh, nd = (counts[i] for i in range(5))
     wins = (WinDesc * max(nw, 1))()
-    wg = np.zeros(max(ng, 1), dtype=np.int32)
+    wg = (WinGroup * max(ng, 1))()
+    wt = (WinTerm * max(nt, 1))()
+    hoff = np.zeros(max(nh, 1), dtype=np.uint32)
     wide = (GroupDesc * max(nd, 1))()
     rc = lib.vqe_inspect_windows(n_qubits, prec, x.ctypes.data, z.ctypes.data, c.ctypes.data,
-                                 c.size, float(threshold), ctypes.addressof(wins), nw,
-                                 wg.ctypes.data, ng, ctypes.addressof(wide), nd, counts)
+                                 c.size, float(threshold), int(diag_terms), ctypes.addressof(wins),
+                                 nw, ctypes.addressof(wg), ng, ctypes.addressof(wt), nt,
+                                 hoff.ctypes.data, nh, ctypes.addressof(wide), nd, counts)
     if rc != 0:
         raise ValueError("vqe_inspect_windows rejected the input")
-    return {"windows": list(wins)[:nw], "wgroups": wg[:ng], "wide": list(wide)[:nd]}
+    return {"windows": list(wins)[:nw], "wgroups": list(wg)[:ng], "wterms": list(wt)[:nt],
+            "hoff": hoff[:nh], "wide": list(wide)[:nd]}

@@ -296,57 +296,121 @@ def apply_h_terms(ham, n, psi):
     return lam
 
 
-def energy_windows(ham, win, n, psi):
-    """The windowed expectation kernel on the CPU: each window's tiles staged,
-    its groups evaluated from the tile, wide groups swept; (E, norm)."""
-    groups, tz, tc = ham["groups"], ham["tz"], ham["tc"]
+def _insert0(p, hl):
+    return ((p >> hl) << (hl + 1)) | (p & ((1 << hl) - 1))
+
+
+def _wht_last(F):
+    """f[..., j] = sum_v F[..., v] (-1)^{popc(j & v)} (unnormalised)."""
+    F = F.copy()
+    N = F.shape[-1]
+    h = 1
+    while h < N:
+        for i in range(N):
+            if i & h:
+                continue
+            x, y = F[..., i].copy(), F[..., i | h].copy()
+            F[..., i], F[..., i | h] = x + y, x - y
+        h <<= 1
+    return F
+
+
+def energy_windows(ham, win, n, psi, hdiag=None):
+    """The windowed expectation kernel on the CPU, step by step as the device
+    runs it: base bits from the tile number, elements placed through the
+    window's offset table, coefficients with the base sign folded in, per-run
+    sign sums at each thread's first pair and a Walsh-Hadamard transform over
+    the register patterns; wide groups swept; (E, norm)."""
+    tz, tc = ham["tz"], ham["tc"]
     acc, nrm = 0.0, 0.0
-    covered = 0
+    norms = 0
+    LT, THR = 9, 512
+    tid = np.arange(THR, dtype=np.int64)
     for W in win["windows"]:
-        k, m, a = W.k, W.m, W.a
-        mid = a - m
-        assert 0 <= mid and a + (k - m) <= n and k <= 14
+        k, m = W.k, W.m
+        EPT = 1 << (k - LT)
+        PPT = EPT // 2
         tiles = 1 << (n - k)
-        tile = np.arange(tiles, dtype=np.int64)[:, None]
-        e = np.arange(1 << k, dtype=np.int64)[None, :]
-        base = ((tile & ((1 << mid) - 1)) << m) | ((tile >> mid) << (a + (k - m)))
-        g = base | (e & ((1 << m) - 1)) | ((e >> m) << a)
+        assert W.t_count <= P.K_WIN_MAX_TERMS and W.g_end - W.g_begin <= P.K_WIN_MAX_GROUPS
+        bpos = [bb for bb in range(32) if (W.bmask >> bb) & 1]
+        assert len(bpos) == n - k and max(bpos + [0]) < n
+        tn = np.arange(tiles, dtype=np.int64)
+        base = np.zeros(tiles, dtype=np.int64)
+        for i, bb in enumerate(bpos):
+            base |= ((tn >> i) & 1) << bb
+        hoff = np.asarray(win["hoff"][W.hoff:W.hoff + (1 << (k - m))], dtype=np.int64)
+        assert hoff.size == 1 << (k - m)
+        e = np.arange(1 << k, dtype=np.int64)
+        g = base[:, None] | (e & ((1 << m) - 1))[None, :] | hoff[e >> m][None, :]
         flat = g.ravel()
-        assert np.unique(flat).size == flat.size == (1 << n)
+        assert flat.min() >= 0 and flat.max() < (1 << n)
+        assert np.unique(flat).size == flat.size == (1 << n), "tiles must partition the state"
         sp = psi[g]
+        terms = win["wterms"][W.t_begin:W.t_begin + W.t_count]
+        zt = np.array([t.zt for t in terms], dtype=np.int64)
+        zout = np.array([t.zout for t in terms], dtype=np.int64)
+        cc = np.array([t.c for t in terms], dtype=np.float64)
+        assert np.all(zout & ~W.bmask == 0) and np.all(zt < (1 << k))
+        sc = cc[None, :] * (1 - 2 * (popc(base[:, None] & zout[None, :]) & 1)) if len(terms) else np.zeros((tiles, 0))
         if W.with_norm:
             nrm += float((np.abs(sp) ** 2).sum())
-            covered += 1
-        for gi in win["wgroups"][W.g_begin:W.g_end]:
-            G = groups[gi]
-            if G.x == 0:
-                f = np.zeros(g.shape)
-                for t_ in range(G.t_begin, G.t_mid):
-                    f += tc[t_] * (1 - 2 * (popc(g & int(tz[t_])) & 1))
-                acc += float((np.abs(sp) ** 2 * f).sum())
+            norms += 1
+        for G in win["wgroups"][W.g_begin:W.g_end]:
+            NV = PPT if G.xl else EPT
+            assert 0 <= G.a_begin <= G.b_begin <= G.b_end <= W.t_count
+            assert G.arun[0] == 0 and G.a_begin + G.arun[NV] == G.b_begin
+            assert G.brun[0] == 0 and G.b_begin + G.brun[NV] == G.b_end
+            assert all(G.arun[v] <= G.arun[v + 1] for v in range(NV))
+            assert all(G.brun[v] <= G.brun[v + 1] for v in range(NV))
+
+            def run_sums(run, begin, e0):
+                F = np.zeros((tiles, THR, NV))
+                for v in range(NV):
+                    for t in range(begin + run[v], begin + run[v + 1]):
+                        sgn = 1 - 2 * (popc(e0 & zt[t]) & 1)
+                        F[:, :, v] += sc[:, t][:, None] * sgn[None, :]
+                return _wht_last(F)
+
+            if G.xl == 0:
+                el = tid[:, None] + THR * np.arange(EPT)[None, :]          # (THR, EPT)
+                w2 = np.abs(sp[:, el]) ** 2                                 # (tiles, THR, EPT)
+                if hdiag is not None:
+                    f = hdiag[g[:, el]]
+                else:
+                    f = run_sums(G.arun, G.a_begin, tid)
+                acc += float((w2 * f).sum())
                 continue
-            xl = (G.x & ((1 << m) - 1)) | ((G.x >> a) << m)
-            assert xl < (1 << k), "group outside its window"
-            # the window must hold every bit of x
-            assert ((xl & ((1 << m) - 1)) | ((xl >> m) << a)) == G.x
-            hl = int(xl).bit_length() - 1
-            p = np.arange(1 << (k - 1), dtype=np.int64)[None, :]
-            i0 = ((p >> hl) << (hl + 1)) | (p & ((1 << hl) - 1))
-            i1 = i0 ^ xl
-            x0 = np.take_along_axis(sp, np.broadcast_to(i0, (tiles, i0.shape[1])), axis=1)
-            x1 = np.take_along_axis(sp, np.broadcast_to(i1, (tiles, i1.shape[1])), axis=1)
-            gi0 = base | (i0 & ((1 << m) - 1)) | ((i0 >> m) << a)
+            xl, hl = int(G.xl), int(G.hl)
+            assert xl < (1 << k) and (xl >> hl) == 1
+            pj = tid[:, None] + THR * np.arange(PPT)[None, :]
+            il = _insert0(pj, hl)
+            assert il.max() < (1 << k) and (il ^ xl).max() < (1 << k)
+            x0, x1 = sp[:, il], sp[:, il ^ xl]
             prod = np.conj(x0) * x1
-            fa = np.zeros(gi0.shape)
-            fb = np.zeros(gi0.shape)
-            for t_ in range(G.t_begin, G.t_mid):
-                fa += tc[t_] * (1 - 2 * (popc(gi0 & int(tz[t_])) & 1))
-            for t_ in range(G.t_mid, G.t_end):
-                fb += tc[t_] * (1 - 2 * (popc(gi0 & int(tz[t_])) & 1))
-            acc += 2.0 * float((prod.real * fa + prod.imag * fb).sum())
+            il0 = _insert0(tid, hl)
+
+            def direct_sums(t0, t1):
+                f = np.zeros((tiles, THR, PPT))
+                for t in range(t0, t1):
+                    sgn = 1 - 2 * (popc(il & zt[t]) & 1)          # (THR, PPT)
+                    f += sc[:, t][:, None, None] * sgn[None, :, :]
+                return f
+
+            if G.direct:
+                part = (prod.real * direct_sums(G.a_begin, G.b_begin)).sum()
+                if G.b_end > G.b_begin:
+                    part += (prod.imag * direct_sums(G.b_begin, G.b_end)).sum()
+            else:
+                part = (prod.real * run_sums(G.arun, G.a_begin, il0)).sum()
+                if G.b_end > G.b_begin:
+                    part += (prod.imag * run_sums(G.brun, G.b_begin, il0)).sum()
+            acc += 2.0 * float(part)
     if win["wide"]:
         sub = {"groups": win["wide"], "tz": tz, "tc": tc}
-        e_w, _ = energy_terms(sub, n, psi)
+        e_w, n_w = energy_terms(sub, n, psi)
         acc += e_w
-    assert covered == 1
+        if any(G.x == 0 for G in win["wide"]):
+            nrm += n_w
+            norms += 1
+    assert norms == 1
     return acc, nrm

@@ -191,14 +191,20 @@ def test_energy_windows_emulated(oracle_mod, prec, case):
     p = vi.ansatz_params(31, n, 1)
     psi = oracle_mod.ansatz_state(n, 1, p)
     ham = P.hamiltonian(n, H.x, H.z, H.c)
-    win = P.windows(n, prec, H.x, H.z, H.c)
-    assert win["windows"], "expected windows above the tile size"
-    n_in = len(win["wgroups"]) + len(win["wide"])
-    assert n_in == len(ham["groups"])
-    assert sorted(win["wgroups"].tolist()) == sorted(set(win["wgroups"].tolist()))
-    e, nn = energy_windows(ham, win, n, psi)
     e_ref, _, n_ref = oracle_mod.expectation(psi, H.x, H.z, H.c)
-    assert abs(e - e_ref) < 1e-11 * H.sum_abs() and abs(nn - n_ref) < 1e-12
+    # the diagonal of H from the x = 0 group, as the library precomputes it
+    i = np.arange(1 << n, dtype=np.int64)
+    hdiag = np.zeros(1 << n)
+    for G in ham["groups"]:
+        if G.x == 0:
+            for t in range(G.t_begin, G.t_mid):
+                hdiag += ham["tc"][t] * (1 - 2 * (np.vectorize(lambda v: bin(v).count("1"))(i & int(ham["tz"][t])) & 1))
+    for diag_terms in (True, False):
+        win = P.windows(n, prec, H.x, H.z, H.c, diag_terms=diag_terms)
+        assert win["windows"], "expected windows above the tile size"
+        assert len(win["wgroups"]) + len(win["wide"]) == len(ham["groups"])
+        e, nn = energy_windows(ham, win, n, psi, hdiag=None if diag_terms else hdiag)
+        assert abs(e - e_ref) < 1e-11 * H.sum_abs() and abs(nn - n_ref) < 1e-12
 
 
 def _tile_map_ok(n, k, m, a):
@@ -241,13 +247,14 @@ def test_full_size_index_ranges(n, D, prec):
     H = vi.hubbard_2d_snake(4, 4, 1.0, 4.0) if n == 32 else vi.hubbard_1d(n // 2, 1.0, 4.0, periodic=True)
     w = P.windows(n, prec, H.x, H.z, H.c)
     for W in w["windows"]:
-        _tile_map_ok(n, W.k, W.m, W.a)
+        assert bin(W.bmask).count("1") == n - W.k and W.bmask < (1 << n)
+        hoff = w["hoff"][W.hoff:W.hoff + (1 << (W.k - W.m))]
+        hbits = int(np.bitwise_or.reduce(hoff)) if hoff.size else 0
+        # tile bits: the low run, the offset table's bits and the tile-number bits partition [0, n)
+        assert hbits & W.bmask == 0 and hbits & ((1 << W.m) - 1) == 0
+        assert (hbits | W.bmask | ((1 << W.m) - 1)) == (1 << n) - 1
         assert (1 << (n - W.k)) <= 2 ** 31 - 1
-    hp = P.hamiltonian(n, H.x, H.z, H.c)
-    for W in w["windows"]:
-        win_bits = ((1 << W.m) - 1) | (((1 << (W.k - W.m)) - 1) << W.a)
-        for gi in w["wgroups"][W.g_begin:W.g_end]:
-            assert hp["groups"][gi].x & ~win_bits == 0, "group X mask outside its window"
+        assert W.t_count <= P.K_WIN_MAX_TERMS
 
 
 @pytest.mark.parametrize("prec", ["c64", "c128"])

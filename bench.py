@@ -29,10 +29,10 @@ U_VALUES = (2.0, 4.0, 8.0)
 CHUNK = 64                      # states per workspace chunk (64 x 16 MiB = 1 GiB > L2)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
 # DRAM read+write bytes per state of one forward-pass launch (k_pass<double,3,fwd>,
-# 20 qubits, default plan), from the ncu capture summarised in
-# profiles/k_pass_c128_fwd_20q.md.  None once the kernel changes, until the
-# capture is taken again.
-PASS_DRAM_BYTES_PER_STATE = None
+# 20 qubits, default plan), from the ncu capture of bench-sized launches
+# summarised in profiles/launches_hubbard20_bench.md.  None once the kernel
+# changes, until the capture is taken again.
+PASS_DRAM_BYTES_PER_STATE = 2096917504 / 64
 METRIC = "energy+gradient evals/s at 8-32 qubits; achieved HBM GB/s vs GB300 peak"
 WORKLOAD = ("20q FP64 (complex128) 10-site periodic 1D Hubbard t=1 U in {2,4,8}, "
             "HEA depth 10, 1000 param vectors per U, energy only")

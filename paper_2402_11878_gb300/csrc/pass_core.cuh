@@ -57,6 +57,12 @@ template <typename T> __host__ __device__ constexpr uint32_t pad_of(uint32_t e) 
     return e + (e >> PadShift<T>::value);
 }
 
+// A chunk known only at run time, with the same `value` member as ChunkC: code
+// written against `pc.value` compiles for both (constant-folded for ChunkC).
+struct RtChunk {
+    int value;
+};
+
 // Calls f(std::integral_constant<int, P>) for the runtime chunk p, P in [0, 14 - R].
 template <int R, class F>
 __device__ __forceinline__ void with_chunk(int p, F &&f) {
@@ -202,7 +208,7 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
             const int p = op.chunk;
             if (chunk < 0) {
                 if (active) {
-                    with_chunk<R>(p, [&](auto pc) {
+                    auto first_round = [&](auto pc) {
                         constexpr int P = decltype(pc)::value;
                         if constexpr (Env::kLoad == 1) {
                             direct_load(pc);
@@ -213,15 +219,18 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                                 v[r] = buf[sb + pad_of<T>((uint32_t)r << P)];
                                 if (BWD) w[r] = lbuf[sb + pad_of<T>((uint32_t)r << P)];
                             }
-                        } else {
-                            const uint32_t e0 = elem_of(t, 0, P, R);
-#pragma unroll
-                            for (int r = 0; r < NR; ++r) {
-                                v[r] = buf[e0 + ((uint32_t)r << P)];
-                                if (BWD) w[r] = lbuf[e0 + ((uint32_t)r << P)];
-                            }
                         }
-                    });
+                    };
+                    if constexpr (Env::kLoad == 0) {   // plain order: one runtime instance
+                        const uint32_t e0 = elem_of(t, 0, p, R);
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            v[r] = buf[e0 + ((uint32_t)r << p)];
+                            if (BWD) w[r] = lbuf[e0 + ((uint32_t)r << p)];
+                        }
+                    } else {
+                        with_chunk<R>(p, first_round);
+                    }
                 }
             } else {
                 __syncthreads();
@@ -390,8 +399,10 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                 }
             }
             if (active) {
-                with_chunk<R>(chunk, [&](auto pc) {
-                    constexpr int P = decltype(pc)::value;
+                // compile-time chunk (constant register offsets) only where the
+                // diagonal is read as full table rows; else one runtime instance
+                auto diag_body = [&](auto pc) {
+                    const int P = pc.value;
                     const uint32_t e0 = elem_of(t, 0, P, R);
                     const uint32_t g0 = g32(e0);
                     // CZ signs of all NR registers as one mask (bit r = register r).
@@ -451,7 +462,9 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                             w[r] = z;
                         }
                     }
-                });
+                };
+                if constexpr (Env::kDiagRow) with_chunk<R>(chunk, diag_body);
+                else diag_body(RtChunk{chunk});
             }
         } else if (BWD && op.kind == OP_FLUSH) {
             __syncthreads();
@@ -474,15 +487,12 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
         // back to plain order in shared memory
         __syncthreads();
         if (active) {
-            with_chunk<R>(chunk, [&](auto pc) {
-                constexpr int P = decltype(pc)::value;
-                const uint32_t e0 = elem_of(t, 0, P, R);
+            const uint32_t e0 = elem_of(t, 0, chunk, R);
 #pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    buf[e0 + ((uint32_t)r << P)] = v[r];
-                    if (BWD) lbuf[e0 + ((uint32_t)r << P)] = w[r];
-                }
-            });
+            for (int r = 0; r < NR; ++r) {
+                buf[e0 + ((uint32_t)r << chunk)] = v[r];
+                if (BWD) lbuf[e0 + ((uint32_t)r << chunk)] = w[r];
+            }
         }
         __syncthreads();
     }

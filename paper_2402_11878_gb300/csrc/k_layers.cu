@@ -17,6 +17,7 @@
 // at a point of the sweep where both are valid (after the slot's diagonal is
 // undone and before q's own rotation is undone).
 #include <algorithm>
+#include <vector>
 
 #include "pass_core.cuh"
 
@@ -186,6 +187,117 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
     run_tile<T, R, BWD>(d, d.ops, d.n_ops, base, sp, sl, gsh, env);
 }
 
+// Forward pass with a program shape fixed at compile time (run_tile_fixed);
+// same staging and environment as k_pass.
+template <typename T, int R, int... Codes>
+__global__ void __launch_bounds__(kPassMaxThreads, (R > 4) ? 1 : 2)
+k_pass_fixed(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *__restrict__ psi,
+             size_t stride, const RotCoef<T> *__restrict__ coefs, size_t coef_stride,
+             const typename V2<T>::type *__restrict__ dtab, size_t dtab_stride) {
+    using C = typename V2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ PassDesc sd;
+    const int b = blockIdx.y;
+    const int kk = desc->k;
+    const uint32_t size = tile_buf_elems(kk, (int)sizeof(C));
+    C *sp = reinterpret_cast<C *>(smem_raw);
+    RotCoef<T> *scf = reinterpret_cast<RotCoef<T> *>(sp + size);
+    stage_pass<T>(desc, coefs + (size_t)b * coef_stride, &sd, scf);
+    const PassDesc &d = sd;
+    const int k = d.k, m = d.m, a = d.a;
+    const uint64_t tile = blockIdx.x;
+    const int mid = a - m;
+    const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (k - m)));
+    const uint32_t lowmask = (1u << m) - 1u;
+    GridEnv<T> env{&sd, scf, dtab + (size_t)b * dtab_stride, nullptr, tile, psi + (size_t)b * stride,
+                   nullptr, base, lowmask, m, a, init_zero};
+    run_tile_fixed<T, R, GridEnv<T>, Codes...>(d, d.ops, base, sp, env);
+}
+
+namespace {
+
+using FixedLaunch = cudaError_t (*)(const PassDesc *, const PassDesc &, int, int, void *, size_t,
+                                    const void *, size_t, const void *, size_t, int, cudaStream_t);
+
+template <typename T, int R, int... Codes>
+cudaError_t launch_fixed(const PassDesc *desc_dev, const PassDesc &dh, int n_qubits, int batch,
+                         void *psi, size_t stride, const void *coefs, size_t coef_stride,
+                         const void *dtab, size_t dtab_stride, int init_zero, cudaStream_t s) {
+    using C = typename V2<T>::type;
+    const int threads = 1 << (dh.k - dh.R);
+    const size_t smem = pass_smem_bytes(dh, false, sizeof(C));
+    auto kern = k_pass_fixed<T, R, Codes...>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)(1ull << (n_qubits - dh.k)), batch);
+    kern<<<grid, threads, smem, s>>>(desc_dev, init_zero, static_cast<C *>(psi), stride,
+                                     static_cast<const RotCoef<T> *>(coefs), coef_stride,
+                                     static_cast<const C *>(dtab), dtab_stride);
+    return cudaGetLastError();
+}
+
+struct FixedEntry {
+    int elem_bytes, R;
+    std::vector<int> codes;
+    FixedLaunch fn;
+};
+
+#define VQE_RD(c) prog_round(c)
+#define VQE_B kProgBF
+#define VQE_D kProgDiag
+#define VQE_FIXED(TT, RR, ...) \
+    FixedEntry{int(2 * sizeof(TT)), RR, std::vector<int>{__VA_ARGS__}, &launch_fixed<TT, RR, __VA_ARGS__>}
+
+// The forward program shapes of the default plans (tiles of 2^11; FP32 with
+// 16 amplitudes per thread: chunks 0, 4, 7; FP64 with 8: chunks 0, 3, 6, 8).
+const std::vector<FixedEntry> &fixed_programs() {
+    static const std::vector<FixedEntry> table = {
+        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_D, VQE_RD(7)),
+        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_RD(0), VQE_B, VQE_D, VQE_RD(7)),
+        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_RD(0), VQE_B, VQE_D, VQE_B,
+                  VQE_RD(4), VQE_B, VQE_RD(7), VQE_B, VQE_D),
+        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_D, VQE_B, VQE_RD(7), VQE_B, VQE_D),
+        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_D, VQE_B, VQE_D),
+        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_D),
+        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_D, VQE_RD(8)),
+        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_RD(0), VQE_B,
+                  VQE_D, VQE_RD(8)),
+        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_RD(0), VQE_B,
+                  VQE_D, VQE_B, VQE_RD(3), VQE_B, VQE_RD(6), VQE_B, VQE_RD(8), VQE_B, VQE_D),
+        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_D, VQE_B,
+                  VQE_RD(6), VQE_B, VQE_RD(8), VQE_B, VQE_D),
+        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_D, VQE_B, VQE_RD(8), VQE_B, VQE_D),
+        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_D, VQE_RD(8)),
+        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_D, VQE_B, VQE_D),
+        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_D),
+    };
+    return table;
+}
+#undef VQE_FIXED
+#undef VQE_RD
+#undef VQE_B
+#undef VQE_D
+
+// The fixed-shape launcher of a forward pass program, or null.
+FixedLaunch find_fixed(const PassDesc &dh, size_t elem_bytes) {
+    std::vector<int> codes;
+    codes.reserve(dh.n_ops);
+    for (int i = 0; i < dh.n_ops; ++i) {
+        const PassOp &op = dh.ops[i];
+        if (op.kind == OP_ROUND) codes.push_back(prog_round(op.chunk));
+        else if (op.kind == OP_BF) codes.push_back(kProgBF);
+        else if (op.kind == OP_DIAG) codes.push_back(kProgDiag);
+        else return nullptr;
+    }
+    for (const FixedEntry &f : fixed_programs())
+        if (f.elem_bytes == int(elem_bytes) && f.R == dh.R && f.codes == codes) return f.fn;
+    return nullptr;
+}
+
+}  // namespace
+
 int pass_threads(const PassDesc &d) { return 1 << (d.k - d.R); }
 
 size_t pass_smem_bytes(const PassDesc &d, bool backward, size_t elem_bytes) {
@@ -224,6 +336,11 @@ cudaError_t launch_pass(const PassDesc *desc_dev, const PassDesc &dh, int n_qubi
                         size_t coef_stride, const void *dtab, size_t dtab_stride,
                         double *gpart, size_t grad_stride, bool backward, int init_zero,
                         cudaStream_t s) {
+    if (!backward) {   // a forward program of a known shape runs unrolled
+        if (FixedLaunch f = find_fixed(dh, 2 * sizeof(T)))
+            return f(desc_dev, dh, n_qubits, batch, psi, stride, coefs, coef_stride, dtab,
+                     dtab_stride, init_zero, s);
+    }
 #define VQE_PASS_CASE(RR)                                                                       \
     case RR:                                                                                    \
         return backward ? launch_pass_r<T, RR, true>(desc_dev, dh, n_qubits, batch, psi, lam,   \

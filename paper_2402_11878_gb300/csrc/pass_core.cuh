@@ -499,4 +499,195 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
     (void)nwarps;
 }
 
+// ---------------------------------------------------------------- fixed programs
+//
+// The forward pass programs of the default plans come in a handful of shapes:
+// the same sequence of op kinds and round chunks, differing only in masks and
+// slots.  For a known shape (the template pack, one code per op) the program
+// runs fully unrolled: every chunk is a compile-time constant, the op list is
+// read at constant indices, and no value has to return to a fixed register
+// at an interpreter back-edge.  Forward only, for environments that read and
+// write the state directly (kLoad == 1, kStore == 1) with full diagonal rows.
+
+constexpr int prog_round(int chunk) { return 256 | chunk; }
+constexpr int kProgBF = 512, kProgDiag = 768;
+
+template <int I>
+struct IdxC {
+    static constexpr int value = I;
+};
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (I < N) {
+        f(IdxC<I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
+// Chunk of the round in effect at op i of the program (-1 before the first).
+template <int... Codes>
+__host__ __device__ constexpr int prog_chunk_at(int i) {
+    constexpr int code[] = {Codes...};
+    for (int j = i; j >= 0; --j)
+        if ((code[j] >> 8) == 1) return code[j] & 255;
+    return -1;
+}
+
+template <typename T, int R, class Env, int... Codes>
+__device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *ops, uint64_t gbase,
+                                               typename V2<T>::type *buf, Env &env) {
+    static_assert(Env::kLoad == 1 && Env::kStore == 1 && Env::kDiagRow, "direct environment");
+    using C = typename V2<T>::type;
+    constexpr int NR = 1 << R;
+    constexpr int N = sizeof...(Codes);
+    constexpr int code[] = {Codes...};
+    const int k = d.k, m = d.m, a = d.a;
+    const uint32_t t = threadIdx.x;
+    const uint32_t lowmask = (1u << m) - 1u;
+    auto g32 = [&](uint32_t e) -> uint32_t {
+        return (uint32_t)(gbase | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a));
+    };
+    // global strides of the R register bits of chunk P, and register offsets
+    auto strides = [&](auto pc, uint32_t (&gst)[R]) {
+        constexpr int P = decltype(pc)::value;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int bt = P + j;
+            gst[j] = bt < m ? (1u << bt) : (1u << (a + bt - m));
+        }
+    };
+    auto offset = [&](auto pc, int r, const uint32_t (&gst)[R]) -> uint32_t {
+        constexpr int P = decltype(pc)::value;
+        uint32_t off = 0;
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            if ((r >> j) & 1) off += (P + R <= m) ? (1u << (P + j)) : gst[j];
+        return off;
+    };
+    C v[NR];
+    static_for<0, N>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int kind = code[i] >> 8;
+        constexpr int P = prog_chunk_at<Codes...>(i);
+        using PC = ChunkC<P < 0 ? 0 : P>;
+        if constexpr (kind == 1 && i == 0) {   // first round: load from global memory
+            const uint32_t g0 = g32(elem_of(t, 0, P, R));
+            uint32_t gst[R];
+            strides(PC{}, gst);
+            const C *Pb = env.P + g0;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const uint32_t off = offset(PC{}, r, gst);
+                if (env.init_zero) {
+                    v[r].x = (g0 + off == 0u) ? T(1) : T(0);
+                    v[r].y = T(0);
+                } else {
+                    v[r] = Pb[off];
+                }
+            }
+        } else if constexpr (kind == 1) {       // round change through shared memory
+            constexpr int PO = prog_chunk_at<Codes...>(i - 1);
+            __syncthreads();
+            {
+                C *bp = buf + pad_of<T>(elem_of(t, 0, PO, R));
+#pragma unroll
+                for (int r = 0; r < NR; ++r) bp[pad_of<T>((uint32_t)r << PO)] = v[r];
+            }
+            __syncthreads();
+            {
+                const C *bp = buf + pad_of<T>(elem_of(t, 0, P, R));
+#pragma unroll
+                for (int r = 0; r < NR; ++r) v[r] = bp[pad_of<T>((uint32_t)r << P)];
+            }
+        } else if constexpr (kind == 2) {       // RY butterflies of the chunk's gated bits
+            const PassOp op = ops[i];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (!((op.mask >> j) & 1)) continue;
+                const RotCoef<T> rc = env.coef(op.slot, P + j);
+                const T cv = rc.v;
+                const uint32_t md = (uint32_t)rc.mode;
+                if constexpr (sizeof(T) == 8) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        if (r & (1 << j)) continue;
+                        const int r1 = r | (1 << j);
+                        const C x = v[r], y = v[r1];
+                        C Pp, Q;
+                        Pp.x = md ? y.x : x.x;  Pp.y = md ? y.y : x.y;
+                        Q.x = md ? x.x : y.x;   Q.y = md ? x.y : y.y;
+                        v[r1].x = fma(cv, Pp.x, Q.x);
+                        v[r1].y = fma(cv, Pp.y, Q.y);
+                        v[r].x = flip_sign(fma(-cv, Q.x, Pp.x), md);
+                        v[r].y = flip_sign(fma(-cv, Q.y, Pp.y), md);
+                    }
+                } else if (md == 0) {   // [[1,-t],[t,1]]
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        if (r & (1 << j)) continue;
+                        const int r1 = r | (1 << j);
+                        const C x = v[r], y = v[r1];
+                        v[r].x = fma(-cv, y.x, x.x);  v[r].y = fma(-cv, y.y, x.y);
+                        v[r1].x = fma(cv, x.x, y.x);  v[r1].y = fma(cv, x.y, y.y);
+                    }
+                } else {                // [[u,-1],[1,u]]
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        if (r & (1 << j)) continue;
+                        const int r1 = r | (1 << j);
+                        const C x = v[r], y = v[r1];
+                        v[r].x = fma(cv, x.x, -y.x);  v[r].y = fma(cv, x.y, -y.y);
+                        v[r1].x = fma(cv, y.x, x.x);  v[r1].y = fma(cv, y.y, x.y);
+                    }
+                }
+            }
+        } else if constexpr (kind == 3) {       // RZ phases, scales and CZ signs
+            const PassOp op = ops[i];
+            const uint32_t cz = d.slot_czmask[op.slot];
+            const uint32_t e0 = elem_of(t, 0, P, R);
+            const uint32_t g0 = g32(e0);
+            // CZ signs of the NR registers as one mask (see run_tile)
+            constexpr uint32_t kFull = NR >= 32 ? 0xffffffffu : ((1u << NR) - 1u);
+            const uint32_t W = ((g0 & cz) << 1) ^ ((g0 >> 1) & cz);
+            const int lo_cnt = min(max(m - P, 0), R);
+            uint32_t wv = (W >> P) & ((1u << lo_cnt) - 1u);
+            if (lo_cnt < R) wv |= ((W >> (a + max(P - m, 0))) & ((1u << (R - lo_cnt)) - 1u)) << lo_cnt;
+            uint32_t czt = 0u;
+            if (m >= 1) {
+                czt = cz & ((1u << (m - 1)) - 1u);
+                if (a == m && k > m) czt |= cz & (1u << (m - 1));
+            }
+            if (k - m >= 2) czt |= ((cz >> a) & ((1u << (k - m - 1)) - 1u)) << m;
+            const uint32_t adj = czt >> P;
+            uint32_t sm = (__popc(g0 & (g0 >> 1) & cz) & 1u) ? kFull : 0u;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if ((wv >> j) & 1u) sm ^= reg_bit_table(j);
+                if (j + 1 < R && ((adj >> j) & 1u)) sm ^= reg_bit_table(j) & reg_bit_table(j + 1);
+            }
+            sm &= kFull;
+            const C *drow = env.diag_row(op.slot, e0);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const uint32_t sgn = (sm >> r) & 1u;
+                C y = cmul(v[r], drow[(uint32_t)r << P]);
+                y.x = flip_sign(y.x, sgn);
+                y.y = flip_sign(y.y, sgn);
+                v[r] = y;
+            }
+        }
+    });
+    {   // last round: store to global memory
+        constexpr int P = prog_chunk_at<Codes...>(N - 1);
+        using PC = ChunkC<P>;
+        const uint32_t g0 = g32(elem_of(t, 0, P, R));
+        uint32_t gst[R];
+        strides(PC{}, gst);
+        C *Pb = env.P + g0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) Pb[offset(PC{}, r, gst)] = v[r];
+    }
+}
+
 }  // namespace vqe

@@ -187,13 +187,15 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
     run_tile<T, R, BWD>(d, d.ops, d.n_ops, base, sp, sl, gsh, env);
 }
 
-// Forward pass with a program shape fixed at compile time (run_tile_fixed);
-// same staging and environment as k_pass.
-template <typename T, int R, int... Codes>
-__global__ void __launch_bounds__(kPassMaxThreads, (R > 4) ? 1 : 2)
+// Pass with a program shape fixed at compile time (run_tile_fixed); same
+// staging, shared-memory layout and environment as k_pass.
+template <typename T, int R, bool BWD, int... Codes>
+__global__ void __launch_bounds__(kPassMaxThreads, (BWD || R > 4) ? 1 : 2)
 k_pass_fixed(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *__restrict__ psi,
-             size_t stride, const RotCoef<T> *__restrict__ coefs, size_t coef_stride,
-             const typename V2<T>::type *__restrict__ dtab, size_t dtab_stride) {
+             typename V2<T>::type *__restrict__ lam, size_t stride,
+             const RotCoef<T> *__restrict__ coefs, size_t coef_stride,
+             const typename V2<T>::type *__restrict__ dtab, size_t dtab_stride,
+             double *__restrict__ gpart, size_t grad_stride) {
     using C = typename V2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ PassDesc sd;
@@ -201,7 +203,11 @@ k_pass_fixed(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::t
     const int kk = desc->k;
     const uint32_t size = tile_buf_elems(kk, (int)sizeof(C));
     C *sp = reinterpret_cast<C *>(smem_raw);
-    RotCoef<T> *scf = reinterpret_cast<RotCoef<T> *>(sp + size);
+    C *sl = sp + (BWD ? size : 0u);
+    double *gsh = reinterpret_cast<double *>(sp + (BWD ? 2 * size : size));
+    RotCoef<T> *scf = reinterpret_cast<RotCoef<T> *>(
+        reinterpret_cast<unsigned char *>(gsh) +
+        (BWD ? tile_grad_scratch_bytes((int)blockDim.x, kk) : 0));
     stage_pass<T>(desc, coefs + (size_t)b * coef_stride, &sd, scf);
     const PassDesc &d = sd;
     const int k = d.k, m = d.m, a = d.a;
@@ -209,37 +215,42 @@ k_pass_fixed(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::t
     const int mid = a - m;
     const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (k - m)));
     const uint32_t lowmask = (1u << m) - 1u;
-    GridEnv<T> env{&sd, scf, dtab + (size_t)b * dtab_stride, nullptr, tile, psi + (size_t)b * stride,
-                   nullptr, base, lowmask, m, a, init_zero};
-    run_tile_fixed<T, R, GridEnv<T>, Codes...>(d, d.ops, base, sp, env);
+    GridEnv<T> env{&sd, scf, dtab + (size_t)b * dtab_stride,
+                   BWD ? gpart + (size_t)b * grad_stride : nullptr, tile, psi + (size_t)b * stride,
+                   BWD ? lam + (size_t)b * stride : nullptr, base, lowmask, m, a, init_zero};
+    run_tile_fixed<T, R, BWD, GridEnv<T>, Codes...>(d, d.ops, base, sp, sl, gsh, env);
 }
 
 namespace {
 
-using FixedLaunch = cudaError_t (*)(const PassDesc *, const PassDesc &, int, int, void *, size_t,
-                                    const void *, size_t, const void *, size_t, int, cudaStream_t);
+using FixedLaunch = cudaError_t (*)(const PassDesc *, const PassDesc &, int, int, void *, void *,
+                                    size_t, const void *, size_t, const void *, size_t, double *,
+                                    size_t, int, cudaStream_t);
 
-template <typename T, int R, int... Codes>
+template <typename T, int R, bool BWD, int... Codes>
 cudaError_t launch_fixed(const PassDesc *desc_dev, const PassDesc &dh, int n_qubits, int batch,
-                         void *psi, size_t stride, const void *coefs, size_t coef_stride,
-                         const void *dtab, size_t dtab_stride, int init_zero, cudaStream_t s) {
+                         void *psi, void *lam, size_t stride, const void *coefs,
+                         size_t coef_stride, const void *dtab, size_t dtab_stride, double *gpart,
+                         size_t grad_stride, int init_zero, cudaStream_t s) {
     using C = typename V2<T>::type;
     const int threads = 1 << (dh.k - dh.R);
-    const size_t smem = pass_smem_bytes(dh, false, sizeof(C));
-    auto kern = k_pass_fixed<T, R, Codes...>;
+    const size_t smem = pass_smem_bytes(dh, BWD, sizeof(C));
+    auto kern = k_pass_fixed<T, R, BWD, Codes...>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)(1ull << (n_qubits - dh.k)), batch);
-    kern<<<grid, threads, smem, s>>>(desc_dev, init_zero, static_cast<C *>(psi), stride,
+    kern<<<grid, threads, smem, s>>>(desc_dev, init_zero, static_cast<C *>(psi),
+                                     static_cast<C *>(lam), stride,
                                      static_cast<const RotCoef<T> *>(coefs), coef_stride,
-                                     static_cast<const C *>(dtab), dtab_stride);
+                                     static_cast<const C *>(dtab), dtab_stride, gpart, grad_stride);
     return cudaGetLastError();
 }
 
 struct FixedEntry {
     int elem_bytes, R;
+    bool backward;
     std::vector<int> codes;
     FixedLaunch fn;
 };
@@ -247,41 +258,67 @@ struct FixedEntry {
 #define VQE_RD(c) prog_round(c)
 #define VQE_B kProgBF
 #define VQE_D kProgDiag
-#define VQE_FIXED(TT, RR, ...) \
-    FixedEntry{int(2 * sizeof(TT)), RR, std::vector<int>{__VA_ARGS__}, &launch_fixed<TT, RR, __VA_ARGS__>}
+#define VQE_F kProgFlush
+#define VQE_FWD(TT, RR, ...) \
+    FixedEntry{int(2 * sizeof(TT)), RR, false, std::vector<int>{__VA_ARGS__}, &launch_fixed<TT, RR, false, __VA_ARGS__>}
+#define VQE_BWD(TT, RR, ...) \
+    FixedEntry{int(2 * sizeof(TT)), RR, true, std::vector<int>{__VA_ARGS__}, &launch_fixed<TT, RR, true, __VA_ARGS__>}
 
-// The forward program shapes of the default plans (tiles of 2^11; FP32 with
-// 16 amplitudes per thread: chunks 0, 4, 7; FP64 with 8: chunks 0, 3, 6, 8).
+// The pass program shapes of the default plans (tiles of 2^11; FP32 with 16
+// amplitudes per thread: chunks 0, 4, 7; FP64 with 8: chunks 0, 3, 6, 8),
+// forward and backward.
 const std::vector<FixedEntry> &fixed_programs() {
     static const std::vector<FixedEntry> table = {
-        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_D, VQE_RD(7)),
-        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_RD(0), VQE_B, VQE_D, VQE_RD(7)),
-        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_RD(0), VQE_B, VQE_D, VQE_B,
-                  VQE_RD(4), VQE_B, VQE_RD(7), VQE_B, VQE_D),
-        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_D, VQE_B, VQE_RD(7), VQE_B, VQE_D),
-        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_D, VQE_B, VQE_D),
-        VQE_FIXED(float, 4, VQE_RD(7), VQE_B, VQE_D),
-        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_D, VQE_RD(8)),
-        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_RD(0), VQE_B,
-                  VQE_D, VQE_RD(8)),
-        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_RD(0), VQE_B,
-                  VQE_D, VQE_B, VQE_RD(3), VQE_B, VQE_RD(6), VQE_B, VQE_RD(8), VQE_B, VQE_D),
-        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_D, VQE_B,
-                  VQE_RD(6), VQE_B, VQE_RD(8), VQE_B, VQE_D),
-        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_D, VQE_B, VQE_RD(8), VQE_B, VQE_D),
-        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_D, VQE_RD(8)),
-        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_D, VQE_B, VQE_D),
-        VQE_FIXED(double, 3, VQE_RD(8), VQE_B, VQE_D),
+        VQE_FWD(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_D, VQE_RD(7)),
+        VQE_FWD(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_RD(0), VQE_B, VQE_D, VQE_RD(7)),
+        VQE_FWD(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_RD(0), VQE_B, VQE_D, VQE_B,
+                VQE_RD(4), VQE_B, VQE_RD(7), VQE_B, VQE_D),
+        VQE_FWD(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_D, VQE_B, VQE_RD(7), VQE_B, VQE_D),
+        VQE_FWD(float, 4, VQE_RD(7), VQE_B, VQE_D, VQE_B, VQE_D),
+        VQE_FWD(float, 4, VQE_RD(7), VQE_B, VQE_D),
+        VQE_FWD(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_D, VQE_RD(8)),
+        VQE_FWD(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_RD(0), VQE_B,
+                VQE_D, VQE_RD(8)),
+        VQE_FWD(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_RD(0), VQE_B,
+                VQE_D, VQE_B, VQE_RD(3), VQE_B, VQE_RD(6), VQE_B, VQE_RD(8), VQE_B, VQE_D),
+        VQE_FWD(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_D, VQE_B,
+                VQE_RD(6), VQE_B, VQE_RD(8), VQE_B, VQE_D),
+        VQE_FWD(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_D, VQE_B, VQE_RD(8), VQE_B, VQE_D),
+        VQE_FWD(double, 3, VQE_RD(8), VQE_B, VQE_RD(6), VQE_B, VQE_D, VQE_RD(8)),
+        VQE_FWD(double, 3, VQE_RD(8), VQE_B, VQE_D, VQE_B, VQE_D),
+        VQE_FWD(double, 3, VQE_RD(8), VQE_B, VQE_D),
+        VQE_BWD(float, 4, VQE_RD(7), VQE_RD(4), VQE_D, VQE_B, VQE_RD(7), VQE_B, VQE_F),
+        VQE_BWD(float, 4, VQE_RD(7), VQE_RD(0), VQE_D, VQE_B, VQE_RD(4), VQE_B, VQE_RD(7), VQE_B, VQE_F),
+        VQE_BWD(float, 4, VQE_RD(7), VQE_D, VQE_B, VQE_RD(4), VQE_B, VQE_RD(0), VQE_B, VQE_F, VQE_D,
+                VQE_B, VQE_RD(4), VQE_B, VQE_RD(7), VQE_B, VQE_F),
+        VQE_BWD(float, 4, VQE_RD(7), VQE_D, VQE_B, VQE_RD(4), VQE_B, VQE_F, VQE_D, VQE_B, VQE_RD(7),
+                VQE_B, VQE_F),
+        VQE_BWD(float, 4, VQE_RD(7), VQE_D, VQE_B, VQE_F, VQE_D, VQE_B, VQE_F),
+        VQE_BWD(float, 4, VQE_RD(7), VQE_D, VQE_B, VQE_F),
+        VQE_BWD(double, 3, VQE_RD(8), VQE_RD(3), VQE_D, VQE_B, VQE_RD(6), VQE_B, VQE_RD(8), VQE_B, VQE_F),
+        VQE_BWD(double, 3, VQE_RD(8), VQE_RD(0), VQE_D, VQE_B, VQE_RD(3), VQE_B, VQE_RD(6), VQE_B,
+                VQE_RD(8), VQE_B, VQE_F),
+        VQE_BWD(double, 3, VQE_RD(8), VQE_D, VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_RD(0),
+                VQE_B, VQE_F, VQE_D, VQE_B, VQE_RD(3), VQE_B, VQE_RD(6), VQE_B, VQE_RD(8), VQE_B, VQE_F),
+        VQE_BWD(double, 3, VQE_RD(8), VQE_D, VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_F, VQE_D,
+                VQE_B, VQE_RD(6), VQE_B, VQE_RD(8), VQE_B, VQE_F),
+        VQE_BWD(double, 3, VQE_RD(8), VQE_D, VQE_B, VQE_RD(6), VQE_B, VQE_F, VQE_D, VQE_B, VQE_RD(8),
+                VQE_B, VQE_F),
+        VQE_BWD(double, 3, VQE_RD(8), VQE_RD(6), VQE_D, VQE_B, VQE_RD(8), VQE_B, VQE_F),
+        VQE_BWD(double, 3, VQE_RD(8), VQE_D, VQE_B, VQE_F, VQE_D, VQE_B, VQE_F),
+        VQE_BWD(double, 3, VQE_RD(8), VQE_D, VQE_B, VQE_F),
     };
     return table;
 }
-#undef VQE_FIXED
+#undef VQE_FWD
+#undef VQE_BWD
 #undef VQE_RD
 #undef VQE_B
 #undef VQE_D
+#undef VQE_F
 
-// The fixed-shape launcher of a forward pass program, or null.
-FixedLaunch find_fixed(const PassDesc &dh, size_t elem_bytes) {
+// The fixed-shape launcher of a pass program, or null.
+FixedLaunch find_fixed(const PassDesc &dh, size_t elem_bytes, bool backward) {
     std::vector<int> codes;
     codes.reserve(dh.n_ops);
     for (int i = 0; i < dh.n_ops; ++i) {
@@ -289,10 +326,12 @@ FixedLaunch find_fixed(const PassDesc &dh, size_t elem_bytes) {
         if (op.kind == OP_ROUND) codes.push_back(prog_round(op.chunk));
         else if (op.kind == OP_BF) codes.push_back(kProgBF);
         else if (op.kind == OP_DIAG) codes.push_back(kProgDiag);
+        else if (op.kind == OP_FLUSH) codes.push_back(kProgFlush);
         else return nullptr;
     }
     for (const FixedEntry &f : fixed_programs())
-        if (f.elem_bytes == int(elem_bytes) && f.R == dh.R && f.codes == codes) return f.fn;
+        if (f.elem_bytes == int(elem_bytes) && f.R == dh.R && f.backward == backward && f.codes == codes)
+            return f.fn;
     return nullptr;
 }
 
@@ -336,11 +375,10 @@ cudaError_t launch_pass(const PassDesc *desc_dev, const PassDesc &dh, int n_qubi
                         size_t coef_stride, const void *dtab, size_t dtab_stride,
                         double *gpart, size_t grad_stride, bool backward, int init_zero,
                         cudaStream_t s) {
-    if (!backward) {   // a forward program of a known shape runs unrolled
-        if (FixedLaunch f = find_fixed(dh, 2 * sizeof(T)))
-            return f(desc_dev, dh, n_qubits, batch, psi, stride, coefs, coef_stride, dtab,
-                     dtab_stride, init_zero, s);
-    }
+    // a program of a known shape runs unrolled
+    if (FixedLaunch f = find_fixed(dh, 2 * sizeof(T), backward))
+        return f(desc_dev, dh, n_qubits, batch, psi, backward ? lam : nullptr, stride, coefs,
+                 coef_stride, dtab, dtab_stride, gpart, grad_stride, init_zero, s);
 #define VQE_PASS_CASE(RR)                                                                       \
     case RR:                                                                                    \
         return backward ? launch_pass_r<T, RR, true>(desc_dev, dh, n_qubits, batch, psi, lam,   \

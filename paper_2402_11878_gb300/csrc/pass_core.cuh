@@ -510,7 +510,7 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
 // write the state directly (kLoad == 1, kStore == 1) with full diagonal rows.
 
 constexpr int prog_round(int chunk) { return 256 | chunk; }
-constexpr int kProgBF = 512, kProgDiag = 768;
+constexpr int kProgBF = 512, kProgDiag = 768, kProgFlush = 1024;
 
 template <int I>
 struct IdxC {
@@ -534,9 +534,11 @@ __host__ __device__ constexpr int prog_chunk_at(int i) {
     return -1;
 }
 
-template <typename T, int R, class Env, int... Codes>
+template <typename T, int R, bool BWD, class Env, int... Codes>
 __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *ops, uint64_t gbase,
-                                               typename V2<T>::type *buf, Env &env) {
+                                               typename V2<T>::type *buf,
+                                               typename V2<T>::type *lbuf, double *gsh,
+                                               Env &env) {
     static_assert(Env::kLoad == 1 && Env::kStore == 1 && Env::kDiagRow, "direct environment");
     using C = typename V2<T>::type;
     constexpr int NR = 1 << R;
@@ -544,6 +546,10 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
     constexpr int code[] = {Codes...};
     const int k = d.k, m = d.m, a = d.a;
     const uint32_t t = threadIdx.x;
+    const uint32_t nthr = 1u << (k - R);   // == blockDim.x for these kernels
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned wmask = nthr >= 32 ? 0xffffffffu : ((1u << nthr) - 1u);
+    const int wlanes = nthr >= 32 ? 32 : (int)nthr;
     const uint32_t lowmask = (1u << m) - 1u;
     auto g32 = [&](uint32_t e) -> uint32_t {
         return (uint32_t)(gbase | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a));
@@ -566,6 +572,7 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
         return off;
     };
     C v[NR];
+    C w[NR];
     static_for<0, N>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int kind = code[i] >> 8;
@@ -576,6 +583,7 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
             uint32_t gst[R];
             strides(PC{}, gst);
             const C *Pb = env.P + g0;
+            const C *Lb = BWD ? env.L + g0 : nullptr;
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 const uint32_t off = offset(PC{}, r, gst);
@@ -585,20 +593,29 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                 } else {
                     v[r] = Pb[off];
                 }
+                if (BWD) w[r] = Lb[off];
             }
         } else if constexpr (kind == 1) {       // round change through shared memory
             constexpr int PO = prog_chunk_at<Codes...>(i - 1);
             __syncthreads();
             {
                 C *bp = buf + pad_of<T>(elem_of(t, 0, PO, R));
+                C *lp = BWD ? lbuf + pad_of<T>(elem_of(t, 0, PO, R)) : nullptr;
 #pragma unroll
-                for (int r = 0; r < NR; ++r) bp[pad_of<T>((uint32_t)r << PO)] = v[r];
+                for (int r = 0; r < NR; ++r) {
+                    bp[pad_of<T>((uint32_t)r << PO)] = v[r];
+                    if (BWD) lp[pad_of<T>((uint32_t)r << PO)] = w[r];
+                }
             }
             __syncthreads();
             {
                 const C *bp = buf + pad_of<T>(elem_of(t, 0, P, R));
+                const C *lp = BWD ? lbuf + pad_of<T>(elem_of(t, 0, P, R)) : nullptr;
 #pragma unroll
-                for (int r = 0; r < NR; ++r) v[r] = bp[pad_of<T>((uint32_t)r << P)];
+                for (int r = 0; r < NR; ++r) {
+                    v[r] = bp[pad_of<T>((uint32_t)r << P)];
+                    if (BWD) w[r] = lp[pad_of<T>((uint32_t)r << P)];
+                }
             }
         } else if constexpr (kind == 2) {       // RY butterflies of the chunk's gated bits
             const PassOp op = ops[i];
@@ -608,37 +625,75 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                 const RotCoef<T> rc = env.coef(op.slot, P + j);
                 const T cv = rc.v;
                 const uint32_t md = (uint32_t)rc.mode;
-                if constexpr (sizeof(T) == 8) {
+                if constexpr (BWD) {
+                    // dE/dtheta = Im<l|Y|p>; per pair Re(conj(l1) p0) - Re(conj(l0) p1)
+                    T gt = T(0);
 #pragma unroll
                     for (int r = 0; r < NR; ++r) {
                         if (r & (1 << j)) continue;
-                        const int r1 = r | (1 << j);
-                        const C x = v[r], y = v[r1];
-                        C Pp, Q;
-                        Pp.x = md ? y.x : x.x;  Pp.y = md ? y.y : x.y;
-                        Q.x = md ? x.x : y.x;   Q.y = md ? x.y : y.y;
-                        v[r1].x = fma(cv, Pp.x, Q.x);
-                        v[r1].y = fma(cv, Pp.y, Q.y);
-                        v[r].x = flip_sign(fma(-cv, Q.x, Pp.x), md);
-                        v[r].y = flip_sign(fma(-cv, Q.y, Pp.y), md);
+                        const C p0 = v[r], p1 = v[r | (1 << j)];
+                        const C l0 = w[r], l1 = w[r | (1 << j)];
+                        gt = fma(l1.x, p0.x, gt);
+                        gt = fma(l1.y, p0.y, gt);
+                        gt = fma(-l0.x, p1.x, gt);
+                        gt = fma(-l0.y, p1.y, gt);
                     }
-                } else if (md == 0) {   // [[1,-t],[t,1]]
+                    T wgt = gt * rc.gs;
+                    for (int o = wlanes >> 1; o > 0; o >>= 1) wgt += __shfl_xor_sync(wmask, wgt, o);
+                    if (lane == 0) gsh[(warp * k + P + j) * 2 + 0] = (double)wgt;
+                }
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        if (r & (1 << j)) continue;
-                        const int r1 = r | (1 << j);
-                        const C x = v[r], y = v[r1];
-                        v[r].x = fma(-cv, y.x, x.x);  v[r].y = fma(-cv, y.y, x.y);
-                        v[r1].x = fma(cv, x.x, y.x);  v[r1].y = fma(cv, x.y, y.y);
-                    }
-                } else {                // [[u,-1],[1,u]]
+                for (int bufi = 0; bufi < (BWD ? 2 : 1); ++bufi) {
+                    C *u = bufi ? w : v;
+                    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        if (r & (1 << j)) continue;
-                        const int r1 = r | (1 << j);
-                        const C x = v[r], y = v[r1];
-                        v[r].x = fma(cv, x.x, -y.x);  v[r].y = fma(cv, x.y, -y.y);
-                        v[r1].x = fma(cv, y.x, x.x);  v[r1].y = fma(cv, y.y, x.y);
+                        for (int r = 0; r < NR; ++r) {
+                            if (r & (1 << j)) continue;
+                            const int r1 = r | (1 << j);
+                            const C x = u[r], y = u[r1];
+                            C Pp, Q;
+                            Pp.x = md ? y.x : x.x;  Pp.y = md ? y.y : x.y;
+                            Q.x = md ? x.x : y.x;   Q.y = md ? x.y : y.y;
+                            if (!BWD) {
+                                u[r1].x = fma(cv, Pp.x, Q.x);
+                                u[r1].y = fma(cv, Pp.y, Q.y);
+                                u[r].x = flip_sign(fma(-cv, Q.x, Pp.x), md);
+                                u[r].y = flip_sign(fma(-cv, Q.y, Pp.y), md);
+                            } else {
+                                u[r].x = fma(cv, Q.x, Pp.x);
+                                u[r].y = fma(cv, Q.y, Pp.y);
+                                u[r1].x = flip_sign(fma(-cv, Pp.x, Q.x), md);
+                                u[r1].y = flip_sign(fma(-cv, Pp.y, Q.y), md);
+                            }
+                        }
+                    } else if (md == 0) {
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            if (r & (1 << j)) continue;
+                            const int r1 = r | (1 << j);
+                            const C x = u[r], y = u[r1];
+                            if (!BWD) {   // [[1,-t],[t,1]]
+                                u[r].x = fma(-cv, y.x, x.x);  u[r].y = fma(-cv, y.y, x.y);
+                                u[r1].x = fma(cv, x.x, y.x);  u[r1].y = fma(cv, x.y, y.y);
+                            } else {      // transpose: [[1,t],[-t,1]]
+                                u[r].x = fma(cv, y.x, x.x);    u[r].y = fma(cv, y.y, x.y);
+                                u[r1].x = fma(-cv, x.x, y.x);  u[r1].y = fma(-cv, x.y, y.y);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            if (r & (1 << j)) continue;
+                            const int r1 = r | (1 << j);
+                            const C x = u[r], y = u[r1];
+                            if (!BWD) {   // [[u,-1],[1,u]]
+                                u[r].x = fma(cv, x.x, -y.x);  u[r].y = fma(cv, x.y, -y.y);
+                                u[r1].x = fma(cv, y.x, x.x);  u[r1].y = fma(cv, y.y, x.y);
+                            } else {      // transpose: [[u,1],[-1,u]]
+                                u[r].x = fma(cv, x.x, y.x);    u[r].y = fma(cv, x.y, y.y);
+                                u[r1].x = fma(cv, y.x, -x.x);  u[r1].y = fma(cv, y.y, -x.y);
+                            }
+                        }
                     }
                 }
             }
@@ -646,6 +701,31 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
             const PassOp op = ops[i];
             const uint32_t cz = d.slot_czmask[op.slot];
             const uint32_t e0 = elem_of(t, 0, P, R);
+            if constexpr (BWD) {
+                // dE/dphi_q = Im<l|Z_q|p> = sum_i u_i (-1)^{bit_q(i)}, u = Im(conj(l) p),
+                // taken before the diagonal is undone
+                T u[NR];
+                T tot = T(0);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    u[r] = fma(w[r].x, v[r].y, -w[r].y * v[r].x);
+                    tot += u[r];
+                }
+                const uint32_t gated = d.slot_gated[op.slot];
+                for (int q = 0; q < k; ++q) {
+                    if (!((gated >> q) & 1u)) continue;
+                    T gq;
+                    if (q >= P && q < P + R) {
+                        gq = T(0);
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) gq += ((r >> (q - P)) & 1) ? -u[r] : u[r];
+                    } else {
+                        gq = ((e0 >> q) & 1u) ? -tot : tot;
+                    }
+                    for (int o = wlanes >> 1; o > 0; o >>= 1) gq += __shfl_xor_sync(wmask, gq, o);
+                    if (lane == 0) gsh[(warp * k + q) * 2 + 1] = (double)gq;
+                }
+            }
             const uint32_t g0 = g32(e0);
             // CZ signs of the NR registers as one mask (see run_tile)
             constexpr uint32_t kFull = NR >= 32 ? 0xffffffffu : ((1u << NR) - 1u);
@@ -671,10 +751,33 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 const uint32_t sgn = (sm >> r) & 1u;
-                C y = cmul(v[r], drow[(uint32_t)r << P]);
+                const C dv = drow[(uint32_t)r << P];
+                C y = BWD ? cmul_conj(v[r], dv) : cmul(v[r], dv);
                 y.x = flip_sign(y.x, sgn);
                 y.y = flip_sign(y.y, sgn);
                 v[r] = y;
+                if (BWD) {
+                    C z = cmul_conj(w[r], dv);
+                    z.x = flip_sign(z.x, sgn);
+                    z.y = flip_sign(z.y, sgn);
+                    w[r] = z;
+                }
+            }
+        } else if constexpr (kind == 4) {       // block totals of a slot's gradient partials
+            if constexpr (BWD) {
+                const PassOp op = ops[i];
+                __syncthreads();
+                const uint32_t gated = d.slot_gated[op.slot];
+                const int used_warps = (int)((nthr + 31) >> 5);
+                if (threadIdx.x == 0) {
+                    for (int idx = 0; idx < 2 * k; ++idx) {
+                        if (!((gated >> (idx >> 1)) & 1u)) continue;
+                        double s = 0.0;
+                        for (int wi = 0; wi < used_warps; ++wi) s += gsh[wi * 2 * k + idx];
+                        env.grad(op.slot, idx >> 1, idx & 1, s);
+                    }
+                }
+                __syncthreads();
             }
         }
     });
@@ -685,8 +788,13 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
         uint32_t gst[R];
         strides(PC{}, gst);
         C *Pb = env.P + g0;
+        C *Lb = BWD ? env.L + g0 : nullptr;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) Pb[offset(PC{}, r, gst)] = v[r];
+        for (int r = 0; r < NR; ++r) {
+            const uint32_t off = offset(PC{}, r, gst);
+            Pb[off] = v[r];
+            if (BWD) Lb[off] = w[r];
+        }
     }
 }
 

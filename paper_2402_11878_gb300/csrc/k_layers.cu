@@ -187,8 +187,17 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
     run_tile<T, R, BWD>(d, d.ops, d.n_ops, base, sp, sl, gsh, env);
 }
 
+// Gradient scratch of a fixed-shape backward pass: FP32 keeps one row of
+// per-thread partials per (tile bit, component); FP64 the per-warp totals of
+// the interpreter.
+template <typename T>
+__host__ __device__ inline size_t fixed_grad_scratch_bytes(int threads, int k) {
+    return sizeof(T) == 4 ? size_t(threads) * 2 * k * sizeof(float)
+                          : tile_grad_scratch_bytes(threads, k);
+}
+
 // Pass with a program shape fixed at compile time (run_tile_fixed); same
-// staging, shared-memory layout and environment as k_pass.
+// staging and environment as k_pass, the gradient scratch as above.
 template <typename T, int R, bool BWD, int... Codes>
 __global__ void __launch_bounds__(kPassMaxThreads, (BWD || R > 4) ? 1 : 2)
 k_pass_fixed(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *__restrict__ psi,
@@ -207,7 +216,7 @@ k_pass_fixed(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::t
     double *gsh = reinterpret_cast<double *>(sp + (BWD ? 2 * size : size));
     RotCoef<T> *scf = reinterpret_cast<RotCoef<T> *>(
         reinterpret_cast<unsigned char *>(gsh) +
-        (BWD ? tile_grad_scratch_bytes((int)blockDim.x, kk) : 0));
+        (BWD ? fixed_grad_scratch_bytes<T>((int)blockDim.x, kk) : 0));
     stage_pass<T>(desc, coefs + (size_t)b * coef_stride, &sd, scf);
     const PassDesc &d = sd;
     const int k = d.k, m = d.m, a = d.a;
@@ -234,7 +243,8 @@ cudaError_t launch_fixed(const PassDesc *desc_dev, const PassDesc &dh, int n_qub
                          size_t grad_stride, int init_zero, cudaStream_t s) {
     using C = typename V2<T>::type;
     const int threads = 1 << (dh.k - dh.R);
-    const size_t smem = pass_smem_bytes(dh, BWD, sizeof(C));
+    size_t smem = pass_smem_bytes(dh, BWD, sizeof(C));
+    if (BWD) smem += fixed_grad_scratch_bytes<T>(threads, dh.k) - tile_grad_scratch_bytes(threads, dh.k);
     auto kern = k_pass_fixed<T, R, BWD, Codes...>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -638,9 +638,14 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                         gt = fma(-l0.x, p1.x, gt);
                         gt = fma(-l0.y, p1.y, gt);
                     }
-                    T wgt = gt * rc.gs;
-                    for (int o = wlanes >> 1; o > 0; o >>= 1) wgt += __shfl_xor_sync(wmask, wgt, o);
-                    if (lane == 0) gsh[(warp * k + P + j) * 2 + 0] = (double)wgt;
+                    if constexpr (sizeof(T) == 4) {
+                        // FP32: one shared-memory row per (bit, component), summed at the flush
+                        reinterpret_cast<float *>(gsh)[(2 * (P + j) + 0) * nthr + t] = gt * rc.gs;
+                    } else {
+                        T wgt = gt * rc.gs;
+                        for (int o = wlanes >> 1; o > 0; o >>= 1) wgt += __shfl_xor_sync(wmask, wgt, o);
+                        if (lane == 0) gsh[(warp * k + P + j) * 2 + 0] = (double)wgt;
+                    }
                 }
 #pragma unroll
                 for (int bufi = 0; bufi < (BWD ? 2 : 1); ++bufi) {
@@ -722,8 +727,12 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                     } else {
                         gq = ((e0 >> q) & 1u) ? -tot : tot;
                     }
-                    for (int o = wlanes >> 1; o > 0; o >>= 1) gq += __shfl_xor_sync(wmask, gq, o);
-                    if (lane == 0) gsh[(warp * k + q) * 2 + 1] = (double)gq;
+                    if constexpr (sizeof(T) == 4) {
+                        reinterpret_cast<float *>(gsh)[(2 * q + 1) * nthr + t] = gq;
+                    } else {
+                        for (int o = wlanes >> 1; o > 0; o >>= 1) gq += __shfl_xor_sync(wmask, gq, o);
+                        if (lane == 0) gsh[(warp * k + q) * 2 + 1] = (double)gq;
+                    }
                 }
             }
             const uint32_t g0 = g32(e0);
@@ -764,7 +773,23 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                 }
             }
         } else if constexpr (kind == 4) {       // block totals of a slot's gradient partials
-            if constexpr (BWD) {
+            if constexpr (BWD && sizeof(T) == 4) {
+                // each warp sums whole rows in a fixed order: lanes add a strided
+                // part of the row, then a shuffle tree (bitwise reproducible)
+                const PassOp op = ops[i];
+                __syncthreads();
+                const uint32_t gated = d.slot_gated[op.slot];
+                const int nw = (int)((nthr + 31) >> 5);
+                const float *gpt = reinterpret_cast<const float *>(gsh);
+                for (int idx = warp; idx < 2 * k; idx += nw) {
+                    if (!((gated >> (idx >> 1)) & 1u)) continue;
+                    float sum = 0.f;
+                    for (uint32_t tt = lane; tt < nthr; tt += 32) sum += gpt[idx * nthr + tt];
+                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                    if (lane == 0) env.grad(op.slot, idx >> 1, idx & 1, (double)sum);
+                }
+                __syncthreads();
+            } else if constexpr (BWD) {
                 const PassOp op = ops[i];
                 __syncthreads();
                 const uint32_t gated = d.slot_gated[op.slot];

@@ -616,6 +616,199 @@ size_t win_smem_bytes(const WinDesc &W, size_t elem_bytes) {
            (size_t(1) << (W.k - W.m)) * 4;
 }
 
+// Windowed apply-H (the adjoint's lambda = H psi, same windows as above but
+// with each group's terms ordered by their pattern over a thread's elements).
+// lambda is accumulated window by window in a fixed order: the first window
+// writes it, the others add to it; the last window also yields the block
+// partials of Re<psi|lambda> and <psi|psi>.  For an element e of the tile,
+//     lambda_e += psi_{e ^ xl} (FA(e) - i FB(e)),
+//     F(e) = sum_t c_t (-1)^{popc(g(e) & z_t)}   (base sign folded into c').
+template <typename T, int K, bool RUNS>
+__global__ void __launch_bounds__(kEnergyWinThreads, 1)
+k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__restrict__ wterms,
+              const uint32_t *__restrict__ hoff, const T *__restrict__ hdiag,
+              const typename EV2<T>::type *__restrict__ psi, typename EV2<T>::type *__restrict__ lam,
+              size_t stride, int first, int last, double *__restrict__ partials) {
+    using C = typename EV2<T>::type;
+    static_assert(kEnergyWinThreads == 512, "element layout assumes 512 threads");
+    constexpr uint32_t size = 1u << K;
+    constexpr int EPT = size / kEnergyWinThreads;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *sp = reinterpret_cast<C *>(smem_raw);
+    T *sc = reinterpret_cast<T *>(sp + size);
+    uint32_t *szt = reinterpret_cast<uint32_t *>(sc + W.t_count);
+    uint32_t *soff = szt + W.t_count;
+    __shared__ double sh[2 * (kEnergyWinThreads / 32)];
+    __shared__ WinGroup sg[kWinMaxGroups];
+    const int m = W.m;
+    const int b = blockIdx.y;
+    const C *P = psi + (size_t)b * stride;
+    C *L = lam + (size_t)b * stride;
+    const uint32_t tid = threadIdx.x;
+    uint32_t base = 0;
+    {
+        uint32_t bm = W.bmask, tn = blockIdx.x;
+        while (bm) {
+            const int bit = __ffs(bm) - 1;
+            base |= (tn & 1u) << bit;
+            tn >>= 1;
+            bm &= bm - 1u;
+        }
+    }
+    const uint32_t nh = 1u << (K - m);
+    for (uint32_t i = tid; i < nh; i += blockDim.x) soff[i] = hoff[W.hoff + i];
+    {
+        const int ng = W.g_end - W.g_begin;
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(wgroups + W.g_begin);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(sg);
+        for (int i = tid; i < ng * (int)(sizeof(WinGroup) / 4); i += blockDim.x) dst[i] = src[i];
+    }
+    for (int t = tid; t < W.t_count; t += blockDim.x) {
+        const WinTerm wt = wterms[W.t_begin + t];
+        sc[t] = (T)sgn_flip(wt.c, __popc(base & wt.zout) & 1u);
+        szt[t] = wt.zt;
+    }
+    __syncthreads();
+    const uint32_t lowmask = (1u << m) - 1u;
+    for (uint32_t e = tid; e < size; e += blockDim.x)
+        sp[e] = P[(size_t)(base | (e & lowmask) | soff[e >> m])];
+    __syncthreads();
+    auto gidx = [&](uint32_t e) -> size_t { return (size_t)(base | (e & lowmask) | soff[e >> m]); };
+    T lr[EPT], li[EPT];
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+        if (first) {
+            lr[j] = T(0);
+            li[j] = T(0);
+        } else {
+            const C l = L[gidx(tid + j * kEnergyWinThreads)];
+            lr[j] = l.x;
+            li[j] = l.y;
+        }
+    }
+    for (int gi = 0; gi < W.g_end - W.g_begin; ++gi) {
+        const WinGroup &G = sg[gi];
+        const uint32_t xl = G.xl;
+        const bool has_b = G.b_end > G.b_begin;
+        if (xl == 0u) {
+            T F[EPT];
+            if (!RUNS || hdiag) {
+#pragma unroll
+                for (int j = 0; j < EPT; ++j) F[j] = __ldg(hdiag + gidx(tid + j * kEnergyWinThreads));
+            } else if constexpr (RUNS) {
+                run_sums<EPT>(F, G.arun, G.a_begin, sc, szt, tid);
+                wht_inplace<EPT>(F);
+            }
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                const C y = sp[tid + j * kEnergyWinThreads];
+                lr[j] = fma(y.x, F[j], lr[j]);
+                li[j] = fma(y.y, F[j], li[j]);
+            }
+        } else if (!RUNS || G.direct) {
+            T ca[kWinDirectMax], cb[kWinDirectMax];
+            uint32_t za[kWinDirectMax], zb[kWinDirectMax];
+            const int na = G.b_begin - G.a_begin, nb = G.b_end - G.b_begin;
+#pragma unroll
+            for (int u = 0; u < kWinDirectMax; ++u) {
+                ca[u] = u < na ? sc[G.a_begin + u] : T(0);
+                za[u] = u < na ? szt[G.a_begin + u] : 0u;
+                cb[u] = u < nb ? sc[G.b_begin + u] : T(0);
+                zb[u] = u < nb ? szt[G.b_begin + u] : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                const uint32_t e = tid + j * kEnergyWinThreads;
+                const C y = sp[e ^ xl];
+                T fa = T(0), fb = T(0);
+#pragma unroll
+                for (int u = 0; u < kWinDirectMax; ++u)
+                    if (u < na) fa += sgn_flip(ca[u], __popc(e & za[u]) & 1u);
+                if (has_b) {
+#pragma unroll
+                    for (int u = 0; u < kWinDirectMax; ++u)
+                        if (u < nb) fb += sgn_flip(cb[u], __popc(e & zb[u]) & 1u);
+                }
+                // (y.x + i y.y)(fa - i fb)
+                lr[j] = fma(y.x, fa, fma(y.y, fb, lr[j]));
+                li[j] = fma(y.y, fa, fma(-y.x, fb, li[j]));
+            }
+        } else if constexpr (RUNS) {
+            T F[EPT];
+            run_sums<EPT>(F, G.arun, G.a_begin, sc, szt, tid);
+            wht_inplace<EPT>(F);
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                const C y = sp[(tid + j * kEnergyWinThreads) ^ xl];
+                lr[j] = fma(y.x, F[j], lr[j]);
+                li[j] = fma(y.y, F[j], li[j]);
+            }
+            if (has_b) {
+                run_sums<EPT>(F, G.brun, G.b_begin, sc, szt, tid);
+                wht_inplace<EPT>(F);
+#pragma unroll
+                for (int j = 0; j < EPT; ++j) {
+                    const C y = sp[(tid + j * kEnergyWinThreads) ^ xl];
+                    lr[j] = fma(y.y, F[j], lr[j]);
+                    li[j] = fma(-y.x, F[j], li[j]);
+                }
+            }
+        }
+    }
+    double acc = 0.0, nrm = 0.0;
+    {
+        T pa = T(0), pn = T(0);
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) {
+            const uint32_t e = tid + j * kEnergyWinThreads;
+            C out;
+            out.x = lr[j];
+            out.y = li[j];
+            L[gidx(e)] = out;
+            if (last) {
+                const C x = sp[e];
+                pa = fma(x.x, lr[j], fma(x.y, li[j], pa));
+                pn = fma(x.x, x.x, fma(x.y, x.y, pn));
+            }
+        }
+        acc = (double)pa;
+        nrm = (double)pn;
+    }
+    if (last) {   // uniform over the launch
+        block_reduce2(acc, nrm, sh);
+        if (threadIdx.x == 0) {
+            double *o = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
+            o[0] = acc;
+            o[1] = nrm;
+            o[2] = 0.0;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_apply_h_win(const WinDesc &W, const WinGroup *wgroups, const WinTerm *wterms,
+                               const uint32_t *hoff, const void *hdiag, int n_qubits, int batch,
+                               const void *psi, void *lam, size_t state_stride, int first,
+                               int last, double *partials, cudaStream_t s) {
+    using C = typename EV2<T>::type;
+    const size_t smem = win_smem_bytes(W, sizeof(C));
+    auto kern = W.any_runs
+        ? (W.k == 13 ? k_apply_h_win<T, 13, true> : (W.k == 12 ? k_apply_h_win<T, 12, true> : nullptr))
+        : (W.k == 13 ? k_apply_h_win<T, 13, false> : (W.k == 12 ? k_apply_h_win<T, 12, false> : nullptr));
+    if (!kern || W.t_count > kWinMaxTerms || W.g_end - W.g_begin > kWinMaxGroups)
+        return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)(1ull << (n_qubits - W.k)), batch);
+    kern<<<grid, kEnergyWinThreads, smem, s>>>(W, wgroups, wterms, hoff, static_cast<const T *>(hdiag),
+                                               static_cast<const C *>(psi), static_cast<C *>(lam),
+                                               state_stride, first, last, partials);
+    return cudaGetLastError();
+}
+
+
 template <typename T>
 cudaError_t launch_energy_win(const WinDesc &W, const WinGroup *wgroups, const WinTerm *wterms,
                               const uint32_t *hoff, const void *hdiag, int n_qubits, int batch,
@@ -656,6 +849,14 @@ cudaError_t launch_energy_sub(const GroupDesc *groups, int n_groups, const uint3
     return cudaGetLastError();
 }
 
+template cudaError_t launch_apply_h_win<float>(const WinDesc &, const WinGroup *, const WinTerm *,
+                                               const uint32_t *, const void *, int, int,
+                                               const void *, void *, size_t, int, int, double *,
+                                               cudaStream_t);
+template cudaError_t launch_apply_h_win<double>(const WinDesc &, const WinGroup *, const WinTerm *,
+                                                const uint32_t *, const void *, int, int,
+                                                const void *, void *, size_t, int, int, double *,
+                                                cudaStream_t);
 template cudaError_t launch_energy_win<float>(const WinDesc &, const WinGroup *, const WinTerm *,
                                               const uint32_t *, const void *, int, int,
                                               const void *, size_t, double *, int, cudaStream_t);

@@ -68,6 +68,10 @@ struct vqe_ctx {
     std::vector<WinDesc> wins;
     DevBuf d_wgroups, d_wterms, d_whoff, d_wide;
     int n_wide = 0;
+    // windows of the windowed apply-H (terms ordered per element pattern);
+    // empty when some group fits no window (then apply-H sweeps globally)
+    std::vector<WinDesc> awins;
+    DevBuf d_awgroups, d_awterms, d_awhoff;
     int win_tiles = 0;   // columns of all windows per state
     // diagonal of H (one T per basis state), built when it fits in a quarter
     // of the free device memory; null: the x = 0 terms are evaluated inline
@@ -671,7 +675,11 @@ uint32_t win_gather(uint32_t g, int m, const std::vector<int> &pos) {
 // bits), each window holding at most kWinMaxTerms terms.  Groups with more
 // high bits than a window has go to the global sweep.  `diag_terms`: store
 // the diagonal group's terms (false when the diagonal of H is precomputed).
-void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms, WinPlan &wp) {
+// elem_layout: order each group's terms by their pattern over a thread's
+// elements (the windowed apply-H, which signs at the output element) instead
+// of over its pairs (the windowed expectation).
+void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms, WinPlan &wp,
+                  bool elem_layout = false) {
     wp = WinPlan{};
     const bool c128 = prec == VQE_C128;
     const int kE = win_tile_bits(c128);
@@ -776,7 +784,7 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
             WinGroup wg{};
             wg.xl = win_gather(G.x, c.m, pos);
             wg.hl = wg.xl ? 31 - __builtin_clz(wg.xl) : 0;
-            const int NV = wg.xl ? PPT : EPT;
+            const int NV = (wg.xl && !elem_layout) ? PPT : EPT;
             // few terms: per-pair sign sums beat the transform over the
             // register patterns and its per-run loop (FP64: up to 3 terms,
             // FP32: up to 2)
@@ -788,7 +796,7 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
                 uint32_t v = 0;
                 for (int bb = 0; (1 << bb) < NV; ++bb) {
                     int q = lt + bb;
-                    if (wg.xl && q >= wg.hl) q += 1;
+                    if (wg.xl && !elem_layout && q >= wg.hl) q += 1;
                     v |= ((zt >> q) & 1u) << bb;
                 }
                 return v;
@@ -878,6 +886,19 @@ vqe_status build_ham_plan(vqe_ctx *h) {
         if ((st = upload(h, h->d_wterms, wp.terms, "window terms")) != VQE_OK) return st;
         if ((st = upload(h, h->d_whoff, wp.hoff, "window offsets")) != VQE_OK) return st;
         if ((st = upload(h, h->d_wide, wp.wide, "wide groups")) != VQE_OK) return st;
+        WinPlan ap;
+        plan_windows(h->n, h->prec, hp, !h->hdiag_ok, ap, true);
+        h->awins.clear();
+        // windowed apply-H re-reads and re-writes lambda once per window; it
+        // pays when the windows hold many groups each (measured: 24 qubits,
+        // 25 Hubbard groups in 3 windows favour the global sweep, the
+        // molecular 5,479 groups in 246 windows the windows)
+        if (ap.wide.empty() && hp.groups.size() >= 10 * ap.wins.size()) {
+            h->awins = ap.wins;
+            if ((st = upload(h, h->d_awgroups, ap.groups, "window groups")) != VQE_OK) return st;
+            if ((st = upload(h, h->d_awterms, ap.terms, "window terms")) != VQE_OK) return st;
+            if ((st = upload(h, h->d_awhoff, ap.hoff, "window offsets")) != VQE_OK) return st;
+        }
     }
     if ((st = upload(h, h->d_groups, hp.groups, "groups")) != VQE_OK) return st;
     if ((st = upload(h, h->d_tz, hp.tz, "terms")) != VQE_OK) return st;
@@ -1072,17 +1093,39 @@ vqe_status gradient_chunk(vqe_ctx *h, const double *params_dev, int B, double *g
     vqe_status st = run_forward<T>(h, 1, params_dev, B, psi);
     if (st != VQE_OK) return st;
     const vqe_ctx::DevPlan &P = h->plan[1];
-    const int bps = blocks_per_state(h, B);
     const int mk_h = prof_begin(h, 2);
-    VQE_CUDA(h, launch_apply_h<T>(static_cast<const GroupDesc *>(h->d_groups.p), h->n_groups,
-                                  static_cast<const uint32_t *>(h->d_tz.p),
-                                  static_cast<const double *>(h->d_tc.p), h->hdiag(), h->n, B, psi,
-                                  lam, N,
-                                  static_cast<double *>(h->d_epart.p), bps, s));
-    prof_end(h, mk_h, 1);
-    VQE_CUDA(h, launch_energy_finish(static_cast<double *>(h->d_epart.p), bps, B, E, nullptr,
-                                     nullptr, s));
-    h->stats.kernel_launches += 2;
+    const uint64_t atiles = h->awins.empty() ? 0 : (uint64_t(1) << (h->n - h->awins[0].k));
+    if (!h->awins.empty() && atiles * B >= uint64_t(2 * h->sms)) {
+        // windowed: lambda accumulated window by window; the last window's
+        // blocks hold the partials of the energy
+        const int bps_w = int(atiles);
+        vqe_status st2 = ensure(h, h->d_epart, sizeof(double) * 3 * size_t(bps_w) * B + 16, "partials");
+        if (st2 != VQE_OK) return st2;
+        const int nw = int(h->awins.size());
+        for (int w = 0; w < nw; ++w) {
+            VQE_CUDA(h, launch_apply_h_win<T>(h->awins[w], static_cast<const WinGroup *>(h->d_awgroups.p),
+                                              static_cast<const WinTerm *>(h->d_awterms.p),
+                                              static_cast<const uint32_t *>(h->d_awhoff.p),
+                                              h->hdiag(), h->n, B, psi, lam, N, w == 0 ? 1 : 0,
+                                              w == nw - 1 ? 1 : 0,
+                                              static_cast<double *>(h->d_epart.p), s));
+            h->stats.kernel_launches++;
+        }
+        prof_end(h, mk_h, nw);
+        VQE_CUDA(h, launch_energy_finish(static_cast<double *>(h->d_epart.p), bps_w, B, E, nullptr,
+                                         nullptr, s));
+        h->stats.kernel_launches++;
+    } else {
+        const int bps = blocks_per_state(h, B);
+        VQE_CUDA(h, launch_apply_h<T>(static_cast<const GroupDesc *>(h->d_groups.p), h->n_groups,
+                                      static_cast<const uint32_t *>(h->d_tz.p),
+                                      static_cast<const double *>(h->d_tc.p), h->hdiag(), h->n, B,
+                                      psi, lam, N, static_cast<double *>(h->d_epart.p), bps, s));
+        prof_end(h, mk_h, 1);
+        VQE_CUDA(h, launch_energy_finish(static_cast<double *>(h->d_epart.p), bps, B, E, nullptr,
+                                         nullptr, s));
+        h->stats.kernel_launches += 2;
+    }
     auto *coefs = static_cast<RotCoef<T> *>(h->d_coefs.p);
     const PassDesc *dd = static_cast<const PassDesc *>(P.d_bwd.p);
     double *gpart = static_cast<double *>(h->d_gpart.p);
@@ -1221,7 +1264,7 @@ vqe_status vqe_destroy(vqe_handle h) {
     h->plan[0].release();
     h->plan[1].release();
     for (DevBuf *b : {&h->d_groups, &h->d_tz, &h->d_tc, &h->d_wgroups, &h->d_wterms, &h->d_whoff,
-                      &h->d_wide, &h->d_hdiag,
+                      &h->d_wide, &h->d_awgroups, &h->d_awterms, &h->d_awhoff, &h->d_hdiag,
                       &h->d_hdiag_z, &h->d_hdiag_c, &h->ws_own, &h->d_params, &h->d_coefs,
                       &h->d_dtab, &h->d_gpart, &h->d_epart, &h->d_out, &h->hb_params,
                       &h->hb_e, &h->hb_n, &h->hb_g, &h->d_err})
@@ -1587,7 +1630,8 @@ int vqe_inspect_hamiltonian(int n_qubits, const uint64_t *x_masks, const uint64_
 
 int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
                         const uint64_t *z_masks, const double *coeffs, size_t n_terms,
-                        double threshold, int diag_terms, void *windows, int max_windows,
+                        double threshold, int diag_terms, int elem_layout, void *windows,
+                        int max_windows,
                         void *wgroups, int max_wgroups, void *wterms, int max_wterms,
                         uint32_t *hoff, int max_hoff, void *wide, int max_wide, int counts[5]) {
     if (n_qubits < 1 || n_qubits > 32 || (precision != 0 && precision != 1)) return -1;
@@ -1604,7 +1648,7 @@ int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
     HamPlan hp;
     make_ham_plan(cx, cz, cc, keep, hp);
     WinPlan wp;
-    plan_windows(n_qubits, vqe_precision(precision), hp, diag_terms != 0, wp);
+    plan_windows(n_qubits, vqe_precision(precision), hp, diag_terms != 0, wp, elem_layout != 0);
     if (counts) {
         counts[0] = int(wp.wins.size());
         counts[1] = int(wp.groups.size());

@@ -187,6 +187,15 @@ cudaError_t launch_energy_win(const WinDesc &W, const WinGroup *wgroups, const W
                               const uint32_t *hoff, const void *hdiag, int n_qubits, int batch,
                               const void *psi, size_t state_stride, double *partials,
                               int bps_total, cudaStream_t s);
+// Windowed apply-H over windows planned with each group's terms ordered by
+// their pattern over a thread's elements: `first` writes lambda, later windows
+// add to it; the `last` window writes block partials (Re<psi|lambda>, norm)
+// at [state][blockIdx.x] with 2^(n - W.k) columns per state.
+template <typename T>
+cudaError_t launch_apply_h_win(const WinDesc &W, const WinGroup *wgroups, const WinTerm *wterms,
+                               const uint32_t *hoff, const void *hdiag, int n_qubits, int batch,
+                               const void *psi, void *lam, size_t state_stride, int first,
+                               int last, double *partials, cudaStream_t s);
 // Tile bits (log2 of elements) of the windowed expectation for a precision:
 // 512 threads hold 2^(kWinBits - 9) elements each.
 constexpr int win_tile_bits(bool c128) { return c128 ? 12 : 13; }

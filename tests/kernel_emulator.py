@@ -414,3 +414,70 @@ def energy_windows(ham, win, n, psi, hdiag=None):
             norms += 1
     assert norms == 1
     return acc, nrm
+
+
+def apply_h_windows(win, n, psi, hdiag=None):
+    """The windowed apply-H kernel on the CPU: lambda accumulated window by
+    window (first window writes, later ones add), each group's sign sums at the
+    output element (direct, or per element-pattern run plus a Walsh-Hadamard
+    transform); the last window's Re<psi|lambda> and norm.  (lambda, E, norm)."""
+    LT, THR = 9, 512
+    tid = np.arange(THR, dtype=np.int64)
+    lam = np.zeros(1 << n, dtype=np.complex128)
+    wins = win["windows"]
+    assert not win["wide"], "apply-H windows cover every group"
+    acc = nrm = 0.0
+    for wi, W in enumerate(wins):
+        k, m = W.k, W.m
+        EPT = 1 << (k - LT)
+        tiles = 1 << (n - k)
+        bpos = [bb for bb in range(32) if (W.bmask >> bb) & 1]
+        tn = np.arange(tiles, dtype=np.int64)
+        base = np.zeros(tiles, dtype=np.int64)
+        for i, bb in enumerate(bpos):
+            base |= ((tn >> i) & 1) << bb
+        hoff = np.asarray(win["hoff"][W.hoff:W.hoff + (1 << (k - m))], dtype=np.int64)
+        e = np.arange(1 << k, dtype=np.int64)
+        g = base[:, None] | (e & ((1 << m) - 1))[None, :] | hoff[e >> m][None, :]
+        assert np.unique(g.ravel()).size == (1 << n)
+        sp = psi[g]
+        terms = win["wterms"][W.t_begin:W.t_begin + W.t_count]
+        zt = np.array([t.zt for t in terms], dtype=np.int64)
+        zout = np.array([t.zout for t in terms], dtype=np.int64)
+        cc = np.array([t.c for t in terms], dtype=np.float64)
+        sc = cc[None, :] * (1 - 2 * (popc(base[:, None] & zout[None, :]) & 1)) if len(terms) else np.zeros((tiles, 0))
+        el = tid[:, None] + THR * np.arange(EPT)[None, :]          # (THR, EPT) element of (thread, j)
+        lt = np.zeros((tiles, THR, EPT), dtype=np.complex128) if wi == 0 else lam[g[:, el]]
+
+        def run_sums(run, begin):
+            F = np.zeros((tiles, THR, EPT))
+            for v in range(EPT):
+                for t in range(begin + run[v], begin + run[v + 1]):
+                    sgn = 1 - 2 * (popc(tid & zt[t]) & 1)
+                    F[:, :, v] += sc[:, t][:, None] * sgn[None, :]
+            return _wht_last(F)
+
+        def direct(t0, t1):
+            f = np.zeros((tiles, THR, EPT))
+            for t in range(t0, t1):
+                f += sc[:, t][:, None, None] * (1 - 2 * (popc(el & zt[t]) & 1))[None, :, :]
+            return f
+
+        for G in win["wgroups"][W.g_begin:W.g_end]:
+            if G.xl == 0:
+                f = hdiag[g[:, el]] if hdiag is not None else run_sums(G.arun, G.a_begin)
+                lt += sp[:, el] * f
+                continue
+            y = sp[:, el ^ int(G.xl)]
+            if G.direct:
+                fa, fb = direct(G.a_begin, G.b_begin), direct(G.b_begin, G.b_end)
+            else:
+                fa = run_sums(G.arun, G.a_begin)
+                fb = run_sums(G.brun, G.b_begin) if G.b_end > G.b_begin else 0.0
+            lt += y * (fa - 1j * fb)
+        lam[g[:, el]] = lt
+        if wi == len(wins) - 1:
+            x = sp[:, el]
+            acc = float((x.real * lt.real + x.imag * lt.imag).sum())
+            nrm = float((np.abs(x) ** 2).sum())
+    return lam, acc, nrm

@@ -278,3 +278,30 @@ def test_padded_layout_conflict_free_for_default_plans(n, prec):
                     for h in range(0, lanes.size, lanes_per_wave):
                         part = slots[h:h + lanes_per_wave] % lanes_per_wave
                         assert np.unique(part).size == part.size, (d.k, R, p, r)
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("case", ["hubbard", "molecular"])
+def test_apply_h_windows_emulated(oracle_mod, prec, case):
+    """The windowed apply-H plan (terms ordered per element pattern) reproduces
+    the oracle's lambda = H psi and Re<psi|lambda>, with and without the
+    precomputed diagonal."""
+    from kernel_emulator import apply_h_windows
+    H = vi.hubbard_1d(8, 1.0, 3.0, periodic=True) if case == "hubbard" else vi.synthetic_molecular(8, seed=5)
+    n = H.n
+    psi = oracle_mod.ansatz_state(n, 1, vi.ansatz_params(33, n, 1))
+    lam_ref = oracle_mod.apply_h(psi, H.x, H.z, H.c)
+    ham = P.hamiltonian(n, H.x, H.z, H.c)
+    i = np.arange(1 << n, dtype=np.int64)
+    hdiag = np.zeros(1 << n)
+    for G in ham["groups"]:
+        if G.x == 0:
+            for t in range(G.t_begin, G.t_mid):
+                hdiag += ham["tc"][t] * (1 - 2 * (np.vectorize(lambda v: bin(v).count("1"))(i & int(ham["tz"][t])) & 1))
+    for diag_terms in (True, False):
+        win = P.windows(n, prec, H.x, H.z, H.c, diag_terms=diag_terms, elem_layout=True)
+        assert not win["wide"]
+        lam, e, nn = apply_h_windows(win, n, psi, hdiag=None if diag_terms else hdiag)
+        assert np.max(np.abs(lam - lam_ref)) < 1e-12 * H.sum_abs()
+        assert abs(e - float(np.real(np.vdot(psi, lam_ref)))) < 1e-11 * H.sum_abs()
+        assert abs(nn - float(np.vdot(psi, psi).real)) < 1e-12

@@ -28,11 +28,11 @@ N_QUBITS, DEPTH, SITES, N_VEC = 20, 10, 10, 1000
 U_VALUES = (2.0, 4.0, 8.0)
 CHUNK = 64                      # states per workspace chunk (64 x 16 MiB = 1 GiB > L2)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
-# DRAM read+write bytes per state of one forward-pass launch (k_pass<double,3,fwd>,
+# DRAM read+write bytes per state of one forward-pass launch (k_pass_fixed<double,3,fwd>,
 # 20 qubits, default plan), from the ncu capture of bench-sized launches
 # summarised in profiles/launches_hubbard20_bench.md.  None once the kernel
 # changes, until the capture is taken again.
-PASS_DRAM_BYTES_PER_STATE = 2096917504 / 64
+PASS_DRAM_BYTES_PER_STATE = 2095400619 / 64
 METRIC = "energy+gradient evals/s at 8-32 qubits; achieved HBM GB/s vs GB300 peak"
 WORKLOAD = ("20q FP64 (complex128) 10-site periodic 1D Hubbard t=1 U in {2,4,8}, "
             "HEA depth 10, 1000 param vectors per U, energy only")
@@ -265,7 +265,7 @@ def run_gpu(args, world, rank, local, pg):
     traffic = PASS_DRAM_BYTES_PER_STATE * CHUNK if PASS_DRAM_BYTES_PER_STATE else None
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-                "traffic": traffic, "kernel": "k_pass<double,3,fwd>",
+                "traffic": traffic, "kernel": "k_pass_fixed<double,3,fwd> (unrolled fused layer pass)",
                 "peak_source": "FP64 units x max SM clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "mean_launch_us": 1e3 * fwd_ms / max(fwd_launches, 1),
                 "share_of_step": fwd_ms / ms if ms else None,

@@ -126,6 +126,22 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def max_over_ranks(x: float, pg, device="cpu") -> float:
+    """The largest of the ranks' values of x (a time); x itself without a group."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank runs the same per-rank workload)."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 def barrier(pg, device=None):
     if pg is not None:
         if device is not None:
@@ -239,12 +255,9 @@ def run_gpu(args, world, rank, local, pg):
         e.profile(False)
     launches = sum(e.stats()["kernel_launches"] for e in engines) - launches0
     # max over ranks
-    if pg is not None:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, pg, dev)
     evals = len(U_VALUES) * N_VEC * args.steps * world
-    value = evals / (ms / 1e3)
+    value = job_throughput(len(U_VALUES) * N_VEC * args.steps, world, ms)
 
     # dominant kernel: the fused forward pass; FP64 FLOP model per amplitude
     # and layer = 4 per gated qubit (scaled rotation, 2 FMA per real pair)
@@ -292,10 +305,7 @@ def run_gpu(args, world, rank, local, pg):
             step_host()
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
-        if pg is not None:
-            t = torch.tensor([dt], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, pg, dev)
         h2d = sum(p.numel() * 8 for p in P_pin) + sum(h.x.nbytes + h.z.nbytes + h.c.nbytes for h in H)
         d2h = 2 * len(U_VALUES) * N_VEC * 8
         e2e = {"value": evals / dt, "unit": "evals/s", "h2d_bytes_per_step": int(h2d),

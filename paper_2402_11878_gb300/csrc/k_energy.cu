@@ -531,57 +531,92 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
                 }
             }
         } else {
+            // pair P = tid + 512 s of pattern u = P >> plog has lower element
+            // i0 = spread(P mod 2^plog) | fval[u]: e0 spreads the thread's
+            // bits below 9, D[s] the bits of s below plog - 9
             const uint32_t xl = G.xl;
-            const int hl = G.hl;
-            const uint32_t lm = (1u << hl) - 1u;
-            const uint32_t il0 = ((tid >> hl) << (hl + 1)) | (tid & lm);
+            const int plog = G.plog;
+            const uint32_t t0 = tid & (plog >= 9 ? 511u : ((1u << plog) - 1u));
+            const uint32_t e0 = (t0 & G.smask[0]) | ((t0 & G.smask[1]) << 1) | ((t0 & G.smask[2]) << 2) |
+                                ((t0 & G.smask[3]) << 3) | ((t0 & G.smask[4]) << 4);
+            uint32_t D[PPT];
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                uint32_t d = 0;
+#pragma unroll
+                for (int bb = 0; (1 << bb) < PPT; ++bb)
+                    if ((j >> bb) & 1) d |= G.dj[bb];
+                D[j] = d;
+            }
             const bool has_b = G.b_end > G.b_begin;
             if (!RUNS || G.direct) {
-                // few terms (at most kWinDirectMax per class): the terms sit in
-                // registers and each pair adds c * sign * conj(x0) x1 directly
+                // terms listed per pattern (at most kWinDirectMax per class),
+                // one sign evaluation per term and pair.  FP32 holds a
+                // pattern's terms in registers while the slots stay on it;
+                // FP64 (fewer registers per value) reads them per slot.
+                const uint32_t npat = (uint32_t)G.npat;
                 T ca[kWinDirectMax], cb[kWinDirectMax];
                 uint32_t za[kWinDirectMax], zb[kWinDirectMax];
-                const int na = G.b_begin - G.a_begin, nb = G.b_end - G.b_begin;
-#pragma unroll
-                for (int u = 0; u < kWinDirectMax; ++u) {
-                    ca[u] = u < na ? sc[G.a_begin + u] : T(0);
-                    za[u] = u < na ? szt[G.a_begin + u] : 0u;
-                    cb[u] = u < nb ? sc[G.b_begin + u] : T(0);
-                    zb[u] = u < nb ? szt[G.b_begin + u] : 0u;
-                }
+                int na = 0, nb = 0;
+                uint32_t ucur = ~0u;
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
-                    const uint32_t p = tid + j * kEnergyWinThreads;
-                    const uint32_t il = ((p >> hl) << (hl + 1)) | (p & lm);
+                    const uint32_t u = (tid + ((uint32_t)j << 9)) >> plog;   // warp-uniform
+                    if (u >= npat) break;
+                    const uint32_t il = e0 | D[j] | G.fval[u];
                     const C x0 = sp[il], x1 = sp[il ^ xl];
                     const T ar = fma(x0.x, x1.x, x0.y * x1.y);   // Re conj(x0) x1
+                    const T ai = has_b ? fma(x0.x, x1.y, -x0.y * x1.x) : T(0);   // Im conj(x0) x1
+                    if constexpr (sizeof(T) == 8) {
+                        const int a1 = G.a_begin + G.arun[u + 1];
+                        for (int t = G.a_begin + G.arun[u]; t < a1; ++t)
+                            part = fma(ar, sgn_flip(sc[t], __popc(il & szt[t]) & 1u), part);
+                        if (has_b) {
+                            const int b1 = G.b_begin + G.brun[u + 1];
+                            for (int t = G.b_begin + G.brun[u]; t < b1; ++t)
+                                part = fma(ai, sgn_flip(sc[t], __popc(il & szt[t]) & 1u), part);
+                        }
+                    } else {
+                        if (u != ucur) {
+                            ucur = u;
+                            const int a0 = G.a_begin + G.arun[u], b0 = G.b_begin + G.brun[u];
+                            na = G.arun[u + 1] - G.arun[u];
+                            nb = G.brun[u + 1] - G.brun[u];
 #pragma unroll
-                    for (int u = 0; u < kWinDirectMax; ++u)
-                        if (u < na) part = fma(ar, sgn_flip(ca[u], __popc(il & za[u]) & 1u), part);
-                    if (has_b) {
-                        const T ai = fma(x0.x, x1.y, -x0.y * x1.x);   // Im conj(x0) x1
+                            for (int w = 0; w < kWinDirectMax; ++w) {
+                                ca[w] = w < na ? sc[a0 + w] : T(0);
+                                za[w] = w < na ? szt[a0 + w] : 0u;
+                                cb[w] = w < nb ? sc[b0 + w] : T(0);
+                                zb[w] = w < nb ? szt[b0 + w] : 0u;
+                            }
+                        }
 #pragma unroll
-                        for (int u = 0; u < kWinDirectMax; ++u)
-                            if (u < nb) part = fma(ai, sgn_flip(cb[u], __popc(il & zb[u]) & 1u), part);
+                        for (int w = 0; w < kWinDirectMax; ++w)
+                            if (w < na) part = fma(ar, sgn_flip(ca[w], __popc(il & za[w]) & 1u), part);
+                        if (has_b) {
+#pragma unroll
+                            for (int w = 0; w < kWinDirectMax; ++w)
+                                if (w < nb) part = fma(ai, sgn_flip(cb[w], __popc(il & zb[w]) & 1u), part);
+                        }
                     }
                 }
             } else if constexpr (RUNS) {
+                // a whole group (one pattern, plog = K - 1: every slot valid)
                 T ar[PPT], ai[PPT];
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
-                    const uint32_t p = tid + j * kEnergyWinThreads;
-                    const uint32_t il = ((p >> hl) << (hl + 1)) | (p & lm);
+                    const uint32_t il = e0 | D[j];
                     const C x0 = sp[il], x1 = sp[il ^ xl];
                     ar[j] = fma(x0.x, x1.x, x0.y * x1.y);
                     ai[j] = fma(x0.x, x1.y, -x0.y * x1.x);
                 }
                 T F[PPT];
-                run_sums<PPT>(F, G.arun, G.a_begin, sc, szt, il0);
+                run_sums<PPT>(F, G.arun, G.a_begin, sc, szt, e0);
                 wht_inplace<PPT>(F);
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) part = fma(ar[j], F[j], part);
                 if (has_b) {
-                    run_sums<PPT>(F, G.brun, G.b_begin, sc, szt, il0);
+                    run_sums<PPT>(F, G.brun, G.b_begin, sc, szt, e0);
                     wht_inplace<PPT>(F);
 #pragma unroll
                     for (int j = 0; j < PPT; ++j) part = fma(ai[j], F[j], part);

@@ -149,6 +149,15 @@ __device__ __forceinline__ void stage_pass(const PassDesc *__restrict__ desc,
     __syncthreads();
 }
 
+// A forward tile known to be zero (its base has a bit of zmask set): the
+// pass maps it to zero, so it is written without being read or transformed.
+template <typename C>
+__device__ __forceinline__ void write_zero_tile(C *P, uint64_t base, uint32_t lowmask, int m, int a, int k) {
+    const C z{};
+    for (uint32_t e = threadIdx.x; e < (1u << k); e += blockDim.x)
+        P[base | (e & lowmask) | ((uint64_t)(e >> m) << a)] = z;
+}
+
 // One CTA per (tile, state): global -> shared (plain order), the pass
 // program, shared -> global.
 // Forward passes hold one buffer per thread: two blocks of 512 threads fit an
@@ -181,6 +190,10 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
     C *L = BWD ? lam + (size_t)b * stride : nullptr;
     const uint64_t tile = blockIdx.x;
     const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (k - m)));
+    if (!BWD && (base & d.zmask)) {   // block-uniform
+        write_zero_tile(P, base, lowmask, m, a, k);
+        return;
+    }
     GridEnv<T> env{&sd, scf, dtab + (size_t)b * dtab_stride,
                    BWD ? gpart + (size_t)b * grad_stride : nullptr, tile, P, L, base, lowmask,
                    m, a, init_zero};
@@ -224,6 +237,10 @@ k_pass_fixed(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::t
     const int mid = a - m;
     const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (k - m)));
     const uint32_t lowmask = (1u << m) - 1u;
+    if (!BWD && (base & d.zmask)) {   // block-uniform
+        write_zero_tile(psi + (size_t)b * stride, base, lowmask, m, a, k);
+        return;
+    }
     GridEnv<T> env{&sd, scf, dtab + (size_t)b * dtab_stride,
                    BWD ? gpart + (size_t)b * grad_stride : nullptr, tile, psi + (size_t)b * stride,
                    BWD ? lam + (size_t)b * stride : nullptr, base, lowmask, m, a, init_zero};

@@ -472,6 +472,19 @@ bool make_plan(int n, int D, vqe_precision prec, const PlanOptions &opt, HostPla
             for (int u = 0; u < ss.n_gated; ++u) ss.before[u] = before[s][ss.tile_bit[u]];
         }
     }
+    // Support of the state before each forward pass (it starts from |0...0>):
+    // bits of qubits no earlier pass has rotated are 0.
+    {
+        uint32_t rotated = 0;
+        const uint32_t nmask = n >= 32 ? ~0u : ((1u << n) - 1u);
+        for (int p = 0; p < np; ++p) {
+            hp.fwd[p].zmask = nmask & ~rotated;
+            hp.bwd[p].zmask = 0u;
+            const Group &G = hp.groups[plans[p].group];
+            for (int j = 0; j < G.k; ++j)
+                if ((G.gated >> j) & 1u) rotated |= 1u << G.qubit_of(j);
+        }
+    }
     // CZ(q, q+1) of layer l goes to the later of the slots holding RY_l(q), RY_l(q+1).
     for (int l = 0; l < D; ++l) {
         for (int q = 0; q + 1 < n; ++q) {
@@ -668,6 +681,84 @@ uint32_t win_gather(uint32_t g, int m, const std::vector<int> &pos) {
     return t;
 }
 
+// bit i of v -> the i-th set bit of mask (a software bit deposit)
+uint32_t deposit_bits(uint32_t v, uint32_t mask) {
+    uint32_t out = 0;
+    int i = 0;
+    for (int q = 0; q < 32; ++q)
+        if ((mask >> q) & 1u) {
+            if ((v >> i) & 1u) out |= 1u << q;
+            ++i;
+        }
+    return out;
+}
+
+// p with a zero inserted at every set bit of mask (ascending): the tile index
+// of free-index p when the bits of mask are fixed
+uint32_t spread_bits(uint32_t p, uint32_t mask) {
+    for (int q = 0; q < 32; ++q)
+        if ((mask >> q) & 1u) p = ((p >> q) << (q + 1)) | (p & ((1u << q) - 1u));
+    return p;
+}
+
+// A group of the expectation split per pattern b of its X bits below the top
+// one (global coordinates).  For the lower element i0 of a pair (top X bit 0)
+// with those bits equal to b, (-1)^{popc(i0 & z)} = (-1)^{popc(i0 & (z & ~x))}
+// * (-1)^{popc(b & z)}: terms sharing the Z bits outside x merge into one
+// coefficient per pattern, and patterns whose merged coefficients all vanish
+// (the pairs the group does not connect, e.g. |00> <-> |11> for a hop) are
+// left out.  With more than 3 such bits the group stays whole.
+struct VTerm {
+    uint32_t z;
+    double c;
+};
+struct VGroup {
+    uint32_t fix_mask, fix_val;
+    std::vector<VTerm> a, b;
+};
+
+std::vector<VGroup> split_group(const GroupDesc &G, const HamPlan &hp) {
+    std::vector<VGroup> out;
+    const uint32_t x = G.x;
+    const int h = 31 - __builtin_clz(x);
+    const uint32_t xp = x & ~(1u << h);
+    const int rp = __builtin_popcount(xp);
+    if (rp > 3) {
+        VGroup v{1u << h, 0u, {}, {}};
+        for (int t = G.t_begin; t < G.t_mid; ++t) v.a.push_back({hp.tz[t], hp.tc[t]});
+        for (int t = G.t_mid; t < G.t_end; ++t) v.b.push_back({hp.tz[t], hp.tc[t]});
+        out.push_back(v);
+        return out;
+    }
+    const int np = 1 << rp;
+    auto classes = [&](int t0, int t1, std::vector<uint32_t> &keys, std::vector<std::vector<double>> &tab) {
+        for (int t = t0; t < t1; ++t) {
+            const uint32_t z = hp.tz[t], zc = z & ~x;
+            size_t ci = 0;
+            while (ci < keys.size() && keys[ci] != zc) ++ci;
+            if (ci == keys.size()) {
+                keys.push_back(zc);
+                tab.emplace_back(np, 0.0);
+            }
+            for (int bb = 0; bb < np; ++bb)
+                tab[ci][bb] += (__builtin_popcount(deposit_bits(bb, xp) & z) & 1) ? -hp.tc[t] : hp.tc[t];
+        }
+    };
+    std::vector<uint32_t> ka, kb;
+    std::vector<std::vector<double>> ta, tb;
+    classes(G.t_begin, G.t_mid, ka, ta);
+    classes(G.t_mid, G.t_end, kb, tb);
+    for (int bb = 0; bb < np; ++bb) {
+        VGroup v{(1u << h) | xp, deposit_bits(bb, xp), {}, {}};
+        for (size_t c = 0; c < ka.size(); ++c)
+            if (ta[c][bb] != 0.0) v.a.push_back({ka[c], ta[c][bb]});
+        for (size_t c = 0; c < kb.size(); ++c)
+            if (tb[c][bb] != 0.0) v.b.push_back({kb[c], tb[c][bb]});
+        if (!v.a.empty() || !v.b.empty()) out.push_back(std::move(v));
+    }
+    return out;
+}
+
 // Windows of the windowed expectation (Sec. II-B Eq. 7 evaluated per X-mask
 // group): the low tile (with <psi|psi> and the diagonal group), then windows
 // of mrun low bits plus kE - mrun further bits chosen greedily so that every
@@ -688,6 +779,18 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
     const int hw = kE - mrun;
     const int lt = 9;                      // log2 of the kernel's 512 threads
     const int EPT = 1 << (kE - lt), PPT = EPT / 2;
+    // the fixed bits of i0 in tile coordinates, and from them the spread of a
+    // pair's free index: smask by shift, dj for the bits at and above lt
+    auto set_fixed = [&](WinGroup &wg, uint32_t fmask) {
+        wg.fmask = fmask;
+        wg.plog = kE - __builtin_popcount(fmask);
+        for (int i = 0; i < wg.plog; ++i) {
+            const uint32_t o = spread_bits(1u << i, fmask);
+            wg.smask[(31 - __builtin_clz(o)) - i] |= 1u << i;
+        }
+        for (int bb = 0; bb < 4; ++bb)
+            wg.dj[bb] = (lt + bb < wg.plog) ? spread_bits(1u << (lt + bb), fmask) : 0u;
+    };
 
     struct Cand {
         int m;
@@ -695,13 +798,44 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
         std::vector<int> groups;
         int terms = 0;
         bool norm = false;
+        int ngroups = 0;                   // window groups after splitting
     };
     std::vector<Cand> cands;
+    // expectation layout: a pair group is split by the patterns of its X bits
+    // below the top one when every kept pattern has few terms (one sign
+    // evaluation per term and pair); otherwise it stays whole
+    const int split_max = c128 ? 3 : 2;
+    std::vector<std::vector<VGroup>> vgs(hp.groups.size());
+    std::vector<char> is_split(hp.groups.size(), 0), vanishes(hp.groups.size(), 0);
+    if (!elem_layout)
+        for (size_t g = 0; g < hp.groups.size(); ++g) {
+            const GroupDesc &G = hp.groups[g];
+            if (G.x == 0u) continue;
+            std::vector<VGroup> v = split_group(G, hp);
+            if (v.empty()) {
+                vanishes[g] = 1;
+                continue;
+            }
+            bool ok = v[0].fix_mask != (1u << (31 - __builtin_clz(G.x)));
+            for (const VGroup &vg : v)
+                ok = ok && int(vg.a.size()) <= kWinDirectMax && int(vg.b.size()) <= kWinDirectMax &&
+                     int(vg.a.size() + vg.b.size()) <= split_max;
+            if (ok) {
+                vgs[g] = std::move(v);
+                is_split[g] = 1;
+            }
+        }
     auto group_terms = [&](int g) {
         const GroupDesc &G = hp.groups[g];
         if (G.x == 0u && !diag_terms) return 0;
+        if (is_split[g]) {
+            int t = 0;
+            for (const VGroup &v : vgs[g]) t += int(v.a.size() + v.b.size());
+            return t;
+        }
         return G.t_end - G.t_begin;
     };
+    auto group_count = [&](int g) { return vanishes[g] ? 0 : 1; };
     // the low tile: every group whose X mask lies in bits [0, kE); split when
     // the term cap is reached (only the first part yields the norm)
     cands.push_back({kE, 0u, {}, 0, true});
@@ -715,11 +849,14 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
                 if (x == 0u) cands[0].norm = false;  // the sweep of the diagonal group yields the norm
                 continue;
             }
+            const int gc = group_count(int(g));
+            if (gc == 0) continue;                   // every pair of the group vanishes
             if (cands.back().m != kE || cands.back().terms + tg > kWinMaxTerms ||
-                int(cands.back().groups.size()) >= kWinMaxGroups)
+                cands.back().ngroups + gc > kWinMaxGroups)
                 cands.push_back({kE, 0u, {}, 0, false});
             cands.back().groups.push_back(int(g));
             cands.back().terms += tg;
+            cands.back().ngroups += gc;
         } else {
             rest.push_back(int(g));
         }
@@ -733,7 +870,9 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
     for (int g : rest) {
         const uint32_t H = hp.groups[g].x & ~lowm;
         const int tg = group_terms(g);
-        if (__builtin_popcount(H) > hw || tg > kWinMaxTerms) {
+        const int gc = group_count(g);
+        if (gc == 0) continue;
+        if (__builtin_popcount(H) > hw || tg > kWinMaxTerms || gc > kWinMaxGroups) {
             wp.wide.push_back(hp.groups[g]);
             continue;
         }
@@ -741,8 +880,7 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
         for (size_t c = first_free; c < cands.size(); ++c) {
             const uint32_t U = cands[c].S | H;
             const int sz = __builtin_popcount(U);
-            if (sz > hw || cands[c].terms + tg > kWinMaxTerms ||
-                int(cands[c].groups.size()) >= kWinMaxGroups)
+            if (sz > hw || cands[c].terms + tg > kWinMaxTerms || cands[c].ngroups + gc > kWinMaxGroups)
                 continue;
             const int add = sz - __builtin_popcount(cands[c].S);
             if (add < best_add) {
@@ -757,6 +895,7 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
         cands[best].S |= H;
         cands[best].groups.push_back(g);
         cands[best].terms += tg;
+        cands[best].ngroups += gc;
     }
     const uint32_t nmask = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
     for (Cand &c : cands) {
@@ -781,6 +920,35 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
         W.t_begin = int(wp.terms.size());
         for (int g : c.groups) {
             const GroupDesc &G = hp.groups[g];
+            if (is_split[g]) {
+                WinGroup wg{};
+                wg.xl = win_gather(G.x, c.m, pos);
+                wg.hl = 31 - __builtin_clz(wg.xl);
+                wg.direct = 1;
+                set_fixed(wg, win_gather(vgs[g][0].fix_mask, c.m, pos));
+                wg.npat = int(vgs[g].size());
+                for (int u = 0; u < wg.npat; ++u) wg.fval[u] = win_gather(vgs[g][u].fix_val, c.m, pos);
+                auto emit_p = [&](bool cls_b, uint16_t *run, int &begin) {
+                    begin = int(wp.terms.size()) - W.t_begin;
+                    for (int u = 0; u < wg.npat; ++u) {
+                        run[u] = uint16_t(int(wp.terms.size()) - W.t_begin - begin);
+                        for (const VTerm &vt : cls_b ? vgs[g][u].b : vgs[g][u].a) {
+                            WinTerm wt{};
+                            wt.zt = win_gather(vt.z, c.m, pos);
+                            wt.zout = vt.z & W.bmask;
+                            wt.c = vt.c;
+                            wp.terms.push_back(wt);
+                        }
+                    }
+                    run[wg.npat] = uint16_t(int(wp.terms.size()) - W.t_begin - begin);
+                };
+                emit_p(false, wg.arun, wg.a_begin);
+                emit_p(true, wg.brun, wg.b_begin);
+                wg.b_end = int(wp.terms.size()) - W.t_begin;
+                wp.groups.push_back(wg);
+                continue;
+            }
+            if (vanishes[g]) continue;
             WinGroup wg{};
             wg.xl = win_gather(G.x, c.m, pos);
             wg.hl = wg.xl ? 31 - __builtin_clz(wg.xl) : 0;
@@ -823,6 +991,12 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
                 }
                 for (auto &p : ts) wp.terms.push_back(p.second);
             };
+            if (wg.xl && !elem_layout) {
+                set_fixed(wg, 1u << wg.hl);
+                wg.npat = 1;
+            } else {
+                wg.plog = kE;
+            }
             const bool keep = G.x != 0u || diag_terms;
             int bdummy = 0;
             emit(G.t_begin, keep ? G.t_mid : G.t_begin, wg.arun, wg.a_begin);

@@ -44,6 +44,10 @@ struct PassDesc {
     int R;          // register bits per thread (thread holds 2^R amplitudes)
     int n_ops;
     int n_slots;
+    // Forward passes start from |0...0>: before this pass only the qubits
+    // rotated by earlier passes can be 1, so a tile whose base has a bit of
+    // zmask set is zero and stays zero (0 in backward passes)
+    uint32_t zmask;
     int slot_layer[kMaxSlots];
     uint32_t slot_czmask[kMaxSlots];  // bit q: CZ(q, q+1) applied in this slot's DIAG
     uint32_t slot_gated[kMaxSlots];   // tile bits gated (RY, RZ) in this slot
@@ -139,10 +143,29 @@ constexpr int kWinDirectMax = 3;   // terms per class of a window group in direc
 // thread's pairs, or a thread's elements for the diagonal group xl == 0);
 // arun[v] / brun[v] are the run starts relative to the class start and
 // arun[NV] / brun[NV] the class length.
+//
+// In the expectation's windows a pair group may be split by the pattern of
+// the bits of xl below its top bit (the top bit hl of i0 is always 0).  With
+// those bits fixed, the terms merge per Z mask outside xl into one
+// coefficient per pattern; the npat patterns whose coefficients do not all
+// vanish are kept, pattern u fixing the tile bits `fmask` of i0 to fval[u].
+// Pair P = tid + 512 s of a thread (slot s) has pattern u = P >> plog and free
+// index f = P mod 2^plog, deposited around fmask: i0 = spread(f) | fval[u],
+// spread(f) = sum_s (f & smask[s]) << s, and the bits of f at and above 9
+// spread to dj[b] (0 beyond plog).  An unsplit group is the case npat = 1,
+// fmask = 1 << hl.  Direct groups keep pattern u's class-A terms at
+// a_begin + [arun[u], arun[u + 1]) and its class-B terms at
+// b_begin + [brun[u], brun[u + 1]); run groups (unsplit) keep the runs above.
 struct WinGroup {
     uint32_t xl;            // X mask in tile coordinates (0: the diagonal group)
     int hl;                 // top bit of xl
-    int direct;             // 1: terms unsorted, sign sums per pair (groups of few terms)
+    int direct;             // 1: sign sums per pair, terms listed per pattern
+    uint32_t fmask;         // fixed tile bits of i0 (expectation windows)
+    int plog;               // log2 of the pairs per pattern
+    int npat;               // patterns kept (direct groups)
+    uint32_t fval[8];       // the fmask bits of i0 per pattern
+    uint32_t smask[5];      // free-index bits moved up by s places in spread()
+    uint32_t dj[4];         // spread of free-index bit 9 + b (0 beyond plog)
     int a_begin, b_begin, b_end;
     uint16_t arun[kWinMaxRuns + 1];
     uint16_t brun[kWinMaxRuns + 1];

@@ -26,7 +26,7 @@ class PassOp(ctypes.Structure):
 
 class PassDesc(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("m", ctypes.c_int), ("a", ctypes.c_int), ("R", ctypes.c_int),
-                ("n_ops", ctypes.c_int), ("n_slots", ctypes.c_int),
+                ("n_ops", ctypes.c_int), ("n_slots", ctypes.c_int), ("zmask", ctypes.c_uint32),
                 ("slot_layer", ctypes.c_int * K_MAX_SLOTS),
                 ("slot_czmask", ctypes.c_uint32 * K_MAX_SLOTS),
                 ("slot_gated", ctypes.c_uint32 * K_MAX_SLOTS),
@@ -63,6 +63,9 @@ class WinDesc(ctypes.Structure):
 
 class WinGroup(ctypes.Structure):
     _fields_ = [("xl", ctypes.c_uint32), ("hl", ctypes.c_int), ("direct", ctypes.c_int),
+                ("fmask", ctypes.c_uint32), ("plog", ctypes.c_int), ("npat", ctypes.c_int),
+                ("fval", ctypes.c_uint32 * 8), ("smask", ctypes.c_uint32 * 5),
+                ("dj", ctypes.c_uint32 * 4),
                 ("a_begin", ctypes.c_int),
                 ("b_begin", ctypes.c_int), ("b_end", ctypes.c_int),
                 ("arun", ctypes.c_uint16 * (K_WIN_MAX_RUNS + 1)),

@@ -215,6 +215,15 @@ class Emu:
                 raise AssertionError(f"unknown op kind {op.kind}")
         assert not written, "gradient partials left unflushed"
         g = gaddr(elem_of(t, r, chunk, R))
+        # forward from |0...0>: tiles whose base has a bit of zmask are
+        # written as zeros without being transformed; they must be zero
+        zt = (base[:, 0, 0] & int(d.zmask)) != 0
+        if backward:
+            assert d.zmask == 0
+        else:
+            assert np.all(psi[g[zt]] == 0) if not init_zero else True
+            assert np.allclose(v[zt], 0, atol=1e-300), "a tile marked zero is not"
+            v = np.where(zt[:, None, None], 0, v)
         psi[g] = v
         if backward:
             lam[g] = w
@@ -300,6 +309,15 @@ def _insert0(p, hl):
     return ((p >> hl) << (hl + 1)) | (p & ((1 << hl) - 1))
 
 
+def _spread(p, mask):
+    """p with a zero inserted at every set bit of mask, ascending."""
+    p = np.asarray(p, dtype=np.int64)
+    for q in range(32):
+        if (mask >> q) & 1:
+            p = ((p >> q) << (q + 1)) | (p & ((1 << q) - 1))
+    return p
+
+
 def _wht_last(F):
     """f[..., j] = sum_v F[..., v] (-1)^{popc(j & v)} (unnormalised)."""
     F = F.copy()
@@ -357,6 +375,8 @@ def energy_windows(ham, win, n, psi, hdiag=None):
             norms += 1
         for G in win["wgroups"][W.g_begin:W.g_end]:
             NV = PPT if G.xl else EPT
+            if G.xl and G.direct:
+                NV = int(G.npat)
             assert 0 <= G.a_begin <= G.b_begin <= G.b_end <= W.t_count
             assert G.arun[0] == 0 and G.a_begin + G.arun[NV] == G.b_begin
             assert G.brun[0] == 0 and G.b_begin + G.brun[NV] == G.b_end
@@ -382,25 +402,54 @@ def energy_windows(ham, win, n, psi, hdiag=None):
                 continue
             xl, hl = int(G.xl), int(G.hl)
             assert xl < (1 << k) and (xl >> hl) == 1
+            # pattern u fixes the tile bits fmask of the lower element to
+            # fval[u]; pair P = tid + 512 s has u = P >> plog and free index
+            # P mod 2^plog, spread around fmask
+            fm, plog, npat = int(G.fmask), int(G.plog), int(G.npat)
+            assert (fm >> hl) & 1 and fm < (1 << k) and plog == k - popc(fm)
+            assert 1 <= npat <= 8 and (npat == 1 or G.direct)
+            fval = [int(G.fval[u]) for u in range(npat)]
+            assert all(v & ~fm == 0 and not (v >> hl) & 1 for v in fval)
+            assert len(set(fval)) == npat
+            t0 = tid & (511 if plog >= 9 else (1 << plog) - 1)
+            e0 = sum((t0 & int(G.smask[q])) << q for q in range(5))
+            dsum = np.zeros(PPT, dtype=np.int64)
+            for j in range(PPT):
+                for bb in range(4):
+                    if (j >> bb) & 1:
+                        dsum[j] |= int(G.dj[bb])
             pj = tid[:, None] + THR * np.arange(PPT)[None, :]
-            il = _insert0(pj, hl)
+            u = pj >> plog
+            valid = u < npat
+            fv = np.array(fval + [0] * (9 - npat), dtype=np.int64)[np.minimum(u, 8)]
+            il = np.where(valid, e0[:, None] | dsum[None, :] | fv, 0)
+            # the kernel's composition equals the definition spread(f) | fval[u]
+            ref = _spread(pj & ((1 << plog) - 1), fm) | fv
+            assert np.array_equal(il[valid], ref[valid])
             assert il.max() < (1 << k) and (il ^ xl).max() < (1 << k)
             x0, x1 = sp[:, il], sp[:, il ^ xl]
-            prod = np.conj(x0) * x1
-            il0 = _insert0(tid, hl)
+            prod = np.where(valid[None, :, :], np.conj(x0) * x1, 0)
+            il0 = e0
 
-            def direct_sums(t0, t1):
+            def direct_sums(begin, run):
                 f = np.zeros((tiles, THR, PPT))
-                for t in range(t0, t1):
-                    sgn = 1 - 2 * (popc(il & zt[t]) & 1)          # (THR, PPT)
-                    f += sc[:, t][:, None, None] * sgn[None, :, :]
+                for uu in range(npat):
+                    sel = (u == uu)
+                    for t in range(begin + run[uu], begin + run[uu + 1]):
+                        sgn = 1 - 2 * (popc(il & zt[t]) & 1)          # (THR, PPT)
+                        f += sc[:, t][:, None, None] * (sgn * sel)[None, :, :]
                 return f
 
             if G.direct:
-                part = (prod.real * direct_sums(G.a_begin, G.b_begin)).sum()
+                assert G.a_begin + G.arun[npat] == G.b_begin and G.b_begin + G.brun[npat] == G.b_end
+                # the kernel holds a pattern's terms in registers: at most 3 per class
+                assert all(G.arun[v + 1] - G.arun[v] <= 3 and G.brun[v + 1] - G.brun[v] <= 3
+                           for v in range(npat))
+                part = (prod.real * direct_sums(G.a_begin, G.arun)).sum()
                 if G.b_end > G.b_begin:
-                    part += (prod.imag * direct_sums(G.b_begin, G.b_end)).sum()
+                    part += (prod.imag * direct_sums(G.b_begin, G.brun)).sum()
             else:
+                assert npat == 1 and plog == k - 1 and fval == [0]
                 part = (prod.real * run_sums(G.arun, G.a_begin, il0)).sum()
                 if G.b_end > G.b_begin:
                     part += (prod.imag * run_sums(G.brun, G.b_begin, il0)).sum()

@@ -82,6 +82,25 @@ def test_emulated_kernels_match_oracle(oracle_mod, n, D, prec):
         assert np.max(np.abs(g - g_ref)) < 1e-11 * max(1.0, np.max(np.abs(g_ref)))
 
 
+@pytest.mark.parametrize("n,D,prec", [(20, 10, "c128"), (24, 4, "c64"), (28, 4, "c64"), (32, 8, "c128")])
+def test_forward_zero_tile_masks(n, D, prec):
+    """Forward passes start from |0...0>: the first pass's zmask holds every
+    qubit (only the tile at base 0 is nonzero), each later pass's mask drops
+    the qubits the earlier passes rotated, once every qubit has been rotated
+    the mask is empty, and backward passes never skip."""
+    pl = P.plan(n, D, prec)
+    nmask = (1 << n) - 1
+    rotated = 0
+    for i, d in enumerate(pl["fwd"]):
+        assert d.zmask == nmask & ~rotated
+        for j in range(d.k):
+            if (d.slot_gated[0] >> j) & 1:
+                rotated |= 1 << (j if j < d.m else d.a + j - d.m)
+    assert i == 0 or pl["fwd"][0].zmask == nmask
+    assert rotated == nmask and pl["fwd"][-1].zmask == 0
+    assert all(d.zmask == 0 for d in pl["bwd"])
+
+
 def test_emulated_full_size_20q_plan(oracle_mod):
     """The 20-qubit FP64 plan of the benchmark workload, checked end to end."""
     n, D = 20, 10
@@ -202,7 +221,11 @@ def test_energy_windows_emulated(oracle_mod, prec, case):
     for diag_terms in (True, False):
         win = P.windows(n, prec, H.x, H.z, H.c, diag_terms=diag_terms)
         assert win["windows"], "expected windows above the tile size"
-        assert len(win["wgroups"]) + len(win["wide"]) == len(ham["groups"])
+        # pair groups are split into virtual groups (one per pattern of the
+        # X bits below the top one, vanishing patterns dropped): at most
+        # 2^3 per group, never more terms than the group had
+        assert len(win["wgroups"]) + len(win["wide"]) <= 8 * len(ham["groups"])
+        assert len(win["wterms"]) <= len(ham["tz"]) * 8
         e, nn = energy_windows(ham, win, n, psi, hdiag=None if diag_terms else hdiag)
         assert abs(e - e_ref) < 1e-11 * H.sum_abs() and abs(nn - n_ref) < 1e-12
 

@@ -436,7 +436,7 @@ def run_workload(name: str, args):
                      "ms_per_step": ms, "dtype": "c64",
                      "config": {"workload": "512 instances, 12-18 qubits (uniform), open Hubbard "
                                 "sites n/2, U~U[1,8], depth n/2, complex64 energy + adjoint gradient, "
-                                "one persistent launch under a CUDA graph",
+                                "persistent launches (one per register-bit class) in one CUDA graph",
                                 "autotuned_tile_bits": kb},
                      "fp64_one_by_one_baseline": {"value": 1.0 / per_inst,
                                                    "unit": "instance evals/s",

@@ -50,7 +50,9 @@ struct BatchArgs {
     BatchLayout layout;
 };
 
+// r4: the kernel for instances whose plans hold 16 amplitudes per thread
+// (R = 4); the other kernel takes R <= 3.
 template <typename T>
-cudaError_t launch_batch(const BatchArgs &args, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_batch(const BatchArgs &args, bool r4, int grid, size_t smem, cudaStream_t s);
 
 }  // namespace vqe

@@ -52,20 +52,28 @@ __device__ __forceinline__ T bsign_sum(uint32_t i, const uint32_t *__restrict__ 
     return f;
 }
 
-template <typename T, bool BWD, class Env>
-__device__ void run_tile_any(int R, const PassDesc &d, uint64_t gbase, typename V2<T>::type *sp,
-                             typename V2<T>::type *sl, double *gsh, Env &env) {
-    switch (R) {
-        case 1: run_tile<T, 1, BWD>(d, d.ops, d.n_ops, gbase, sp, sl, gsh, env); break;
-        case 2: run_tile<T, 2, BWD>(d, d.ops, d.n_ops, gbase, sp, sl, gsh, env); break;
-        case 3: run_tile<T, 3, BWD>(d, d.ops, d.n_ops, gbase, sp, sl, gsh, env); break;
-        default: run_tile<T, 4, BWD>(d, d.ops, d.n_ops, gbase, sp, sl, gsh, env); break;
+// The tile program for the instance's register bits.  Kernels are split by
+// R4 (R = 4 alone, or R <= 3): one kernel holding all four bodies spills
+// heavily, each half does not.
+template <typename T, bool BWD, bool R4, class Env>
+__device__ __forceinline__ void run_tile_any(int R, const PassDesc &d, uint64_t gbase,
+                                             typename V2<T>::type *sp, typename V2<T>::type *sl,
+                                             double *gsh, Env &env) {
+    if constexpr (R4) {
+        (void)R;
+        run_tile<T, 4, BWD>(d, d.ops, d.n_ops, gbase, sp, sl, gsh, env);
+    } else {
+        switch (R) {
+            case 1: run_tile<T, 1, BWD>(d, d.ops, d.n_ops, gbase, sp, sl, gsh, env); break;
+            case 2: run_tile<T, 2, BWD>(d, d.ops, d.n_ops, gbase, sp, sl, gsh, env); break;
+            default: run_tile<T, 3, BWD>(d, d.ops, d.n_ops, gbase, sp, sl, gsh, env); break;
+        }
     }
 }
 
 }  // namespace
 
-template <typename T>
+template <typename T, bool R4>
 __global__ void __launch_bounds__(kBatchThreads, 1)
 k_batch(BatchArgs args) {
     using C = typename V2<T>::type;
@@ -202,7 +210,7 @@ k_batch(BatchArgs args) {
                     }
                     __syncthreads();
                 }
-                run_tile_any<T, false>(d.R, d, base, sp, nullptr, gsh, env);
+                run_tile_any<T, false, R4>(d.R, d, base, sp, nullptr, gsh, env);
                 if (!in_smem) {
                     for (uint32_t e = threadIdx.x; e < (1u << k); e += blockDim.x) {
                         const uint64_t g = base | (e & ((1u << m) - 1u)) | ((uint64_t)(e >> m) << a);
@@ -280,7 +288,7 @@ k_batch(BatchArgs args) {
                     }
                     __syncthreads();
                 }
-                run_tile_any<T, true>(d.R, d, base, sp, sl, gsh, env);
+                run_tile_any<T, true, R4>(d.R, d, base, sp, sl, gsh, env);
                 if (!in_smem) {
                     for (uint32_t e = threadIdx.x; e < (1u << k); e += blockDim.x) {
                         const uint64_t g = base | (e & ((1u << m) - 1u)) | ((uint64_t)(e >> m) << a);
@@ -298,15 +306,20 @@ k_batch(BatchArgs args) {
 }
 
 template <typename T>
-cudaError_t launch_batch(const BatchArgs &args, int grid, size_t smem, cudaStream_t s) {
-    auto kern = k_batch<T>;
+cudaError_t launch_batch(const BatchArgs &args, bool r4, int grid, size_t smem, cudaStream_t s) {
+    auto kern = k_batch<T, false>;
+    if constexpr (sizeof(T) == 4) {
+        if (r4) kern = k_batch<T, true>;
+    } else if (r4) {
+        return cudaErrorInvalidValue;   // FP64 plans keep R <= 3 (tiles of at most 2^12)
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kBatchThreads, smem, s>>>(args);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_batch<float>(const BatchArgs &, int, size_t, cudaStream_t);
-template cudaError_t launch_batch<double>(const BatchArgs &, int, size_t, cudaStream_t);
+template cudaError_t launch_batch<float>(const BatchArgs &, bool, int, size_t, cudaStream_t);
+template cudaError_t launch_batch<double>(const BatchArgs &, bool, int, size_t, cudaStream_t);
 
 }  // namespace vqe

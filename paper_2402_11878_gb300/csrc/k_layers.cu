@@ -158,6 +158,39 @@ __device__ __forceinline__ void write_zero_tile(C *P, uint64_t base, uint32_t lo
         P[base | (e & lowmask) | ((uint64_t)(e >> m) << a)] = z;
 }
 
+// The first forward pass when it holds one slot: its only nonzero tile (base
+// 0) starts as |0...0>, so the slot's scaled butterflies give each element
+// the product of one factor per tile bit (|0> -> (1, v) in tan form, (v, 1)
+// in cot form; an ungated bit stays 0), and the slot's diagonal (table entry
+// and CZ sign) follows.  Written straight to global memory, no tile rounds.
+template <typename T>
+__device__ __forceinline__ void write_product_tile(const PassDesc &d, const RotCoef<T> *cf,
+                                                   const typename V2<T>::type *dt,
+                                                   typename V2<T>::type *P, uint64_t base,
+                                                   uint32_t lowmask, int m, int a, int k) {
+    using C = typename V2<T>::type;
+    const uint32_t gated = d.slot_gated[0], cz = d.slot_czmask[0];
+    const C *tab = dt + d.slot_dtab_off[0];
+    for (uint32_t e = threadIdx.x; e < (1u << k); e += blockDim.x) {
+        const uint64_t g = base | (e & lowmask) | ((uint64_t)(e >> m) << a);
+        T f = T(1);
+        for (int j = 0; j < k; ++j) {
+            const uint32_t bit = (e >> j) & 1u;
+            if (!((gated >> j) & 1u)) {
+                if (bit) f = T(0);
+                continue;
+            }
+            const RotCoef<T> rc = cf[j];
+            if (bit ^ (uint32_t)rc.mode) f *= rc.v;
+        }
+        C y = tab[e];
+        const uint32_t s = __popc((uint32_t)g & ((uint32_t)g >> 1) & cz) & 1u;
+        y.x = flip_sign(y.x * f, s);
+        y.y = flip_sign(y.y * f, s);
+        P[g] = y;
+    }
+}
+
 // One CTA per (tile, state): global -> shared (plain order), the pass
 // program, shared -> global.
 // Forward passes hold one buffer per thread: two blocks of 512 threads fit an
@@ -192,6 +225,10 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
     const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (k - m)));
     if (!BWD && (base & d.zmask)) {   // block-uniform
         write_zero_tile(P, base, lowmask, m, a, k);
+        return;
+    }
+    if (!BWD && init_zero && d.n_slots == 1) {   // the tile at base 0
+        write_product_tile<T>(d, scf, dtab + (size_t)b * dtab_stride, P, base, lowmask, m, a, k);
         return;
     }
     GridEnv<T> env{&sd, scf, dtab + (size_t)b * dtab_stride,
@@ -239,6 +276,11 @@ k_pass_fixed(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::t
     const uint32_t lowmask = (1u << m) - 1u;
     if (!BWD && (base & d.zmask)) {   // block-uniform
         write_zero_tile(psi + (size_t)b * stride, base, lowmask, m, a, k);
+        return;
+    }
+    if (!BWD && init_zero && d.n_slots == 1) {   // the tile at base 0
+        write_product_tile<T>(d, scf, dtab + (size_t)b * dtab_stride, psi + (size_t)b * stride, base,
+                              lowmask, m, a, k);
         return;
     }
     GridEnv<T> env{&sd, scf, dtab + (size_t)b * dtab_stride,

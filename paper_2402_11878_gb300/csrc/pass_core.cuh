@@ -95,6 +95,21 @@ __host__ __device__ constexpr uint32_t reg_bit_table(int j) {
          : j == 3 ? 0xFF00FF00u : 0xFFFF0000u;
 }
 
+// a * x + y on both components of a complex value: FP32 issues one packed
+// f32x2 FMA (sm_100 and later), FP64 two DFMA.
+__device__ __forceinline__ float2 caxpy(float a, float2 x, float2 y) {
+    return __ffma2_rn(make_float2(a, a), x, y);
+}
+__device__ __forceinline__ double2 caxpy(double a, double2 x, double2 y) {
+    return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
+}
+template <typename C>
+__device__ __forceinline__ C cneg(C x) {
+    x.x = -x.x;
+    x.y = -x.y;
+    return x;
+}
+
 template <typename C>
 __device__ __forceinline__ C cmul(C x, C d) {
     C r;
@@ -342,9 +357,9 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                             if (!BWD) {   // [[1,-t],[t,1]]
                                 u[r].x = fma(-cv, y.x, x.x);  u[r].y = fma(-cv, y.y, x.y);
                                 u[r1].x = fma(cv, x.x, y.x);  u[r1].y = fma(cv, x.y, y.y);
-                            } else {      // transpose: [[1,t],[-t,1]]
-                                u[r].x = fma(cv, y.x, x.x);    u[r].y = fma(cv, y.y, x.y);
-                                u[r1].x = fma(-cv, x.x, y.x);  u[r1].y = fma(-cv, x.y, y.y);
+                            } else {      // transpose: [[1,t],[-t,1]], packed f32x2
+                                u[r] = caxpy(cv, y, x);
+                                u[r1] = caxpy(cv, cneg(x), y);
                             }
                         }
                     }
@@ -361,8 +376,8 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                                 u[r].x = fma(cv, x.x, -y.x);  u[r].y = fma(cv, x.y, -y.y);
                                 u[r1].x = fma(cv, y.x, x.x);  u[r1].y = fma(cv, y.y, x.y);
                             } else {      // transpose: [[u,1],[-1,u]]
-                                u[r].x = fma(cv, x.x, y.x);    u[r].y = fma(cv, x.y, y.y);
-                                u[r1].x = fma(cv, y.x, -x.x);  u[r1].y = fma(cv, y.y, -x.y);
+                                u[r] = caxpy(cv, x, y);
+                                u[r1] = caxpy(cv, y, cneg(x));
                             }
                         }
                     }
@@ -628,15 +643,27 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                 if constexpr (BWD) {
                     // dE/dtheta = Im<l|Y|p>; per pair Re(conj(l1) p0) - Re(conj(l0) p1)
                     T gt = T(0);
+                    if constexpr (sizeof(T) == 4) {
+                        // packed: both components in one f32x2 accumulator
+                        float2 g2 = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        if (r & (1 << j)) continue;
-                        const C p0 = v[r], p1 = v[r | (1 << j)];
-                        const C l0 = w[r], l1 = w[r | (1 << j)];
-                        gt = fma(l1.x, p0.x, gt);
-                        gt = fma(l1.y, p0.y, gt);
-                        gt = fma(-l0.x, p1.x, gt);
-                        gt = fma(-l0.y, p1.y, gt);
+                        for (int r = 0; r < NR; ++r) {
+                            if (r & (1 << j)) continue;
+                            g2 = __ffma2_rn(w[r | (1 << j)], v[r], g2);
+                            g2 = __ffma2_rn(cneg(w[r]), v[r | (1 << j)], g2);
+                        }
+                        gt = g2.x + g2.y;
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            if (r & (1 << j)) continue;
+                            const C p0 = v[r], p1 = v[r | (1 << j)];
+                            const C l0 = w[r], l1 = w[r | (1 << j)];
+                            gt = fma(l1.x, p0.x, gt);
+                            gt = fma(l1.y, p0.y, gt);
+                            gt = fma(-l0.x, p1.x, gt);
+                            gt = fma(-l0.y, p1.y, gt);
+                        }
                     }
                     if constexpr (sizeof(T) == 4) {
                         // FP32: one shared-memory row per (bit, component), summed at the flush
@@ -680,9 +707,9 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                             if (!BWD) {   // [[1,-t],[t,1]]
                                 u[r].x = fma(-cv, y.x, x.x);  u[r].y = fma(-cv, y.y, x.y);
                                 u[r1].x = fma(cv, x.x, y.x);  u[r1].y = fma(cv, x.y, y.y);
-                            } else {      // transpose: [[1,t],[-t,1]]
-                                u[r].x = fma(cv, y.x, x.x);    u[r].y = fma(cv, y.y, x.y);
-                                u[r1].x = fma(-cv, x.x, y.x);  u[r1].y = fma(-cv, x.y, y.y);
+                            } else {      // transpose: [[1,t],[-t,1]], packed f32x2
+                                u[r] = caxpy(cv, y, x);
+                                u[r1] = caxpy(cv, cneg(x), y);
                             }
                         }
                     } else {
@@ -695,8 +722,8 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                                 u[r].x = fma(cv, x.x, -y.x);  u[r].y = fma(cv, x.y, -y.y);
                                 u[r1].x = fma(cv, y.x, x.x);  u[r1].y = fma(cv, y.y, x.y);
                             } else {      // transpose: [[u,1],[-1,u]]
-                                u[r].x = fma(cv, x.x, y.x);    u[r].y = fma(cv, x.y, y.y);
-                                u[r1].x = fma(cv, y.x, -x.x);  u[r1].y = fma(cv, y.y, -x.y);
+                                u[r] = caxpy(cv, x, y);
+                                u[r1] = caxpy(cv, y, cneg(x));
                             }
                         }
                     }

@@ -1868,6 +1868,7 @@ struct vqe_batch_ctx {
     DevBuf hb_p, hb_e, hb_g;   // device copies for vqe_batch_run (host buffers)
     BatchLayout layout{};
     int grid = 0;
+    int count_r4 = 0;                  // instances of the R = 4 kernel (first in d_order)
     size_t scratch_elems = 0;
     std::vector<BatchInst> inst;
     // captured graph for the last pointer triple
@@ -1943,6 +1944,7 @@ vqe_status batch_build(vqe_batch_ctx *b) {
     std::vector<PassDesc> fwd, bwd;
     std::vector<StageSlot> stage;
     std::vector<std::pair<int, int>> keys;   // (n, depth) -> plan index
+    std::vector<char> plan_r4;               // plan runs in the R = 4 kernel
     b->inst.assign(b->count, BatchInst{});
     size_t max_tile = 0, max_coef = 0, max_lo = 0, max_hi = 0, max_np = 0, max_stage = 0;
     int max_multi_n = 0;
@@ -1971,6 +1973,10 @@ vqe_status batch_build(vqe_batch_ctx *b) {
             int slot = 0;
             int kk = 0;
             P.whole_tile = 1;
+            for (int p = 1; p < P.n_passes; ++p)
+                if (hp.fwd[p].R != hp.fwd[0].R)
+                    return bfail(b, VQE_ERR_ARG, "batch plan: register bits differ between passes");
+            plan_r4.push_back(hp.fwd[0].R == 4 ? 1 : 0);
             for (int p = 0; p < P.n_passes; ++p) {
                 P.slot_first[p] = slot;
                 slot += hp.fwd[p].n_slots;
@@ -2027,14 +2033,18 @@ vqe_status batch_build(vqe_batch_ctx *b) {
     if ((st = bupload(b, b->d_fwd, fwd, "batch passes")) != VQE_OK) return st;
     if ((st = bupload(b, b->d_bwd, bwd, "batch passes")) != VQE_OK) return st;
     if ((st = bupload(b, b->d_stage, stage, "batch stage")) != VQE_OK) return st;
-    // largest first
+    // the R = 4 kernel's instances, then the others; largest first in each
     std::vector<int> order(b->count);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+        const int rp = plan_r4[b->inst[p].plan], rq = plan_r4[b->inst[q].plan];
+        if (rp != rq) return rp > rq;
         const double cp = double(size_t(1) << b->n[p]) * b->depth[p];
         const double cq = double(size_t(1) << b->n[q]) * b->depth[q];
         return cp > cq;
     });
+    b->count_r4 = 0;
+    for (int i = 0; i < b->count; ++i) b->count_r4 += plan_r4[b->inst[i].plan];
     if ((st = bupload(b, b->d_order, order, "batch order")) != VQE_OK) return st;
     int sms = 0;
     VQE_BCUDA(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
@@ -2091,7 +2101,7 @@ vqe_status batch_upload_hams(vqe_batch_ctx *b) {
 
 vqe_status batch_launch(vqe_batch_ctx *b, const double *params, double *energies, double *grads,
                         cudaStream_t s) {
-    VQE_BCUDA(b, cudaMemsetAsync(b->d_counter.p, 0, sizeof(int), s));
+    VQE_BCUDA(b, cudaMemsetAsync(b->d_counter.p, 0, 2 * sizeof(int), s));
     BatchArgs a{};
     a.inst = static_cast<const BatchInst *>(b->d_inst.p);
     a.order = static_cast<const int *>(b->d_order.p);
@@ -2110,9 +2120,20 @@ vqe_status batch_launch(vqe_batch_ctx *b, const double *params, double *energies
     a.scratch = b->d_scratch.p;
     a.scratch_elems = b->scratch_elems;
     a.layout = b->layout;
-    cudaError_t e = b->prec == VQE_C128 ? launch_batch<double>(a, b->grid, b->layout.total, s)
-                                        : launch_batch<float>(a, b->grid, b->layout.total, s);
-    if (e != cudaSuccess) return bfail(b, VQE_ERR_CUDA, std::string("k_batch: ") + cudaGetErrorString(e));
+    // two persistent launches: the R = 4 instances, then the rest
+    for (int half = 0; half < 2; ++half) {
+        const int first = half ? b->count_r4 : 0;
+        const int cnt = half ? b->count - b->count_r4 : b->count_r4;
+        if (cnt == 0) continue;
+        BatchArgs h = a;
+        h.order = a.order + first;
+        h.count = cnt;
+        h.counter = a.counter + half;
+        const int grid = std::max(1, std::min(b->grid, cnt));
+        cudaError_t e = b->prec == VQE_C128 ? launch_batch<double>(h, half == 0, grid, b->layout.total, s)
+                                            : launch_batch<float>(h, half == 0, grid, b->layout.total, s);
+        if (e != cudaSuccess) return bfail(b, VQE_ERR_CUDA, std::string("k_batch: ") + cudaGetErrorString(e));
+    }
     return VQE_OK;
 }
 

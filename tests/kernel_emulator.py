@@ -215,6 +215,27 @@ class Emu:
                 raise AssertionError(f"unknown op kind {op.kind}")
         assert not written, "gradient partials left unflushed"
         g = gaddr(elem_of(t, r, chunk, R))
+        if not backward and init_zero and d.n_slots == 1:
+            # the kernels write the first pass's tile at base 0 as a product:
+            # one factor per tile bit (tan form (1, v), cot form (v, 1), an
+            # ungated bit (1, 0)), then the slot's table entry and CZ sign
+            e = elem_of(t, r, chunk, R)
+            f = np.ones(np.broadcast_shapes(e.shape, (1, threads, NR)))
+            for j in range(k):
+                bit = (e >> j) & 1
+                if not (d.slot_gated[0] >> j) & 1:
+                    f = np.where(bit == 1, 0.0, f)
+                    continue
+                idx = d.slot_coef_off[0] + j
+                c, mode = cv[idx], cm[idx]
+                f = f * np.where((bit ^ mode) == 1, c, 1.0)
+            off = d.slot_dtab_off[0]
+            tab = dt[off + np.broadcast_to(e, g.shape)]
+            sgn = np.where(popc(g & (g >> 1) & d.slot_czmask[0]) & 1, -1.0, 1.0)
+            prod = tab * f * sgn
+            z0 = base[:, 0, 0] == 0
+            assert np.abs(prod[z0] - v[z0]).max() <= 1e-13 * max(1.0, np.abs(v).max())
+            v = np.where(z0[:, None, None], prod, v)
         # forward from |0...0>: tiles whose base has a bit of zmask are
         # written as zeros without being transformed; they must be zero
         zt = (base[:, 0, 0] & int(d.zmask)) != 0

@@ -38,6 +38,28 @@ WORKLOAD = ("20q FP64 (complex128) 10-site periodic 1D Hubbard t=1 U in {2,4,8},
             "HEA depth 10, 1000 param vectors per U, energy only")
 
 
+def executed_forward_flops(n: int, depth: int, prec: str) -> int:
+    """FP64 (or FP32) flops the forward passes of one state execute, from the
+    library's own plan: per live tile and slot, 4 per gated bit and amplitude
+    (scaled rotation, 2 FMA per real pair) plus 6 (one complex multiply by the
+    slot's RZ/CZ diagonal).  Tiles a pass skips as known zeros, and the first
+    pass when it writes its one live tile as a product, execute none."""
+    from paper_2402_11878_gb300 import plans
+    pl = plans.plan(n, depth, prec)
+    total = 0
+    for i, d in enumerate(pl["fwd"]):
+        if i == 0 and d.n_slots == 1:
+            continue
+        mid = d.a - d.m
+        live = 0
+        for tile in range(1 << (n - d.k)):
+            base = ((tile & ((1 << mid) - 1)) << d.m) | ((tile >> mid) << (d.a + d.k - d.m))
+            live += (base & d.zmask) == 0
+        per_tile = sum(4 * bin(d.slot_gated[s]).count("1") + 6 for s in range(d.n_slots)) << d.k
+        total += live * per_tile
+    return total
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -259,13 +281,13 @@ def run_gpu(args, world, rank, local, pg):
     evals = len(U_VALUES) * N_VEC * args.steps * world
     value = job_throughput(len(U_VALUES) * N_VEC * args.steps, world, ms)
 
-    # dominant kernel: the fused forward pass; FP64 FLOP model per amplitude
-    # and layer = 4 per gated qubit (scaled rotation, 2 FMA per real pair)
-    # + 6 (one complex multiply by the RZ/CZ diagonal).
+    # dominant kernel: the fused forward pass; FP64 flops it executes per
+    # state, from the plan (4 per gated bit and amplitude, 6 per slot's
+    # diagonal, skipped zero tiles excluded)
     fwd_ms = sum(p["forward_passes"]["ms"] for p in prof)
     fwd_launches = sum(p["forward_passes"]["launches"] for p in prof)
     en_ms = sum(p["energy"]["ms"] for p in prof)
-    flops_fwd = len(U_VALUES) * N_VEC * args.steps * DEPTH * (4 * N_QUBITS + 6) * (1 << N_QUBITS)
+    flops_fwd = len(U_VALUES) * N_VEC * args.steps * executed_forward_flops(N_QUBITS, DEPTH, "c128")
     achieved_tflops = flops_fwd / (fwd_ms / 1e3) / 1e12
     n_pass = engines[0].stats()["ansatz_passes"]
     bytes_fwd = len(U_VALUES) * N_VEC * args.steps * n_pass * 2 * 16 * (1 << N_QUBITS)
@@ -519,6 +541,7 @@ def run_case(name: str, batch: int):
         "fwd20c128": (20, 10, "c128", False), "grad20c128": (20, 10, "c128", True),
         "fwd24c64": (24, 4, "c64", False), "grad24c64": (24, 4, "c64", True),
         "fwd26c64": (26, 4, "c64", False),
+        "mol24c64": (24, 2, "c64", True),   # synthetic molecular Hamiltonian, 12 orbitals
     }
     if name == "batch512":
         inst = vi.batched_instances(512, seed=7)
@@ -535,7 +558,8 @@ def run_case(name: str, batch: int):
         print("energies", E[:4].tolist())
         return
     n, D, prec, grad = cases[name]
-    H = vi.hubbard_1d(n // 2, 1.0, 4.0, periodic=True)
+    H = vi.synthetic_molecular(n // 2, 2024) if name.startswith("mol") else \
+        vi.hubbard_1d(n // 2, 1.0, 4.0, periodic=True)
     eng = pkg.Engine(n, D, prec)
     eng.set_hamiltonian(H.x, H.z, H.c)
     P = torch.tensor(np.stack([vi.ansatz_params(j, n, D) for j in range(batch)]), device="cuda")

@@ -54,14 +54,12 @@ int vqe_inspect_hamiltonian(int n_qubits, const uint64_t *x_masks, const uint64_
  * and the groups swept over the whole state instead (max_wide).  diag_terms:
  * 1 = keep the diagonal group's terms in the low window, 0 = leave them out
  * (the library does so when it precomputes the diagonal of H).
- * elem_layout: 0 = the expectation's windows (a group's terms ordered by
- * their pattern over a thread's pairs), 1 = the apply-H windows (over a
- * thread's elements).
+ * The windowed apply-H of the adjoint uses the same windows.
  * counts[5] = windows, window groups, window terms, offsets, wide groups.
  * Returns 0, or -1 on invalid input or too-small buffers. */
 int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
                         const uint64_t *z_masks, const double *coeffs, size_t n_terms,
-                        double threshold, int diag_terms, int elem_layout, void *windows,
+                        double threshold, int diag_terms, void *windows,
                         int max_windows,
                         void *wgroups, int max_wgroups, void *wterms, int max_wterms,
                         uint32_t *hoff, int max_hoff, void *wide, int max_wide, int counts[5]);

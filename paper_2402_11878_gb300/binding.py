@@ -109,7 +109,7 @@ def load() -> ctypes.CDLL:
         "vqe_set_pass_kernel": [vp, i],
         "vqe_inspect_hamiltonian": [i, vp, vp, vp, sz, ctypes.c_double, vp, i, vp, vp, i, vp,
                                     vp, vp],
-        "vqe_inspect_windows": [i, i, vp, vp, vp, sz, ctypes.c_double, i, i, vp, i, vp, i, vp,
+        "vqe_inspect_windows": [i, i, vp, vp, vp, sz, ctypes.c_double, i, vp, i, vp, i, vp,
                                 i, vp, i, vp, i, vp],
     }
     for name, args in sig.items():

@@ -489,8 +489,17 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
     }
     __syncthreads();
     const uint32_t lowmask = (1u << m) - 1u;
-    for (uint32_t e = tid; e < size; e += blockDim.x)
-        sp[e] = P[(size_t)(base | (e & lowmask) | soff[e >> m])];
+    {
+        // all of a thread's loads in flight at once, then the stores
+        C x[EPT];
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) {
+            const uint32_t e = tid + j * kEnergyWinThreads;
+            x[j] = P[(size_t)(base | (e & lowmask) | soff[e >> m])];
+        }
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) sp[tid + j * kEnergyWinThreads] = x[j];
+    }
     __syncthreads();
     double acc = 0.0, nrm = 0.0;
     if (W.with_norm) {
@@ -651,13 +660,16 @@ size_t win_smem_bytes(const WinDesc &W, size_t elem_bytes) {
            (size_t(1) << (W.k - W.m)) * 4;
 }
 
-// Windowed apply-H (the adjoint's lambda = H psi, same windows as above but
-// with each group's terms ordered by their pattern over a thread's elements).
-// lambda is accumulated window by window in a fixed order: the first window
-// writes it, the others add to it; the last window also yields the block
-// partials of Re<psi|lambda> and <psi|psi>.  For an element e of the tile,
-//     lambda_e += psi_{e ^ xl} (FA(e) - i FB(e)),
-//     F(e) = sum_t c_t (-1)^{popc(g(e) & z_t)}   (base sign folded into c').
+// Windowed apply-H (the adjoint's lambda = H psi) over the expectation's
+// windows and pair groups.  A tile of lambda is held in shared memory beside
+// the tile of psi; the first window starts it from zero, the others from the
+// lambda written by the previous window (a fixed order); the last window also
+// yields the block partials of Re<psi|lambda> and <psi|psi>.  For a pair
+// (i0, i1 = i0 ^ xl) of a group with sign sums FA, FB at i0 (the terms' signs
+// at i1 are those at i0 times (-1)^{popc(x & z)}: +1 on class A, -1 on B),
+//     lambda_i0 += psi_i1 (FA - i FB),   lambda_i1 += psi_i0 (FA + i FB).
+// One thread owns a pair; a group's pairs are disjoint, so a barrier between
+// groups orders the read-modify-writes of shared lambda.
 template <typename T, int K, bool RUNS>
 __global__ void __launch_bounds__(kEnergyWinThreads, 1)
 k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__restrict__ wterms,
@@ -665,12 +677,14 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
               const typename EV2<T>::type *__restrict__ psi, typename EV2<T>::type *__restrict__ lam,
               size_t stride, int first, int last, double *__restrict__ partials) {
     using C = typename EV2<T>::type;
-    static_assert(kEnergyWinThreads == 512, "element layout assumes 512 threads");
+    static_assert(kEnergyWinThreads == 512, "pair layout assumes 512 threads");
     constexpr uint32_t size = 1u << K;
     constexpr int EPT = size / kEnergyWinThreads;
+    constexpr int PPT = EPT / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *sp = reinterpret_cast<C *>(smem_raw);
-    T *sc = reinterpret_cast<T *>(sp + size);
+    C *sp = reinterpret_cast<C *>(smem_raw);                      // [size] psi tile
+    C *sl = sp + size;                                            // [size] lambda tile
+    T *sc = reinterpret_cast<T *>(sl + size);
     uint32_t *szt = reinterpret_cast<uint32_t *>(sc + W.t_count);
     uint32_t *soff = szt + W.t_count;
     __shared__ double sh[2 * (kEnergyWinThreads / 32)];
@@ -705,23 +719,35 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
     }
     __syncthreads();
     const uint32_t lowmask = (1u << m) - 1u;
-    for (uint32_t e = tid; e < size; e += blockDim.x)
-        sp[e] = P[(size_t)(base | (e & lowmask) | soff[e >> m])];
-    __syncthreads();
     auto gidx = [&](uint32_t e) -> size_t { return (size_t)(base | (e & lowmask) | soff[e >> m]); };
-    T lr[EPT], li[EPT];
+    {
+        // all of a thread's loads in flight at once, then the stores
+        C x[EPT], l[EPT];
 #pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-        if (first) {
-            lr[j] = T(0);
-            li[j] = T(0);
-        } else {
-            const C l = L[gidx(tid + j * kEnergyWinThreads)];
-            lr[j] = l.x;
-            li[j] = l.y;
+        for (int j = 0; j < EPT; ++j) {
+            const size_t g = gidx(tid + j * kEnergyWinThreads);
+            x[j] = P[g];
+            l[j] = first ? C{} : L[g];
+        }
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) {
+            sp[tid + j * kEnergyWinThreads] = x[j];
+            sl[tid + j * kEnergyWinThreads] = l[j];
         }
     }
-    for (int gi = 0; gi < W.g_end - W.g_begin; ++gi) {
+    __syncthreads();
+    // lambda_i0 += x1 (fa - i fb), lambda_i1 += x0 (fa + i fb)
+    auto pair_update = [&](uint32_t i0, uint32_t i1, C x0, C x1, T fa, T fb) {
+        C l0 = sl[i0], l1 = sl[i1];
+        l0.x = fma(x1.x, fa, fma(x1.y, fb, l0.x));
+        l0.y = fma(x1.y, fa, fma(-x1.x, fb, l0.y));
+        l1.x = fma(x0.x, fa, fma(-x0.y, fb, l1.x));
+        l1.y = fma(x0.y, fa, fma(x0.x, fb, l1.y));
+        sl[i0] = l0;
+        sl[i1] = l1;
+    };
+    const int ng = W.g_end - W.g_begin;
+    for (int gi = 0; gi < ng; ++gi) {
         const WinGroup &G = sg[gi];
         const uint32_t xl = G.xl;
         const bool has_b = G.b_end > G.b_begin;
@@ -736,59 +762,67 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
             }
 #pragma unroll
             for (int j = 0; j < EPT; ++j) {
-                const C y = sp[tid + j * kEnergyWinThreads];
-                lr[j] = fma(y.x, F[j], lr[j]);
-                li[j] = fma(y.y, F[j], li[j]);
-            }
-        } else if (!RUNS || G.direct) {
-            T ca[kWinDirectMax], cb[kWinDirectMax];
-            uint32_t za[kWinDirectMax], zb[kWinDirectMax];
-            const int na = G.b_begin - G.a_begin, nb = G.b_end - G.b_begin;
-#pragma unroll
-            for (int u = 0; u < kWinDirectMax; ++u) {
-                ca[u] = u < na ? sc[G.a_begin + u] : T(0);
-                za[u] = u < na ? szt[G.a_begin + u] : 0u;
-                cb[u] = u < nb ? sc[G.b_begin + u] : T(0);
-                zb[u] = u < nb ? szt[G.b_begin + u] : 0u;
-            }
-#pragma unroll
-            for (int j = 0; j < EPT; ++j) {
                 const uint32_t e = tid + j * kEnergyWinThreads;
-                const C y = sp[e ^ xl];
-                T fa = T(0), fb = T(0);
+                const C y = sp[e];
+                C l = sl[e];
+                l.x = fma(y.x, F[j], l.x);
+                l.y = fma(y.y, F[j], l.y);
+                sl[e] = l;
+            }
+        } else {
+            // pairs as in the expectation: pair P = tid + 512 s of pattern
+            // u = P >> plog has i0 = spread(P mod 2^plog) | fval[u]
+            const int plog = G.plog;
+            const uint32_t t0 = tid & (plog >= 9 ? 511u : ((1u << plog) - 1u));
+            const uint32_t e0 = (t0 & G.smask[0]) | ((t0 & G.smask[1]) << 1) | ((t0 & G.smask[2]) << 2) |
+                                ((t0 & G.smask[3]) << 3) | ((t0 & G.smask[4]) << 4);
+            uint32_t D[PPT];
 #pragma unroll
-                for (int u = 0; u < kWinDirectMax; ++u)
-                    if (u < na) fa += sgn_flip(ca[u], __popc(e & za[u]) & 1u);
-                if (has_b) {
+            for (int j = 0; j < PPT; ++j) {
+                uint32_t d = 0;
 #pragma unroll
-                    for (int u = 0; u < kWinDirectMax; ++u)
-                        if (u < nb) fb += sgn_flip(cb[u], __popc(e & zb[u]) & 1u);
+                for (int bb = 0; (1 << bb) < PPT; ++bb)
+                    if ((j >> bb) & 1) d |= G.dj[bb];
+                D[j] = d;
+            }
+            if (!RUNS || G.direct) {
+                const uint32_t npat = (uint32_t)G.npat;
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    const uint32_t u = (tid + ((uint32_t)j << 9)) >> plog;   // warp-uniform
+                    if (u >= npat) break;
+                    const uint32_t il = e0 | D[j] | G.fval[u];
+                    T fa = T(0), fb = T(0);
+                    const int a1 = G.a_begin + G.arun[u + 1];
+                    for (int t = G.a_begin + G.arun[u]; t < a1; ++t)
+                        fa += sgn_flip(sc[t], __popc(il & szt[t]) & 1u);
+                    if (has_b) {
+                        const int b1 = G.b_begin + G.brun[u + 1];
+                        for (int t = G.b_begin + G.brun[u]; t < b1; ++t)
+                            fb += sgn_flip(sc[t], __popc(il & szt[t]) & 1u);
+                    }
+                    pair_update(il, il ^ xl, sp[il], sp[il ^ xl], fa, fb);
                 }
-                // (y.x + i y.y)(fa - i fb)
-                lr[j] = fma(y.x, fa, fma(y.y, fb, lr[j]));
-                li[j] = fma(y.y, fa, fma(-y.x, fb, li[j]));
-            }
-        } else if constexpr (RUNS) {
-            T F[EPT];
-            run_sums<EPT>(F, G.arun, G.a_begin, sc, szt, tid);
-            wht_inplace<EPT>(F);
+            } else if constexpr (RUNS) {
+                // a whole group (one pattern, plog = K - 1: every slot valid)
+                T FA[PPT], FB[PPT];
+                run_sums<PPT>(FA, G.arun, G.a_begin, sc, szt, e0);
+                wht_inplace<PPT>(FA);
+                if (has_b) {
+                    run_sums<PPT>(FB, G.brun, G.b_begin, sc, szt, e0);
+                    wht_inplace<PPT>(FB);
+                } else {
 #pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                const C y = sp[(tid + j * kEnergyWinThreads) ^ xl];
-                lr[j] = fma(y.x, F[j], lr[j]);
-                li[j] = fma(y.y, F[j], li[j]);
-            }
-            if (has_b) {
-                run_sums<EPT>(F, G.brun, G.b_begin, sc, szt, tid);
-                wht_inplace<EPT>(F);
+                    for (int j = 0; j < PPT; ++j) FB[j] = T(0);
+                }
 #pragma unroll
-                for (int j = 0; j < EPT; ++j) {
-                    const C y = sp[(tid + j * kEnergyWinThreads) ^ xl];
-                    lr[j] = fma(y.y, F[j], lr[j]);
-                    li[j] = fma(-y.x, F[j], li[j]);
+                for (int j = 0; j < PPT; ++j) {
+                    const uint32_t il = e0 | D[j];
+                    pair_update(il, il ^ xl, sp[il], sp[il ^ xl], FA[j], FB[j]);
                 }
             }
         }
+        __syncthreads();   // the next group's pairs touch other threads' elements
     }
     double acc = 0.0, nrm = 0.0;
     {
@@ -796,13 +830,11 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
             const uint32_t e = tid + j * kEnergyWinThreads;
-            C out;
-            out.x = lr[j];
-            out.y = li[j];
-            L[gidx(e)] = out;
+            const C l = sl[e];
+            L[gidx(e)] = l;
             if (last) {
                 const C x = sp[e];
-                pa = fma(x.x, lr[j], fma(x.y, li[j], pa));
+                pa = fma(x.x, l.x, fma(x.y, l.y, pa));
                 pn = fma(x.x, x.x, fma(x.y, x.y, pn));
             }
         }
@@ -826,7 +858,7 @@ cudaError_t launch_apply_h_win(const WinDesc &W, const WinGroup *wgroups, const 
                                const void *psi, void *lam, size_t state_stride, int first,
                                int last, double *partials, cudaStream_t s) {
     using C = typename EV2<T>::type;
-    const size_t smem = win_smem_bytes(W, sizeof(C));
+    const size_t smem = win_smem_bytes(W, sizeof(C)) + (size_t(1) << W.k) * sizeof(C);   // + lambda tile
     auto kern = W.any_runs
         ? (W.k == 13 ? k_apply_h_win<T, 13, true> : (W.k == 12 ? k_apply_h_win<T, 12, true> : nullptr))
         : (W.k == 13 ? k_apply_h_win<T, 13, false> : (W.k == 12 ? k_apply_h_win<T, 12, false> : nullptr));

@@ -70,8 +70,7 @@ struct vqe_ctx {
     int n_wide = 0;
     // windows of the windowed apply-H (terms ordered per element pattern);
     // empty when some group fits no window (then apply-H sweeps globally)
-    std::vector<WinDesc> awins;
-    DevBuf d_awgroups, d_awterms, d_awhoff;
+    bool apply_windows = false;   // lambda = H psi over the windows above
     int win_tiles = 0;   // columns of all windows per state
     // diagonal of H (one T per basis state), built when it fits in a quarter
     // of the free device memory; null: the x = 0 terms are evaluated inline
@@ -760,17 +759,14 @@ std::vector<VGroup> split_group(const GroupDesc &G, const HamPlan &hp) {
 }
 
 // Windows of the windowed expectation (Sec. II-B Eq. 7 evaluated per X-mask
-// group): the low tile (with <psi|psi> and the diagonal group), then windows
+// group) and of the windowed apply-H, which walks the same pairs: the low
+// tile (with <psi|psi> and the diagonal group), then windows
 // of mrun low bits plus kE - mrun further bits chosen greedily so that every
 // group's X mask lies inside one window (a greedy cover of the groups' high
 // bits), each window holding at most kWinMaxTerms terms.  Groups with more
 // high bits than a window has go to the global sweep.  `diag_terms`: store
 // the diagonal group's terms (false when the diagonal of H is precomputed).
-// elem_layout: order each group's terms by their pattern over a thread's
-// elements (the windowed apply-H, which signs at the output element) instead
-// of over its pairs (the windowed expectation).
-void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms, WinPlan &wp,
-                  bool elem_layout = false) {
+void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms, WinPlan &wp) {
     wp = WinPlan{};
     const bool c128 = prec == VQE_C128;
     const int kE = win_tile_bits(c128);
@@ -807,24 +803,23 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
     const int split_max = c128 ? 3 : 2;
     std::vector<std::vector<VGroup>> vgs(hp.groups.size());
     std::vector<char> is_split(hp.groups.size(), 0), vanishes(hp.groups.size(), 0);
-    if (!elem_layout)
-        for (size_t g = 0; g < hp.groups.size(); ++g) {
-            const GroupDesc &G = hp.groups[g];
-            if (G.x == 0u) continue;
-            std::vector<VGroup> v = split_group(G, hp);
-            if (v.empty()) {
-                vanishes[g] = 1;
-                continue;
-            }
-            bool ok = v[0].fix_mask != (1u << (31 - __builtin_clz(G.x)));
-            for (const VGroup &vg : v)
-                ok = ok && int(vg.a.size()) <= kWinDirectMax && int(vg.b.size()) <= kWinDirectMax &&
-                     int(vg.a.size() + vg.b.size()) <= split_max;
-            if (ok) {
-                vgs[g] = std::move(v);
-                is_split[g] = 1;
-            }
+    for (size_t g = 0; g < hp.groups.size(); ++g) {
+        const GroupDesc &G = hp.groups[g];
+        if (G.x == 0u) continue;
+        std::vector<VGroup> v = split_group(G, hp);
+        if (v.empty()) {
+            vanishes[g] = 1;
+            continue;
         }
+        bool ok = v[0].fix_mask != (1u << (31 - __builtin_clz(G.x)));
+        for (const VGroup &vg : v)
+            ok = ok && int(vg.a.size()) <= kWinDirectMax && int(vg.b.size()) <= kWinDirectMax &&
+                 int(vg.a.size() + vg.b.size()) <= split_max;
+        if (ok) {
+            vgs[g] = std::move(v);
+            is_split[g] = 1;
+        }
+    }
     auto group_terms = [&](int g) {
         const GroupDesc &G = hp.groups[g];
         if (G.x == 0u && !diag_terms) return 0;
@@ -952,19 +947,20 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
             WinGroup wg{};
             wg.xl = win_gather(G.x, c.m, pos);
             wg.hl = wg.xl ? 31 - __builtin_clz(wg.xl) : 0;
-            const int NV = (wg.xl && !elem_layout) ? PPT : EPT;
+            const int NV = wg.xl ? PPT : EPT;
             // few terms: per-pair sign sums beat the transform over the
             // register patterns and its per-run loop (FP64: up to 3 terms,
             // FP32: up to 2)
             const int n_t = (G.x != 0u || diag_terms) ? G.t_end - G.t_begin : 0;
             wg.direct = (wg.xl != 0u && n_t <= std::min(kWinDirectMax, c128 ? 3 : 2)) ? 1 : 0;
             // tile bit of register-pattern bit b: element bit lt + b of a
-            // thread's elements, or of its pairs after the zero inserted at hl
+            // thread's elements (diagonal group), or of its pairs after the
+            // zero inserted at hl
             auto pattern = [&](uint32_t zt) {
                 uint32_t v = 0;
                 for (int bb = 0; (1 << bb) < NV; ++bb) {
                     int q = lt + bb;
-                    if (wg.xl && !elem_layout && q >= wg.hl) q += 1;
+                    if (wg.xl && q >= wg.hl) q += 1;
                     v |= ((zt >> q) & 1u) << bb;
                 }
                 return v;
@@ -991,17 +987,15 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
                 }
                 for (auto &p : ts) wp.terms.push_back(p.second);
             };
-            if (wg.xl && !elem_layout) {
+            if (wg.xl) {
                 set_fixed(wg, 1u << wg.hl);
                 wg.npat = 1;
             } else {
                 wg.plog = kE;
             }
             const bool keep = G.x != 0u || diag_terms;
-            int bdummy = 0;
             emit(G.t_begin, keep ? G.t_mid : G.t_begin, wg.arun, wg.a_begin);
             emit(G.t_mid, keep ? G.t_end : G.t_mid, wg.brun, wg.b_begin);
-            (void)bdummy;
             wg.b_end = int(wp.terms.size()) - W.t_begin;
             wp.groups.push_back(wg);
         }
@@ -1060,19 +1054,13 @@ vqe_status build_ham_plan(vqe_ctx *h) {
         if ((st = upload(h, h->d_wterms, wp.terms, "window terms")) != VQE_OK) return st;
         if ((st = upload(h, h->d_whoff, wp.hoff, "window offsets")) != VQE_OK) return st;
         if ((st = upload(h, h->d_wide, wp.wide, "wide groups")) != VQE_OK) return st;
-        WinPlan ap;
-        plan_windows(h->n, h->prec, hp, !h->hdiag_ok, ap, true);
-        h->awins.clear();
-        // windowed apply-H re-reads and re-writes lambda once per window; it
-        // pays when the windows hold many groups each (measured: 24 qubits,
-        // 25 Hubbard groups in 3 windows favour the global sweep, the
-        // molecular 5,479 groups in 246 windows the windows)
-        if (ap.wide.empty() && hp.groups.size() >= 10 * ap.wins.size()) {
-            h->awins = ap.wins;
-            if ((st = upload(h, h->d_awgroups, ap.groups, "window groups")) != VQE_OK) return st;
-            if ((st = upload(h, h->d_awterms, ap.terms, "window terms")) != VQE_OK) return st;
-            if ((st = upload(h, h->d_awhoff, ap.hoff, "window offsets")) != VQE_OK) return st;
-        }
+        // windowed apply-H (same windows and groups): psi is read and lambda
+        // read and written once per window, against one gathered read of psi
+        // per group in the global sweep.  It pays when the windows hold many
+        // groups each (measured at 24 qubits: the 25 Hubbard groups in 2
+        // windows favour the global sweep, the molecular 5,479 groups in 246
+        // windows the windows).
+        h->apply_windows = wp.wide.empty() && !wp.wins.empty() && hp.groups.size() >= 10 * wp.wins.size();
     }
     if ((st = upload(h, h->d_groups, hp.groups, "groups")) != VQE_OK) return st;
     if ((st = upload(h, h->d_tz, hp.tz, "terms")) != VQE_OK) return st;
@@ -1268,18 +1256,18 @@ vqe_status gradient_chunk(vqe_ctx *h, const double *params_dev, int B, double *g
     if (st != VQE_OK) return st;
     const vqe_ctx::DevPlan &P = h->plan[1];
     const int mk_h = prof_begin(h, 2);
-    const uint64_t atiles = h->awins.empty() ? 0 : (uint64_t(1) << (h->n - h->awins[0].k));
-    if (!h->awins.empty() && atiles * B >= uint64_t(2 * h->sms)) {
+    const uint64_t atiles = h->apply_windows ? (uint64_t(1) << (h->n - h->wins[0].k)) : 0;
+    if (h->apply_windows && atiles * B >= uint64_t(2 * h->sms)) {
         // windowed: lambda accumulated window by window; the last window's
         // blocks hold the partials of the energy
         const int bps_w = int(atiles);
         vqe_status st2 = ensure(h, h->d_epart, sizeof(double) * 3 * size_t(bps_w) * B + 16, "partials");
         if (st2 != VQE_OK) return st2;
-        const int nw = int(h->awins.size());
+        const int nw = int(h->wins.size());
         for (int w = 0; w < nw; ++w) {
-            VQE_CUDA(h, launch_apply_h_win<T>(h->awins[w], static_cast<const WinGroup *>(h->d_awgroups.p),
-                                              static_cast<const WinTerm *>(h->d_awterms.p),
-                                              static_cast<const uint32_t *>(h->d_awhoff.p),
+            VQE_CUDA(h, launch_apply_h_win<T>(h->wins[w], static_cast<const WinGroup *>(h->d_wgroups.p),
+                                              static_cast<const WinTerm *>(h->d_wterms.p),
+                                              static_cast<const uint32_t *>(h->d_whoff.p),
                                               h->hdiag(), h->n, B, psi, lam, N, w == 0 ? 1 : 0,
                                               w == nw - 1 ? 1 : 0,
                                               static_cast<double *>(h->d_epart.p), s));
@@ -1438,7 +1426,7 @@ vqe_status vqe_destroy(vqe_handle h) {
     h->plan[0].release();
     h->plan[1].release();
     for (DevBuf *b : {&h->d_groups, &h->d_tz, &h->d_tc, &h->d_wgroups, &h->d_wterms, &h->d_whoff,
-                      &h->d_wide, &h->d_awgroups, &h->d_awterms, &h->d_awhoff, &h->d_hdiag,
+                      &h->d_wide, &h->d_hdiag,
                       &h->d_hdiag_z, &h->d_hdiag_c, &h->ws_own, &h->d_params, &h->d_coefs,
                       &h->d_dtab, &h->d_gpart, &h->d_epart, &h->d_out, &h->hb_params,
                       &h->hb_e, &h->hb_n, &h->hb_g, &h->d_err})
@@ -1804,7 +1792,7 @@ int vqe_inspect_hamiltonian(int n_qubits, const uint64_t *x_masks, const uint64_
 
 int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
                         const uint64_t *z_masks, const double *coeffs, size_t n_terms,
-                        double threshold, int diag_terms, int elem_layout, void *windows,
+                        double threshold, int diag_terms, void *windows,
                         int max_windows,
                         void *wgroups, int max_wgroups, void *wterms, int max_wterms,
                         uint32_t *hoff, int max_hoff, void *wide, int max_wide, int counts[5]) {
@@ -1822,7 +1810,7 @@ int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
     HamPlan hp;
     make_ham_plan(cx, cz, cc, keep, hp);
     WinPlan wp;
-    plan_windows(n_qubits, vqe_precision(precision), hp, diag_terms != 0, wp, elem_layout != 0);
+    plan_windows(n_qubits, vqe_precision(precision), hp, diag_terms != 0, wp);
     if (counts) {
         counts[0] = int(wp.wins.size());
         counts[1] = int(wp.groups.size());

@@ -141,8 +141,8 @@ def hamiltonian(n_qubits: int, x, z, c, threshold: float = 0.0) -> dict:
 
 
 def windows(n_qubits: int, precision: str, x, z, c, threshold: float = 0.0,
-            diag_terms: bool = True, elem_layout: bool = False) -> dict:
-    """Windows of the windowed expectation kernel, as the library plans them:
+            diag_terms: bool = True) -> dict:
+    """Windows of the windowed expectation and apply-H kernels, as the library plans them:
     window records, window groups, window terms, high-part offsets, wide groups."""
     lib = load()
     _check_layouts(lib)
@@ -152,7 +152,7 @@ def windows(n_qubits: int, precision: str, x, z, c, threshold: float = 0.0,
     c = np.ascontiguousarray(c, dtype=np.float64)
     counts = (ctypes.c_int * 5)()
     lib.vqe_inspect_windows(n_qubits, prec, x.ctypes.data, z.ctypes.data, c.ctypes.data, c.size,
-                            float(threshold), int(diag_terms), int(elem_layout), None, 0, None, 0,
+                            float(threshold), int(diag_terms), None, 0, None, 0,
                             None, 0, None, 0, None, 0, counts)
     nw, ng, nt, nh, nd = (counts[i] for i in range(5))
     wins = (WinDesc * max(nw, 1))()
@@ -161,7 +161,7 @@ def windows(n_qubits: int, precision: str, x, z, c, threshold: float = 0.0,
     hoff = np.zeros(max(nh, 1), dtype=np.uint32)
     wide = (GroupDesc * max(nd, 1))()
     rc = lib.vqe_inspect_windows(n_qubits, prec, x.ctypes.data, z.ctypes.data, c.ctypes.data,
-                                 c.size, float(threshold), int(diag_terms), int(elem_layout),
+                                 c.size, float(threshold), int(diag_terms),
                                  ctypes.addressof(wins),
                                  nw, ctypes.addressof(wg), ng, ctypes.addressof(wt), nt,
                                  hoff.ctypes.data, nh, ctypes.addressof(wide), nd, counts)

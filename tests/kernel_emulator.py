@@ -487,10 +487,12 @@ def energy_windows(ham, win, n, psi, hdiag=None):
 
 
 def apply_h_windows(win, n, psi, hdiag=None):
-    """The windowed apply-H kernel on the CPU: lambda accumulated window by
-    window (first window writes, later ones add), each group's sign sums at the
-    output element (direct, or per element-pattern run plus a Walsh-Hadamard
-    transform); the last window's Re<psi|lambda> and norm.  (lambda, E, norm)."""
+    """The windowed apply-H kernel on the CPU: the expectation's windows and
+    pair groups; a shared-memory tile of lambda per window (first window from
+    zero, later ones from the previous window's lambda); per pair (i0, i1) the
+    sign sums FA, FB at i0 (direct per pattern, or runs plus a Walsh-Hadamard
+    transform), lambda_i0 += psi_i1 (FA - i FB), lambda_i1 += psi_i0 (FA + i FB);
+    the last window's Re<psi|lambda> and norm.  (lambda, E, norm)."""
     LT, THR = 9, 512
     tid = np.arange(THR, dtype=np.int64)
     lam = np.zeros(1 << n, dtype=np.complex128)
@@ -500,6 +502,7 @@ def apply_h_windows(win, n, psi, hdiag=None):
     for wi, W in enumerate(wins):
         k, m = W.k, W.m
         EPT = 1 << (k - LT)
+        PPT = EPT // 2
         tiles = 1 << (n - k)
         bpos = [bb for bb in range(32) if (W.bmask >> bb) & 1]
         tn = np.arange(tiles, dtype=np.int64)
@@ -516,38 +519,64 @@ def apply_h_windows(win, n, psi, hdiag=None):
         zout = np.array([t.zout for t in terms], dtype=np.int64)
         cc = np.array([t.c for t in terms], dtype=np.float64)
         sc = cc[None, :] * (1 - 2 * (popc(base[:, None] & zout[None, :]) & 1)) if len(terms) else np.zeros((tiles, 0))
+        sl = np.zeros((tiles, 1 << k), dtype=np.complex128) if wi == 0 else lam[g]
         el = tid[:, None] + THR * np.arange(EPT)[None, :]          # (THR, EPT) element of (thread, j)
-        lt = np.zeros((tiles, THR, EPT), dtype=np.complex128) if wi == 0 else lam[g[:, el]]
-
-        def run_sums(run, begin):
-            F = np.zeros((tiles, THR, EPT))
-            for v in range(EPT):
-                for t in range(begin + run[v], begin + run[v + 1]):
-                    sgn = 1 - 2 * (popc(tid & zt[t]) & 1)
-                    F[:, :, v] += sc[:, t][:, None] * sgn[None, :]
-            return _wht_last(F)
-
-        def direct(t0, t1):
-            f = np.zeros((tiles, THR, EPT))
-            for t in range(t0, t1):
-                f += sc[:, t][:, None, None] * (1 - 2 * (popc(el & zt[t]) & 1))[None, :, :]
-            return f
-
         for G in win["wgroups"][W.g_begin:W.g_end]:
             if G.xl == 0:
-                f = hdiag[g[:, el]] if hdiag is not None else run_sums(G.arun, G.a_begin)
-                lt += sp[:, el] * f
+                if hdiag is not None:
+                    f = hdiag[g[:, el]]
+                else:
+                    F = np.zeros((tiles, THR, EPT))
+                    for v in range(EPT):
+                        for t in range(G.a_begin + G.arun[v], G.a_begin + G.arun[v + 1]):
+                            F[:, :, v] += sc[:, t][:, None] * (1 - 2 * (popc(tid & zt[t]) & 1))[None, :]
+                    f = _wht_last(F)
+                sl[:, el] += sp[:, el] * f
                 continue
-            y = sp[:, el ^ int(G.xl)]
+            xl, hl = int(G.xl), int(G.hl)
+            fm, plog, npat = int(G.fmask), int(G.plog), int(G.npat)
+            assert (fm >> hl) & 1 and plog == k - popc(fm) and 1 <= npat <= 8
+            fval = [int(G.fval[u]) for u in range(npat)]
+            t0 = tid & (511 if plog >= 9 else (1 << plog) - 1)
+            e0 = sum((t0 & int(G.smask[q])) << q for q in range(5))
+            dsum = np.zeros(PPT, dtype=np.int64)
+            for j in range(PPT):
+                for bb in range(4):
+                    if (j >> bb) & 1:
+                        dsum[j] |= int(G.dj[bb])
+            pj = tid[:, None] + THR * np.arange(PPT)[None, :]
+            u = pj >> plog
+            valid = u < npat
+            fv = np.array(fval + [0] * (9 - npat), dtype=np.int64)[np.minimum(u, 8)]
+            il = e0[:, None] | dsum[None, :] | fv
+            assert np.array_equal(il[valid], (_spread(pj & ((1 << plog) - 1), fm) | fv)[valid])
+            fa = np.zeros((tiles, THR, PPT))
+            fb = np.zeros((tiles, THR, PPT))
             if G.direct:
-                fa, fb = direct(G.a_begin, G.b_begin), direct(G.b_begin, G.b_end)
+                for uu in range(npat):
+                    sel = (u == uu)
+                    for t in range(G.a_begin + G.arun[uu], G.a_begin + G.arun[uu + 1]):
+                        fa += sc[:, t][:, None, None] * ((1 - 2 * (popc(il & zt[t]) & 1)) * sel)[None]
+                    for t in range(G.b_begin + G.brun[uu], G.b_begin + G.brun[uu + 1]):
+                        fb += sc[:, t][:, None, None] * ((1 - 2 * (popc(il & zt[t]) & 1)) * sel)[None]
             else:
-                fa = run_sums(G.arun, G.a_begin)
-                fb = run_sums(G.brun, G.b_begin) if G.b_end > G.b_begin else 0.0
-            lt += y * (fa - 1j * fb)
-        lam[g[:, el]] = lt
+                assert npat == 1 and plog == k - 1 and np.all(valid)
+                for F, run, begin in ((fa, G.arun, G.a_begin), (fb, G.brun, G.b_begin)):
+                    R = np.zeros((tiles, THR, PPT))
+                    for v in range(PPT):
+                        for t in range(begin + run[v], begin + run[v + 1]):
+                            R[:, :, v] += sc[:, t][:, None] * (1 - 2 * (popc(e0 & zt[t]) & 1))[None, :]
+                    F += _wht_last(R)
+            i0, i1 = il[valid], il[valid] ^ xl
+            assert i0.max() < (1 << k) and i1.max() < (1 << k)
+            # a group's pairs are disjoint: no element is written twice
+            assert np.unique(np.concatenate([i0, i1])).size == 2 * i0.size
+            x0, x1 = sp[:, i0], sp[:, i1]
+            FA, FB = fa[:, valid], fb[:, valid]
+            sl[:, i0] += x1 * (FA - 1j * FB)
+            sl[:, i1] += x0 * (FA + 1j * FB)
+        lam[g] = sl
         if wi == len(wins) - 1:
-            x = sp[:, el]
-            acc = float((x.real * lt.real + x.imag * lt.imag).sum())
-            nrm = float((np.abs(x) ** 2).sum())
+            acc = float((sp.real * sl.real + sp.imag * sl.imag).sum())
+            nrm = float((np.abs(sp) ** 2).sum())
     return lam, acc, nrm

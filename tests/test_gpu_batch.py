@@ -1,4 +1,4 @@
-"""GPU parity of the batched driver (one persistent kernel, CUDA graph) against the oracle."""
+"""GPU parity of the batched driver (persistent kernels per register-bit class, one CUDA graph) against the oracle."""
 import numpy as np
 import pytest
 

@@ -306,9 +306,10 @@ def test_padded_layout_conflict_free_for_default_plans(n, prec):
 @pytest.mark.parametrize("prec", ["c64", "c128"])
 @pytest.mark.parametrize("case", ["hubbard", "molecular"])
 def test_apply_h_windows_emulated(oracle_mod, prec, case):
-    """The windowed apply-H plan (terms ordered per element pattern) reproduces
-    the oracle's lambda = H psi and Re<psi|lambda>, with and without the
-    precomputed diagonal."""
+    """The windowed apply-H over the expectation's windows (pair groups, split
+    by pattern where the plan splits them) reproduces the oracle's
+    lambda = H psi and Re<psi|lambda>, with and without the precomputed
+    diagonal."""
     from kernel_emulator import apply_h_windows
     H = vi.hubbard_1d(8, 1.0, 3.0, periodic=True) if case == "hubbard" else vi.synthetic_molecular(8, seed=5)
     n = H.n
@@ -322,7 +323,7 @@ def test_apply_h_windows_emulated(oracle_mod, prec, case):
             for t in range(G.t_begin, G.t_mid):
                 hdiag += ham["tc"][t] * (1 - 2 * (np.vectorize(lambda v: bin(v).count("1"))(i & int(ham["tz"][t])) & 1))
     for diag_terms in (True, False):
-        win = P.windows(n, prec, H.x, H.z, H.c, diag_terms=diag_terms, elem_layout=True)
+        win = P.windows(n, prec, H.x, H.z, H.c, diag_terms=diag_terms)
         assert not win["wide"]
         lam, e, nn = apply_h_windows(win, n, psi, hdiag=None if diag_terms else hdiag)
         assert np.max(np.abs(lam - lam_ref)) < 1e-12 * H.sum_abs()

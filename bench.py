@@ -29,10 +29,10 @@ U_VALUES = (2.0, 4.0, 8.0)
 CHUNK = 64                      # states per workspace chunk (64 x 16 MiB = 1 GiB > L2)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
 # DRAM read+write bytes per state of one forward-pass launch (k_pass_fixed<double,3,fwd>,
-# 20 qubits, default plan), from the ncu capture of bench-sized launches
-# summarised in profiles/launches_hubbard20_bench.md.  None once the kernel
-# changes, until the capture is taken again.
-PASS_DRAM_BYTES_PER_STATE = 2095400619 / 64
+# 20 qubits, default plan; mean over the 11 passes of a sweep), from the ncu
+# capture of bench-sized launches summarised in profiles/launches_hubbard20_bench.md.
+# None once the kernel changes, until the capture is taken again.
+PASS_DRAM_BYTES_PER_STATE = 1995710697 / 64
 METRIC = "energy+gradient evals/s at 8-32 qubits; achieved HBM GB/s vs GB300 peak"
 WORKLOAD = ("20q FP64 (complex128) 10-site periodic 1D Hubbard t=1 U in {2,4,8}, "
             "HEA depth 10, 1000 param vectors per U, energy only")
@@ -294,8 +294,9 @@ def run_gpu(args, world, rank, local, pg):
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     # DRAM bytes (read + write) of one launch of this kernel, from the ncu
-    # capture summarised in profiles/k_pass_c128_fwd_20q.md (dram__bytes_read.sum +
-    # dram__bytes_write.sum per state, times the states of one bench launch).
+    # capture summarised in profiles/launches_hubbard20_bench.md (mean of
+    # dram__bytes_read.sum + dram__bytes_write.sum over a sweep's launches,
+    # per state, times the states of one bench launch).
     # Set to None whenever the kernel changes until it is captured again.
     traffic = PASS_DRAM_BYTES_PER_STATE * CHUNK if PASS_DRAM_BYTES_PER_STATE else None
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,

@@ -79,6 +79,46 @@ __device__ __forceinline__ void block_reduce2(double &a, double &b, double *sh) 
     }
 }
 
+// Block sum of two per-thread values for the FP32 kernels: a shuffle tree in
+// FP32 within each warp and one warp over the warp totals, so the FP64 pipe
+// (scarce on this GPU) sees only the conversions.  The result (thread 0) is
+// widened to FP64 for the fixed-order reduction across blocks.
+__device__ __forceinline__ void block_reduce2_f32(double &a, double &b, float *sh) {
+    float fa = (float)a, fb = (float)b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fa += __shfl_xor_sync(0xffffffffu, fa, o);
+        fb += __shfl_xor_sync(0xffffffffu, fb, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sh[2 * warp] = fa;
+        sh[2 * warp + 1] = fb;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        fa = lane < nw ? sh[2 * lane] : 0.f;
+        fb = lane < nw ? sh[2 * lane + 1] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fa += __shfl_xor_sync(0xffffffffu, fa, o);
+            fb += __shfl_xor_sync(0xffffffffu, fb, o);
+        }
+        a = (double)fa;
+        b = (double)fb;
+    }
+}
+
+// Block reduction for a window kernel of element type T.
+template <typename T>
+__device__ __forceinline__ void block_reduce2_t(double &a, double &b, double *sh) {
+    if constexpr (sizeof(T) == 4)
+        block_reduce2_f32(a, b, reinterpret_cast<float *>(sh));
+    else
+        block_reduce2(a, b, sh);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kEnergyThreads)
 k_energy_cols(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__restrict__ tz,
@@ -441,6 +481,14 @@ __device__ __forceinline__ void run_sums(T (&F)[NV], const uint16_t *run, int be
     }
 }
 
+// Shared-memory slot of tile element e in the window kernels: one pad
+// element per 128-byte row, so that pair reads whose indices skip fixed bits
+// (strides of 2..16 elements) spread over the banks.
+template <typename C>
+__host__ __device__ constexpr uint32_t wpad(uint32_t e) {
+    return e + (e >> (sizeof(C) == 16 ? 3 : 4));
+}
+
 template <typename T, int K, bool RUNS>
 __global__ void __launch_bounds__(kEnergyWinThreads, 2)
 k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__restrict__ wterms,
@@ -453,8 +501,8 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
     constexpr int EPT = size / kEnergyWinThreads;   // tile elements per thread
     constexpr int PPT = EPT / 2;                    // pairs per thread and group
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *sp = reinterpret_cast<C *>(smem_raw);                      // [size] the tile
-    T *sc = reinterpret_cast<T *>(sp + size);                     // [t_count] coefficients, base sign folded
+    C *sp = reinterpret_cast<C *>(smem_raw);                      // [wpad(size)] the tile (padded)
+    T *sc = reinterpret_cast<T *>(sp + wpad<C>(size));           // [t_count] coefficients, base sign folded
     uint32_t *szt = reinterpret_cast<uint32_t *>(sc + W.t_count); // [t_count] tile Z bits
     uint32_t *soff = szt + W.t_count;                             // [2^(K-m)] high-part offsets
     __shared__ double sh[2 * (kEnergyWinThreads / 32)];
@@ -498,7 +546,7 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
             x[j] = P[(size_t)(base | (e & lowmask) | soff[e >> m])];
         }
 #pragma unroll
-        for (int j = 0; j < EPT; ++j) sp[tid + j * kEnergyWinThreads] = x[j];
+        for (int j = 0; j < EPT; ++j) sp[wpad<C>(tid + j * kEnergyWinThreads)] = x[j];
     }
     __syncthreads();
     double acc = 0.0, nrm = 0.0;
@@ -506,7 +554,7 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
         T pn = T(0);
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
-            const C x = sp[tid + j * kEnergyWinThreads];
+            const C x = sp[wpad<C>(tid + j * kEnergyWinThreads)];
             pn += fma(x.x, x.x, x.y * x.y);
         }
         nrm = (double)pn;
@@ -524,7 +572,7 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) {
                     const uint32_t e = tid + j * kEnergyWinThreads;
-                    const C x = sp[e];
+                    const C x = sp[wpad<C>(e)];
                     part = fma(fma(x.x, x.x, x.y * x.y), __ldg(hdiag + (size_t)(base | e)), part);
                 }
             } else {
@@ -534,7 +582,7 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
                 wht_inplace<EPT>(F);
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) {
-                    const C x = sp[tid + j * kEnergyWinThreads];
+                    const C x = sp[wpad<C>(tid + j * kEnergyWinThreads)];
                     part = fma(fma(x.x, x.x, x.y * x.y), F[j], part);
                 }
                 }
@@ -573,7 +621,7 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
                     const uint32_t u = (tid + ((uint32_t)j << 9)) >> plog;   // warp-uniform
                     if (u >= npat) break;
                     const uint32_t il = e0 | D[j] | G.fval[u];
-                    const C x0 = sp[il], x1 = sp[il ^ xl];
+                    const C x0 = sp[wpad<C>(il)], x1 = sp[wpad<C>(il ^ xl)];
                     const T ar = fma(x0.x, x1.x, x0.y * x1.y);   // Re conj(x0) x1
                     const T ai = has_b ? fma(x0.x, x1.y, -x0.y * x1.x) : T(0);   // Im conj(x0) x1
                     if constexpr (sizeof(T) == 8) {
@@ -615,7 +663,7 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
                     const uint32_t il = e0 | D[j];
-                    const C x0 = sp[il], x1 = sp[il ^ xl];
+                    const C x0 = sp[wpad<C>(il)], x1 = sp[wpad<C>(il ^ xl)];
                     ar[j] = fma(x0.x, x1.x, x0.y * x1.y);
                     ai[j] = fma(x0.x, x1.y, -x0.y * x1.x);
                 }
@@ -645,7 +693,7 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
         }
     }
     if constexpr (sizeof(T) == 4) acc += (double)run;
-    block_reduce2(acc, nrm, sh);
+    block_reduce2_t<T>(acc, nrm, sh);
     if (threadIdx.x == 0) {
         double *o = partials + ((size_t)b * bps_total + W.block_off + blockIdx.x) * 3;
         o[0] = acc;
@@ -656,7 +704,8 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
 
 size_t win_smem_bytes(const WinDesc &W, size_t elem_bytes) {
     const size_t real = elem_bytes / 2;
-    return (size_t(1) << W.k) * elem_bytes + size_t(W.t_count) * (real + 4) +
+    const size_t tile = (size_t(1) << W.k) + ((size_t(1) << W.k) >> (elem_bytes == 16 ? 3 : 4));   // padded
+    return tile * elem_bytes + size_t(W.t_count) * (real + 4) +
            (size_t(1) << (W.k - W.m)) * 4;
 }
 
@@ -683,8 +732,8 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
     constexpr int PPT = EPT / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sp = reinterpret_cast<C *>(smem_raw);                      // [size] psi tile
-    C *sl = sp + size;                                            // [size] lambda tile
-    T *sc = reinterpret_cast<T *>(sl + size);
+    C *sl = sp + wpad<C>(size);                                   // [wpad(size)] lambda tile
+    T *sc = reinterpret_cast<T *>(sl + wpad<C>(size));
     uint32_t *szt = reinterpret_cast<uint32_t *>(sc + W.t_count);
     uint32_t *soff = szt + W.t_count;
     __shared__ double sh[2 * (kEnergyWinThreads / 32)];
@@ -731,20 +780,20 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
         }
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
-            sp[tid + j * kEnergyWinThreads] = x[j];
-            sl[tid + j * kEnergyWinThreads] = l[j];
+            sp[wpad<C>(tid + j * kEnergyWinThreads)] = x[j];
+            sl[wpad<C>(tid + j * kEnergyWinThreads)] = l[j];
         }
     }
     __syncthreads();
     // lambda_i0 += x1 (fa - i fb), lambda_i1 += x0 (fa + i fb)
     auto pair_update = [&](uint32_t i0, uint32_t i1, C x0, C x1, T fa, T fb) {
-        C l0 = sl[i0], l1 = sl[i1];
+        C l0 = sl[wpad<C>(i0)], l1 = sl[wpad<C>(i1)];
         l0.x = fma(x1.x, fa, fma(x1.y, fb, l0.x));
         l0.y = fma(x1.y, fa, fma(-x1.x, fb, l0.y));
         l1.x = fma(x0.x, fa, fma(-x0.y, fb, l1.x));
         l1.y = fma(x0.y, fa, fma(x0.x, fb, l1.y));
-        sl[i0] = l0;
-        sl[i1] = l1;
+        sl[wpad<C>(i0)] = l0;
+        sl[wpad<C>(i1)] = l1;
     };
     const int ng = W.g_end - W.g_begin;
     for (int gi = 0; gi < ng; ++gi) {
@@ -763,11 +812,11 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
 #pragma unroll
             for (int j = 0; j < EPT; ++j) {
                 const uint32_t e = tid + j * kEnergyWinThreads;
-                const C y = sp[e];
-                C l = sl[e];
+                const C y = sp[wpad<C>(e)];
+                C l = sl[wpad<C>(e)];
                 l.x = fma(y.x, F[j], l.x);
                 l.y = fma(y.y, F[j], l.y);
-                sl[e] = l;
+                sl[wpad<C>(e)] = l;
             }
         } else {
             // pairs as in the expectation: pair P = tid + 512 s of pattern
@@ -801,7 +850,7 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
                         for (int t = G.b_begin + G.brun[u]; t < b1; ++t)
                             fb += sgn_flip(sc[t], __popc(il & szt[t]) & 1u);
                     }
-                    pair_update(il, il ^ xl, sp[il], sp[il ^ xl], fa, fb);
+                    pair_update(il, il ^ xl, sp[wpad<C>(il)], sp[wpad<C>(il ^ xl)], fa, fb);
                 }
             } else if constexpr (RUNS) {
                 // a whole group (one pattern, plog = K - 1: every slot valid)
@@ -818,7 +867,7 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
                     const uint32_t il = e0 | D[j];
-                    pair_update(il, il ^ xl, sp[il], sp[il ^ xl], FA[j], FB[j]);
+                    pair_update(il, il ^ xl, sp[wpad<C>(il)], sp[wpad<C>(il ^ xl)], FA[j], FB[j]);
                 }
             }
         }
@@ -830,10 +879,10 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
             const uint32_t e = tid + j * kEnergyWinThreads;
-            const C l = sl[e];
+            const C l = sl[wpad<C>(e)];
             L[gidx(e)] = l;
             if (last) {
-                const C x = sp[e];
+                const C x = sp[wpad<C>(e)];
                 pa = fma(x.x, l.x, fma(x.y, l.y, pa));
                 pn = fma(x.x, x.x, fma(x.y, x.y, pn));
             }
@@ -842,7 +891,7 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
         nrm = (double)pn;
     }
     if (last) {   // uniform over the launch
-        block_reduce2(acc, nrm, sh);
+        block_reduce2_t<T>(acc, nrm, sh);
         if (threadIdx.x == 0) {
             double *o = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
             o[0] = acc;
@@ -858,7 +907,8 @@ cudaError_t launch_apply_h_win(const WinDesc &W, const WinGroup *wgroups, const 
                                const void *psi, void *lam, size_t state_stride, int first,
                                int last, double *partials, cudaStream_t s) {
     using C = typename EV2<T>::type;
-    const size_t smem = win_smem_bytes(W, sizeof(C)) + (size_t(1) << W.k) * sizeof(C);   // + lambda tile
+    const size_t smem = win_smem_bytes(W, sizeof(C)) +
+                        size_t(wpad<C>(1u << W.k)) * sizeof(C);   // + lambda tile (padded)
     auto kern = W.any_runs
         ? (W.k == 13 ? k_apply_h_win<T, 13, true> : (W.k == 12 ? k_apply_h_win<T, 12, true> : nullptr))
         : (W.k == 13 ? k_apply_h_win<T, 13, false> : (W.k == 12 ? k_apply_h_win<T, 12, false> : nullptr));

@@ -329,3 +329,44 @@ def test_apply_h_windows_emulated(oracle_mod, prec, case):
         assert np.max(np.abs(lam - lam_ref)) < 1e-12 * H.sum_abs()
         assert abs(e - float(np.real(np.vdot(psi, lam_ref)))) < 1e-11 * H.sum_abs()
         assert abs(nn - float(np.vdot(psi, psi).real)) < 1e-12
+
+
+def _smem_wavefronts(elem_index, elem_bytes, pad_shift):
+    """Shared-memory wavefronts of one warp reading 32 elements: the largest
+    number of distinct 128-byte rows that hit one 4-byte bank."""
+    slot = elem_index + (elem_index >> pad_shift) if pad_shift else elem_index
+    words = (slot[:, None] * elem_bytes + 4 * np.arange(elem_bytes // 4)[None, :]).ravel()
+    bank, row = (words // 4) % 32, words // 128
+    return max(len(set(row[bank == b].tolist())) for b in range(32))
+
+
+@pytest.mark.parametrize("case", ["hubbard20_c128", "molecular24_c64"])
+def test_window_pair_reads_spread_over_banks(case):
+    """The window kernels' padded tile layout (one pad element per 128-byte
+    row) keeps a warp's pair reads near the minimum number of shared-memory
+    wavefronts (4 for 16-byte, 2 for 8-byte elements), where the unpadded
+    layout reaches 16-32 for groups that fix low tile bits."""
+    from kernel_emulator import _spread
+    if case == "hubbard20_c128":
+        H, prec, esz, shift, worst = vi.hubbard_1d(10, 1.0, 4.0, periodic=True), "c128", 16, 3, 4
+    else:
+        H, prec, esz, shift, worst = vi.synthetic_molecular(12, 2024), "c64", 8, 4, 8
+    win = P.windows(H.n, prec, H.x, H.z, H.c, diag_terms=False)
+    padded, plain = [], []
+    for W in win["windows"][:40]:
+        for G in win["wgroups"][W.g_begin:W.g_end]:
+            if G.xl == 0:
+                continue
+            fm, plog, npat = int(G.fmask), int(G.plog), int(G.npat)
+            for warp in (0, 5):
+                p = np.arange(32, dtype=np.int64) + 32 * warp
+                u = p >> plog
+                if u.max() >= npat:
+                    continue
+                fv = np.array([int(G.fval[x]) for x in u], dtype=np.int64)
+                i0 = _spread(p & ((1 << plog) - 1), fm) | fv
+                for idx in (i0, i0 ^ int(G.xl)):
+                    padded.append(_smem_wavefronts(idx, esz, shift))
+                    plain.append(_smem_wavefronts(idx, esz, 0))
+    assert padded and max(padded) <= worst
+    assert np.mean(padded) <= np.mean(plain)

@@ -224,10 +224,10 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
             if (chunk < 0) {
                 if (active) {
                     auto first_round = [&](auto pc) {
-                        constexpr int P = decltype(pc)::value;
                         if constexpr (Env::kLoad == 1) {
                             direct_load(pc);
                         } else if constexpr (Env::kLoad == 2) {
+                            constexpr int P = decltype(pc)::value;
                             const uint32_t sb = pad_of<T>(elem_of(t, 0, P, R));
 #pragma unroll
                             for (int r = 0; r < NR; ++r) {

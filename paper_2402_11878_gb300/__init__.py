@@ -8,11 +8,14 @@ absence raises ImportError (there is no other code path).
 from .binding import Batch, Engine, VQEError, load, version, library_path  # noqa: F401
 
 __all__ = ["Batch", "Engine", "VQEError", "load", "version", "library_path", "EnergyFunction",
-           "energy_and_grad"]
+           "energy_and_grad", "minimize_energy", "minimize_batch"]
 
 
 def __getattr__(name):
     if name in ("EnergyFunction", "energy_and_grad"):
         from . import autograd as _ag
         return getattr(_ag, name)
+    if name in ("minimize_energy", "minimize_batch"):
+        from . import optimize as _opt
+        return getattr(_opt, name)
     raise AttributeError(name)

@@ -14,6 +14,12 @@ Two drivers:
 
 Both accept any object with the Engine's ``gradient`` / ``gradient_batch``
 methods, so the host logic is testable without a GPU.
+
+``cutoff_ratio_search`` is the paper's way of choosing the cutoff of
+Sec. II-D (Algorithm 1): converge VQE on a smaller problem at decreasing
+kept fractions of the terms and keep the smallest fraction whose energy stays
+within the required accuracy; ``threshold_for_ratio`` turns that fraction
+into the threshold for a larger problem.
 """
 from __future__ import annotations
 
@@ -64,3 +70,69 @@ def minimize_batch(engine, params0, steps: int = 300, lr: float = 0.05,
     _, E = engine.gradient_batch(P)
     E = np.asarray(E, dtype=np.float64)
     return {"params": P, "energies": E, "best": int(np.argmin(E)), "history": hist}
+
+
+# ---------------------------------------------------------------- cutoff ratio
+
+def merged_abs_coefficients(x_masks, z_masks, coeffs) -> np.ndarray:
+    """|c| of the Pauli strings after merging equal (x, z) pairs and dropping
+    exact zeros (the terms the library's cutoff acts on), largest first."""
+    x = np.asarray(x_masks, dtype=np.uint64)
+    z = np.asarray(z_masks, dtype=np.uint64)
+    c = np.asarray(coeffs, dtype=np.float64)
+    keys = np.stack([x, z], axis=1)
+    _, inv = np.unique(keys, axis=0, return_inverse=True)
+    merged = np.zeros(int(inv.max()) + 1 if inv.size else 0)
+    np.add.at(merged, inv.ravel(), c)
+    a = np.abs(merged[merged != 0.0])
+    return np.sort(a)[::-1]
+
+
+def threshold_for_ratio(abs_coeffs_desc, ratio: float) -> float:
+    """Cutoff threshold that keeps the ceil(ratio * N) largest-|c| terms of a
+    Hamiltonian whose merged |c| are given largest first (Sec. II-D: terms
+    with |c| < threshold are dropped; terms tied with the last kept one stay
+    too).  ratio >= 1 keeps every term (threshold 0)."""
+    a = np.asarray(abs_coeffs_desc, dtype=np.float64)
+    if ratio >= 1.0 or a.size == 0:
+        return 0.0
+    k = max(1, int(np.ceil(ratio * a.size - 1e-9)))
+    return float(a[k - 1])
+
+
+def cutoff_ratio_search(engine, x_masks, z_masks, coeffs, params0, delta_e: float,
+                        step: float = 0.1, min_ratio: float = 0.1, vqe=None) -> dict:
+    """The cutoff-ratio search of Sec. II-D (Algorithm 1), on a problem small
+    enough to converge: starting from the whole Hamiltonian (ratio 1), lower
+    the kept fraction of terms (largest |c| first) by ``step`` while the
+    converged VQE energy stays within ``delta_e`` of the whole Hamiltonian's;
+    the answer is the smallest ratio that still met the accuracy (the ratio
+    before the first failure, or ``min_ratio`` if none failed).  Apply it to a
+    larger problem with ``threshold_for_ratio``.
+
+    ``vqe(engine, params0)`` returns the converged energy (default: L-BFGS
+    from ``params0``).  The engine is left slimmed to the returned ratio.
+    Returns {"ratio", "threshold", "runs": [(ratio, kept, energy), ...]}."""
+    if vqe is None:
+        def vqe(eng, p0):
+            return minimize_energy(eng, p0)["energy"]
+    a = merged_abs_coefficients(x_masks, z_masks, coeffs)
+    runs = []
+    e_full = None
+    ratio = 1.0
+    best = 1.0
+    n_steps = int(round((1.0 - min_ratio) / step))
+    for i in range(n_steps + 1):
+        ratio = round(1.0 - i * step, 12)
+        th = threshold_for_ratio(a, ratio)
+        kept, _ = engine.slim(th)
+        e = float(vqe(engine, params0))
+        runs.append((ratio, int(kept), e))
+        if e_full is None:
+            e_full = e
+        if abs(e - e_full) >= delta_e:
+            break
+        best = ratio
+    th = threshold_for_ratio(a, best)
+    engine.slim(th)
+    return {"ratio": best, "threshold": th, "runs": runs}

@@ -57,3 +57,22 @@ def test_lbfgs_four_site_hubbard_variational_bound(lib_built):
     eng.close()
     assert r["energy"] < r["history"][0] - 0.5
     assert r["history"].min() >= e0 - 1e-10
+
+
+def test_cutoff_ratio_search_c128(lib_built):
+    """Algorithm 1 through the C ABI: 2-site Hubbard plus 30 tiny terms; the
+    search keeps every Hubbard term and stops at the first ratio that cuts
+    one."""
+    from paper_2402_11878_gb300 import cutoff_ratio_search
+    Hb = vi.hubbard_1d(2, 1.0, 4.0, periodic=False)
+    Hs = vi.random_pauli_sum(4, 30, seed=9)
+    H = vi.PauliSum(4, np.concatenate([Hb.x, Hs.x]), np.concatenate([Hb.z, Hs.z]),
+                    np.concatenate([Hb.c, 1e-5 * Hs.c / np.abs(Hs.c).max()]))
+    eng = _engine(H, 4, "c128")
+    out = cutoff_ratio_search(eng, H.x, H.z, H.c, vi.ansatz_params(103, 4, 4), delta_e=1e-3)
+    kept, dropped = eng.slim(out["threshold"])
+    eng.close()
+    assert out["threshold"] <= np.abs(Hb.c[Hb.c != 0]).min()
+    assert dropped <= 30 * 1e-5 + 1e-12
+    e_full = out["runs"][0][2]
+    assert all(abs(e - e_full) < 1e-3 for r, k, e in out["runs"] if r >= out["ratio"] - 1e-9)

@@ -49,8 +49,9 @@ def minimize_energy(engine, params0, maxiter: int = 500, gtol: float = 1e-9,
 
 def minimize_batch(engine, params0, steps: int = 300, lr: float = 0.05,
                    beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-12) -> dict:
-    """Advance S starts (``params0``: S x n_params) together with Adam, one
-    batched adjoint gradient per step.  Returns {"params" (S x n_params),
+    """Advance S starts (``params0``: S x n_params) together with Adam
+    (Kingma and Ba, 2015: bias-corrected first and second moment estimates),
+    one batched adjoint gradient per step.  Returns {"params" (S x n_params),
     "energies" (S,), "best" (index of the lowest), "history" (steps x S)}."""
     P = np.array(params0, dtype=np.float64, copy=True)
     if P.ndim != 2:

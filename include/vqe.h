@@ -209,9 +209,11 @@ const char *vqe_version(void);
  * Sec. II-C): instance i has n_qubits[i] (1..24) qubits, depth[i] (1..64)
  * ansatz layers and its own Hamiltonian and parameters.  One run computes,
  * for every instance, the energy <psi|H|psi>/<psi|psi> and the adjoint
- * gradient, in ONE persistent kernel (each CTA takes whole instances from a
- * queue ordered largest first; states that fit one tile stay in shared
- * memory) launched through a CUDA graph captured on first use.
+ * gradient, with persistent CTAs (each takes whole instances from a queue
+ * ordered largest first; states that fit one tile stay in shared memory):
+ * one kernel for the instances whose plans hold 16 amplitudes per thread,
+ * one for the rest, both launched through ONE CUDA graph captured on first
+ * use (vqe_batch_launch_count counts graph launches).
  *
  * Parameters and gradients of all instances are concatenated: instance i
  * owns entries [offsets[i], offsets[i+1]) (vqe_batch_param_offsets), laid

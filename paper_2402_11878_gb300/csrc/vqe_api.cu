@@ -856,11 +856,13 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
             rest.push_back(int(g));
         }
     }
-    // other groups: greedy cover, groups with more high bits first
+    // other groups: greedy cover in decreasing X mask order, so that masks
+    // sharing their top bits meet in the same windows (the synthetic
+    // molecular Hamiltonian at 24 qubits: 108 windows, against 246 when the
+    // groups went by decreasing number of high bits)
     const uint32_t lowm = (1u << mrun) - 1u;
-    std::stable_sort(rest.begin(), rest.end(), [&](int p, int q) {
-        return __builtin_popcount(hp.groups[p].x & ~lowm) > __builtin_popcount(hp.groups[q].x & ~lowm);
-    });
+    std::stable_sort(rest.begin(), rest.end(),
+                     [&](int p, int q) { return hp.groups[p].x > hp.groups[q].x; });
     const size_t first_free = cands.size();
     for (int g : rest) {
         const uint32_t H = hp.groups[g].x & ~lowm;

@@ -370,3 +370,17 @@ def test_window_pair_reads_spread_over_banks(case):
                     plain.append(_smem_wavefronts(idx, esz, 0))
     assert padded and max(padded) <= worst
     assert np.mean(padded) <= np.mean(plain)
+
+
+def test_window_cover_of_the_molecular_hamiltonian():
+    """The greedy cover in decreasing X-mask order: every group of the 24-qubit
+    synthetic molecular Hamiltonian lands in a window (none swept globally),
+    within the per-window caps, in at most 110 windows (C64) / 126 (C128);
+    ordering by the number of high bits needed 246."""
+    H = vi.synthetic_molecular(12, 2024)
+    for prec, most in (("c64", 110), ("c128", 126)):
+        win = P.windows(H.n, prec, H.x, H.z, H.c, diag_terms=False)
+        assert not win["wide"]
+        assert len(win["windows"]) <= most
+        for W in win["windows"]:
+            assert W.g_end - W.g_begin <= P.K_WIN_MAX_GROUPS and W.t_count <= P.K_WIN_MAX_TERMS

@@ -1,21 +1,31 @@
 #!/usr/bin/env python
 """Throughput benchmark of the VQE hot path on GB300.
 
-Workload (default): 20 qubits, plain FP64 state (16 MiB), 10-site periodic
-1D Fermi-Hubbard (t = 1, U in {2, 4, 8}, Jordan-Wigner, interleaved spins),
-hardware-efficient ansatz of depth 10, 1000 seeded parameter vectors per U,
-energy only.  One step = for each U: Hamiltonian canonicalisation + cutoff
-(threshold 0) on the host, then 1000 energy evaluations (parameter staging,
-fused ansatz passes, grouped expectation) on the GPU.
+Default workload (the largest single-GPU configuration of the evaluation set,
+the 32-qubit scale of the paper's complete VQE, Sec. III-E): 32 qubits,
+4x4 periodic 2D Fermi-Hubbard lattice (snake order, t = 1, U = 4,
+Jordan-Wigner, 177 Pauli strings in 65 X-mask groups), hardware-efficient
+ansatz of depth 8 (512 parameters).  One step = one energy + adjoint-gradient
+evaluation in FP64 (complex128 state: psi and lambda are 2 x 64 GiB) through
+the C ABI: parameter staging, 25 forward tile passes, lambda = H psi with the
+fused energy, 25 backward passes, gradient reduction.
+
+Beside the headline the line reports, on the same Hamiltonian and
+parameters: the complex64 form of the same evaluation (state in complex64,
+FP64 accumulation), its accuracy against the FP64 result, and the FP64
+energy alone, unslimmed and slimmed at threshold 0.6 (Sec. II-D: every
+hopping term dropped, with the bound sum|c_dropped|).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on a bounded sample of the same workload instead.
+oracle on a bounded sample of the workload instead.  ``--workload`` selects
+the other configurations (one line each).
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -24,40 +34,120 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_QUBITS, DEPTH, SITES, N_VEC = 20, 10, 10, 1000
-U_VALUES = (2.0, 4.0, 8.0)
-CHUNK = 64                      # states per workspace chunk (64 x 16 MiB = 1 GiB > L2)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max clock
-# DRAM read+write bytes per state of one forward-pass launch (k_pass_fixed<double,3,fwd>,
-# 20 qubits, default plan; mean over the 11 passes of a sweep), from the ncu
-# capture of bench-sized launches summarised in profiles/launches_hubbard20_bench.md.
-# None once the kernel changes, until the capture is taken again.
-PASS_DRAM_BYTES_PER_STATE = 1995710697 / 64
+N_QUBITS, DEPTH, LX, LY, T_HOP, U_INT = 32, 8, 4, 4, 1.0, 4.0
+SLIM_THRESHOLD = 0.6          # drops every hopping term (|c| = t/2) of the lattice
+N_VEC = 4                     # distinct parameter vectors, cycled over the steps
 METRIC = "energy+gradient evals/s at 8-32 qubits; achieved HBM GB/s vs GB300 peak"
-WORKLOAD = ("20q FP64 (complex128) 10-site periodic 1D Hubbard t=1 U in {2,4,8}, "
-            "HEA depth 10, 1000 param vectors per U, energy only")
+WORKLOAD = ("32q FP64 (complex128) 4x4 periodic 2D Fermi-Hubbard (snake order, t=1, U=4, JW), "
+            "HEA depth 8 (512 params): energy + adjoint gradient per evaluation")
+# CPU-oracle samples of the same model family and depth (the 32-qubit state
+# does not fit the oracle's host memory budget): a 4x3 periodic lattice (24
+# qubits) for the line's baseline and a 5x2 lattice (20 qubits) per step of
+# the reference arm; each is extrapolated to 32 qubits (see oracle_scale).
+SAMPLE_BASELINE = (4, 3)
+SAMPLE_REFERENCE = (5, 2)
+FP64_UNITS_PEAK = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max SM clock
 
 
-def executed_forward_flops(n: int, depth: int, prec: str) -> int:
-    """FP64 (or FP32) flops the forward passes of one state execute, from the
-    library's own plan: per live tile and slot, 4 per gated bit and amplitude
-    (scaled rotation, 2 FMA per real pair) plus 6 (one complex multiply by the
-    slot's RZ/CZ diagonal).  Tiles a pass skips as known zeros, and the first
-    pass when it writes its one live tile as a product, execute none."""
+# ---------------------------------------------------------------- work models
+
+def slot_sweeps(n: int, depth: int, prec: str, options=(0, 0, 0)):
+    """Per tile pass of the library's plan: (tiles, live tiles of the forward
+    sweep, 2^k, gated bits per slot).  Forward tiles whose base has a bit of
+    the pass's zero mask are known zeros and are written without work."""
     from paper_2402_11878_gb300 import plans
-    pl = plans.plan(n, depth, prec)
+    pl = plans.plan(n, depth, prec, options)
+    out = []
+    for i, (f, b) in enumerate(zip(pl["fwd"], pl["bwd"])):
+        mid = f.a - f.m
+        tiles = 1 << (n - f.k)
+        if f.zmask:
+            live = 0
+            for tile in range(tiles):
+                base = ((tile & ((1 << mid) - 1)) << f.m) | ((tile >> mid) << (f.a + f.k - f.m))
+                live += (base & f.zmask) == 0
+        else:
+            live = tiles
+        gated = [bin(f.slot_gated[s]).count("1") for s in range(f.n_slots)]
+        out.append({"tiles": tiles, "live": live, "k": f.k, "gated": gated, "first": i == 0})
+    return out
+
+
+def forward_flops(n: int, depth: int, prec: str) -> float:
+    """Floating-point operations the forward passes of one state execute: per
+    live tile and slot, 4 per gated bit and amplitude (scaled rotation, 2 FMA
+    per real pair) and 6 (one complex multiply by the slot's RZ/CZ diagonal).
+    Zero tiles, and the first pass when it writes its one live tile as a
+    product, execute none."""
     total = 0
-    for i, d in enumerate(pl["fwd"]):
-        if i == 0 and d.n_slots == 1:
+    for p in slot_sweeps(n, depth, prec):
+        if p["first"] and len(p["gated"]) == 1:
             continue
-        mid = d.a - d.m
-        live = 0
-        for tile in range(1 << (n - d.k)):
-            base = ((tile & ((1 << mid) - 1)) << d.m) | ((tile >> mid) << (d.a + d.k - d.m))
-            live += (base & d.zmask) == 0
-        per_tile = sum(4 * bin(d.slot_gated[s]).count("1") + 6 for s in range(d.n_slots)) << d.k
-        total += live * per_tile
-    return total
+        total += p["live"] * (1 << p["k"]) * sum(4 * g + 6 for g in p["gated"])
+    return float(total)
+
+
+def backward_flops(n: int, depth: int, prec: str) -> float:
+    """Floating-point operations of the adjoint backward passes of one state
+    (every tile is live): per amplitude and slot, 12 per gated bit (the scaled
+    rotation un-applied on psi and on lambda, 4 each, and Im<lambda|Y|psi>, 4)
+    and 16 (the diagonal undone on both buffers, 6 each, and Im(conj(lambda)
+    psi) with its sum, 4)."""
+    total = 0
+    for p in slot_sweeps(n, depth, prec):
+        total += p["tiles"] * (1 << p["k"]) * sum(12 * g + 16 for g in p["gated"])
+    return float(total)
+
+
+def pass_bytes(n: int, depth: int, prec: str):
+    """HBM bytes of one state's forward passes (read + write per live tile,
+    write only per zero tile) and backward passes (psi and lambda read and
+    written)."""
+    b = 16 if prec == "c128" else 8
+    fwd = bwd = 0
+    for p in slot_sweeps(n, depth, prec):
+        amps = 1 << p["k"]
+        fwd += (2 * p["live"] + (p["tiles"] - p["live"])) * amps * b
+        bwd += 4 * p["tiles"] * amps * b
+    return float(fwd), float(bwd)
+
+
+def oracle_sweeps(n: int, depth: int, n_terms: int) -> int:
+    """State sweeps of one oracle energy + adjoint gradient: the gate-by-gate
+    forward (2n rotations and n-1 CZ per layer), the per-term lambda = H psi,
+    and the adjoint's un-apply of every gate on psi and lambda with one inner
+    product per parameter."""
+    gates = depth * (3 * n - 1)
+    return gates + n_terms + 2 * gates + 2 * n * depth
+
+
+def oracle_scale(lx: int, ly: int) -> float:
+    """Extrapolation of an oracle time on an lx x ly lattice to the 32-qubit
+    workload: state size times the ratio of state sweeps per evaluation."""
+    import vqe_inputs as vi
+    n = 2 * lx * ly
+    small = vi.hubbard_2d_snake(lx, ly, T_HOP, U_INT)
+    big = vi.hubbard_2d_snake(LX, LY, T_HOP, U_INT)
+    return 2.0 ** (N_QUBITS - n) * oracle_sweeps(N_QUBITS, DEPTH, len(big.c)) / \
+        oracle_sweeps(n, DEPTH, len(small.c))
+
+
+# ---------------------------------------------------------------- inputs
+
+def seeds_for(rank: int, index: int) -> int:
+    return 1_000_000 * (rank + 1) + 1000 + index
+
+
+def make_params(rank: int):
+    """The rank's parameter vectors, i.i.d. U[-pi, pi) (N_VEC x 2nD)."""
+    import numpy as np
+    import vqe_inputs as vi
+    return np.stack([vi.ansatz_params(seeds_for(rank, j), N_QUBITS, DEPTH) for j in range(N_VEC)])
+
+
+def hamiltonian():
+    import vqe_inputs as vi
+    return vi.hubbard_2d_snake(LX, LY, T_HOP, U_INT)
 
 
 def measured_peaks():
@@ -68,24 +158,18 @@ def measured_peaks():
         return {}
 
 
-def seeds_for(rank: int, u_index: int) -> int:
-    return 1_000_000 * (rank + 1) + 1000 * u_index
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
 
 
-def make_params(rank: int):
-    import numpy as np
-    import vqe_inputs as vi
-    out = []
-    for ui, _ in enumerate(U_VALUES):
-        base = seeds_for(rank, ui)
-        out.append(np.stack([vi.ansatz_params(base + j, N_QUBITS, DEPTH) for j in range(N_VEC)]))
-    return out
-
-
-def hamiltonians():
-    import vqe_inputs as vi
-    return [vi.hubbard_1d(SITES, 1.0, U, periodic=True) for U in U_VALUES]
-
+# ---------------------------------------------------------------- clocks
 
 class ClockSampler:
     """nvidia-smi samples during the timed region."""
@@ -135,6 +219,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- ranks
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -172,62 +258,108 @@ def barrier(pg, device=None):
             pg.barrier()
 
 
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_eval_seconds(lx: int, ly: int, seed: int) -> float:
+    """One oracle energy + adjoint gradient on an lx x ly lattice, depth 8."""
+    import oracle
+    import vqe_inputs as vi
+    H = vi.hubbard_2d_snake(lx, ly, T_HOP, U_INT)
+    n = 2 * lx * ly
+    p = vi.ansatz_params(seed, n, DEPTH)
+    t0 = time.perf_counter()
+    oracle.gradient_adjoint(n, DEPTH, p, H.x, H.z, H.c)
+    return time.perf_counter() - t0
+
+
+def _one_thread_seconds(lx: int, ly: int) -> float | None:
+    """The same oracle evaluation in a child process limited to one thread."""
+    code = ("import sys; sys.path.insert(0, %r); import bench; "
+            "print(bench.oracle_eval_seconds(%d, %d, 7))" % (ROOT, lx, ly))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                           timeout=300)
+        return float(r.stdout.strip().splitlines()[-1])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
+def cpu_baseline_sample(budget_s: float = 20.0):
+    """The oracle on the host cores: one evaluation of the 24-qubit sample
+    lattice with every thread, a 20-qubit one with one thread, each
+    extrapolated to the 32-qubit workload."""
+    import oracle
+    oracle.build.build()
+    lx, ly = SAMPLE_BASELINE
+    done, spent = 0, 0.0
+    while done < 1 or (spent < budget_s * 0.5 and done < 3):
+        spent += oracle_eval_seconds(lx, ly, 11 + done)
+        done += 1
+    per = spent / done
+    scale = oracle_scale(lx, ly)
+    one = _one_thread_seconds(*SAMPLE_REFERENCE)
+    out = {"value": 1.0 / (per * scale), "unit": "evals/s", "cores": oracle.threads(),
+           "kind": "oracle", "cpu_model": cpu_model(),
+           "sample": (f"{done} FP64 energy + adjoint gradient evaluation(s) of the {lx}x{ly} "
+                      f"periodic lattice ({2 * lx * ly} qubits, depth {DEPTH}) at {per:.2f} s each on "
+                      f"{oracle.threads()} threads, extrapolated to 32 qubits by x{scale:.4g} "
+                      "(state size x state sweeps per evaluation)"),
+           "sample_evals_per_s": 1.0 / per}
+    if one is not None:
+        s1 = oracle_scale(*SAMPLE_REFERENCE)
+        out["one_thread"] = {"value": 1.0 / (one * s1), "unit": "evals/s",
+                             "sample": (f"{SAMPLE_REFERENCE[0]}x{SAMPLE_REFERENCE[1]} lattice "
+                                        f"({2 * SAMPLE_REFERENCE[0] * SAMPLE_REFERENCE[1]} qubits) "
+                                        f"at {one:.2f} s, x{s1:.4g} to 32 qubits")}
+    return out
+
+
 def run_reference(args, world, rank, pg):
-    """The FP64 CPU oracle on a bounded sample of the workload."""
+    """The FP64 CPU oracle: each step one energy + adjoint gradient of the
+    20-qubit sample lattice, reported as 32-qubit evaluations per second."""
     if rank != 0:
         return
     import oracle
     oracle.build.build()
-    H = hamiltonians()
-    P = make_params(0)
-    per_step = 1
-    def step(i):
-        k = i % len(U_VALUES)
-        h = H[k]
-        xs, zs, cs, _ = oracle.slim(h.x, h.z, h.c, 0.0)
-        psi = oracle.ansatz_state(N_QUBITS, DEPTH, P[k][i % N_VEC])
-        oracle.energy(psi, xs, zs, cs)
+    lx, ly = SAMPLE_REFERENCE
     for i in range(args.warmup):
-        step(i)
+        oracle_eval_seconds(lx, ly, 100 + i)
     t0 = time.perf_counter()
     for i in range(args.steps):
-        step(args.warmup + i)
+        oracle_eval_seconds(lx, ly, 200 + i)
     dt = time.perf_counter() - t0
-    value = per_step * args.steps / dt
+    scale = oracle_scale(lx, ly)
+    value = args.steps / (dt * scale)
+    sample = (f"one FP64 energy + adjoint gradient of the {lx}x{ly} lattice ({2 * lx * ly} qubits, "
+              f"depth {DEPTH}) per step, extrapolated to 32 qubits by x{scale:.4g} "
+              "(state size x state sweeps per evaluation)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"{per_step} energy evaluation per step"},
+        "config": {"workload": WORKLOAD, "sample": sample},
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": oracle.threads(),
-                         "kind": "oracle",
-                         "sample": f"{per_step} of the 3000 energy evaluations per step"},
+                         "kind": "oracle", "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample(budget_s: float = 15.0):
-    """Oracle evaluations of the same workload for about ``budget_s`` seconds."""
-    import oracle
-    oracle.build.build()
-    H = hamiltonians()
-    P = make_params(0)
-    done, t0 = 0, time.perf_counter()
-    while True:
-        k = done % len(U_VALUES)
-        h = H[k]
-        xs, zs, cs, _ = oracle.slim(h.x, h.z, h.c, 0.0)
-        psi = oracle.ansatz_state(N_QUBITS, DEPTH, P[k][done])
-        oracle.energy(psi, xs, zs, cs)
-        done += 1
-        if time.perf_counter() - t0 >= budget_s and done >= 2:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": "evals/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{done} energy evaluations (20q FP64 Hubbard, U cycling 2/4/8), {dt:.1f} s"}
+# ---------------------------------------------------------------- GPU
+
+def _event_ms(stream, fn, reps: int) -> float:
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
 
 
 def run_gpu(args, world, rank, local, pg):
@@ -236,128 +368,169 @@ def run_gpu(args, world, rank, local, pg):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     import paper_2402_11878_gb300 as pkg
+    from paper_2402_11878_gb300 import binding
 
     stream = torch.cuda.current_stream(dev)
-    H = hamiltonians()
+    H = hamiltonian()
+    n, D = N_QUBITS, DEPTH
     P_host = make_params(rank)
-    P_dev = [torch.tensor(p, device=dev) for p in P_host]
-    E_dev = [torch.empty(N_VEC, dtype=torch.float64, device=dev) for _ in U_VALUES]
-    engines = [pkg.Engine(N_QUBITS, DEPTH, "c128", stream=stream) for _ in U_VALUES]
-    ws = torch.empty(engines[0].workspace_size(CHUNK) // 16, dtype=torch.complex128, device=dev)
-    for e in engines:
-        e.bind_workspace(ws)
+    P_dev = torch.tensor(P_host, device=dev)
+    G = torch.empty(1, 2 * n * D, dtype=torch.float64, device=dev)
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    Nrm = torch.empty(1, dtype=torch.float64, device=dev)
 
-    def step(pergate=False, profile_engines=None):
-        for k, eng in enumerate(engines):
-            eng.set_hamiltonian(H[k].x, H[k].z, H[k].c)
-            eng.slim(0.0)
-            eng.energy_batch_dev(P_dev[k], E_dev[k], pergate=pergate)
+    # measured FP64 FMA rate of this GPU (the "alu" roofline denominator)
+    fp64_peak = max(binding.measure_fma_peak(True, stream) for _ in range(3))
 
-    for _ in range(args.warmup):
-        step()
+    eng = pkg.Engine(n, D, "c128", stream=stream)
+    eng.set_hamiltonian(H.x, H.z, H.c)
+    tuned = None
+    if not args.no_autotune and hasattr(eng, "autotune"):
+        tuned = eng.autotune(P_dev[:1], gradient=True)
+
+    def step(i):
+        eng.gradient_batch_dev(P_dev[i % N_VEC:i % N_VEC + 1], G, E)
+
+    for i in range(args.warmup):
+        step(i)
     torch.cuda.synchronize(dev)
-    launches0 = sum(e.stats()["kernel_launches"] for e in engines)
-    for e in engines:
-        e.profile(True)
+    launches0 = eng.stats()["kernel_launches"]
+    eng.profile(True)
     sampler = ClockSampler(local)
     sampler.start()
     barrier(pg, local)
     torch.cuda.synchronize(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
-        step()
+    for i in range(args.steps):
+        step(i)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(pg, local)
     ms = ev0.elapsed_time(ev1)
     clocks = sampler.stop()
-    prof = [e.profile_read() for e in engines]
-    for e in engines:
-        e.profile(False)
-    launches = sum(e.stats()["kernel_launches"] for e in engines) - launches0
-    # max over ranks
+    prof = eng.profile_read()
+    eng.profile(False)
+    launches = eng.stats()["kernel_launches"] - launches0
     ms = max_over_ranks(ms, pg, dev)
-    evals = len(U_VALUES) * N_VEC * args.steps * world
-    value = job_throughput(len(U_VALUES) * N_VEC * args.steps, world, ms)
+    value = job_throughput(args.steps, world, ms)
+    g128 = G[0].cpu().numpy().copy()        # step K-1's vector
+    last = (args.steps - 1) % N_VEC
+    e128 = float(E[0])
 
-    # dominant kernel: the fused forward pass; FP64 flops it executes per
-    # state, from the plan (4 per gated bit and amplitude, 6 per slot's
-    # diagonal, skipped zero tiles excluded)
-    fwd_ms = sum(p["forward_passes"]["ms"] for p in prof)
-    fwd_launches = sum(p["forward_passes"]["launches"] for p in prof)
-    en_ms = sum(p["energy"]["ms"] for p in prof)
-    flops_fwd = len(U_VALUES) * N_VEC * args.steps * executed_forward_flops(N_QUBITS, DEPTH, "c128")
-    achieved_tflops = flops_fwd / (fwd_ms / 1e3) / 1e12
-    n_pass = engines[0].stats()["ansatz_passes"]
-    bytes_fwd = len(U_VALUES) * N_VEC * args.steps * n_pass * 2 * 16 * (1 << N_QUBITS)
+    # per kernel group, per evaluation
+    steps = args.steps
+    fwd_ms = prof["forward_passes"]["ms"] / steps
+    app_ms = prof["apply_h"]["ms"] / steps
+    bwd_ms = prof["backward_passes"]["ms"] / steps
+    bwd_launches = prof["backward_passes"]["launches"] / steps
+    fl_f, fl_b = forward_flops(n, D, "c128"), backward_flops(n, D, "c128")
+    by_f, by_b = pass_bytes(n, D, "c128")
+    state_b = 16.0 * (1 << n)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
-    # DRAM bytes (read + write) of one launch of this kernel, from the ncu
-    # capture summarised in profiles/launches_hubbard20_bench.md (mean of
-    # dram__bytes_read.sum + dram__bytes_write.sum over a sweep's launches,
-    # per state, times the states of one bench launch).
-    # Set to None whenever the kernel changes until it is captured again.
-    traffic = PASS_DRAM_BYTES_PER_STATE * CHUNK if PASS_DRAM_BYTES_PER_STATE else None
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-                "traffic": traffic, "kernel": "k_pass_fixed<double,3,fwd> (unrolled fused layer pass)",
-                "peak_source": "FP64 units x max SM clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                "mean_launch_us": 1e3 * fwd_ms / max(fwd_launches, 1),
-                "share_of_step": fwd_ms / ms if ms else None,
-                "hbm_algorithmic_gbs": bytes_fwd / (fwd_ms / 1e3) / 1e9,
-                "hbm_peak_gbs": hbm_peak}
+    kernels = {
+        "forward_passes": {"ms": fwd_ms, "launches": prof["forward_passes"]["launches"] / steps,
+                           "tflops": fl_f / (fwd_ms / 1e3) / 1e12,
+                           "hbm_gbs": by_f / (fwd_ms / 1e3) / 1e9},
+        "apply_h": {"ms": app_ms, "launches": prof["apply_h"]["launches"] / steps,
+                    "hbm_gbs_algorithmic": 2 * state_b / (app_ms / 1e3) / 1e9},
+        "backward_passes": {"ms": bwd_ms, "launches": bwd_launches,
+                            "tflops": fl_b / (bwd_ms / 1e3) / 1e12,
+                            "hbm_gbs": by_b / (bwd_ms / 1e3) / 1e9},
+    }
+    achieved = fl_b / (bwd_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "kernel": "k_pass_fixed<double,3,bwd> (adjoint backward tile passes)",
+                "peak_source": ("measured FP64 FMA rate of this GPU (vqe_measure_fma_peak, "
+                                "independent FMA chains on every SM, CUDA events); unit count x "
+                                f"max clock gives {FP64_UNITS_PEAK:.4g}"),
+                "algorithmic_flops_per_launch": fl_b / bwd_launches,
+                "mean_launch_ms": bwd_ms / bwd_launches,
+                "share_of_step": bwd_ms / (ms / steps),
+                "hbm_gbs_moved": by_b / (bwd_ms / 1e3) / 1e9, "hbm_peak_gbs": hbm_peak}
 
-    # end to end through the public host-buffer API (pinned host memory)
+    # end to end through the host-buffer API (pinned host memory)
     e2e = None
     if not args.no_e2e:
-        P_pin = [torch.from_numpy(p).pin_memory() for p in P_host]
-        E_pin = [torch.empty(N_VEC, dtype=torch.float64).pin_memory() for _ in U_VALUES]
-        N_pin = [torch.empty(N_VEC, dtype=torch.float64).pin_memory() for _ in U_VALUES]
-
-        def step_host():
-            for k, eng in enumerate(engines):
-                eng.set_hamiltonian(H[k].x, H[k].z, H[k].c)
-                eng.slim(0.0)
-                eng.energy_batch_into(P_pin[k], E_pin[k], N_pin[k])
-        step_host()
-        torch.cuda.synchronize(dev)
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        P_pin = torch.from_numpy(P_host).pin_memory()
+        G_pin = torch.empty(1, 2 * n * D, dtype=torch.float64).pin_memory()
+        E_pin = torch.empty(1, dtype=torch.float64).pin_memory()
         barrier(pg, local)
+        torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            step_host()
+        for i in range(e2e_steps):
+            j = (args.steps - e2e_steps + i) % N_VEC
+            eng.gradient_batch_into(P_pin[j:j + 1], G_pin, E_pin)
         torch.cuda.synchronize(dev)
-        dt = time.perf_counter() - t0
-        dt = max_over_ranks(dt, pg, dev)
-        h2d = sum(p.numel() * 8 for p in P_pin) + sum(h.x.nbytes + h.z.nbytes + h.c.nbytes for h in H)
-        d2h = 2 * len(U_VALUES) * N_VEC * 8
-        e2e = {"value": evals / dt, "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
-        # the host path must agree with the device path bit for bit
-        for k in range(len(U_VALUES)):
-            assert np.array_equal(E_pin[k].numpy(), E_dev[k].cpu().numpy()), "e2e mismatch"
+        dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
+        e2e = {"value": e2e_steps * world / dt, "unit": "evals/s",
+               "h2d_bytes_per_step": int(P_pin[0].numel() * 8),
+               "d2h_bytes_per_step": int((G_pin.numel() + E_pin.numel()) * 8),
+               "steps": e2e_steps, "api": "vqe_gradient_batch (host buffers)"}
+        # the host path must agree with the device path bit for bit (same vector)
+        assert np.array_equal(G_pin[0].numpy(), g128), "e2e gradient differs from the device path"
 
-    pergate = None
-    if args.pergate and rank == 0:
-        # one-gate-per-pass reference kernel on one U, 64 vectors
-        sub = P_dev[0][:CHUNK]
-        e_sub = torch.empty(CHUNK, dtype=torch.float64, device=dev)
-        engines[0].energy_batch_dev(sub, e_sub, pergate=True)
-        torch.cuda.synchronize(dev)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        engines[0].energy_batch_dev(sub, e_sub, pergate=True)
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        t_pg = a.elapsed_time(b)
-        a.record(stream)
-        engines[0].energy_batch_dev(sub, E_dev[0][:CHUNK])
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        t_fu = a.elapsed_time(b)
-        pergate = {"pergate_evals_per_s": CHUNK / (t_pg / 1e3),
-                   "fused_evals_per_s": CHUNK / (t_fu / 1e3), "speedup": t_pg / t_fu,
-                   "max_abs_energy_diff": float((e_sub - E_dev[0][:CHUNK]).abs().max())}
+    # FP64 energy alone, unslimmed and slimmed (Sec. II-D)
+    p_last = P_dev[last:last + 1]
+    energy = {}
+    if not args.no_extras:
+        fe = lambda: eng.energy_batch_dev(p_last, E, Nrm)  # noqa: E731
+        fe()
+        t_full = _event_ms(stream, fe, 2)
+        e_full, nrm = float(E[0]), float(Nrm[0])
+        kept, dropped = eng.slim(SLIM_THRESHOLD)
+        fe()
+        t_slim = _event_ms(stream, fe, 2)
+        e_slim = float(E[0])
+        eng.slim(0.0)
+        energy = {"s_per_eval": t_full / 1e3, "energy": e_full, "norm": nrm,
+                  "slimmed": {"threshold": SLIM_THRESHOLD, "terms_kept": kept,
+                              "terms_canonical": eng.stats()["n_terms_canonical"],
+                              "sum_abs_dropped": dropped, "s_per_eval": t_slim / 1e3,
+                              "energy": e_slim, "abs_diff": abs(e_full - e_slim),
+                              "bound_holds": abs(e_full - e_slim) * nrm <= dropped * (1 + 1e-12)},
+                  "energy_from_gradient_call": e128}
+    eng.close()
+    del eng
+    torch.cuda.empty_cache()
+
+    # complex64 form of the same evaluation (FP64 accumulation)
+    c64 = None
+    if not args.no_extras:
+        e64 = pkg.Engine(n, D, "c64", stream=stream)
+        e64.set_hamiltonian(H.x, H.z, H.c)
+        G64 = torch.empty_like(G)
+        f64 = lambda: e64.gradient_batch_dev(p_last, G64, E)  # noqa: E731
+        f64()
+        e64.profile(True)
+        reps = 3
+        t64 = _event_ms(stream, f64, reps)
+        pr = e64.profile_read()
+        e64.profile(False)
+        g64 = G64[0].cpu().numpy()
+        E64 = float(E[0])
+        b_f, b_b = pass_bytes(n, D, "c64")
+        f_ms = pr["forward_passes"]["ms"] / reps
+        a_ms = pr["apply_h"]["ms"] / reps
+        b_ms = pr["backward_passes"]["ms"] / reps
+        st64 = 8.0 * (1 << n)
+        c64 = {"evals_per_s": 1e3 / t64, "s_per_eval": t64 / 1e3,
+               "speedup_vs_fp64": (ms / steps) / t64,
+               "energy_abs_err_vs_fp64": abs(E64 - e128),
+               "energy_err_over_sum_abs_c": abs(E64 - e128) / H.sum_abs(),
+               "gradient_rel_err_vs_fp64": float(np.max(np.abs(g64 - g128)) / np.max(np.abs(g128))),
+               "kernels": {"forward_passes": {"ms": f_ms, "hbm_gbs": b_f / (f_ms / 1e3) / 1e9},
+                           "apply_h": {"ms": a_ms,
+                                       "hbm_gbs_algorithmic": 2 * st64 / (a_ms / 1e3) / 1e9},
+                           "backward_passes": {"ms": b_ms, "hbm_gbs": b_b / (b_ms / 1e3) / 1e9}},
+               "hbm_gbs_algorithmic_eval": (6 * D + 2) * st64 / (t64 / 1e3) / 1e9,
+               "hbm_peak_gbs": hbm_peak}
+        e64.close()
+        del e64
+        torch.cuda.empty_cache()
 
     if rank == 0:
         line = {
@@ -365,22 +538,23 @@ def run_gpu(args, world, rank, local, pg):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "depth": DEPTH,
-                       "evals_per_step_per_gpu": len(U_VALUES) * N_VEC,
-                       "parallelism": f"replicas x{world}",
-                       "l2": f"working set > L2: {CHUNK} states x 16 MiB per chunk, 1 GiB"},
+            "config": {"workload": WORKLOAD, "n_qubits": n, "depth": D, "terms": len(H.c),
+                       "evals_per_step_per_gpu": 1, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2: psi and lambda 64 GiB each",
+                       "plan": tuned},
             "clocks": clocks, "gpu_launches": int(launches), "roofline": roofline,
-            "energy_kernel_ms_per_step": en_ms / args.steps,
-            "e2e": e2e,
+            "kernels_fp64": kernels, "e2e": e2e,
         }
-        if pergate:
-            line["pergate_vs_fused"] = pergate
+        if energy:
+            line["fp64_energy"] = energy
+        if c64:
+            line["c64_energy_gradient"] = c64
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline_sample(args.cpu_seconds)
         print(json.dumps(line), flush=True)
-    for e in engines:
-        e.close()
 
+
+# ---------------------------------------------------------------- other configurations
 
 def _timed(fn, reps):
     import torch
@@ -405,7 +579,36 @@ def run_workload(name: str, args):
     dev = torch.device("cuda", 0)
     line = {"metric": METRIC, "unit": "evals/s", "n_gpus": 1, "higher_is_better": True,
             "data": "synthetic", "scaling": "weak", "vs_baseline": None}
-    if name == "molecular24":
+    if name == "hubbard20":
+        # 20 qubits FP64: 10-site periodic chain, U in {2, 4, 8}, 1000 vectors per U, energy only
+        n, D, chunk = 20, 10, 64
+        Hs = [vi.hubbard_1d(10, 1.0, U, periodic=True) for U in (2.0, 4.0, 8.0)]
+        P = [torch.tensor(np.stack([vi.ansatz_params(1000 * k + j, n, D) for j in range(1000)]),
+                          device=dev) for k in range(3)]
+        E = torch.empty(1000, dtype=torch.float64, device=dev)
+        engs = [pkg.Engine(n, D, "c128") for _ in Hs]
+        ws = torch.empty(engs[0].workspace_size(chunk) // 16, dtype=torch.complex128, device=dev)
+        for e, H in zip(engs, Hs):
+            e.bind_workspace(ws)
+            e.set_hamiltonian(H.x, H.z, H.c)
+
+        def all_u():
+            for e, p in zip(engs, P):
+                e.energy_batch_dev(p, E)
+        ms = _timed(all_u, max(1, args.steps))
+        sub = P[0][:chunk]
+        e_sub = torch.empty(chunk, dtype=torch.float64, device=dev)
+        t_pg = _timed(lambda: engs[0].energy_batch_dev(sub, e_sub, pergate=True), 1)
+        t_fu = _timed(lambda: engs[0].energy_batch_dev(sub, E[:chunk]), 1)
+        line.update({"value": 3000 / (ms / 1e3), "dtype": "f64", "ms_per_step": ms,
+                     "config": {"workload": "20q FP64 10-site periodic 1D Hubbard t=1 U in {2,4,8}, "
+                                "HEA depth 10, 1000 param vectors per U, energy only"},
+                     "pergate_vs_fused": {"pergate_evals_per_s": chunk / (t_pg / 1e3),
+                                          "fused_evals_per_s": chunk / (t_fu / 1e3),
+                                          "speedup": t_pg / t_fu}})
+        for e in engs:
+            e.close()
+    elif name == "molecular24":
         # 24 qubits complex64: synthetic molecular-style Pauli sum, cutoff sweep
         H = vi.synthetic_molecular(12, seed=2024)
         n, D, B = 24, 12, 2
@@ -432,6 +635,7 @@ def run_workload(name: str, args):
                                 "JW), HEA depth 12, energy + adjoint gradient, cutoff sweep",
                                 "terms": len(H), "groups": H.n_groups},
                      "cutoff_sweep": rows})
+        eng.close()
     elif name == "batch512":
         inst = vi.batched_instances(512, seed=7)
         b = pkg.Batch([d["n"] for d in inst], [d["depth"] for d in inst], "c64",
@@ -464,58 +668,6 @@ def run_workload(name: str, args):
                      "fp64_one_by_one_baseline": {"value": 1.0 / per_inst,
                                                    "unit": "instance evals/s",
                                                    "sample": "first 32 instances, warm handles"}})
-    elif name == "hubbard32":
-        # 32 qubits: 4x4 periodic Hubbard (snake order), depth 8.  FP64 energy on
-        # one 64 GiB caller-owned state, unslimmed and slimmed (th = 0.6 drops
-        # every hopping term); complex64 energy + adjoint gradient on psi and
-        # lambda (2 x 32 GiB).
-        H = vi.hubbard_2d_snake(4, 4, 1.0, 4.0)
-        n, D = 32, 8
-        P = torch.tensor(vi.ansatz_params(3232, n, D)[None, :], device=dev)
-        E = torch.empty(1, dtype=torch.float64, device=dev)
-        G = torch.empty(1, 2 * n * D, dtype=torch.float64, device=dev)
-        eng = pkg.Engine(n, D, "c128")
-        eng.set_hamiltonian(H.x, H.z, H.c)
-        ws = torch.empty(1 << n, dtype=torch.complex128, device=dev)
-        eng.bind_workspace(ws)
-        eng.profile(True)
-        ms128 = _timed(lambda: eng.energy_batch_dev(P, E), 1)
-        pr = eng.profile_read()
-        e_full = float(E[0])
-        kept, dropped = eng.slim(0.6)
-        ms128s = _timed(lambda: eng.energy_batch_dev(P, E), 1)
-        e_slim = float(E[0])
-        passes128 = eng.stats()["ansatz_passes"]
-        eng.close()
-        del ws
-        torch.cuda.empty_cache()
-        e64 = pkg.Engine(n, D, "c64")
-        e64.set_hamiltonian(H.x, H.z, H.c)
-        e64.profile(True)
-        ms64 = _timed(lambda: e64.gradient_batch_dev(P, G, E), 1)
-        pg = e64.profile_read()
-        e64.close()
-        torch.cuda.empty_cache()
-        flops_fwd = D * (4 * n + 6) * float(1 << n)
-        fwd128_ms = pr["forward_passes"]["ms"] / 2
-        fwd64_ms = pg["forward_passes"]["ms"] / 2
-        bwd64_ms = pg["backward_passes"]["ms"] / 2
-        npass64 = pg["forward_passes"]["launches"] // 2
-        line.update({"value": 1e3 / ms64, "dtype": "c64", "ms_per_step": ms64,
-                     "config": {"workload": "32q 4x4 periodic Hubbard (snake order, t=1, U=4), "
-                                "HEA depth 8: complex64 energy + adjoint gradient (psi, lambda: "
-                                "2 x 32 GiB); FP64 energy on a 64 GiB state"},
-                     "fp64_energy": {"s_per_eval": ms128 / 1e3, "slimmed_s_per_eval": ms128s / 1e3,
-                                     "energy": e_full, "energy_slimmed": e_slim,
-                                     "terms_kept_slimmed": kept, "sum_abs_dropped": dropped,
-                                     "forward_tflops": flops_fwd / (fwd128_ms / 1e3) / 1e12,
-                                     "forward_passes": passes128},
-                     "c64_gradient": {"forward_ms": fwd64_ms, "backward_ms": bwd64_ms,
-                                      "apply_h_ms": pg["apply_h"]["ms"] / 2,
-                                      "forward_passes": npass64,
-                                      "forward_hbm_gbs": npass64 * 2 * 8 * float(1 << n) / (fwd64_ms / 1e3) / 1e9,
-                                      "backward_hbm_gbs": npass64 * 4 * 8 * float(1 << n) / (bwd64_ms / 1e3) / 1e9,
-                                      "hbm_peak_gbs": measured_peaks().get("hbm_gbs")}})
     elif name == "small8":
         H = vi.hubbard_1d(4, 1.0, 4.0, periodic=False)
         n, D, B = 8, 4, 1024
@@ -528,6 +680,7 @@ def run_workload(name: str, args):
         line.update({"value": B / (ms / 1e3), "dtype": "f64", "ms_per_step": ms,
                      "config": {"workload": "8q FP64 4-site open Hubbard, depth 4, energy + "
                                 "adjoint gradient, 1024 parameter vectors per step"}})
+        eng.close()
     elif name == "vqe8":
         # a whole VQE: 64 starts advanced together with Adam, one batched
         # adjoint gradient per step through the host-buffer API; the result
@@ -567,11 +720,13 @@ def run_case(name: str, batch: int):
     import torch
     import paper_2402_11878_gb300 as pkg
     import vqe_inputs as vi
-    cases = {  # name: (n, depth, precision, gradient)
-        "fwd20c128": (20, 10, "c128", False), "grad20c128": (20, 10, "c128", True),
-        "fwd24c64": (24, 4, "c64", False), "grad24c64": (24, 4, "c64", True),
-        "fwd26c64": (26, 4, "c64", False),
-        "mol24c64": (24, 2, "c64", True),   # synthetic molecular Hamiltonian, 12 orbitals
+    cases = {  # name: (n, depth, precision, gradient, Hamiltonian)
+        "fwd20c128": (20, 10, "c128", False, "chain"), "grad20c128": (20, 10, "c128", True, "chain"),
+        "fwd24c64": (24, 4, "c64", False, "chain"), "grad24c64": (24, 4, "c64", True, "chain"),
+        "fwd26c64": (26, 4, "c64", False, "chain"),
+        "mol24c64": (24, 2, "c64", True, "mol"),     # synthetic molecular Hamiltonian, 12 orbitals
+        "lat24c128": (24, 2, "c128", True, "lattice"),   # 4x3 periodic lattice: the 32q model's family
+        "lat24c64": (24, 2, "c64", True, "lattice"),
     }
     if name == "batch512":
         inst = vi.batched_instances(512, seed=7)
@@ -587,9 +742,13 @@ def run_case(name: str, batch: int):
         torch.cuda.synchronize()
         print("energies", E[:4].tolist())
         return
-    n, D, prec, grad = cases[name]
-    H = vi.synthetic_molecular(n // 2, 2024) if name.startswith("mol") else \
-        vi.hubbard_1d(n // 2, 1.0, 4.0, periodic=True)
+    n, D, prec, grad, kind = cases[name]
+    if kind == "mol":
+        H = vi.synthetic_molecular(n // 2, 2024)
+    elif kind == "lattice":
+        H = vi.hubbard_2d_snake(4, 3, 1.0, 4.0)
+    else:
+        H = vi.hubbard_1d(n // 2, 1.0, 4.0, periodic=True)
     eng = pkg.Engine(n, D, prec)
     eng.set_hamiltonian(H.x, H.z, H.c)
     P = torch.tensor(np.stack([vi.ansatz_params(j, n, D) for j in range(batch)]), device="cuda")
@@ -609,23 +768,26 @@ def main():
     ap.add_argument("--case", default=None,
                     help="run a small named workload for profiler captures instead of the benchmark")
     ap.add_argument("--case-batch", type=int, default=16)
-    ap.add_argument("--workload", default="hubbard20",
-                    choices=["hubbard20", "molecular24", "batch512", "small8", "hubbard32", "vqe8"],
-                    help="hubbard20 (default) is the benchmark line; the others report the "
+    ap.add_argument("--workload", default="hubbard32",
+                    choices=["hubbard32", "hubbard20", "molecular24", "batch512", "small8", "vqe8"],
+                    help="hubbard32 (default) is the benchmark line; the others report the "
                          "remaining configurations")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64-energy and complex64 legs beside the headline")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--pergate", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     args = ap.parse_args()
     if args.case:
         run_case(args.case, args.case_batch)
         return
-    if args.workload != "hubbard20" and args.impl != "reference":
+    if args.workload != "hubbard32" and args.impl != "reference":
         run_workload(args.workload, args)
         return
     if args.warmup < 3 and args.impl != "reference":

@@ -64,7 +64,7 @@ typedef enum {
     VQE_ERR_STATE = 2,    /* call out of order (e.g. energy before any ansatz) */
     VQE_ERR_OOM = 3,      /* device memory could not be allocated */
     VQE_ERR_CUDA = 4,     /* a CUDA runtime call or kernel launch failed */
-    VQE_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up (reported at the next synchronising call) */
+    VQE_ERR_TIMEOUT = 5,  /* reserved (no call of this version returns it) */
     VQE_ERR_DEVICE = 6    /* a kernel reported an internal error through its error word */
 } vqe_status;
 
@@ -112,15 +112,15 @@ vqe_status vqe_bind_workspace(vqe_handle h, void *dev_ptr, size_t bytes);
  * floating-point rounding order. */
 vqe_status vqe_set_plan_options(vqe_handle h, int tile_bits_max, int run_bits, int reg_bits);
 
-/* Kernel used for the ansatz passes: 0 (default) = one CTA per tile, first
- * and last register round straight from/to global memory; 1 = persistent
- * CTAs that pipeline tiles through shared memory with bulk copies; 2 =
- * persistent CTAs that prefetch their next tile into shared memory with
- * cp.async while running the current one (not for the first pass of a forward
- * sweep, which loads nothing).  A pass whose double-buffered tiles exceed
- * shared memory, or that uses 32 amplitudes per thread, runs with kind 0.
- * Results are identical. */
-vqe_status vqe_set_pass_kernel(vqe_handle h, int kind);
+/* Form of lambda = H psi in gradient evaluations (the adjoint's apply-H):
+ * mode 0 = one sweep over the state that gathers psi_{i^x} for every X-mask
+ * group; mode 1 = accumulated window by window over the expectation's tile
+ * windows (where every group fits a window, else the sweep); mode -1
+ * (default) = windows when they hold at least 10 groups each.  The choice
+ * persists across vqe_set_hamiltonian and vqe_slim; *windowed (may be NULL)
+ * reports the form the current Hamiltonian will use.  Results agree to
+ * rounding order. */
+vqe_status vqe_set_apply_mode(vqe_handle h, int mode, int *windowed);
 
 /* Set the Hamiltonian H = sum_t coeffs[t] * P(x_masks[t], z_masks[t])
  * (Sec. II-B, Eqs. 2-4).  Host arrays of length n_terms; masks must have no
@@ -178,6 +178,28 @@ vqe_status vqe_energy_batch_pergate_dev(vqe_handle h, const double *params_dev, 
                                         double *energies_dev, double *norms_dev);
 
 vqe_status vqe_get_stats(vqe_handle h, vqe_stats *out);
+
+/* Autotuner: times the evaluation of `batch` parameter vectors (device
+ * memory, as the *_batch_dev calls take them; gradient = 1 times energy +
+ * adjoint gradient, 0 the energy) under candidate tile plans (the default
+ * first, then other tile sizes -- the qubits fused per pass --, register
+ * counts and run lengths; see vqe_set_plan_options), and, for gradients, both
+ * forms of lambda = H psi (vqe_set_apply_mode) on the same state.  It keeps
+ * the fastest plan and form on the handle.  Candidates after the default are
+ * tried while the summed timed milliseconds stay below budget_ms.  Each
+ * candidate runs once untimed (while evaluations take under 2 s) and once
+ * timed with CUDA events on the handle's stream; the call synchronises.
+ * Results of every candidate agree to rounding order.  The state of
+ * vqe_apply_ansatz is discarded.  out (may be NULL) receives the choice. */
+typedef struct {
+    int tile_bits_max, run_bits, reg_bits;   /* chosen plan options (resolved values) */
+    int apply_windowed;                      /* 1: lambda = H psi over windows */
+    int candidates;                          /* plans timed */
+    double ms_default, ms_best;              /* per evaluation: default plan, chosen plan */
+    double apply_ms_global, apply_ms_windows;   /* per state, gradient tuning only (else 0) */
+} vqe_tuning;
+vqe_status vqe_autotune(vqe_handle h, const double *params_dev, int batch, int gradient,
+                        double budget_ms, vqe_tuning *out);
 
 /* Kernel timing by CUDA events on the handle's stream.  When enabled, each
  * evaluation chunk records an event pair around each of its kernel groups:

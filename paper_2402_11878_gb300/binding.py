@@ -22,15 +22,14 @@ STATUS = {0: "VQE_OK", 1: "VQE_ERR_ARG", 2: "VQE_ERR_STATE", 3: "VQE_ERR_OOM",
 # C ABI entry points declared in include/vqe.h and include/vqe_inspect.h
 EXPORTED = [
     "vqe_create", "vqe_destroy", "vqe_workspace_size", "vqe_bind_workspace", "vqe_set_plan_options",
-    "vqe_set_pass_kernel",
-    "vqe_set_hamiltonian", "vqe_slim", "vqe_apply_ansatz", "vqe_energy", "vqe_get_state",
+    "vqe_set_apply_mode", "vqe_autotune", "vqe_set_hamiltonian", "vqe_slim", "vqe_apply_ansatz", "vqe_energy", "vqe_get_state",
     "vqe_gradient", "vqe_energy_batch_dev", "vqe_gradient_batch_dev", "vqe_energy_batch",
     "vqe_gradient_batch", "vqe_energy_batch_pergate_dev", "vqe_get_stats", "vqe_last_error",
     "vqe_version", "vqe_profile", "vqe_profile_read", "vqe_inspect_sizeof", "vqe_inspect_plan",
     "vqe_inspect_hamiltonian", "vqe_inspect_windows", "vqe_energy_noalloc", "vqe_batch_create", "vqe_batch_destroy",
     "vqe_batch_set_hamiltonian", "vqe_batch_param_offsets", "vqe_batch_run_dev", "vqe_batch_run",
     "vqe_batch_set_tile_bits", "vqe_batch_autotune", "vqe_batch_launch_count",
-    "vqe_batch_last_error",
+    "vqe_batch_last_error", "vqe_measure_fma_peak", "vqe_testing_fail_allocations",
 ]
 
 
@@ -46,6 +45,14 @@ class Stats(ctypes.Structure):
                 ("n_groups", ctypes.c_uint64), ("sum_abs_dropped", ctypes.c_double),
                 ("threshold", ctypes.c_double), ("ansatz_passes", ctypes.c_uint32),
                 ("tile_bits_max", ctypes.c_uint32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile_bits_max", ctypes.c_int), ("run_bits", ctypes.c_int),
+                ("reg_bits", ctypes.c_int), ("apply_windowed", ctypes.c_int),
+                ("candidates", ctypes.c_int), ("ms_default", ctypes.c_double),
+                ("ms_best", ctypes.c_double), ("apply_ms_global", ctypes.c_double),
+                ("apply_ms_windows", ctypes.c_double)]
 
 
 class KernelTimes(ctypes.Structure):
@@ -104,9 +111,11 @@ def load() -> ctypes.CDLL:
         "vqe_batch_autotune": [vp, dp, dp, dp, i, ctypes.POINTER(i)],
         "vqe_batch_launch_count": [vp, ctypes.POINTER(ctypes.c_uint64)],
         "vqe_batch_last_error": [vp],
+        "vqe_measure_fma_peak": [i, vp, ctypes.POINTER(ctypes.c_double)],
         "vqe_inspect_plan": [i, i, i, vp, vp, vp, i, vp, i, vp, i, vp, vp],
         "vqe_set_plan_options": [vp, i, i, i],
-        "vqe_set_pass_kernel": [vp, i],
+        "vqe_set_apply_mode": [vp, i, ctypes.POINTER(i)],
+        "vqe_autotune": [vp, dp, i, i, ctypes.c_double, ctypes.POINTER(Tuning)],
         "vqe_inspect_hamiltonian": [i, vp, vp, vp, sz, ctypes.c_double, vp, i, vp, vp, i, vp,
                                     vp, vp],
         "vqe_inspect_windows": [i, i, vp, vp, vp, sz, ctypes.c_double, i, vp, i, vp, i, vp,
@@ -116,6 +125,8 @@ def load() -> ctypes.CDLL:
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.vqe_testing_fail_allocations.argtypes = [i]
+    lib.vqe_testing_fail_allocations.restype = None
     lib.vqe_last_error.restype = ctypes.c_char_p
     lib.vqe_batch_last_error.restype = ctypes.c_char_p
     lib.vqe_version.restype = ctypes.c_char_p
@@ -248,6 +259,13 @@ class Engine:
                                                  g.ctypes.data, e.ctypes.data))
         return g, e
 
+    def gradient_batch_into(self, params, grads, energies=None):
+        """Host buffers (NumPy arrays or pinned CPU tensors), written in place."""
+        count = params.numel() if hasattr(params, "numel") else params.size
+        b = count // self.n_params
+        self._check(self._lib.vqe_gradient_batch(self._h, _ptr(params), b, _ptr(grads),
+                                                 _ptr(energies)))
+
     def energy_batch_dev(self, params_dev, energies_dev, norms_dev=None, pergate=False):
         """Device tensors: params (batch x n_params, float64), energies (batch)."""
         b = params_dev.numel() // self.n_params
@@ -263,9 +281,21 @@ class Engine:
         """Choose the tile plan (0 = default); see vqe_set_plan_options."""
         self._check(self._lib.vqe_set_plan_options(self._h, tile_bits_max, run_bits, reg_bits))
 
-    def set_pass_kernel(self, kind: int):
-        """0: one CTA per tile (default), 1: pipelined persistent pass kernel."""
-        self._check(self._lib.vqe_set_pass_kernel(self._h, kind))
+    def set_apply_mode(self, mode: int) -> bool:
+        """lambda = H psi form: -1 automatic, 0 global sweep, 1 windows; returns
+        whether the current Hamiltonian will use the windows."""
+        out = ctypes.c_int()
+        self._check(self._lib.vqe_set_apply_mode(self._h, int(mode), ctypes.byref(out)))
+        return bool(out.value)
+
+    def autotune(self, params_dev, gradient: bool = True, budget_ms: float = 60000.0) -> dict:
+        """Time candidate tile plans (and apply-H forms) on device params and
+        keep the fastest (vqe_autotune); returns the choice."""
+        b = params_dev.numel() // self.n_params
+        t = Tuning()
+        self._check(self._lib.vqe_autotune(self._h, _ptr(params_dev), b, int(gradient),
+                                           float(budget_ms), ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
     def workspace_size(self, batch: int, gradient: bool = False) -> int:
         out = ctypes.c_size_t()
@@ -368,3 +398,13 @@ class Batch:
 
 def version() -> str:
     return load().vqe_version().decode()
+
+
+def measure_fma_peak(fp64: bool = True, stream=None) -> float:
+    """Measured FMA throughput of the current GPU in TFLOP/s (FP64 or FP32)."""
+    lib = load()
+    out = ctypes.c_double()
+    st = lib.vqe_measure_fma_peak(1 if fp64 else 0, _stream_ptr(stream), ctypes.byref(out))
+    if st:
+        raise VQEError(st, "vqe_measure_fma_peak failed")
+    return out.value

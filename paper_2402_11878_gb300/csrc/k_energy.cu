@@ -14,6 +14,7 @@
 // per CTA, and a fixed-order final sum, so results are bitwise reproducible.
 #include <algorithm>
 
+#include "csum.cuh"
 #include "vqe_internal.h"
 
 namespace vqe {
@@ -79,44 +80,31 @@ __device__ __forceinline__ void block_reduce2(double &a, double &b, double *sh) 
     }
 }
 
-// Block sum of two per-thread values for the FP32 kernels: a shuffle tree in
-// FP32 within each warp and one warp over the warp totals, so the FP64 pipe
-// (scarce on this GPU) sees only the conversions.  The result (thread 0) is
-// widened to FP64 for the fixed-order reduction across blocks.
-__device__ __forceinline__ void block_reduce2_f32(double &a, double &b, float *sh) {
-    float fa = (float)a, fb = (float)b;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        fa += __shfl_xor_sync(0xffffffffu, fa, o);
-        fb += __shfl_xor_sync(0xffffffffu, fb, o);
-    }
+// Block sum of two per-thread compensated FP32 values (the complex64 window
+// kernels): a fixed-order butterfly of compensated adds within each warp,
+// then one warp over the warp totals; thread 0 receives both totals widened
+// to FP64 for the fixed-order reduction across blocks.  Every add is an FP32
+// TwoSum, so the block total keeps about 48 bits without FP64 instructions.
+__device__ __forceinline__ void block_reduce2_c(F32c a, F32c b, float *sh, double &ra, double &rb) {
+    a = f32c_warp_sum(a, 0xffffffffu, 32);
+    b = f32c_warp_sum(b, 0xffffffffu, 32);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
-        sh[2 * warp] = fa;
-        sh[2 * warp + 1] = fb;
+        sh[4 * warp] = a.hi;
+        sh[4 * warp + 1] = a.lo;
+        sh[4 * warp + 2] = b.hi;
+        sh[4 * warp + 3] = b.lo;
     }
     __syncthreads();
     if (warp == 0) {
         const int nw = blockDim.x >> 5;
-        fa = lane < nw ? sh[2 * lane] : 0.f;
-        fb = lane < nw ? sh[2 * lane + 1] : 0.f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            fa += __shfl_xor_sync(0xffffffffu, fa, o);
-            fb += __shfl_xor_sync(0xffffffffu, fb, o);
-        }
-        a = (double)fa;
-        b = (double)fb;
+        a = lane < nw ? F32c{sh[4 * lane], sh[4 * lane + 1]} : f32c_zero();
+        b = lane < nw ? F32c{sh[4 * lane + 2], sh[4 * lane + 3]} : f32c_zero();
+        a = f32c_warp_sum(a, 0xffffffffu, 32);
+        b = f32c_warp_sum(b, 0xffffffffu, 32);
+        ra = f32c_value(a);
+        rb = f32c_value(b);
     }
-}
-
-// Block reduction for a window kernel of element type T.
-template <typename T>
-__device__ __forceinline__ void block_reduce2_t(double &a, double &b, double *sh) {
-    if constexpr (sizeof(T) == 4)
-        block_reduce2_f32(a, b, reinterpret_cast<float *>(sh));
-    else
-        block_reduce2(a, b, sh);
 }
 
 template <typename T>
@@ -136,7 +124,10 @@ k_energy_cols(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t
     double acc = 0.0, nrm = 0.0;
     for (int g = 0; g < n_groups; ++g) {
         const GroupDesc G = groups[g];
+        // a thread's sums over its pairs of the group: FP64, or compensated
+        // FP32 pairs in the FP32 kernel (one add per iteration of J pairs)
         T part = T(0), pn = T(0);
+        F32c cpart = f32c_zero(), cpn = f32c_zero();
         const int h = G.x ? G.h : 0;
         const uint64_t lowm = (1ull << h) - 1ull;
         const bool has_b = G.t_end > G.t_mid;
@@ -176,10 +167,18 @@ k_energy_cols(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t
                     sign_sums<T, J>(i0, f0, tz, tc, G.t_begin, G.t_mid);
                     sign_sums<T, J>(i1, f1, tz, tc, G.t_begin, G.t_mid);
                 }
+                T it = T(0), itn = T(0);
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
-                    part = fma(a0[j], f0[j], fma(a1[j], f1[j], part));
-                    pn += a0[j] + a1[j];
+                    it = fma(a0[j], f0[j], fma(a1[j], f1[j], it));
+                    itn += a0[j] + a1[j];
+                }
+                if constexpr (sizeof(T) == 4) {
+                    f32c_add(cpart, it);
+                    f32c_add(cpn, itn);
+                } else {
+                    part += it;
+                    pn += itn;
                 }
             } else {
                 T ar[J], ai[J], fa[J], fb[J];
@@ -194,13 +193,17 @@ k_energy_cols(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t
                 }
                 sign_sums<T, J>(i0, fa, tz, tc, G.t_begin, G.t_mid);
                 if (has_b) sign_sums<T, J>(i0, fb, tz, tc, G.t_mid, G.t_end);
+                T it = T(0);
 #pragma unroll
-                for (int j = 0; j < J; ++j) part = fma(ar[j], fa[j], has_b ? fma(ai[j], fb[j], part) : part);
+                for (int j = 0; j < J; ++j) it = fma(ar[j], fa[j], has_b ? fma(ai[j], fb[j], it) : it);
+                if constexpr (sizeof(T) == 4) f32c_add(cpart, it);
+                else part += it;
             }
         }
-        if (G.x == 0u) nrm += (double)pn;
-        else part *= T(2);
-        acc += (double)part;
+        double dpart = sizeof(T) == 4 ? f32c_value(cpart) : (double)part;
+        if (G.x == 0u) nrm += sizeof(T) == 4 ? f32c_value(cpn) : (double)pn;
+        else dpart *= 2.0;
+        acc += dpart;
     }
     block_reduce2(acc, nrm, sh);
     if (threadIdx.x == 0) {
@@ -549,7 +552,10 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
         for (int j = 0; j < EPT; ++j) sp[wpad<C>(tid + j * kEnergyWinThreads)] = x[j];
     }
     __syncthreads();
+    // Accumulators: FP64 in the FP64 kernels; in the FP32 kernels compensated
+    // FP32 pairs (csum.cuh), into which every group total is added.
     double acc = 0.0, nrm = 0.0;
+    F32c cacc = f32c_zero(), cnrm = f32c_zero();
     if (W.with_norm) {
         T pn = T(0);
 #pragma unroll
@@ -557,13 +563,9 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
             const C x = sp[wpad<C>(tid + j * kEnergyWinThreads)];
             pn += fma(x.x, x.x, x.y * x.y);
         }
-        nrm = (double)pn;
+        if constexpr (sizeof(T) == 4) cnrm.hi = pn;
+        else nrm = (double)pn;
     }
-    // FP32: group totals are summed in FP32 over runs of kRun groups and each
-    // run is folded into the FP64 accumulator (FP64 adds are scarce).
-    constexpr int kRun = 8;
-    T run = T(0);
-    int in_run = 0;
     for (int gi = 0; gi < W.g_end - W.g_begin; ++gi) {
         const WinGroup &G = sg[gi];
         T part = T(0);
@@ -681,19 +683,11 @@ k_energy_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__r
             }
             part *= T(2);
         }
-        if constexpr (sizeof(T) == 4) {
-            run += part;
-            if (++in_run == kRun) {
-                acc += (double)run;
-                run = T(0);
-                in_run = 0;
-            }
-        } else {
-            acc += (double)part;
-        }
+        if constexpr (sizeof(T) == 4) f32c_add(cacc, part);
+        else acc += (double)part;
     }
-    if constexpr (sizeof(T) == 4) acc += (double)run;
-    block_reduce2_t<T>(acc, nrm, sh);
+    if constexpr (sizeof(T) == 4) block_reduce2_c(cacc, cnrm, reinterpret_cast<float *>(sh), acc, nrm);
+    else block_reduce2(acc, nrm, sh);
     if (threadIdx.x == 0) {
         double *o = partials + ((size_t)b * bps_total + W.block_off + blockIdx.x) * 3;
         o[0] = acc;
@@ -891,7 +885,11 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
         nrm = (double)pn;
     }
     if (last) {   // uniform over the launch
-        block_reduce2_t<T>(acc, nrm, sh);
+        if constexpr (sizeof(T) == 4)
+            block_reduce2_c(F32c{(float)acc, 0.f}, F32c{(float)nrm, 0.f}, reinterpret_cast<float *>(sh),
+                            acc, nrm);
+        else
+            block_reduce2(acc, nrm, sh);
         if (threadIdx.x == 0) {
             double *o = partials + ((size_t)b * gridDim.x + blockIdx.x) * 3;
             o[0] = acc;

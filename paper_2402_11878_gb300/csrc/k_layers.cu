@@ -237,13 +237,14 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
     run_tile<T, R, BWD>(d, d.ops, d.n_ops, base, sp, sl, gsh, env);
 }
 
-// Gradient scratch of a fixed-shape backward pass: FP32 keeps one row of
-// per-thread partials per (tile bit, component); FP64 the per-warp totals of
-// the interpreter.
+// Gradient scratch of a fixed-shape backward pass, rows of per-thread
+// partials summed at the flush: FP32 one row per (tile bit, component); FP64
+// one theta row per tile bit, plus the phi total row and one row per
+// register bit (R = 3 in every FP64 program).
 template <typename T>
 __host__ __device__ inline size_t fixed_grad_scratch_bytes(int threads, int k) {
     return sizeof(T) == 4 ? size_t(threads) * 2 * k * sizeof(float)
-                          : tile_grad_scratch_bytes(threads, k);
+                          : size_t(threads) * (k + 1 + 3) * sizeof(double);
 }
 
 // Pass with a program shape fixed at compile time (run_tile_fixed); same
@@ -561,9 +562,17 @@ __global__ void k_zero_state(typename V2<T>::type *psi, size_t stride, int n) {
     }
 }
 
+// Grid of a grid-stride kernel: one thread per work item, at most 16 blocks
+// per SM of the current device.
 static unsigned grid_for(uint64_t work, int threads) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 1;
+    }
     uint64_t g = (work + threads - 1) / threads;
-    if (g > 152ull * 16) g = 152ull * 16;
+    if (g > uint64_t(sms) * 16) g = uint64_t(sms) * 16;
     if (g == 0) g = 1;
     return (unsigned)g;
 }

@@ -30,6 +30,7 @@ constexpr int kFlagSlot = 2 * kPartials;
 static __device__ __align__(256) double g_noalloc_scratch[2 * kPartials + 32];
 
 double *g_scratch_addr[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};
 std::once_flag g_scratch_once[kMaxDevices];
 cudaError_t g_scratch_err[kMaxDevices] = {};
 
@@ -136,17 +137,22 @@ __global__ void k_energy_terms_finish(const double *__restrict__ scratch, int bp
     if (norms) norms[s] = nn;
 }
 
-// Device address of the scratch array on `dev`, looked up once per device
-// with that device current.
-cudaError_t scratch_address(int dev, double **out) {
+// Device address of the scratch array on `dev` and the device's SM count,
+// looked up once per device with that device current.
+cudaError_t scratch_address(int dev, double **out, int *sms) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::call_once(g_scratch_once[dev], [dev]() {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        int n_sm = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) cudaGetLastError();
         g_scratch_err[dev] = e;
         g_scratch_addr[dev] = (e == cudaSuccess) ? static_cast<double *>(p) : nullptr;
+        g_sms[dev] = (e == cudaSuccess && n_sm > 0) ? n_sm : 1;
     });
     *out = g_scratch_addr[dev];
+    *sms = g_sms[dev];
     return g_scratch_err[dev];
 }
 
@@ -170,11 +176,12 @@ extern "C" vqe_status vqe_energy_noalloc(int n_qubits, vqe_precision precision,
         return VQE_ERR_CUDA;
     }
     double *scratch = nullptr;
-    if (scratch_address(dev, &scratch) != cudaSuccess || !scratch) return VQE_ERR_CUDA;
+    int sms = 1;
+    if (scratch_address(dev, &scratch, &sms) != cudaSuccess || !scratch) return VQE_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // blocks per state: about 4 per SM over the whole batch, all partials in scratch
     const uint64_t work = (uint64_t(1) << n_qubits) / kThreads;
-    int bps = (152 * 4 + batch - 1) / batch;
+    int bps = (sms * 4 + batch - 1) / batch;
     bps = std::min(bps, kPartials / batch);
     if (uint64_t(bps) > work) bps = int(std::max<uint64_t>(work, 1));
     bps = std::max(bps, 1);

@@ -1,6 +1,5 @@
 // Device core of the ansatz tile passes, shared by the grid kernels
-// (k_layers.cu), the bulk-copy pipelined kernel (k_pipe.cu) and the
-// persistent batched kernel (k_batch.cu).
+// (k_layers.cu) and the persistent batched kernel (k_batch.cu).
 //
 // A tile holds 2^k amplitudes of the state.  Its tile bits map to global
 // index bits as [0, m) -> [0, m) and [m, k) -> [a, a + k - m); `gbase` carries
@@ -26,6 +25,7 @@
 //        0 = `buf`/`lbuf` in plain order, 1 = the state in global memory (P, L)
 #pragma once
 
+#include "csum.cuh"
 #include "vqe_internal.h"
 
 namespace vqe {
@@ -298,12 +298,17 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                             gt = fma(-l0.x, p1.x, gt);
                             gt = fma(-l0.y, p1.y, gt);
                         }
-                        // warp sum in T (FP32 partials stay FP32 until the warp
-                        // total: FP64 adds are scarce), then FP64 per warp
-                        T wgt = gt * rc.gs;
-                        for (int o = wlanes >> 1; o > 0; o >>= 1)
-                            wgt += __shfl_xor_sync(wmask, wgt, o);
-                        const double dgt = (double)wgt;
+                        // warp sum: FP64, or compensated FP32 pairs (FP64 adds
+                        // are scarce on this GPU), then FP64 per warp
+                        double dgt;
+                        if constexpr (sizeof(T) == 4) {
+                            dgt = f32c_value(f32c_warp_sum(F32c{gt * rc.gs, 0.f}, wmask, wlanes));
+                        } else {
+                            T wgt = gt * rc.gs;
+                            for (int o = wlanes >> 1; o > 0; o >>= 1)
+                                wgt += __shfl_xor_sync(wmask, wgt, o);
+                            dgt = (double)wgt;
+                        }
                         if (lane == 0) gsh[(warp * k + chunk + j) * 2 + 0] = dgt;
                     }
                 }
@@ -408,8 +413,13 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                     } else {
                         gq = ((e0 >> q) & 1u) ? -tot : tot;
                     }
-                    for (int o = wlanes >> 1; o > 0; o >>= 1) gq += __shfl_xor_sync(wmask, gq, o);
-                    const double dg = (double)gq;
+                    double dg;
+                    if constexpr (sizeof(T) == 4) {
+                        dg = f32c_value(f32c_warp_sum(F32c{gq, 0.f}, wmask, wlanes));
+                    } else {
+                        for (int o = wlanes >> 1; o > 0; o >>= 1) gq += __shfl_xor_sync(wmask, gq, o);
+                        dg = (double)gq;
+                    }
                     if (lane == 0) gsh[(warp * k + q) * 2 + 1] = dg;
                 }
             }
@@ -555,6 +565,7 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                                                typename V2<T>::type *lbuf, double *gsh,
                                                Env &env) {
     static_assert(Env::kLoad == 1 && Env::kStore == 1 && Env::kDiagRow, "direct environment");
+    static_assert(!(BWD && sizeof(T) == 8) || R == 3, "FP64 gradient rows are sized for R = 3");
     using C = typename V2<T>::type;
     constexpr int NR = 1 << R;
     constexpr int N = sizeof...(Codes);
@@ -588,6 +599,7 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
     };
     C v[NR];
     C w[NR];
+    int diag_chunk = 0;   // chunk of the last diagonal op (FP64 backward flush)
     static_for<0, N>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int kind = code[i] >> 8;
@@ -669,9 +681,9 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                         // FP32: one shared-memory row per (bit, component), summed at the flush
                         reinterpret_cast<float *>(gsh)[(2 * (P + j) + 0) * nthr + t] = gt * rc.gs;
                     } else {
-                        T wgt = gt * rc.gs;
-                        for (int o = wlanes >> 1; o > 0; o >>= 1) wgt += __shfl_xor_sync(wmask, wgt, o);
-                        if (lane == 0) gsh[(warp * k + P + j) * 2 + 0] = (double)wgt;
+                        // FP64: row P + j of per-thread partials, summed (and scaled by gs)
+                        // at the flush: no shuffle tree per bit on the scarce FP64 pipe
+                        gsh[(P + j) * nthr + t] = gt;
                     }
                 }
 #pragma unroll
@@ -733,7 +745,31 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
             const PassOp op = ops[i];
             const uint32_t cz = d.slot_czmask[op.slot];
             const uint32_t e0 = elem_of(t, 0, P, R);
-            if constexpr (BWD) {
+            if constexpr (BWD && sizeof(T) == 8) {
+                // dE/dphi_q = Im<l|Z_q|p> = sum_i u_i (-1)^{bit_q(i)}, u = Im(conj(l) p),
+                // taken before the diagonal is undone.  FP64: each thread stores
+                // its total (row k) and its signed sums over the chunk's own bits
+                // (rows k + 1 + j); the flush sums the rows, taking the sign of a
+                // bit outside the chunk from the thread's element base.
+                T u[NR];
+                T tot = T(0);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    u[r] = fma(w[r].x, v[r].y, -w[r].y * v[r].x);
+                    tot += u[r];
+                }
+                const uint32_t gated = d.slot_gated[op.slot];
+                gsh[k * nthr + t] = tot;
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    if (!((gated >> (P + j)) & 1u)) continue;
+                    T gq = T(0);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) gq += ((r >> j) & 1) ? -u[r] : u[r];
+                    gsh[(k + 1 + j) * nthr + t] = gq;
+                }
+                diag_chunk = P;
+            } else if constexpr (BWD) {
                 // dE/dphi_q = Im<l|Z_q|p> = sum_i u_i (-1)^{bit_q(i)}, u = Im(conj(l) p),
                 // taken before the diagonal is undone
                 T u[NR];
@@ -802,7 +838,8 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
         } else if constexpr (kind == 4) {       // block totals of a slot's gradient partials
             if constexpr (BWD && sizeof(T) == 4) {
                 // each warp sums whole rows in a fixed order: lanes add a strided
-                // part of the row, then a shuffle tree (bitwise reproducible)
+                // part of the row, then a shuffle tree (bitwise reproducible);
+                // every add is a compensated FP32 add (csum.cuh)
                 const PassOp op = ops[i];
                 __syncthreads();
                 const uint32_t gated = d.slot_gated[op.slot];
@@ -810,24 +847,36 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                 const float *gpt = reinterpret_cast<const float *>(gsh);
                 for (int idx = warp; idx < 2 * k; idx += nw) {
                     if (!((gated >> (idx >> 1)) & 1u)) continue;
-                    float sum = 0.f;
-                    for (uint32_t tt = lane; tt < nthr; tt += 32) sum += gpt[idx * nthr + tt];
-                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-                    if (lane == 0) env.grad(op.slot, idx >> 1, idx & 1, (double)sum);
+                    F32c sum = f32c_zero();
+                    for (uint32_t tt = lane; tt < nthr; tt += 32) f32c_add(sum, gpt[idx * nthr + tt]);
+                    sum = f32c_warp_sum(sum, 0xffffffffu, 32);
+                    if (lane == 0) env.grad(op.slot, idx >> 1, idx & 1, f32c_value(sum));
                 }
                 __syncthreads();
             } else if constexpr (BWD) {
+                // FP64: each warp sums whole rows in a fixed order (lanes add a
+                // strided part, then a shuffle tree): theta rows scaled by the
+                // bit's gs, phi from the chunk rows or the signed total row
                 const PassOp op = ops[i];
                 __syncthreads();
                 const uint32_t gated = d.slot_gated[op.slot];
-                const int used_warps = (int)((nthr + 31) >> 5);
-                if (threadIdx.x == 0) {
-                    for (int idx = 0; idx < 2 * k; ++idx) {
-                        if (!((gated >> (idx >> 1)) & 1u)) continue;
-                        double s = 0.0;
-                        for (int wi = 0; wi < used_warps; ++wi) s += gsh[wi * 2 * k + idx];
-                        env.grad(op.slot, idx >> 1, idx & 1, s);
+                const int nw = (int)((nthr + 31) >> 5);
+                const int dp = diag_chunk;
+                for (int idx = warp; idx < 2 * k; idx += nw) {
+                    const int q = idx >> 1, comp = idx & 1;
+                    if (!((gated >> q) & 1u)) continue;
+                    double sum = 0.0;
+                    if (comp == 0) {
+                        for (uint32_t tt = lane; tt < nthr; tt += 32) sum += gsh[q * nthr + tt];
+                    } else if (q >= dp && q < dp + R) {
+                        for (uint32_t tt = lane; tt < nthr; tt += 32) sum += gsh[(k + 1 + q - dp) * nthr + tt];
+                    } else {
+                        for (uint32_t tt = lane; tt < nthr; tt += 32)
+                            sum += flip_sign(gsh[k * nthr + tt], (elem_of(tt, 0, dp, R) >> q) & 1u);
                     }
+                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                    if (lane == 0)
+                        env.grad(op.slot, q, comp, comp == 0 ? sum * (double)env.coef(op.slot, q).gs : sum);
                 }
                 __syncthreads();
             }

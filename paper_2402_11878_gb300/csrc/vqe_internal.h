@@ -260,24 +260,4 @@ cudaError_t launch_init_zero_state(void *psi, size_t stride, int n, int batch, c
 int pass_threads(const PassDesc &d);
 size_t pass_smem_bytes(const PassDesc &d, bool backward, size_t elem_bytes);
 
-// Persistent, bulk-copy pipelined variant of launch_pass (k_pipe.cu): two
-// tile buffers per CTA; *err is set to 1 if a bounded wait gives up.
-template <typename T>
-cudaError_t launch_pass_pipe(const PassDesc *desc_dev, const PassDesc &desc_host, int n_qubits,
-                             int batch, void *psi, void *lam, size_t state_stride,
-                             const RotCoef<T> *coefs, size_t coef_stride, const void *dtab,
-                             size_t dtab_stride, double *grad_part, size_t grad_stride,
-                             bool backward, int init_zero, int *err, int sms, cudaStream_t s);
-size_t pipe_smem_bytes(const PassDesc &d, bool backward, size_t elem_bytes);
-
-// Software-pipelined pass (k_pass_sp.cu): persistent CTAs prefetch the next
-// tile with cp.async while running the current one.  Not for init_zero passes.
-template <typename T>
-cudaError_t launch_pass_sp(const PassDesc *desc_dev, const PassDesc &desc_host, int n_qubits,
-                           int batch, void *psi, void *lam, size_t state_stride,
-                           const RotCoef<T> *coefs, size_t coef_stride, const void *dtab,
-                           size_t dtab_stride, double *grad_part, size_t grad_stride,
-                           bool backward, int sms, cudaStream_t s);
-size_t sp_smem_bytes(const PassDesc &d, bool backward, size_t elem_bytes);
-
 }  // namespace vqe

@@ -75,17 +75,22 @@ def minimize_batch(engine, params0, steps: int = 300, lr: float = 0.05,
 
 # ---------------------------------------------------------------- cutoff ratio
 
-def merged_abs_coefficients(x_masks, z_masks, coeffs) -> np.ndarray:
+def merged_abs_coefficients(x_masks, z_masks, coeffs, n_qubits: int = 0) -> np.ndarray:
     """|c| of the Pauli strings after merging equal (x, z) pairs and dropping
-    exact zeros (the terms the library's cutoff acts on), largest first."""
-    x = np.asarray(x_masks, dtype=np.uint64)
-    z = np.asarray(z_masks, dtype=np.uint64)
-    c = np.asarray(coeffs, dtype=np.float64)
-    keys = np.stack([x, z], axis=1)
-    _, inv = np.unique(keys, axis=0, return_inverse=True)
-    merged = np.zeros(int(inv.max()) + 1 if inv.size else 0)
-    np.add.at(merged, inv.ravel(), c)
-    a = np.abs(merged[merged != 0.0])
+    exact zeros (the terms the library's cutoff acts on), largest first.
+
+    The canonical terms come from the library's own canonicalisation (its
+    host-side plan inspection), so the threshold chosen from them matches what
+    ``vqe_slim`` keeps.  ``n_qubits`` defaults to the highest mask bit + 1."""
+    from . import plans
+    x = np.ascontiguousarray(x_masks, dtype=np.uint64)
+    z = np.ascontiguousarray(z_masks, dtype=np.uint64)
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    if not n_qubits:
+        top = int(np.bitwise_or.reduce(x | z)) if x.size else 0
+        n_qubits = max(1, top.bit_length())
+    prep = plans.hamiltonian(n_qubits, x, z, c, 0.0)
+    a = np.abs(np.asarray(prep["tc"], dtype=np.float64))
     return np.sort(a)[::-1]
 
 

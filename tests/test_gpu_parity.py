@@ -54,17 +54,22 @@ def test_config_small_hubbard_c128_state_and_energy(eng_mod, oracle_mod, seed):
 SIZES = [1, 2, 3, 4, 5, 7, 8, 9, 12, 13, 14, 15, 16, 17, 18]
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2])
+# tile plans: the default, and two others the autotuner considers (smaller
+# tiles with 4 amplitudes per thread; larger tiles)
+PLANS = [(0, 0, 0), (9, 2, 2), (12, 0, 3)]
+
+
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("n", SIZES)
-def test_random_pauli_sum_all_sizes(eng_mod, oracle_mod, prec, n, kernel):
+def test_random_pauli_sum_all_sizes(eng_mod, oracle_mod, prec, n, plan):
     """Every plan shape (single tile, multi-pass, ragged groups) on random Pauli sums with Y
-    terms, with the one-CTA-per-tile kernel (0) and the pipelined persistent kernel (1)."""
+    terms, under three tile plans."""
     D = 2 if n > 12 else 3
     H = vi.random_pauli_sum(n, 40, seed=100 + n, duplicates=3)
     p = vi.ansatz_params(7 + n, n, D)
     eng = make(eng_mod, n, D, prec, H)
-    eng.set_pass_kernel(kernel)
+    eng.set_plan_options(*plan)
     eng.apply_ansatz(p)
     psi = eng.get_state()
     ref = oracle_mod.ansatz_state(n, D, p)
@@ -88,17 +93,15 @@ def test_batched_energies(eng_mod, oracle_mod, prec):
         check_energy(E[b], E_ref, H, prec)
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("plan", PLANS)
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("n,D", [(2, 2), (3, 2), (8, 4), (13, 2), (14, 2), (16, 2), (17, 1)])
-def test_adjoint_gradient(eng_mod, oracle_mod, prec, n, D, kernel):
+def test_adjoint_gradient(eng_mod, oracle_mod, prec, n, D, plan):
     H = vi.random_pauli_sum(n, 30, seed=200 + n) if n % 2 else vi.hubbard_1d(n // 2, 1.0, 4.0)
     H = vi.PauliSum(n, H.x, H.z, H.c)
     p = vi.ansatz_params(300 + n, n, D)
     eng = make(eng_mod, n, D, prec, H)
-    eng.set_pass_kernel(kernel)
-    if kernel == 1 and n > 12:
-        eng.set_plan_options(11 if prec == "c128" else 12, 0, 0)   # backward tiles fit twice
+    eng.set_plan_options(*plan)
     g, E = eng.gradient(p)
     g_ref, E_ref = oracle_mod.gradient_adjoint(n, D, p, H.x, H.z, H.c)
     check_energy(E, E_ref, H, prec)
@@ -264,3 +267,63 @@ def test_windowed_energy_batch(eng_mod, oracle_mod, prec, case):
         ref = oracle_mod.ansatz_state(n, D, P[b])
         E_ref, _ = oracle_mod.energy(ref, H.x, H.z, H.c)
         check_energy(E[b], E_ref, H, prec)
+
+
+def test_20q_fp64_windowed_energy_bench_chunks(eng_mod, oracle_mod):
+    """20 qubits FP64 with a batch of 64 states (the chunk the 20-qubit bench
+    workload runs): the windowed expectation kernel must be the one taken, and
+    three of the states' energies must match the oracle to 1e-11 sum|c|."""
+    import torch
+    n, D, B = 20, 10, 64
+    H = vi.hubbard_1d(10, 1.0, 4.0, periodic=True)
+    P = np.stack([vi.ansatz_params(7000 + b, n, D) for b in range(B)])
+    eng = make(eng_mod, n, D, "c128", H)
+    Pd = torch.tensor(P, device="cuda")
+    E = torch.empty(B, dtype=torch.float64, device="cuda")
+    eng.profile(True)
+    eng.energy_batch_dev(Pd, E)
+    prof = eng.profile_read()
+    eng.profile(False)
+    from paper_2402_11878_gb300 import plans
+    wins = plans.windows(n, "c128", H.x, H.z, H.c, diag_terms=False)
+    n_win = len(wins["windows"])
+    assert n_win >= 2
+    assert prof["energy"]["launches"] == n_win      # one launch per window: the windowed kernel
+    E = E.cpu().numpy()
+    for b in (0, 31, 63):
+        ref = oracle_mod.ansatz_state(n, D, P[b])
+        E_ref, _ = oracle_mod.energy(ref, H.x, H.z, H.c)
+        check_energy(E[b], E_ref, H, "c128")
+    eng.close()
+
+
+@pytest.mark.parametrize("batch", [1, 4])
+def test_c64_energy_accumulation_matches_fp64_on_same_state(eng_mod, oracle_mod, batch):
+    """Complex64 mode keeps its energy sums at FP64-level accuracy: a
+    Hamiltonian dominated by a large identity and large Z terms, with small
+    hopping terms, evaluated by the complex64 kernels (global sweep for one
+    state, windows for four) against the FP64 oracle on the very same
+    complex64 state.  Products of FP32 amplitudes round independently, so the
+    remaining difference is far below what FP32 running sums over 2^20
+    amplitudes would leave."""
+    import torch
+    n, D = 20, 2
+    base = vi.hubbard_1d(10, 1.0, 4.0, periodic=True)
+    zx = np.array([0] * n, dtype=np.uint64)
+    zz = np.array([1 << q for q in range(n)], dtype=np.uint64)
+    zc = 100.0 * (1.0 + 0.1 * np.arange(n))
+    x = np.concatenate([base.x, zx, [0]]).astype(np.uint64)
+    z = np.concatenate([base.z, zz, [0]]).astype(np.uint64)
+    c = np.concatenate([1e-2 * base.c, zc, [1e3]])
+    H = vi.PauliSum(n, x, z, c)
+    P = np.stack([vi.ansatz_params(8100 + b, n, D) for b in range(batch)])
+    eng = make(eng_mod, n, D, "c64", H)
+    eng.apply_ansatz(P[0])
+    psi = eng.get_state().astype(np.complex128)
+    E_same, _ = oracle_mod.energy(psi, H.x, H.z, H.c)
+    Pd = torch.tensor(P, device="cuda")
+    E = torch.empty(batch, dtype=torch.float64, device="cuda")
+    eng.energy_batch_dev(Pd, E)
+    got = float(E[0])
+    assert abs(got - E_same) <= 2e-9 * H.sum_abs(), (got, E_same, abs(got - E_same) / H.sum_abs())
+    eng.close()

@@ -32,7 +32,7 @@ def _worker(rank, world, port, out):
         ms_local = 10.0 + 5.0 * rank                 # rank 1 is the slowest
         ms = bench.max_over_ranks(ms_local, dist)
         value = bench.job_throughput(1000, world, ms)
-        first = bench.make_params(rank)[0][0]         # first vector of the first U
+        first = bench.make_params(rank)[0]            # the rank's first parameter vector
         out[rank] = (ms, value, float(first[0]), float(first[1]))
         bench.barrier(dist)
     finally:

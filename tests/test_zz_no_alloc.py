@@ -7,6 +7,9 @@ synchronisation, plug-ins handed raw device pointers).  The test calls it
 through the C ABI twice in a row, with different batch sizes, precisions and
 Hamiltonians, and compares each result with the energies of the regular
 entry point (vqe_energy_batch) at the tolerances used by the other GPU tests.
+The energies are also compared with the FP64 oracle (Eq. 7 evaluated term
+by term on the same states), and a term with a mask bit at or above n_qubits
+must turn every energy of that call, and only that call, into NaN.
 This file is collected last, so a failure here leaves every other test run.
 """
 import ctypes
@@ -62,7 +65,7 @@ def run_noalloc(lib, n, prec, psi, H):
     return e.cpu().numpy(), nn.cpu().numpy()
 
 
-def test_noalloc_energy_matches_regular_entry_point_twice(lib_built):
+def test_noalloc_energy_matches_regular_entry_point_twice(lib_built, oracle_mod):
     import torch
     assert torch.cuda.is_available()
     import paper_2402_11878_gb300 as pkg
@@ -76,6 +79,10 @@ def test_noalloc_energy_matches_regular_entry_point_twice(lib_built):
     E1, N1 = run_noalloc(lib, n, "c128", psi1, H1)
     assert np.max(np.abs(E1 - E1_ref)) <= TOL["c128"] * H1.sum_abs()
     assert np.max(np.abs(N1 - N1_ref)) <= 1e-12
+    for b in range(len(P1)):   # the oracle on the oracle's own state
+        E_orc, N_orc = oracle_mod.energy(oracle_mod.ansatz_state(n, D, P1[b]), H1.x, H1.z, H1.c)
+        assert abs(E1[b] - E_orc) <= TOL["c128"] * H1.sum_abs()
+        assert abs(N1[b] - N_orc) <= 1e-12
 
     # call 2: complex64 states, 2 of them, a Hubbard Hamiltonian on another size
     n2, D2 = 14, 2
@@ -85,6 +92,29 @@ def test_noalloc_energy_matches_regular_entry_point_twice(lib_built):
     E2, N2 = run_noalloc(lib, n2, "c64", psi2, H2)
     assert np.max(np.abs(E2 - E2_ref)) <= TOL["c64"] * H2.sum_abs()
     assert np.max(np.abs(N2 - N2_ref)) <= 1e-5
+    for b in range(len(P2)):   # FP64 oracle on the same complex64 state
+        psi_b = psi2[b].cpu().numpy().astype(np.complex128)
+        E_orc, _ = oracle_mod.energy(psi_b, H2.x, H2.z, H2.c)
+        assert abs(E2[b] - E_orc) <= TOL["c64"] * H2.sum_abs()
+
+
+def test_noalloc_invalid_term_sets_nan_for_that_call_only(lib_built):
+    """A term whose X mask has bit n set is skipped before any memory access and
+    makes every energy of the call NaN; the next valid call is finite again."""
+    import torch
+    import paper_2402_11878_gb300 as pkg
+    lib = pkg.load()
+    n, D = 9, 2
+    H = vi.hubbard_1d(4, 1.0, 3.0, periodic=False)
+    P = np.stack([vi.ansatz_params(970 + b, n, D) for b in range(3)])
+    psi, E_ref, _ = states_and_reference(pkg, n, D, "c128", H, P)
+    bad = vi.PauliSum(n, np.append(H.x, np.uint64(1) << np.uint64(n)), np.append(H.z, np.uint64(0)),
+                      np.append(H.c, 0.5))
+    E_bad, _ = run_noalloc(lib, n, "c128", psi, bad)
+    assert np.all(np.isnan(E_bad))
+    E_ok, _ = run_noalloc(lib, n, "c128", psi, H)
+    assert np.all(np.isfinite(E_ok))
+    assert np.max(np.abs(E_ok - E_ref)) <= TOL["c128"] * H.sum_abs()
 
 
 def test_noalloc_rejects_batch_beyond_limit(lib_built):

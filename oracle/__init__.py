@@ -162,3 +162,65 @@ def gradient_fd(n: int, depth: int, params, x, z, c, h: float = 1e-5) -> np.ndar
     _load().orc_gradient_fd(ctypes.c_int(n), ctypes.c_int(depth), _d(p), ctypes.c_size_t(c.size),
                             _u(x), _u(z), _d(c), ctypes.c_double(h), _d(g))
     return g
+
+
+# ---------------------------------------------------------------- particle-conserving ansatz
+
+def _exc(exc):
+    e = np.ascontiguousarray(exc, dtype=np.int32).reshape(-1, 4)
+    return e, e.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def apply_excitation(psi: np.ndarray, exc, theta: float) -> np.ndarray:
+    """exp(theta (T - T^dag)) psi for one excitation (p, q, r, s) (Sec. II-B, Eq. 5)."""
+    n = int(psi.size).bit_length() - 1
+    out = np.ascontiguousarray(psi, dtype=np.complex128).copy()
+    e, ep = _exc(exc)
+    _load().orc_apply_excitation(ctypes.c_int(n), out.ctypes.data_as(ctypes.c_void_p), ep,
+                                 ctypes.c_double(theta))
+    return out
+
+
+def excitation_generator(psi: np.ndarray, exc) -> np.ndarray:
+    n = int(psi.size).bit_length() - 1
+    src = np.ascontiguousarray(psi, dtype=np.complex128)
+    out = np.empty_like(src)
+    e, ep = _exc(exc)
+    _load().orc_excitation_generator(ctypes.c_int(n), src.ctypes.data_as(ctypes.c_void_p), ep,
+                                     out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def pc_ansatz_state(n: int, n_elec: int, exc, theta) -> np.ndarray:
+    """psi(theta) = U(theta) psi_HF of the particle-conserving ansatz (Eqs. 5-6)."""
+    e, ep = _exc(exc)
+    t = np.ascontiguousarray(theta, dtype=np.float64)
+    assert t.size == e.shape[0]
+    psi = np.empty(1 << n, dtype=np.complex128)
+    _load().orc_pc_ansatz(ctypes.c_int(n), ctypes.c_int(n_elec), ctypes.c_int(e.shape[0]), ep, _d(t),
+                          psi.ctypes.data_as(ctypes.c_void_p))
+    return psi
+
+
+def pc_gradient_adjoint(n: int, n_elec: int, exc, theta, x, z, c):
+    """Adjoint gradient of <psi|H|psi> for the particle-conserving ansatz; (grad, energy)."""
+    e, ep = _exc(exc)
+    t = np.ascontiguousarray(theta, dtype=np.float64)
+    x, z, c = _terms(x, z, c)
+    g = np.empty(max(e.shape[0], 1))
+    en = ctypes.c_double()
+    _load().orc_pc_gradient_adjoint(ctypes.c_int(n), ctypes.c_int(n_elec), ctypes.c_int(e.shape[0]),
+                                    ep, _d(t), ctypes.c_size_t(c.size), _u(x), _u(z), _d(c), _d(g),
+                                    ctypes.byref(en))
+    return g[:e.shape[0]], en.value
+
+
+def pc_gradient_fd(n: int, n_elec: int, exc, theta, x, z, c, h: float = 1e-5) -> np.ndarray:
+    e, ep = _exc(exc)
+    t = np.ascontiguousarray(theta, dtype=np.float64)
+    x, z, c = _terms(x, z, c)
+    g = np.empty(max(e.shape[0], 1))
+    _load().orc_pc_gradient_fd(ctypes.c_int(n), ctypes.c_int(n_elec), ctypes.c_int(e.shape[0]), ep,
+                               _d(t), ctypes.c_size_t(c.size), _u(x), _u(z), _d(c),
+                               ctypes.c_double(h), _d(g))
+    return g[:e.shape[0]]

@@ -311,3 +311,136 @@ void orc_gradient_fd(int n, int depth, const double *params, size_t n_terms,
     free(psi);
     free(p);
 }
+
+/* ---------------------------------------------------------------- particle-conserving ansatz
+ *
+ * Sec. II-B, Eq. 5: U(theta) = prod D_pqrs(theta_pqrs) prod S_pq(theta_pq), applied to
+ * the Hartree-Fock state (Eq. 6 with psi_HF).  The paper takes S and D from
+ * an earlier gate set without printing them; the reading used here is the
+ * fermionic excitation exp(theta (T - T^dag)) of the excitation operator
+ * T = a_p^dag a_r (single) or T = a_p^dag a_q^dag a_r a_s (double) under the
+ * Jordan-Wigner mapping (occupied mode m = bit m set), written out by
+ * applying the ladder operators to basis states one at a time. */
+
+/* a_m^dag (create = 1) or a_m (create = 0) on basis state *j: returns the
+ * Jordan-Wigner sign (-1)^(number of occupied modes below m) and updates *j,
+ * or returns 0 when the state is annihilated. */
+static int jw_ladder(uint64_t *j, int m, int create) {
+    const uint64_t bit = (uint64_t)1 << m;
+    const int occupied = (*j & bit) != 0;
+    if (create == occupied) return 0;
+    int parity = 0;
+    for (int k = 0; k < m; ++k) parity ^= (int)((*j >> k) & 1);
+    *j ^= bit;
+    return parity ? -1 : 1;
+}
+
+/* T|j> = sign |*out> for the excitation exc = (p, q, r, s): T = a_p^dag a_r
+ * when q < 0 (s ignored), else a_p^dag a_q^dag a_r a_s; operators act right
+ * to left.  Returns 0 when T|j> = 0. */
+static int excitation_apply(const int exc[4], uint64_t j, uint64_t *out) {
+    int sign = 1;
+    if (exc[1] < 0) {
+        int s1 = jw_ladder(&j, exc[2], 0);
+        if (!s1) return 0;
+        int s2 = jw_ladder(&j, exc[0], 1);
+        if (!s2) return 0;
+        sign = s1 * s2;
+    } else {
+        const int modes[4] = {exc[3], exc[2], exc[1], exc[0]};
+        const int create[4] = {0, 0, 1, 1};
+        for (int k = 0; k < 4; ++k) {
+            int sk = jw_ladder(&j, modes[k], create[k]);
+            if (!sk) return 0;
+            sign *= sk;
+        }
+    }
+    *out = j;
+    return sign;
+}
+
+void orc_apply_excitation(int n, double complex *psi, const int exc[4], double theta) {
+    const int64_t dim = (int64_t)1 << n;
+    const double c = cos(theta), s = sin(theta);
+    /* exp(theta G), G = T - T^dag, on each pair (j, j') with T|j> = sgn |j'>:
+     * G|j> = sgn |j'>, G|j'> = -sgn |j>. */
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < dim; ++j) {
+        uint64_t jp;
+        const int sgn = excitation_apply(exc, (uint64_t)j, &jp);
+        if (!sgn) continue;
+        const double complex a = psi[j], b = psi[jp];
+        psi[j] = c * a - sgn * s * b;
+        psi[jp] = c * b + sgn * s * a;
+    }
+}
+
+void orc_excitation_generator(int n, const double complex *psi, const int exc[4],
+                              double complex *out) {
+    const int64_t dim = (int64_t)1 << n;
+    memset(out, 0, sizeof(double complex) * (size_t)dim);
+    for (int64_t j = 0; j < dim; ++j) {
+        uint64_t jp;
+        const int sgn = excitation_apply(exc, (uint64_t)j, &jp);
+        if (!sgn) continue;
+        out[jp] += sgn * psi[j];      /* T   |j>  = sgn |j'> */
+        out[j] -= sgn * psi[jp];      /* -T^dag |j'> = -sgn |j> */
+    }
+}
+
+void orc_pc_ansatz(int n, int n_elec, int n_exc, const int *exc, const double *theta,
+                   double complex *psi) {
+    const int64_t dim = (int64_t)1 << n;
+    memset(psi, 0, sizeof(double complex) * (size_t)dim);
+    const uint64_t hf = n_elec >= 64 ? ~(uint64_t)0 : (((uint64_t)1 << n_elec) - 1);
+    psi[hf] = 1.0;
+    for (int k = 0; k < n_exc; ++k) orc_apply_excitation(n, psi, exc + 4 * k, theta[k]);
+}
+
+void orc_pc_gradient_adjoint(int n, int n_elec, int n_exc, const int *exc, const double *theta,
+                             size_t n_terms, const uint64_t *x, const uint64_t *z,
+                             const double *c, double *grad, double *energy) {
+    const int64_t dim = (int64_t)1 << n;
+    const size_t bytes = sizeof(double complex) * (size_t)dim;
+    double complex *psi = (double complex *)malloc(bytes);
+    double complex *lam = (double complex *)malloc(bytes);
+    double complex *mu = (double complex *)malloc(bytes);
+    orc_pc_ansatz(n, n_elec, n_exc, exc, theta, psi);
+    orc_apply_h(n, psi, n_terms, x, z, c, lam);
+    double e = 0.0;
+    for (int64_t i = 0; i < dim; ++i) e += creal(conj(psi[i]) * lam[i]);
+    *energy = e;
+    /* psi holds U_k ... U_1 psi_HF and lambda the adjoint state at the same
+     * point: g_k = 2 Re <lambda| G_k |psi>, then both step back through U_k. */
+    for (int k = n_exc - 1; k >= 0; --k) {
+        orc_excitation_generator(n, psi, exc + 4 * k, mu);
+        double s = 0.0;
+        for (int64_t i = 0; i < dim; ++i) s += creal(conj(lam[i]) * mu[i]);
+        grad[k] = 2.0 * s;
+        orc_apply_excitation(n, psi, exc + 4 * k, -theta[k]);
+        orc_apply_excitation(n, lam, exc + 4 * k, -theta[k]);
+    }
+    free(mu);
+    free(lam);
+    free(psi);
+}
+
+void orc_pc_gradient_fd(int n, int n_elec, int n_exc, const int *exc, const double *theta,
+                        size_t n_terms, const uint64_t *x, const uint64_t *z, const double *c,
+                        double h, double *grad) {
+    const int64_t dim = (int64_t)1 << n;
+    double *p = (double *)malloc(sizeof(double) * (size_t)(n_exc ? n_exc : 1));
+    double complex *psi = (double complex *)malloc(sizeof(double complex) * (size_t)dim);
+    for (int j = 0; j < n_exc; ++j) {
+        memcpy(p, theta, sizeof(double) * (size_t)n_exc);
+        p[j] = theta[j] + h;
+        orc_pc_ansatz(n, n_elec, n_exc, exc, p, psi);
+        const double ep = energy_of(n, psi, n_terms, x, z, c);
+        p[j] = theta[j] - h;
+        orc_pc_ansatz(n, n_elec, n_exc, exc, p, psi);
+        const double em = energy_of(n, psi, n_terms, x, z, c);
+        grad[j] = (ep - em) / (2.0 * h);
+    }
+    free(psi);
+    free(p);
+}

@@ -70,6 +70,25 @@ void orc_gradient_fd(int n, int depth, const double *params, size_t n_terms,
                      const uint64_t *x, const uint64_t *z, const double *c,
                      double h, double *grad);
 
+/* Particle-conserving ansatz (Sec. II-B, Eqs. 5-6): excitation k is four
+ * ints exc[4k..4k+3] = (p, q, r, s), the operator T = a_p^dag a_q^dag a_r a_s
+ * (double) or, with q = -1, T = a_p^dag a_r (single; s ignored); its gate is
+ * exp(theta_k (T - T^dag)) under the Jordan-Wigner mapping.  The circuit
+ * applies excitations 0, 1, ... in order to psi_HF = the basis state with
+ * modes 0 .. n_elec-1 occupied. */
+void orc_apply_excitation(int n, double complex *psi, const int exc[4], double theta);
+/* out <- (T - T^dag) psi */
+void orc_excitation_generator(int n, const double complex *psi, const int exc[4],
+                              double complex *out);
+void orc_pc_ansatz(int n, int n_elec, int n_exc, const int *exc, const double *theta,
+                   double complex *psi);
+void orc_pc_gradient_adjoint(int n, int n_elec, int n_exc, const int *exc, const double *theta,
+                             size_t n_terms, const uint64_t *x, const uint64_t *z,
+                             const double *c, double *grad, double *energy);
+void orc_pc_gradient_fd(int n, int n_elec, int n_exc, const int *exc, const double *theta,
+                        size_t n_terms, const uint64_t *x, const uint64_t *z, const double *c,
+                        double h, double *grad);
+
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
 int orc_threads(void);
 

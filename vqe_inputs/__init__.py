@@ -350,3 +350,43 @@ def random_pauli_sum(n: int, n_terms: int, seed: int, with_identity: bool = True
         z = np.concatenate([z, z[:k]])
         c = np.concatenate([c, 0.5 * c[:k]])
     return PauliSum(n=n, x=x, z=z, c=c)
+
+
+def excitations(n_qubits: int, n_elec: int, n_singles: int | None = None,
+                n_doubles: int | None = None, seed: int = 0) -> np.ndarray:
+    """Excitation list of the particle-conserving ansatz (Sec. II-B, Eq. 5):
+    rows ``(p, q, r, s)``, singles ``(p, -1, r, -1)`` = a_p^dag a_r and doubles
+    ``(p, q, r, s)`` = a_p^dag a_q^dag a_r a_s, from the occupied modes of the
+    Hartree-Fock state (modes ``0 .. n_elec-1``) to the virtual ones, spin
+    conserving (mode ``2*site + spin``).  The paper picks its excitations from
+    CISD coefficients it does not print; here ``n_singles`` / ``n_doubles``
+    (``None`` = all) are drawn without replacement by a seeded shuffle.
+    Rows are in the order of application: Eq. 5's product read in time order
+    (as the ansatz layer of Eq. 6 is), so the D gates act first and the S
+    gates last, the singles acting as an orbital rotation of the correlated
+    state."""
+    occ = [m for m in range(n_elec)]
+    vir = [m for m in range(n_elec, n_qubits)]
+    singles = [(p, -1, r, -1) for r in occ for p in vir if (p & 1) == (r & 1)]
+    doubles = []
+    for i, r in enumerate(occ):
+        for s in occ[i + 1:]:
+            for j, p in enumerate(vir):
+                for q in vir[j + 1:]:
+                    if (p & 1) + (q & 1) == (r & 1) + (s & 1):
+                        doubles.append((p, q, r, s))
+
+    def pick(items, k, stream):
+        if k is None or k >= len(items):
+            return items
+        keys = uniform01(seed, len(items), stream=stream)
+        order = np.sort(np.argsort(keys, kind="stable")[:k])
+        return [items[i] for i in order]
+
+    rows = pick(doubles, n_doubles, 42) + pick(singles, n_singles, 41)
+    return np.array(rows, dtype=np.int32).reshape(-1, 4)
+
+
+def excitation_params(seed: int, n_exc: int, scale: float = 0.5, stream: int = 43) -> np.ndarray:
+    """Excitation angles, i.i.d. U[-scale*pi, scale*pi)."""
+    return (2.0 * uniform01(seed, n_exc, stream=stream) - 1.0) * scale * np.pi

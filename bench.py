@@ -668,6 +668,56 @@ def run_workload(name: str, args):
                      "fp64_one_by_one_baseline": {"value": 1.0 / per_inst,
                                                    "unit": "instance evals/s",
                                                    "sample": "first 32 instances, warm handles"}})
+    elif name == "pc32":
+        # the particle-conserving ansatz (Sec. II-B, Eqs. 5-6) on the 32-qubit
+        # lattice at half filling: 118 excitation gates (the parameter count
+        # of the paper's 32-qubit run; 102 doubles then 16 singles drawn from
+        # the spin-conserving pool) on the Hartree-Fock state; FP64 and
+        # complex64 energy + adjoint gradient
+        H = hamiltonian()
+        n, ne = N_QUBITS, N_QUBITS // 2
+        exc = vi.excitations(n, ne, n_singles=16, n_doubles=102, seed=32)
+        th = torch.tensor(vi.excitation_params(3232, len(exc))[None, :], device=dev)
+        E = torch.empty(1, dtype=torch.float64, device=dev)
+        G = torch.empty(1, len(exc), dtype=torch.float64, device=dev)
+        out = {}
+        for prec in ("c128", "c64"):
+            eng = pkg.Engine.particle_conserving(n, ne, exc, prec)
+            eng.set_hamiltonian(H.x, H.z, H.c)
+            tune = eng.autotune(th, gradient=True, budget_ms=0.0)
+            eng.gradient_batch_dev(th, G, E)
+            eng.profile(True)
+            ms = _timed(lambda: eng.gradient_batch_dev(th, G, E), max(1, args.steps))
+            pr = eng.profile_read()
+            eng.profile(False)
+            reps = max(1, args.steps) + 1
+            st = 16.0 if prec == "c128" else 8.0
+            npass = eng.stats()["ansatz_passes"]
+            f_ms = pr["forward_passes"]["ms"] / reps
+            b_ms = pr["backward_passes"]["ms"] / reps
+            out[prec] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms, "energy": float(E[0]),
+                         "passes": npass, "apply_windowed": tune["apply_windowed"],
+                         "forward_ms": f_ms, "apply_h_ms": pr["apply_h"]["ms"] / reps,
+                         "backward_ms": b_ms,
+                         "forward_hbm_gbs": npass * 2 * st * float(1 << n) / (f_ms / 1e3) / 1e9,
+                         "backward_hbm_gbs": npass * 4 * st * float(1 << n) / (b_ms / 1e3) / 1e9,
+                         "grad_inf": float(G.abs().max())}
+            g = G[0].cpu().numpy().copy()
+            if prec == "c128":
+                g128 = g
+            else:
+                out["c64"]["gradient_rel_err_vs_fp64"] = float(np.max(np.abs(g - g128)) / np.max(np.abs(g128)))
+                out["c64"]["energy_abs_err_vs_fp64"] = abs(out["c64"]["energy"] - out["c128"]["energy"])
+            eng.close()
+            torch.cuda.empty_cache()
+        line.update({"value": out["c128"]["evals_per_s"], "dtype": "f64",
+                     "ms_per_step": out["c128"]["ms_per_eval"],
+                     "config": {"workload": "32q particle-conserving ansatz (102 doubles + 16 singles on "
+                                "the Hartree-Fock state, 16 electrons) on the 4x4 periodic Hubbard "
+                                "lattice: FP64 energy + adjoint gradient (complex64 beside it)",
+                                "excitations": len(exc)},
+                     "fp64": out["c128"], "c64": out["c64"],
+                     "hbm_peak_gbs": measured_peaks().get("hbm_gbs")})
     elif name == "small8":
         H = vi.hubbard_1d(4, 1.0, 4.0, periodic=False)
         n, D, B = 8, 4, 1024
@@ -769,7 +819,8 @@ def main():
                     help="run a small named workload for profiler captures instead of the benchmark")
     ap.add_argument("--case-batch", type=int, default=16)
     ap.add_argument("--workload", default="hubbard32",
-                    choices=["hubbard32", "hubbard20", "molecular24", "batch512", "small8", "vqe8"],
+                    choices=["hubbard32", "hubbard20", "molecular24", "batch512", "small8", "vqe8",
+                             "pc32"],
                     help="hubbard32 (default) is the benchmark line; the others report the "
                          "remaining configurations")
     ap.add_argument("--gpus", type=int, default=1)

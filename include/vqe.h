@@ -88,6 +88,23 @@ typedef struct {
  * the one current on the calling thread. */
 vqe_status vqe_create(int n_qubits, int depth, vqe_precision precision, void *cuda_stream,
                       vqe_handle *out);
+/* Create a handle whose ansatz is the particle-conserving one of Sec. II-B
+ * (Eqs. 5-6): psi(theta) = U(theta) psi_HF, psi_HF the basis state with modes
+ * 0 .. n_elec-1 occupied (mode m = qubit m, occupied = 1, Jordan-Wigner
+ * mapping), and U the product of n_exc fermionic excitation gates
+ * exp(theta_j (T_j - T_j^dag)) applied in the order given.  Excitation j is
+ * four ints excitations[4j .. 4j+3] = (p, q, r, s):
+ *   q >= 0: double, T = a_p^dag a_q^dag a_r a_s (p, q, r, s distinct);
+ *   q = -1 and s = -1: single, T = a_p^dag a_r (p != r).
+ * Modes must lie in 0 .. n_qubits-1 (VQE_ERR_ARG otherwise).  Parameters are
+ * theta_j, one per excitation (n_exc doubles).  Every other call works as for
+ * vqe_create (Hamiltonian, cutoff, energies, adjoint gradients, batches,
+ * autotuner) except vqe_set_plan_options and the one-gate-per-pass kernel,
+ * which return VQE_ERR_ARG.  The array is copied.  Consecutive gates whose
+ * modes fit one shared-memory tile share one pass over the state. */
+vqe_status vqe_create_pc(int n_qubits, int n_elec, int n_exc, const int *excitations,
+                         vqe_precision precision, void *cuda_stream, vqe_handle *out);
+
 /* Free the handle and every device buffer the library allocated. */
 vqe_status vqe_destroy(vqe_handle h);
 

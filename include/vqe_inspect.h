@@ -18,8 +18,8 @@ extern "C" {
 #endif
 
 /* sizeof of internal record `which`: 0 = pass descriptor, 1 = staging slot,
- * 2 = term group, 3 = energy window, 4 = window group, 5 = window term; 0 for
- * an unknown `which`. */
+ * 2 = term group, 3 = energy window, 4 = window group, 5 = window term,
+ * 6 = excitation pass, 7 = excitation gate; 0 for an unknown `which`. */
 size_t vqe_inspect_sizeof(int which);
 
 /* Tile-pass plan of the ansatz for (n, depth, precision, options) -- options
@@ -63,6 +63,15 @@ int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
                         int max_windows,
                         void *wgroups, int max_wgroups, void *wterms, int max_wterms,
                         uint32_t *hoff, int max_hoff, void *wide, int max_wide, int counts[5]);
+
+/* Pass plan of the particle-conserving ansatz (vqe_create_pc) for the same
+ * arguments: excitation passes (max_passes), their gates with tile masks and
+ * sign masks (max_gates), and the passes' high-part offset tables
+ * (max_hoff).  counts[3] = passes, gates, offsets.  Returns 0, or -1 on
+ * invalid arguments or too-small buffers. */
+int vqe_inspect_pc_plan(int n_qubits, int precision, int n_exc, const int *excitations,
+                        void *passes, int max_passes, void *gates, int max_gates, uint32_t *hoff,
+                        int max_hoff, int counts[3]);
 
 #ifdef __cplusplus
 }

@@ -21,12 +21,12 @@ STATUS = {0: "VQE_OK", 1: "VQE_ERR_ARG", 2: "VQE_ERR_STATE", 3: "VQE_ERR_OOM",
 
 # C ABI entry points declared in include/vqe.h and include/vqe_inspect.h
 EXPORTED = [
-    "vqe_create", "vqe_destroy", "vqe_workspace_size", "vqe_bind_workspace", "vqe_set_plan_options",
+    "vqe_create", "vqe_create_pc", "vqe_destroy", "vqe_workspace_size", "vqe_bind_workspace", "vqe_set_plan_options",
     "vqe_set_apply_mode", "vqe_autotune", "vqe_set_hamiltonian", "vqe_slim", "vqe_apply_ansatz", "vqe_energy", "vqe_get_state",
     "vqe_gradient", "vqe_energy_batch_dev", "vqe_gradient_batch_dev", "vqe_energy_batch",
     "vqe_gradient_batch", "vqe_energy_batch_pergate_dev", "vqe_get_stats", "vqe_last_error",
     "vqe_version", "vqe_profile", "vqe_profile_read", "vqe_inspect_sizeof", "vqe_inspect_plan",
-    "vqe_inspect_hamiltonian", "vqe_inspect_windows", "vqe_energy_noalloc", "vqe_batch_create", "vqe_batch_destroy",
+    "vqe_inspect_hamiltonian", "vqe_inspect_windows", "vqe_inspect_pc_plan", "vqe_energy_noalloc", "vqe_batch_create", "vqe_batch_destroy",
     "vqe_batch_set_hamiltonian", "vqe_batch_param_offsets", "vqe_batch_run_dev", "vqe_batch_run",
     "vqe_batch_set_tile_bits", "vqe_batch_autotune", "vqe_batch_launch_count",
     "vqe_batch_last_error", "vqe_measure_fma_peak", "vqe_testing_fail_allocations",
@@ -81,6 +81,7 @@ def load() -> ctypes.CDLL:
     vp, i, sz, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
     sig = {
         "vqe_create": [i, i, i, vp, ctypes.POINTER(vp)],
+        "vqe_create_pc": [i, i, i, vp, i, vp, ctypes.POINTER(vp)],
         "vqe_destroy": [vp],
         "vqe_workspace_size": [vp, i, i, ctypes.POINTER(sz)],
         "vqe_bind_workspace": [vp, vp, sz],
@@ -120,6 +121,7 @@ def load() -> ctypes.CDLL:
                                     vp, vp],
         "vqe_inspect_windows": [i, i, vp, vp, vp, sz, ctypes.c_double, i, vp, i, vp, i, vp,
                                 i, vp, i, vp, i, vp],
+        "vqe_inspect_pc_plan": [i, i, i, vp, vp, i, vp, i, vp, i, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -161,22 +163,41 @@ def _stream_ptr(stream):
 
 
 class Engine:
-    """One VQE problem size on the current CUDA device (a vqe_handle)."""
+    """One VQE problem size on the current CUDA device (a vqe_handle).
 
-    def __init__(self, n_qubits: int, depth: int, precision: str = "c64", stream=None):
+    ``Engine(n, depth, precision)`` uses the hardware-efficient ansatz;
+    ``Engine.particle_conserving(n, n_elec, excitations, precision)`` the
+    excitation-gate ansatz on the Hartree-Fock state (vqe_create_pc)."""
+
+    def __init__(self, n_qubits: int, depth: int, precision: str = "c64", stream=None,
+                 _excitations=None, _n_elec: int = 0):
         lib = load()
         self._lib = lib
         self.n = int(n_qubits)
         self.depth = int(depth)
         self.precision = precision
         prec = {"c64": VQE_C64, "c128": VQE_C128}[precision]
-        self.n_params = 2 * self.n * self.depth
         self.state_dtype = np.complex64 if prec == VQE_C64 else np.complex128
         h = ctypes.c_void_p()
-        st = lib.vqe_create(self.n, self.depth, prec, _stream_ptr(stream), ctypes.byref(h))
+        if _excitations is None:
+            self.n_params = 2 * self.n * self.depth
+            st = lib.vqe_create(self.n, self.depth, prec, _stream_ptr(stream), ctypes.byref(h))
+        else:
+            exc = np.ascontiguousarray(_excitations, dtype=np.int32).reshape(-1, 4)
+            self.n_params = exc.shape[0]
+            self.excitations = exc
+            st = lib.vqe_create_pc(self.n, int(_n_elec), exc.shape[0], exc.ctypes.data, prec,
+                                   _stream_ptr(stream), ctypes.byref(h))
         if st != 0:
             raise VQEError(st, "vqe_create failed (is a CUDA device available?)")
         self._h = h
+
+    @classmethod
+    def particle_conserving(cls, n_qubits: int, n_elec: int, excitations, precision: str = "c64",
+                            stream=None) -> "Engine":
+        """Excitation rows (p, q, r, s) as vqe_create_pc takes them; one
+        parameter per row."""
+        return cls(n_qubits, 1, precision, stream, _excitations=excitations, _n_elec=n_elec)
 
     def _check(self, st: int):
         if st != 0:

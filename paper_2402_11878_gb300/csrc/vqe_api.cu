@@ -121,6 +121,15 @@ struct vqe_ctx {
     DevBuf hb_params, hb_e, hb_n, hb_g;   // device copies for the host-buffer batch calls
     int scratch_batch = 0;
 
+    // particle-conserving ansatz (vqe_create_pc); ansatz 0 = hardware-efficient
+    int ansatz = 0;
+    int n_elec = 0;
+    uint64_t hf_index = 0;
+    std::vector<int> exc;                // 4 per excitation, in the order of application
+    std::vector<ExcPass> pc_passes;
+    DevBuf d_pc_gates, d_pc_hoff;
+    int pc_k = 0;
+
     // apply-H form: -1 automatic, 0 one global sweep, 1 windowed (where possible)
     int apply_mode = -1;
     int sms = 0;
@@ -590,7 +599,166 @@ vqe_status build_one_plan(vqe_ctx *h, int which) {
     return VQE_OK;
 }
 
+// ---------------------------------------------------------------- particle-conserving plan
+
+struct PcHostPlan {
+    std::vector<ExcPass> passes;
+    std::vector<ExcGate> gates;
+    std::vector<uint32_t> hoff;
+    std::vector<int> goff, gcnt, gstep;
+    size_t grad_stride = 0;
+    int k = 0;
+};
+
+// Passes of the excitation sequence: runs of consecutive gates (at most
+// kExcMaxGates) whose modes outside the low run [0, m) fit the k - m further
+// tile bits.  Tiles hold 2^k amplitudes: 2^11 (32 KiB) in FP64, 2^12 in FP32,
+// with contiguous runs of 2^m = 256 bytes.
+bool make_pc_plan(int n, vqe_precision prec, const std::vector<int> &exc, PcHostPlan &pp,
+                  std::string &err) {
+    pp = PcHostPlan{};
+    int k = prec == VQE_C128 ? 11 : 12;
+    int m = prec == VQE_C128 ? 4 : 5;
+    if (n <= k) {
+        k = n;
+        m = n;
+    }
+    const int hi = k - m;
+    pp.k = k;
+    const int K = int(exc.size() / 4);
+    auto high_bits = [&](int j) {
+        uint32_t b = 0;
+        for (int u = 0; u < 4; ++u) {
+            const int md = exc[4 * j + u];
+            if (md >= m) b |= 1u << md;
+        }
+        return b;
+    };
+    std::vector<std::pair<int, int>> runs;   // (first gate, count)
+    uint32_t cur = 0;
+    int first = 0;
+    for (int j = 0; j < K; ++j) {
+        const uint32_t hb = high_bits(j);
+        const int cnt = j - first;
+        if (cnt > 0 && (__builtin_popcount(cur | hb) > hi || cnt >= kExcMaxGates)) {
+            runs.push_back({first, cnt});
+            first = j;
+            cur = 0;
+        }
+        cur |= hb;
+        if (__builtin_popcount(cur) > hi) {
+            err = "an excitation spans more modes than a tile holds";
+            return false;
+        }
+    }
+    if (K > first) runs.push_back({first, K - first});
+    const uint64_t tiles = uint64_t(1) << (n - k);
+    size_t goff = 0;
+    pp.goff.assign(K, 0);
+    pp.gcnt.assign(K, 0);
+    pp.gstep.assign(K, 0);
+    for (const auto &r : runs) {
+        uint32_t S = 0;
+        for (int j = r.first; j < r.first + r.second; ++j) S |= high_bits(j);
+        for (int b = m; b < n && __builtin_popcount(S) < hi; ++b) S |= 1u << b;   // fill with low bits
+        std::vector<int> pos;
+        for (int b = 0; b < n; ++b)
+            if ((S >> b) & 1u) pos.push_back(b);
+        const uint32_t nmask = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+        const uint32_t tile_global = ((1u << m) - 1u) | S;
+        auto to_tile = [&](uint32_t g) {   // global mask restricted to tile bits -> tile coordinates
+            uint32_t t = g & ((1u << m) - 1u);
+            for (size_t j = 0; j < pos.size(); ++j)
+                if ((g >> pos[j]) & 1u) t |= 1u << (m + int(j));
+            return t;
+        };
+        ExcPass P{};
+        P.k = k;
+        P.m = m;
+        P.g_begin = int(pp.gates.size());
+        P.n_gates = r.second;
+        P.hoff = int(pp.hoff.size());
+        P.bmask = nmask & ~tile_global;
+        if (goff > 0x7fffffff) {
+            err = "gradient partials exceed 2^31 entries";
+            return false;
+        }
+        P.grad_off = int(goff);
+        for (uint32_t hh = 0; hh < (1u << hi); ++hh) {
+            uint32_t g = 0;
+            for (int j = 0; j < hi; ++j)
+                if ((hh >> j) & 1u) g |= 1u << pos[j];
+            pp.hoff.push_back(g);
+        }
+        for (int j = r.first; j < r.first + r.second; ++j) {
+            const int p = exc[4 * j], q = exc[4 * j + 1], rr = exc[4 * j + 2], ss = exc[4 * j + 3];
+            const bool dbl = q >= 0;
+            auto below = [](int md) { return md >= 32 ? 0xffffffffu : ((1u << md) - 1u); };
+            uint32_t amask_g = 1u << rr, cmask_g = 1u << p;
+            uint32_t smask = below(p) ^ below(rr);
+            uint32_t sign0;
+            if (dbl) {
+                amask_g |= 1u << ss;
+                cmask_g |= 1u << q;
+                smask ^= below(q) ^ below(ss);
+                sign0 = uint32_t((ss < rr) + (ss < q) + (rr < q) + (ss < p) + (rr < p) + (q < p)) & 1u;
+            } else {
+                sign0 = uint32_t(rr < p);
+            }
+            ExcGate G{};
+            G.amask = to_tile(amask_g);
+            G.cmask = to_tile(cmask_g);
+            G.smask_t = to_tile(smask & tile_global);
+            G.smask_g = smask & ~tile_global;
+            G.sign0 = sign0;
+            const uint32_t fixed = G.amask | G.cmask;
+            G.n_fixed = __builtin_popcount(fixed);
+            int u = 0;
+            for (int b = 0; b < k; ++b)
+                if ((fixed >> b) & 1u) G.fixed[u++] = uint8_t(b);
+            G.param = j;
+            pp.gates.push_back(G);
+            pp.goff[j] = int(goff) + (j - r.first);
+            pp.gcnt[j] = int(tiles);
+            pp.gstep[j] = r.second;
+        }
+        pp.passes.push_back(P);
+        goff += size_t(tiles) * r.second;
+    }
+    pp.grad_stride = goff;
+    return true;
+}
+
+vqe_status build_pc_plan(vqe_ctx *h) {
+    PcHostPlan pp;
+    std::string err;
+    if (!make_pc_plan(h->n, h->prec, h->exc, pp, err)) return fail(h, VQE_ERR_ARG, err);
+    vqe_status st;
+    if ((st = upload(h, h->d_pc_gates, pp.gates, "excitation gates")) != VQE_OK) return st;
+    if ((st = upload(h, h->d_pc_hoff, pp.hoff, "excitation tiles")) != VQE_OK) return st;
+    vqe_ctx::DevPlan &P = h->plan[1];
+    if ((st = upload(h, P.d_goff, pp.goff, "grad map")) != VQE_OK) return st;
+    if ((st = upload(h, P.d_gcnt, pp.gcnt, "grad map")) != VQE_OK) return st;
+    if ((st = upload(h, P.d_gstep, pp.gstep, "grad map")) != VQE_OK) return st;
+    h->pc_passes = pp.passes;
+    h->pc_k = pp.k;
+    for (int w = 0; w < 2; ++w) {
+        h->plan[w].fwd.clear();
+        h->plan[w].bwd.clear();
+        h->plan[w].groups.clear();
+        h->plan[w].coef_stride = h->exc.size() / 4;   // (cos, sin) per excitation
+        h->plan[w].dtab_stride = 0;
+        h->plan[w].grad_stride = pp.grad_stride;
+        h->plan[w].n_stage = 0;
+    }
+    h->n_params = int(h->exc.size() / 4);
+    h->stats.ansatz_passes = uint32_t(pp.passes.size());
+    h->stats.tile_bits_max = uint32_t(pp.k);
+    return VQE_OK;
+}
+
 vqe_status build_plan(vqe_ctx *h) {
+    if (h->ansatz == 1) return build_pc_plan(h);
     for (int w = 0; w < 2; ++w) {
         vqe_status st = build_one_plan(h, w);
         if (st != VQE_OK) return st;
@@ -1243,8 +1411,46 @@ cudaError_t launch_any_pass(vqe_ctx *h, const vqe_ctx::DevPlan &P, const PassDes
                           h->stream);
 }
 
+// Particle-conserving forward sweep: (cos, sin) of every excitation, then
+// the passes in order, the first one starting from psi_HF.
+template <typename T>
+vqe_status run_forward_pc(vqe_ctx *h, const double *params_dev, int B, void *psi) {
+    const int K = h->n_params;
+    T *cs = static_cast<T *>(h->d_coefs.p);
+    VQE_CUDA(h, launch_exc_stage<T>(params_dev, K, B, cs, h->stream));
+    h->stats.kernel_launches++;
+    const int mk = prof_begin(h, 0);
+    for (size_t p = 0; p < h->pc_passes.size(); ++p) {
+        VQE_CUDA(h, launch_exc_pass<T>(h->pc_passes[p], static_cast<const ExcGate *>(h->d_pc_gates.p),
+                                       static_cast<const uint32_t *>(h->d_pc_hoff.p), h->n, B, psi,
+                                       nullptr, h->state_elems(), cs, K, nullptr, 0, false,
+                                       p == 0 ? 1 : 0, h->hf_index, h->stream));
+        h->stats.kernel_launches++;
+    }
+    prof_end(h, mk, int(h->pc_passes.size()));
+    return VQE_OK;
+}
+
+template <typename T>
+vqe_status run_backward_pc(vqe_ctx *h, int B, void *psi, void *lam) {
+    const int K = h->n_params;
+    const T *cs = static_cast<const T *>(h->d_coefs.p);
+    double *gpart = static_cast<double *>(h->d_gpart.p);
+    const int mk = prof_begin(h, 3);
+    for (int p = int(h->pc_passes.size()) - 1; p >= 0; --p) {
+        VQE_CUDA(h, launch_exc_pass<T>(h->pc_passes[p], static_cast<const ExcGate *>(h->d_pc_gates.p),
+                                       static_cast<const uint32_t *>(h->d_pc_hoff.p), h->n, B, psi,
+                                       lam, h->state_elems(), cs, K, gpart, h->plan[1].grad_stride,
+                                       true, 0, h->hf_index, h->stream));
+        h->stats.kernel_launches++;
+    }
+    prof_end(h, mk, int(h->pc_passes.size()));
+    return VQE_OK;
+}
+
 template <typename T>
 vqe_status run_forward(vqe_ctx *h, int which, const double *params_dev, int B, void *psi) {
+    if (h->ansatz == 1) return run_forward_pc<T>(h, params_dev, B, psi);
     cudaStream_t s = h->stream;
     const vqe_ctx::DevPlan &P = h->plan[which];
     auto *coefs = static_cast<RotCoef<T> *>(h->d_coefs.p);
@@ -1366,15 +1572,19 @@ vqe_status gradient_chunk(vqe_ctx *h, const double *params_dev, int B, double *g
     if (st != VQE_OK) return st;
     if ((st = run_apply_h<T>(h, B, psi, lam, E)) != VQE_OK) return st;
     const vqe_ctx::DevPlan &P = h->plan[1];
-    auto *coefs = static_cast<RotCoef<T> *>(h->d_coefs.p);
-    const PassDesc *dd = static_cast<const PassDesc *>(P.d_bwd.p);
     double *gpart = static_cast<double *>(h->d_gpart.p);
-    const int mk_b = prof_begin(h, 3);
-    for (int p = int(P.bwd.size()) - 1; p >= 0; --p) {
-        VQE_CUDA(h, launch_any_pass<T>(h, P, dd + p, P.bwd[p], B, psi, lam, coefs, gpart, true, 0));
-        h->stats.kernel_launches++;
+    if (h->ansatz == 1) {
+        if ((st = run_backward_pc<T>(h, B, psi, lam)) != VQE_OK) return st;
+    } else {
+        auto *coefs = static_cast<RotCoef<T> *>(h->d_coefs.p);
+        const PassDesc *dd = static_cast<const PassDesc *>(P.d_bwd.p);
+        const int mk_b = prof_begin(h, 3);
+        for (int p = int(P.bwd.size()) - 1; p >= 0; --p) {
+            VQE_CUDA(h, launch_any_pass<T>(h, P, dd + p, P.bwd[p], B, psi, lam, coefs, gpart, true, 0));
+            h->stats.kernel_launches++;
+        }
+        prof_end(h, mk_b, int(P.bwd.size()));
     }
-    prof_end(h, mk_b, int(P.bwd.size()));
     VQE_CUDA(h, launch_grad_finish(gpart, P.grad_stride, static_cast<const int *>(P.d_goff.p),
                                    static_cast<const int *>(P.d_gcnt.p),
                                    static_cast<const int *>(P.d_gstep.p), h->n_params, B, grads,
@@ -1487,6 +1697,50 @@ vqe_status vqe_create(int n_qubits, int depth, vqe_precision precision, void *cu
     return VQE_OK;
 }
 
+vqe_status vqe_create_pc(int n_qubits, int n_elec, int n_exc, const int *excitations,
+                         vqe_precision precision, void *cuda_stream, vqe_handle *out) {
+    if (!out) return VQE_ERR_ARG;
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > 32 || n_elec < 0 || n_elec > n_qubits) return VQE_ERR_ARG;
+    if (n_exc < 1 || n_exc > (1 << 20) || !excitations) return VQE_ERR_ARG;
+    if (precision != VQE_C64 && precision != VQE_C128) return VQE_ERR_ARG;
+    for (int j = 0; j < n_exc; ++j) {
+        const int *e = excitations + 4 * j;
+        const bool dbl = e[1] >= 0;
+        const int cnt = dbl ? 4 : 2;
+        const int modes[4] = {e[0], dbl ? e[1] : e[2], dbl ? e[2] : -1, dbl ? e[3] : -1};
+        uint32_t seen = 0;
+        for (int u = 0; u < cnt; ++u) {
+            const int md = modes[u];
+            if (md < 0 || md >= n_qubits || ((seen >> md) & 1u)) return VQE_ERR_ARG;
+            seen |= 1u << md;
+        }
+        if (!dbl && (e[1] != -1 || e[3] != -1)) return VQE_ERR_ARG;
+    }
+    vqe_ctx *h = new vqe_ctx();
+    h->n = n_qubits;
+    h->depth = 1;
+    h->prec = precision;
+    h->ansatz = 1;
+    h->n_elec = n_elec;
+    h->hf_index = n_elec >= 64 ? ~uint64_t(0) : ((uint64_t(1) << n_elec) - 1);
+    h->exc.assign(excitations, excitations + 4 * size_t(n_exc));
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return VQE_ERR_CUDA;
+    }
+    vqe_status st = build_plan(h);
+    if (st != VQE_OK) {
+        vqe_destroy(h);
+        return st;
+    }
+    *out = h;
+    return VQE_OK;
+}
+
 vqe_status vqe_destroy(vqe_handle h) {
     if (!h) return VQE_ERR_ARG;
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -1495,6 +1749,8 @@ vqe_status vqe_destroy(vqe_handle h) {
     h->plan[0].release();
     h->plan[1].release();
     h->hd.release();
+    h->d_pc_gates.release();
+    h->d_pc_hoff.release();
     for (DevBuf *b : {&h->ws_own, &h->d_params, &h->d_coefs, &h->d_dtab, &h->d_gpart, &h->d_epart,
                       &h->d_out, &h->hb_params, &h->hb_e, &h->hb_n, &h->hb_g})
         b->release();
@@ -1504,6 +1760,8 @@ vqe_status vqe_destroy(vqe_handle h) {
 
 vqe_status vqe_set_plan_options(vqe_handle h, int tile_bits_max, int run_bits, int reg_bits) {
     if (!h) return VQE_ERR_ARG;
+    if (h->ansatz == 1)
+        return fail(h, VQE_ERR_ARG, "plan options apply to the hardware-efficient ansatz");
     PlanOptions o;
     o.tile_bits_max = tile_bits_max;
     o.run_bits = run_bits;
@@ -1696,6 +1954,8 @@ vqe_status vqe_gradient_batch_dev(vqe_handle h, const double *params_dev, int ba
 vqe_status vqe_energy_batch_pergate_dev(vqe_handle h, const double *params_dev, int batch,
                                         double *energies_dev, double *norms_dev) {
     if (!h) return VQE_ERR_ARG;
+    if (h->ansatz == 1)
+        return fail(h, VQE_ERR_ARG, "the one-gate-per-pass kernel is for the hardware-efficient ansatz");
     if (!energies_dev) return fail(h, VQE_ERR_ARG, "energies is NULL");
     h->state_valid = false;
     return run_batch(h, Job::PerGate, params_dev, batch, energies_dev, norms_dev, nullptr);
@@ -1820,6 +2080,7 @@ vqe_status vqe_autotune(vqe_handle h, const double *params_dev, int batch, int g
         std::string err;
         if (options_valid(o, h->prec, err)) cands.push_back(o);
     }
+    if (h->ansatz == 1) cands.resize(1);   // one tile plan for the excitation passes
     const PlanOptions old0 = h->plan[0].opts, old1 = h->plan[1].opts;
     float best_ms = 0.f, default_ms = 0.f;
     int best = -1, tried = 0;
@@ -1923,6 +2184,8 @@ size_t vqe_inspect_sizeof(int which) {
         case 3: return sizeof(WinDesc);
         case 4: return sizeof(WinGroup);
         case 5: return sizeof(WinTerm);
+        case 6: return sizeof(ExcPass);
+        case 7: return sizeof(ExcGate);
         default: return 0;
     }
 }
@@ -1962,6 +2225,29 @@ int vqe_inspect_plan(int n_qubits, int depth, int precision, const int options[3
             grad_map[3 * p + 1] = hp.gcnt[p];
             grad_map[3 * p + 2] = hp.gstep[p];
         }
+    return 0;
+}
+
+int vqe_inspect_pc_plan(int n_qubits, int precision, int n_exc, const int *excitations,
+                        void *passes, int max_passes, void *gates, int max_gates, uint32_t *hoff,
+                        int max_hoff, int counts[3]) {
+    if (n_qubits < 1 || n_qubits > 32 || n_exc < 1 || !excitations) return -1;
+    if (precision != VQE_C64 && precision != VQE_C128) return -1;
+    std::vector<int> exc(excitations, excitations + 4 * size_t(n_exc));
+    PcHostPlan pp;
+    std::string err;
+    if (!make_pc_plan(n_qubits, vqe_precision(precision), exc, pp, err)) return -1;
+    if (counts) {
+        counts[0] = int(pp.passes.size());
+        counts[1] = int(pp.gates.size());
+        counts[2] = int(pp.hoff.size());
+    }
+    if (int(pp.passes.size()) > max_passes || int(pp.gates.size()) > max_gates ||
+        int(pp.hoff.size()) > max_hoff)
+        return -1;
+    if (passes) std::memcpy(passes, pp.passes.data(), pp.passes.size() * sizeof(ExcPass));
+    if (gates) std::memcpy(gates, pp.gates.data(), pp.gates.size() * sizeof(ExcGate));
+    if (hoff) std::memcpy(hoff, pp.hoff.data(), pp.hoff.size() * sizeof(uint32_t));
     return 0;
 }
 

@@ -90,6 +90,50 @@ struct StageSlot {
     uint16_t before[kMaxTileBits];   // tile bits un-rotated before this one in the backward sweep
 };
 
+// ---------------------------------------------------------------- particle-conserving ansatz
+//
+// Excitation gates exp(theta (T - T^dag)) (Sec. II-B, Eq. 5) with
+// T = a_p^dag a_r or a_p^dag a_q^dag a_r a_s under the Jordan-Wigner mapping.
+// T maps a basis state j with the annihilated modes occupied and the created
+// ones empty to j' = j ^ (amask | cmask) with the sign
+//     (-1)^(sign0 + popc(j & smask)),
+// smask the xor of the "modes below" masks of the four (two) operators and
+// sign0 the parity of the order relations between their modes.  A pass
+// stages a tile of 2^k amplitudes (tile bits [0, m) = global bits [0, m),
+// tile bits [m, k) = the pass's k - m further global bits, placed through a
+// table of 2^(k-m) high-part offsets) and applies a run of consecutive gates
+// whose modes all lie in the tile.
+
+constexpr int kExcMaxGates = 16;      // gates of one pass
+constexpr int kExcThreads = 256;
+
+struct ExcGate {
+    uint32_t amask, cmask;   // tile bits annihilated / created by T
+    uint32_t smask_t;        // sign mask at tile bits (tile coordinates)
+    uint32_t smask_g;        // sign mask at the global bits outside the tile
+    uint32_t sign0;          // constant sign parity
+    int n_fixed;             // 2 (single) or 4 (double)
+    uint8_t fixed[4];        // tile bits of amask | cmask, increasing
+    int param;               // parameter (and gate) index
+};
+
+struct ExcPass {
+    int k, m;
+    int g_begin, n_gates;    // gates [g_begin, g_begin + n_gates) of the gate table
+    int hoff;                // first of the pass's 2^(k-m) high-part offsets
+    uint32_t bmask;          // global bits taken from the tile number
+    int grad_off;            // per-state column of the pass's gradient partials (tile-major)
+};
+
+template <typename T>
+cudaError_t launch_exc_stage(const double *params, int n_exc, int batch, T *cs, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_exc_pass(const ExcPass &P, const ExcGate *gates_dev, const uint32_t *hoff_dev,
+                            int n_qubits, int batch, void *psi, void *lam, size_t state_stride,
+                            const T *cs, int n_exc, double *gpart, size_t grad_stride,
+                            bool backward, int init_hf, uint64_t hf_index, cudaStream_t s);
+
 // ---------------------------------------------------------------- Hamiltonian
 //
 // Terms grouped by x mask.  For a group with mask x and top bit h, every

@@ -76,8 +76,22 @@ class WinTerm(ctypes.Structure):
     _fields_ = [("zt", ctypes.c_uint32), ("zout", ctypes.c_uint32), ("c", ctypes.c_double)]
 
 
+class ExcPass(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("m", ctypes.c_int), ("g_begin", ctypes.c_int),
+                ("n_gates", ctypes.c_int), ("hoff", ctypes.c_int), ("bmask", ctypes.c_uint32),
+                ("grad_off", ctypes.c_int)]
+
+
+class ExcGate(ctypes.Structure):
+    _fields_ = [("amask", ctypes.c_uint32), ("cmask", ctypes.c_uint32),
+                ("smask_t", ctypes.c_uint32), ("smask_g", ctypes.c_uint32),
+                ("sign0", ctypes.c_uint32), ("n_fixed", ctypes.c_int),
+                ("fixed", ctypes.c_uint8 * 4), ("param", ctypes.c_int)]
+
+
 def _check_layouts(lib):
-    for which, cls in enumerate((PassDesc, StageSlot, GroupDesc, WinDesc, WinGroup, WinTerm)):
+    for which, cls in enumerate((PassDesc, StageSlot, GroupDesc, WinDesc, WinGroup, WinTerm,
+                                 ExcPass, ExcGate)):
         got = lib.vqe_inspect_sizeof(which)
         if got != ctypes.sizeof(cls):
             raise RuntimeError(f"record layout mismatch for {cls.__name__}: library {got}, "
@@ -169,3 +183,26 @@ def windows(n_qubits: int, precision: str, x, z, c, threshold: float = 0.0,
         raise ValueError("vqe_inspect_windows rejected the input")
     return {"windows": list(wins)[:nw], "wgroups": list(wg)[:ng], "wterms": list(wt)[:nt],
             "hoff": hoff[:nh], "wide": list(wide)[:nd]}
+
+
+def pc_plan(n_qubits: int, precision: str, excitations) -> dict:
+    """Pass plan of the particle-conserving ansatz as the library builds it."""
+    lib = load()
+    _check_layouts(lib)
+    prec = {"c64": 0, "c128": 1}[precision]
+    exc = np.ascontiguousarray(excitations, dtype=np.int32).reshape(-1, 4)
+    counts = (ctypes.c_int * 3)()
+    rc = lib.vqe_inspect_pc_plan(n_qubits, prec, exc.shape[0], exc.ctypes.data, None, 0, None, 0,
+                                 None, 0, counts)
+    if counts[0] == 0:
+        raise ValueError("vqe_inspect_pc_plan rejected the arguments")
+    npass, ng, nh = counts[0], counts[1], counts[2]
+    passes = (ExcPass * npass)()
+    gates = (ExcGate * ng)()
+    hoff = np.zeros(nh, dtype=np.uint32)
+    rc = lib.vqe_inspect_pc_plan(n_qubits, prec, exc.shape[0], exc.ctypes.data,
+                                 ctypes.addressof(passes), npass, ctypes.addressof(gates), ng,
+                                 hoff.ctypes.data, nh, counts)
+    if rc != 0:
+        raise ValueError("vqe_inspect_pc_plan rejected the arguments")
+    return {"passes": list(passes), "gates": list(gates), "hoff": hoff}

@@ -303,18 +303,21 @@ def test_c64_energy_accumulation_matches_fp64_on_same_state(eng_mod, oracle_mod,
     Hamiltonian dominated by a large identity and large Z terms, with small
     hopping terms, evaluated by the complex64 kernels (global sweep for one
     state, windows for four) against the FP64 oracle on the very same
-    complex64 state.  Products of FP32 amplitudes round independently, so the
-    remaining difference is far below what FP32 running sums over 2^20
-    amplitudes would leave."""
+    complex64 state.  Every coefficient and every diagonal sum is a dyadic
+    number that FP32 holds exactly, so the only differences left are the
+    independent roundings of FP32 amplitude products and the accumulation;
+    the bound is far below what FP32 running sums over 2^20 amplitudes would
+    leave."""
     import torch
     n, D = 20, 2
-    base = vi.hubbard_1d(10, 1.0, 4.0, periodic=True)
+    base = vi.hubbard_1d(10, 1.0, 4.0, periodic=True)    # coefficients +-1/2, +-1, U/4
     zx = np.array([0] * n, dtype=np.uint64)
     zz = np.array([1 << q for q in range(n)], dtype=np.uint64)
-    zc = 100.0 * (1.0 + 0.1 * np.arange(n))
+    zc = 100.0 + 10.0 * np.arange(n)
     x = np.concatenate([base.x, zx, [0]]).astype(np.uint64)
     z = np.concatenate([base.z, zz, [0]]).astype(np.uint64)
-    c = np.concatenate([1e-2 * base.c, zc, [1e3]])
+    c = np.concatenate([base.c / 64.0, zc, [1024.0]])
+    assert np.array_equal(c.astype(np.float32).astype(np.float64), c)
     H = vi.PauliSum(n, x, z, c)
     P = np.stack([vi.ansatz_params(8100 + b, n, D) for b in range(batch)])
     eng = make(eng_mod, n, D, "c64", H)

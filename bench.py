@@ -777,6 +777,9 @@ def run_case(name: str, batch: int):
         "mol24c64": (24, 2, "c64", True, "mol"),     # synthetic molecular Hamiltonian, 12 orbitals
         "lat24c128": (24, 2, "c128", True, "lattice"),   # 4x3 periodic lattice: the 32q model's family
         "lat24c64": (24, 2, "c64", True, "lattice"),
+        "rand22c64": (22, 2, "c64", False, "random"),    # random Pauli sum: groups wider than a window
+        "pcl24c128": (24, 0, "c128", True, "pc"),        # particle-conserving ansatz, 4x3 lattice
+        "pcl24c64": (24, 0, "c64", True, "pc"),
     }
     if name == "batch512":
         inst = vi.batched_instances(512, seed=7)
@@ -795,15 +798,23 @@ def run_case(name: str, batch: int):
     n, D, prec, grad, kind = cases[name]
     if kind == "mol":
         H = vi.synthetic_molecular(n // 2, 2024)
-    elif kind == "lattice":
+    elif kind in ("lattice", "pc"):
         H = vi.hubbard_2d_snake(4, 3, 1.0, 4.0)
+    elif kind == "random":
+        H = vi.random_pauli_sum(n, 60, seed=22)
     else:
         H = vi.hubbard_1d(n // 2, 1.0, 4.0, periodic=True)
-    eng = pkg.Engine(n, D, prec)
+    if kind == "pc":
+        exc = vi.excitations(n, n // 2, n_singles=8, n_doubles=32, seed=24)
+        eng = pkg.Engine.particle_conserving(n, n // 2, exc, prec)
+        P = torch.tensor(np.stack([vi.excitation_params(j, len(exc)) for j in range(batch)]),
+                         device="cuda")
+    else:
+        eng = pkg.Engine(n, D, prec)
+        P = torch.tensor(np.stack([vi.ansatz_params(j, n, D) for j in range(batch)]), device="cuda")
     eng.set_hamiltonian(H.x, H.z, H.c)
-    P = torch.tensor(np.stack([vi.ansatz_params(j, n, D) for j in range(batch)]), device="cuda")
     E = torch.empty(batch, dtype=torch.float64, device="cuda")
-    G = torch.empty(batch, 2 * n * D, dtype=torch.float64, device="cuda")
+    G = torch.empty(batch, eng.n_params, dtype=torch.float64, device="cuda")
     for _ in range(2):
         if grad:
             eng.gradient_batch_dev(P, G, E)

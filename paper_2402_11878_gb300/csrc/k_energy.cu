@@ -260,11 +260,19 @@ k_apply_h(const GroupDesc *__restrict__ groups, int n_groups, const uint32_t *__
                 sign_sums<T, J>(i, fa, tz, tc, G.t_begin, G.t_mid);
             }
             if (G.t_end > G.t_mid) sign_sums<T, J>(i, fb, tz, tc, G.t_mid, G.t_end);
+            if (G.t_end > G.t_mid) {
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-                // (pr + i pi)(fa - i fb)
-                lr[j] = fma(pj[j].x, fa[j], fma(pj[j].y, fb[j], lr[j]));
-                li[j] = fma(pj[j].y, fa[j], fma(-pj[j].x, fb[j], li[j]));
+                for (int j = 0; j < J; ++j) {
+                    // (pr + i pi)(fa - i fb)
+                    lr[j] = fma(pj[j].x, fa[j], fma(pj[j].y, fb[j], lr[j]));
+                    li[j] = fma(pj[j].y, fa[j], fma(-pj[j].x, fb[j], li[j]));
+                }
+            } else {   // no class-B term: fb = 0
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    lr[j] = fma(pj[j].x, fa[j], lr[j]);
+                    li[j] = fma(pj[j].y, fa[j], li[j]);
+                }
             }
         }
 #pragma unroll
@@ -779,13 +787,22 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
         }
     }
     __syncthreads();
-    // lambda_i0 += x1 (fa - i fb), lambda_i1 += x0 (fa + i fb)
-    auto pair_update = [&](uint32_t i0, uint32_t i1, C x0, C x1, T fa, T fb) {
+    // lambda_i0 += x1 (fa - i fb), lambda_i1 += x0 (fa + i fb); groups with
+    // no class-B term (fb = 0, e.g. every hopping term XX + YY) take the real
+    // form, half the multiply-adds
+    auto pair_update = [&](uint32_t i0, uint32_t i1, C x0, C x1, T fa, T fb, bool with_b) {
         C l0 = sl[wpad<C>(i0)], l1 = sl[wpad<C>(i1)];
-        l0.x = fma(x1.x, fa, fma(x1.y, fb, l0.x));
-        l0.y = fma(x1.y, fa, fma(-x1.x, fb, l0.y));
-        l1.x = fma(x0.x, fa, fma(-x0.y, fb, l1.x));
-        l1.y = fma(x0.y, fa, fma(x0.x, fb, l1.y));
+        if (with_b) {
+            l0.x = fma(x1.x, fa, fma(x1.y, fb, l0.x));
+            l0.y = fma(x1.y, fa, fma(-x1.x, fb, l0.y));
+            l1.x = fma(x0.x, fa, fma(-x0.y, fb, l1.x));
+            l1.y = fma(x0.y, fa, fma(x0.x, fb, l1.y));
+        } else {
+            l0.x = fma(x1.x, fa, l0.x);
+            l0.y = fma(x1.y, fa, l0.y);
+            l1.x = fma(x0.x, fa, l1.x);
+            l1.y = fma(x0.y, fa, l1.y);
+        }
         sl[wpad<C>(i0)] = l0;
         sl[wpad<C>(i1)] = l1;
     };
@@ -844,7 +861,7 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
                         for (int t = G.b_begin + G.brun[u]; t < b1; ++t)
                             fb += sgn_flip(sc[t], __popc(il & szt[t]) & 1u);
                     }
-                    pair_update(il, il ^ xl, sp[wpad<C>(il)], sp[wpad<C>(il ^ xl)], fa, fb);
+                    pair_update(il, il ^ xl, sp[wpad<C>(il)], sp[wpad<C>(il ^ xl)], fa, fb, has_b);
                 }
             } else if constexpr (RUNS) {
                 // a whole group (one pattern, plog = K - 1: every slot valid)
@@ -861,7 +878,7 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
                     const uint32_t il = e0 | D[j];
-                    pair_update(il, il ^ xl, sp[wpad<C>(il)], sp[wpad<C>(il ^ xl)], FA[j], FB[j]);
+                    pair_update(il, il ^ xl, sp[wpad<C>(il)], sp[wpad<C>(il ^ xl)], FA[j], FB[j], has_b);
                 }
             }
         }

@@ -27,7 +27,9 @@ def _case(n):
     """(n_elec, excitations, Hamiltonian): half filling; all singles and
     doubles up to 8 qubits, a seeded subset above."""
     ne = n // 2
-    if n <= 8:
+    if n == 2:
+        exc = np.array([[1, -1, 0, -1]], dtype=np.int32)   # spin-flipping single: the only one
+    elif n <= 8:
         exc = vi.excitations(n, ne)
     else:
         exc = vi.excitations(n, ne, n_singles=10, n_doubles=30, seed=n)

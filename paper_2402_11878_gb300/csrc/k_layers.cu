@@ -149,6 +149,17 @@ __device__ __forceinline__ void stage_pass(const PassDesc *__restrict__ desc,
     __syncthreads();
 }
 
+// A backward tile outside the support of psi (its base has a bit of the
+// backward zmask): psi is zero there, so its gradient partials are zero and
+// its lambda is never read again; only the partials are written.
+__device__ __forceinline__ void write_zero_partials(const PassDesc &d, double *gout, uint64_t tile) {
+    const int k = d.k;
+    for (int i = threadIdx.x; i < d.n_slots * 2 * k; i += blockDim.x) {
+        const int slot = i / (2 * k), j = i % (2 * k);
+        gout[d.slot_grad_off[slot] + tile * (uint64_t)(2 * k) + j] = 0.0;
+    }
+}
+
 // A forward tile known to be zero (its base has a bit of zmask set): the
 // pass maps it to zero, so it is written without being read or transformed.
 template <typename C>
@@ -223,8 +234,9 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
     C *L = BWD ? lam + (size_t)b * stride : nullptr;
     const uint64_t tile = blockIdx.x;
     const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (k - m)));
-    if (!BWD && (base & d.zmask)) {   // block-uniform
-        write_zero_tile(P, base, lowmask, m, a, k);
+    if (base & d.zmask) {   // block-uniform
+        if (BWD) write_zero_partials(d, gpart + (size_t)b * grad_stride, tile);
+        else write_zero_tile(P, base, lowmask, m, a, k);
         return;
     }
     if (!BWD && init_zero && d.n_slots == 1) {   // the tile at base 0
@@ -275,8 +287,9 @@ k_pass_fixed(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::t
     const int mid = a - m;
     const uint64_t base = ((tile & ((1ull << mid) - 1ull)) << m) | ((tile >> mid) << (a + (k - m)));
     const uint32_t lowmask = (1u << m) - 1u;
-    if (!BWD && (base & d.zmask)) {   // block-uniform
-        write_zero_tile(psi + (size_t)b * stride, base, lowmask, m, a, k);
+    if (base & d.zmask) {   // block-uniform
+        if (BWD) write_zero_partials(d, gpart + (size_t)b * grad_stride, tile);
+        else write_zero_tile(psi + (size_t)b * stride, base, lowmask, m, a, k);
         return;
     }
     if (!BWD && init_zero && d.n_slots == 1) {   // the tile at base 0

@@ -519,17 +519,22 @@ bool make_plan(int n, int D, vqe_precision prec, const PlanOptions &opt, HostPla
         }
     }
     // Support of the state before each forward pass (it starts from |0...0>):
-    // bits of qubits no earlier pass has rotated are 0.
+    // bits of qubits no earlier pass has rotated are 0.  The backward pass p
+    // skips the tiles outside the support of the state after forward pass p
+    // (the forward zmask of pass p + 1): there psi is zero, so the gradient
+    // terms vanish, and passes p' <= p never mix those indices with the
+    // support (they rotate no qubit of that mask), so their lambda is never
+    // read again.
     {
         uint32_t rotated = 0;
         const uint32_t nmask = n >= 32 ? ~0u : ((1u << n) - 1u);
         for (int p = 0; p < np; ++p) {
             hp.fwd[p].zmask = nmask & ~rotated;
-            hp.bwd[p].zmask = 0u;
             const Group &G = hp.groups[plans[p].group];
             for (int j = 0; j < G.k; ++j)
                 if ((G.gated >> j) & 1u) rotated |= 1u << G.qubit_of(j);
         }
+        for (int p = 0; p < np; ++p) hp.bwd[p].zmask = p + 1 < np ? hp.fwd[p + 1].zmask : 0u;
     }
     // CZ(q, q+1) of layer l goes to the later of the slots holding RY_l(q), RY_l(q+1).
     for (int l = 0; l < D; ++l) {

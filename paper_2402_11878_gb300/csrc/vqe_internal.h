@@ -46,7 +46,9 @@ struct PassDesc {
     int n_slots;
     // Forward passes start from |0...0>: before this pass only the qubits
     // rotated by earlier passes can be 1, so a tile whose base has a bit of
-    // zmask set is zero and stays zero (0 in backward passes)
+    // zmask set is zero and stays zero.  Backward pass p carries the forward
+    // zmask of pass p + 1: its tiles with a bit of it set hold psi = 0 and a
+    // lambda no later gradient reads, and are skipped (zero partials).
     uint32_t zmask;
     int slot_layer[kMaxSlots];
     uint32_t slot_czmask[kMaxSlots];  // bit q: CZ(q, q+1) applied in this slot's DIAG

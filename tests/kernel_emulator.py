@@ -209,8 +209,9 @@ class Emu:
                     gp = written.pop(("phi", s, bit))
                     base_off = d.slot_grad_off[s] + np.arange(tiles) * (2 * k) + bit * 2
                     assert base_off.max() + 1 < len(gpart)
-                    gpart[base_off] = gt
-                    gpart[base_off + 1] = gp
+                    skip = (base[:, 0, 0] & int(d.zmask)) != 0   # tiles the kernel skips: zero partials
+                    gpart[base_off] = np.where(skip, 0.0, gt)
+                    gpart[base_off + 1] = np.where(skip, 0.0, gp)
             else:
                 raise AssertionError(f"unknown op kind {op.kind}")
         assert not written, "gradient partials left unflushed"
@@ -240,7 +241,13 @@ class Emu:
         # written as zeros without being transformed; they must be zero
         zt = (base[:, 0, 0] & int(d.zmask)) != 0
         if backward:
-            assert d.zmask == 0
+            # skipped tiles: psi is zero there up to the rounding of the passes
+            # already undone; the kernel leaves psi and lambda untouched and
+            # writes zero partials
+            if zt.any():
+                assert np.abs(psi[g][zt]).max() <= 1e-12
+            v = np.where(zt[:, None, None], psi[g], v)
+            w = np.where(zt[:, None, None], lam[g], w)
         else:
             assert np.all(psi[g[zt]] == 0) if not init_zero else True
             assert np.allclose(v[zt], 0, atol=1e-300), "a tile marked zero is not"

@@ -87,7 +87,7 @@ def test_forward_zero_tile_masks(n, D, prec):
     """Forward passes start from |0...0>: the first pass's zmask holds every
     qubit (only the tile at base 0 is nonzero), each later pass's mask drops
     the qubits the earlier passes rotated, once every qubit has been rotated
-    the mask is empty, and backward passes never skip."""
+    the mask is empty; backward pass p carries the forward mask of pass p + 1."""
     pl = P.plan(n, D, prec)
     nmask = (1 << n) - 1
     rotated = 0
@@ -98,7 +98,8 @@ def test_forward_zero_tile_masks(n, D, prec):
                 rotated |= 1 << (j if j < d.m else d.a + j - d.m)
     assert i == 0 or pl["fwd"][0].zmask == nmask
     assert rotated == nmask and pl["fwd"][-1].zmask == 0
-    assert all(d.zmask == 0 for d in pl["bwd"])
+    fw = pl["fwd"]
+    assert [d.zmask for d in pl["bwd"]] == [fw[i + 1].zmask for i in range(len(fw) - 1)] + [0]
 
 
 def test_emulated_full_size_20q_plan(oracle_mod):

@@ -108,17 +108,31 @@ k_exc_pass(ExcPass P, const ExcGate *__restrict__ gates, const uint32_t *__restr
     for (uint32_t i = tid; i < nh; i += blockDim.x) shoff[i] = hoff[P.hoff + i];
     __syncthreads();
     const uint32_t lowmask = (1u << m) - 1u;
-    for (uint32_t e = tid; e < size; e += blockDim.x) {
-        const uint64_t g = base | (e & lowmask) | shoff[e >> m];
-        if (init_hf) {
-            C v;
-            v.x = (g == hf) ? T(1) : T(0);
-            v.y = T(0);
-            sp[e] = v;
-        } else {
-            sp[e] = Pp[g];
+    // a thread's loads of the tile in flight together (kLoadBatch per
+    // buffer), then their shared-memory stores
+    constexpr int kLoadBatch = 8;
+    for (uint32_t e0 = tid; e0 < size; e0 += kLoadBatch * blockDim.x) {
+        C x[kLoadBatch], l[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const uint32_t e = e0 + u * blockDim.x;
+            if (e >= size) break;
+            const uint64_t g = base | (e & lowmask) | shoff[e >> m];
+            if (init_hf) {
+                x[u].x = (g == hf) ? T(1) : T(0);
+                x[u].y = T(0);
+            } else {
+                x[u] = Pp[g];
+            }
+            if (BWD) l[u] = Lp[g];
         }
-        if (BWD) sl[e] = Lp[g];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+            const uint32_t e = e0 + u * blockDim.x;
+            if (e >= size) break;
+            sp[e] = x[u];
+            if (BWD) sl[e] = l[u];
+        }
     }
     __syncthreads();
     for (int ii = 0; ii < ng; ++ii) {

@@ -47,29 +47,43 @@ WORKLOAD = ("32q FP64 (complex128) 4x4 periodic 2D Fermi-Hubbard (snake order, t
 SAMPLE_BASELINE = (4, 3)
 SAMPLE_REFERENCE = (5, 2)
 FP64_UNITS_PEAK = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max SM clock
+# DRAM read + write bytes of the FP64 backward pass kernel per byte it must
+# move (psi and lambda read and written per live tile), from the ncu capture
+# of its three launch shapes at 24 qubits on the 4x3 lattice
+# (profiles/k_pass_c128_bwd_lat24.md: 3.076 GB measured against 3.221 GB);
+# the per-tile traffic of these passes does not depend on the qubit count.
+# None once the kernel changes, until it is captured again.
+BWD_TRAFFIC_PER_ALGORITHMIC_BYTE = 3076175872 / 3221225472
 
 
 # ---------------------------------------------------------------- work models
 
+def _live_tiles(n: int, d) -> int:
+    """Tiles of pass d whose base has no bit of its zero mask (the others are
+    skipped: known zeros in the forward sweep, outside the support of psi in
+    the backward sweep)."""
+    tiles = 1 << (n - d.k)
+    if not d.zmask:
+        return tiles
+    mid = d.a - d.m
+    hb = d.k - d.m
+    # the tile number's bits fill the global bits outside the tile in order:
+    # count the tile numbers whose deposited base avoids zmask
+    outside = [b for b in range(n) if not (b < d.m or d.a <= b < d.a + hb)]
+    free = sum(1 for b in outside if not (d.zmask >> b) & 1)
+    return 1 << free
+
+
 def slot_sweeps(n: int, depth: int, prec: str, options=(0, 0, 0)):
-    """Per tile pass of the library's plan: (tiles, live tiles of the forward
-    sweep, 2^k, gated bits per slot).  Forward tiles whose base has a bit of
-    the pass's zero mask are known zeros and are written without work."""
+    """Per tile pass of the library's plan: tiles, live tiles of the forward
+    and of the backward sweep, 2^k, gated bits per slot."""
     from paper_2402_11878_gb300 import plans
     pl = plans.plan(n, depth, prec, options)
     out = []
     for i, (f, b) in enumerate(zip(pl["fwd"], pl["bwd"])):
-        mid = f.a - f.m
-        tiles = 1 << (n - f.k)
-        if f.zmask:
-            live = 0
-            for tile in range(tiles):
-                base = ((tile & ((1 << mid) - 1)) << f.m) | ((tile >> mid) << (f.a + f.k - f.m))
-                live += (base & f.zmask) == 0
-        else:
-            live = tiles
         gated = [bin(f.slot_gated[s]).count("1") for s in range(f.n_slots)]
-        out.append({"tiles": tiles, "live": live, "k": f.k, "gated": gated, "first": i == 0})
+        out.append({"tiles": 1 << (n - f.k), "live": _live_tiles(n, f), "live_bwd": _live_tiles(n, b),
+                    "k": f.k, "gated": gated, "first": i == 0})
     return out
 
 
@@ -88,27 +102,27 @@ def forward_flops(n: int, depth: int, prec: str) -> float:
 
 
 def backward_flops(n: int, depth: int, prec: str) -> float:
-    """Floating-point operations of the adjoint backward passes of one state
-    (every tile is live): per amplitude and slot, 12 per gated bit (the scaled
+    """Floating-point operations of the adjoint backward passes of one state:
+    per amplitude of a live tile and slot, 12 per gated bit (the scaled
     rotation un-applied on psi and on lambda, 4 each, and Im<lambda|Y|psi>, 4)
     and 16 (the diagonal undone on both buffers, 6 each, and Im(conj(lambda)
-    psi) with its sum, 4)."""
+    psi) with its sum, 4).  Tiles outside the support of psi need none."""
     total = 0
     for p in slot_sweeps(n, depth, prec):
-        total += p["tiles"] * (1 << p["k"]) * sum(12 * g + 16 for g in p["gated"])
+        total += p["live_bwd"] * (1 << p["k"]) * sum(12 * g + 16 for g in p["gated"])
     return float(total)
 
 
 def pass_bytes(n: int, depth: int, prec: str):
     """HBM bytes of one state's forward passes (read + write per live tile,
     write only per zero tile) and backward passes (psi and lambda read and
-    written)."""
+    written per live tile)."""
     b = 16 if prec == "c128" else 8
     fwd = bwd = 0
     for p in slot_sweeps(n, depth, prec):
         amps = 1 << p["k"]
         fwd += (2 * p["live"] + (p["tiles"] - p["live"])) * amps * b
-        bwd += 4 * p["tiles"] * amps * b
+        bwd += 4 * p["live_bwd"] * amps * b
     return float(fwd), float(bwd)
 
 
@@ -385,8 +399,8 @@ def run_gpu(args, world, rank, local, pg):
     eng = pkg.Engine(n, D, "c128", stream=stream)
     eng.set_hamiltonian(H.x, H.z, H.c)
     tuned = None
-    if not args.no_autotune and hasattr(eng, "autotune"):
-        tuned = eng.autotune(P_dev[:1], gradient=True)
+    if not args.no_autotune:
+        tuned = eng.autotune(P_dev[:1], gradient=True, budget_ms=args.tune_ms)
 
     def step(i):
         eng.gradient_batch_dev(P_dev[i % N_VEC:i % N_VEC + 1], G, E)
@@ -441,7 +455,9 @@ def run_gpu(args, world, rank, local, pg):
     }
     achieved = fl_b / (bwd_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
+                "frac": achieved / fp64_peak,
+                "traffic": (by_b / bwd_launches * BWD_TRAFFIC_PER_ALGORITHMIC_BYTE
+                            if BWD_TRAFFIC_PER_ALGORITHMIC_BYTE else None),
                 "kernel": "k_pass_fixed<double,3,bwd> (adjoint backward tile passes)",
                 "peak_source": ("measured FP64 FMA rate of this GPU (vqe_measure_fma_peak, "
                                 "independent FMA chains on every SM, CUDA events); unit count x "
@@ -843,6 +859,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-energy and complex64 legs beside the headline")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tune-ms", type=float, default=0.0,
+                    help="autotuner budget: plans after the default are timed while the "
+                         "summed time stays below it (0: the default plan and both apply-H forms)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     args = ap.parse_args()

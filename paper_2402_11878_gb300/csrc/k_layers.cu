@@ -349,7 +349,8 @@ struct FixedEntry {
 
 // The pass program shapes of the default plans (tiles of 2^11; FP32 with 16
 // amplitudes per thread: chunks 0, 4, 7; FP64 with 8: chunks 0, 3, 6, 8),
-// forward and backward.
+// forward and backward, and of FP64 plans with 2^12 tiles (chunks 0, 3, 6, 9)
+// as the 32-qubit plan uses them.
 const std::vector<FixedEntry> &fixed_programs() {
     static const std::vector<FixedEntry> table = {
         VQE_FWD(float, 4, VQE_RD(7), VQE_B, VQE_RD(4), VQE_B, VQE_D, VQE_RD(7)),
@@ -390,6 +391,16 @@ const std::vector<FixedEntry> &fixed_programs() {
         VQE_BWD(double, 3, VQE_RD(8), VQE_RD(6), VQE_D, VQE_B, VQE_RD(8), VQE_B, VQE_F),
         VQE_BWD(double, 3, VQE_RD(8), VQE_D, VQE_B, VQE_F, VQE_D, VQE_B, VQE_F),
         VQE_BWD(double, 3, VQE_RD(8), VQE_D, VQE_B, VQE_F),
+        // FP64 with 2^12-amplitude tiles (512 threads): three qubit groups
+        // instead of four at 32 qubits, so fewer slots (diagonal ops) per layer
+        VQE_FWD(double, 3, VQE_RD(9), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_RD(0), VQE_B,
+                VQE_D, VQE_B, VQE_RD(3), VQE_B, VQE_RD(6), VQE_B, VQE_RD(9), VQE_B, VQE_D),
+        VQE_FWD(double, 3, VQE_RD(9), VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_RD(0), VQE_B,
+                VQE_D, VQE_RD(9)),
+        VQE_BWD(double, 3, VQE_RD(9), VQE_D, VQE_B, VQE_RD(6), VQE_B, VQE_RD(3), VQE_B, VQE_RD(0),
+                VQE_B, VQE_F, VQE_D, VQE_B, VQE_RD(3), VQE_B, VQE_RD(6), VQE_B, VQE_RD(9), VQE_B, VQE_F),
+        VQE_BWD(double, 3, VQE_RD(9), VQE_RD(0), VQE_D, VQE_B, VQE_RD(3), VQE_B, VQE_RD(6), VQE_B,
+                VQE_RD(9), VQE_B, VQE_F),
     };
     return table;
 }

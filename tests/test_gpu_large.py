@@ -107,8 +107,9 @@ def test_24q_molecular_c64_amplitudes_energy_gradient():
 def test_32q_hubbard_2d_fp64_energy_and_c64_gradient():
     """4x4 periodic Hubbard in snake order, 32 qubits, depth 8: FP64 energy on
     a 64 GiB caller-owned state (amplitudes vs path sum, norm, vacuum energy,
-    cutoff bound), then the complex64 adjoint gradient on psi and lambda
-    (2 x 32 GiB) against FP64 parameter shifts."""
+    cutoff bound), the FP64 adjoint gradient through the benchmark's call
+    path, then the complex64 adjoint gradient on psi and lambda (2 x 32 GiB),
+    both against FP64 parameter shifts."""
     if torch.cuda.get_device_properties(0).total_memory < 200e9:
         pytest.skip("needs a GPU with at least 200 GB of memory")
     n, D = 32, 8
@@ -134,8 +135,21 @@ def test_32q_hubbard_2d_fp64_energy_and_c64_gradient():
     eng.apply_ansatz(np.zeros(2 * n * D))
     E0, _ = eng.energy()
     assert abs(E0) <= 1e-11 * sabs      # vacuum: no particle, no energy
-    eng.close()
+    # the benchmark's own call path: FP64 energy + adjoint gradient through
+    # vqe_gradient_batch_dev on library-allocated psi and lambda (2 x 64 GiB)
+    eng.bind_workspace(None)
     del ws
+    torch.cuda.empty_cache()
+    P = torch.tensor(p[None, :], device="cuda")
+    G = torch.empty(1, 2 * n * D, dtype=torch.float64, device="cuda")
+    Eg = torch.empty(1, dtype=torch.float64, device="cuda")
+    eng.gradient_batch_dev(P, G, Eg)
+    g = G[0].cpu().numpy()
+    assert abs(float(Eg[0]) - E) <= 1e-11 * sabs
+    gmax = max(1.0, float(np.max(np.abs(g))))
+    for j, gs in shifts.items():
+        assert abs(g[j] - gs) <= 1e-10 * gmax, (j, g[j], gs)
+    eng.close()
     torch.cuda.empty_cache()
 
     e64 = _engine(n, D, "c64", H)

@@ -330,3 +330,22 @@ def test_c64_energy_accumulation_matches_fp64_on_same_state(eng_mod, oracle_mod,
     got = float(E[0])
     assert abs(got - E_same) <= 2e-9 * H.sum_abs(), (got, E_same, abs(got - E_same) / H.sum_abs())
     eng.close()
+
+
+def test_fp64_twelve_bit_tile_programs(eng_mod, oracle_mod):
+    """The unrolled FP64 programs of 2^12-amplitude tiles (the shapes the
+    32-qubit plan with tile_bits_max 12 uses, all four present at 16 qubits,
+    depth 3): state, energy and gradient against the oracle."""
+    n, D = 16, 3
+    H = vi.hubbard_1d(8, 1.0, 4.0, periodic=True)
+    p = vi.ansatz_params(1612, n, D)
+    eng = make(eng_mod, n, D, "c128", H)
+    eng.set_plan_options(12, 2, 3)
+    eng.apply_ansatz(p)
+    ref = oracle_mod.ansatz_state(n, D, p)
+    assert np.max(np.abs(eng.get_state() - ref)) <= 1e-12
+    g, E = eng.gradient(p)
+    g_ref, E_ref = oracle_mod.gradient_adjoint(n, D, p, H.x, H.z, H.c)
+    check_energy(E, E_ref, H, "c128")
+    assert np.max(np.abs(g - g_ref)) <= 1e-10 * max(1.0, np.max(np.abs(g_ref)))
+    eng.close()

@@ -796,6 +796,8 @@ def run_case(name: str, batch: int):
         "rand22c64": (22, 2, "c64", False, "random"),    # random Pauli sum: groups wider than a window
         "pcl24c128": (24, 0, "c128", True, "pc"),        # particle-conserving ansatz, 4x3 lattice
         "pcl24c64": (24, 0, "c64", True, "pc"),
+        "latw24c64": (24, 2, "c64", True, "lattice"),    # windowed apply-H forced (batch >= 3)
+        "latw24c128": (24, 2, "c128", True, "lattice"),
     }
     if name == "batch512":
         inst = vi.batched_instances(512, seed=7)
@@ -829,6 +831,8 @@ def run_case(name: str, batch: int):
         eng = pkg.Engine(n, D, prec)
         P = torch.tensor(np.stack([vi.ansatz_params(j, n, D) for j in range(batch)]), device="cuda")
     eng.set_hamiltonian(H.x, H.z, H.c)
+    if name.startswith("latw"):
+        eng.set_apply_mode(1)
     E = torch.empty(batch, dtype=torch.float64, device="cuda")
     G = torch.empty(batch, eng.n_params, dtype=torch.float64, device="cuda")
     for _ in range(2):

@@ -465,7 +465,12 @@ def run_gpu(args, world, rank, local, pg):
                 "algorithmic_flops_per_launch": fl_b / bwd_launches,
                 "mean_launch_ms": bwd_ms / bwd_launches,
                 "share_of_step": bwd_ms / (ms / steps),
-                "hbm_gbs_moved": by_b / (bwd_ms / 1e3) / 1e9, "hbm_peak_gbs": hbm_peak}
+                "hbm_gbs_moved": by_b / (bwd_ms / 1e3) / 1e9, "hbm_peak_gbs": hbm_peak,
+                # the memory view of the whole evaluation: (6D + 2) state
+                # sweeps of b N bytes at the algorithmic minimum (forward read
+                # + write per layer, lambda written, backward psi and lambda
+                # read + write per layer)
+                "hbm_algorithmic_gbs_eval": (6 * D + 2) * state_b / (ms / steps / 1e3) / 1e9}
 
     # end to end through the host-buffer API (pinned host memory)
     e2e = None

@@ -65,7 +65,7 @@ typedef enum {
     VQE_ERR_OOM = 3,      /* device memory could not be allocated */
     VQE_ERR_CUDA = 4,     /* a CUDA runtime call or kernel launch failed */
     VQE_ERR_TIMEOUT = 5,  /* reserved (no call of this version returns it) */
-    VQE_ERR_DEVICE = 6    /* a kernel reported an internal error through its error word */
+    VQE_ERR_DEVICE = 6    /* reserved (no call of this version returns it) */
 } vqe_status;
 
 typedef enum { VQE_C64 = 0, VQE_C128 = 1 } vqe_precision;

@@ -852,14 +852,17 @@ k_apply_h_win(WinDesc W, const WinGroup *__restrict__ wgroups, const WinTerm *__
                     const uint32_t u = (tid + ((uint32_t)j << 9)) >> plog;   // warp-uniform
                     if (u >= npat) break;
                     const uint32_t il = e0 | D[j] | G.fval[u];
-                    T fa = T(0), fb = T(0);
-                    const int a1 = G.a_begin + G.arun[u + 1];
-                    for (int t = G.a_begin + G.arun[u]; t < a1; ++t)
-                        fa += sgn_flip(sc[t], __popc(il & szt[t]) & 1u);
+                    // sign sums of the pattern's terms, started from the first
+                    // term (a kept pattern has at least one; most hold exactly
+                    // one after the merge, so no add is spent on a zero)
+                    const int a0 = G.a_begin + G.arun[u], a1 = G.a_begin + G.arun[u + 1];
+                    T fa = a1 > a0 ? sgn_flip(sc[a0], __popc(il & szt[a0]) & 1u) : T(0);
+                    for (int t = a0 + 1; t < a1; ++t) fa += sgn_flip(sc[t], __popc(il & szt[t]) & 1u);
+                    T fb = T(0);
                     if (has_b) {
-                        const int b1 = G.b_begin + G.brun[u + 1];
-                        for (int t = G.b_begin + G.brun[u]; t < b1; ++t)
-                            fb += sgn_flip(sc[t], __popc(il & szt[t]) & 1u);
+                        const int b0 = G.b_begin + G.brun[u], b1 = G.b_begin + G.brun[u + 1];
+                        fb = b1 > b0 ? sgn_flip(sc[b0], __popc(il & szt[b0]) & 1u) : T(0);
+                        for (int t = b0 + 1; t < b1; ++t) fb += sgn_flip(sc[t], __popc(il & szt[t]) & 1u);
                     }
                     pair_update(il, il ^ xl, sp[wpad<C>(il)], sp[wpad<C>(il ^ xl)], fa, fb, has_b);
                 }

@@ -44,15 +44,15 @@ WORKLOAD = ("32q FP64 (complex128) 4x4 periodic 2D Fermi-Hubbard (snake order, t
 # does not fit the oracle's host memory budget): a 4x3 periodic lattice (24
 # qubits) for the line's baseline and a 5x2 lattice (20 qubits) per step of
 # the reference arm; each is extrapolated to 32 qubits (see oracle_scale).
-SAMPLE_BASELINE = (4, 3)
+SAMPLE_CPU = (4, 3)
 SAMPLE_REFERENCE = (5, 2)
 FP64_UNITS_PEAK = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max SM clock
 # DRAM read + write bytes of the FP64 backward pass kernel per byte it must
-# move (psi and lambda read and written per live tile), from the ncu capture
-# of its three launch shapes at 24 qubits on the 4x3 lattice
-# (profiles/k_pass_c128_bwd_lat24.md: 3.076 GB measured against 3.221 GB);
-# the per-tile traffic of these passes does not depend on the qubit count.
-# None once the kernel changes, until it is captured again.
+# move (psi and lambda read and written per live tile), from an ncu capture
+# of its three launch shapes at 24 qubits on the 4x3 lattice (dram__bytes
+# read + write: 3.076 GB against 3.221 GB); the per-tile traffic of these
+# passes does not depend on the qubit count.  None once the kernel changes,
+# until it is captured again.
 BWD_TRAFFIC_PER_ALGORITHMIC_BYTE = 3076175872 / 3221225472
 
 
@@ -305,7 +305,7 @@ def cpu_baseline_sample(budget_s: float = 20.0):
     extrapolated to the 32-qubit workload."""
     import oracle
     oracle.build.build()
-    lx, ly = SAMPLE_BASELINE
+    lx, ly = SAMPLE_CPU
     done, spent = 0, 0.0
     while done < 1 or (spent < budget_s * 0.5 and done < 3):
         spent += oracle_eval_seconds(lx, ly, 11 + done)
@@ -716,12 +716,25 @@ def run_workload(name: str, args):
             npass = eng.stats()["ansatz_passes"]
             f_ms = pr["forward_passes"]["ms"] / reps
             b_ms = pr["backward_passes"]["ms"] / reps
+            # bytes the passes must move: one read and write of every tile in
+            # the support of the state (the first pass writes the rest as zeros)
+            from paper_2402_11878_gb300 import plans
+            pl = plans.pc_plan(n, prec, exc, ne)
+            by_f = by_b = 0.0
+            for i, Pp in enumerate(pl["passes"]):
+                tile = st * (1 << Pp.k)
+                tiles = 1 << (n - Pp.k)
+                live_f = 1 << (bin(Pp.bmask).count("1") - bin(Pp.zmask).count("1"))
+                live_b = 1 << (bin(Pp.bmask).count("1") - bin(Pp.bzmask).count("1"))
+                by_f += tile * (2 * live_f + (tiles - live_f if i == 0 else 0))
+                by_b += tile * 4 * live_b
             out[prec] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms, "energy": float(E[0]),
                          "passes": npass, "apply_windowed": tune["apply_windowed"],
                          "forward_ms": f_ms, "apply_h_ms": pr["apply_h"]["ms"] / reps,
                          "backward_ms": b_ms,
-                         "forward_hbm_gbs": npass * 2 * st * float(1 << n) / (f_ms / 1e3) / 1e9,
-                         "backward_hbm_gbs": npass * 4 * st * float(1 << n) / (b_ms / 1e3) / 1e9,
+                         "forward_hbm_gbs": by_f / (f_ms / 1e3) / 1e9,
+                         "backward_hbm_gbs": by_b / (b_ms / 1e3) / 1e9,
+                         "support_fraction": by_b / (npass * 4 * st * float(1 << n)),
                          "grad_inf": float(G.abs().max())}
             g = G[0].cpu().numpy().copy()
             if prec == "c128":

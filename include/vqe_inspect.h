@@ -65,11 +65,11 @@ int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
                         uint32_t *hoff, int max_hoff, void *wide, int max_wide, int counts[5]);
 
 /* Pass plan of the particle-conserving ansatz (vqe_create_pc) for the same
- * arguments: excitation passes (max_passes), their gates with tile masks and
- * sign masks (max_gates), and the passes' high-part offset tables
- * (max_hoff).  counts[3] = passes, gates, offsets.  Returns 0, or -1 on
- * invalid arguments or too-small buffers. */
-int vqe_inspect_pc_plan(int n_qubits, int precision, int n_exc, const int *excitations,
+ * arguments: excitation passes (max_passes) with their support masks, their
+ * gates with tile masks and sign masks (max_gates), and the passes'
+ * high-part offset tables (max_hoff).  counts[3] = passes, gates, offsets.
+ * Returns 0, or -1 on invalid arguments or too-small buffers. */
+int vqe_inspect_pc_plan(int n_qubits, int n_elec, int precision, int n_exc, const int *excitations,
                         void *passes, int max_passes, void *gates, int max_gates, uint32_t *hoff,
                         int max_hoff, int counts[3]);
 

@@ -121,7 +121,7 @@ def load() -> ctypes.CDLL:
                                     vp, vp],
         "vqe_inspect_windows": [i, i, vp, vp, vp, sz, ctypes.c_double, i, vp, i, vp, i, vp,
                                 i, vp, i, vp, i, vp],
-        "vqe_inspect_pc_plan": [i, i, i, vp, vp, i, vp, i, vp, i, vp],
+        "vqe_inspect_pc_plan": [i, i, i, i, vp, vp, i, vp, i, vp, i, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

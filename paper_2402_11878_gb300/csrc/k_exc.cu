@@ -98,6 +98,20 @@ k_exc_pass(ExcPass P, const ExcGate *__restrict__ gates, const uint32_t *__restr
             bm &= bm - 1u;
         }
     }
+    // tiles outside the support of the state (see ExcPass): block-uniform
+    if (!BWD && (base & P.zmask) != P.zval) {
+        if (init_hf) {   // the first pass writes the whole state
+            const uint32_t lowmask = (1u << m) - 1u;
+            for (uint32_t e = tid; e < size; e += blockDim.x)
+                Pp[base | (e & lowmask) | hoff[P.hoff + (e >> m)]] = C{};
+        }
+        return;
+    }
+    if (BWD && (base & P.bzmask) != P.bzval) {
+        double *out = gpart + (size_t)b * grad_stride + P.grad_off + (size_t)blockIdx.x * ng;
+        for (int i = tid; i < ng; i += blockDim.x) out[i] = 0.0;
+        return;
+    }
     for (int i = tid; i < ng; i += blockDim.x) {
         sg[i] = gates[P.g_begin + i];
         const int prm = gates[P.g_begin + i].param;

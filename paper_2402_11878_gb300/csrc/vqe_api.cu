@@ -619,8 +619,8 @@ struct PcHostPlan {
 // kExcMaxGates) whose modes outside the low run [0, m) fit the k - m further
 // tile bits.  Tiles hold 2^k amplitudes: 2^11 (32 KiB) in FP64, 2^12 in FP32,
 // with contiguous runs of 2^m = 256 bytes.
-bool make_pc_plan(int n, vqe_precision prec, const std::vector<int> &exc, PcHostPlan &pp,
-                  std::string &err) {
+bool make_pc_plan(int n, vqe_precision prec, const std::vector<int> &exc, uint64_t hf_index,
+                  PcHostPlan &pp, std::string &err) {
     pp = PcHostPlan{};
     int k = prec == VQE_C128 ? 11 : 12;
     int m = prec == VQE_C128 ? 4 : 5;
@@ -658,6 +658,8 @@ bool make_pc_plan(int n, vqe_precision prec, const std::vector<int> &exc, PcHost
     }
     if (K > first) runs.push_back({first, K - first});
     const uint64_t tiles = uint64_t(1) << (n - k);
+    const uint32_t hf = uint32_t(hf_index);
+    uint32_t touched = 0;   // modes of the gates of earlier passes
     size_t goff = 0;
     pp.goff.assign(K, 0);
     pp.gcnt.assign(K, 0);
@@ -689,6 +691,13 @@ bool make_pc_plan(int n, vqe_precision prec, const std::vector<int> &exc, PcHost
             return false;
         }
         P.grad_off = int(goff);
+        P.zmask = P.bmask & ~touched;
+        P.zval = hf & P.zmask;
+        for (int j = r.first; j < r.first + r.second; ++j)
+            for (int u = 0; u < 4; ++u)
+                if (exc[4 * j + u] >= 0) touched |= 1u << exc[4 * j + u];
+        P.bzmask = P.bmask & ~touched;
+        P.bzval = hf & P.bzmask;
         for (uint32_t hh = 0; hh < (1u << hi); ++hh) {
             uint32_t g = 0;
             for (int j = 0; j < hi; ++j)
@@ -737,7 +746,7 @@ bool make_pc_plan(int n, vqe_precision prec, const std::vector<int> &exc, PcHost
 vqe_status build_pc_plan(vqe_ctx *h) {
     PcHostPlan pp;
     std::string err;
-    if (!make_pc_plan(h->n, h->prec, h->exc, pp, err)) return fail(h, VQE_ERR_ARG, err);
+    if (!make_pc_plan(h->n, h->prec, h->exc, h->hf_index, pp, err)) return fail(h, VQE_ERR_ARG, err);
     vqe_status st;
     if ((st = upload(h, h->d_pc_gates, pp.gates, "excitation gates")) != VQE_OK) return st;
     if ((st = upload(h, h->d_pc_hoff, pp.hoff, "excitation tiles")) != VQE_OK) return st;
@@ -2233,15 +2242,17 @@ int vqe_inspect_plan(int n_qubits, int depth, int precision, const int options[3
     return 0;
 }
 
-int vqe_inspect_pc_plan(int n_qubits, int precision, int n_exc, const int *excitations,
+int vqe_inspect_pc_plan(int n_qubits, int n_elec, int precision, int n_exc, const int *excitations,
                         void *passes, int max_passes, void *gates, int max_gates, uint32_t *hoff,
                         int max_hoff, int counts[3]) {
     if (n_qubits < 1 || n_qubits > 32 || n_exc < 1 || !excitations) return -1;
+    if (n_elec < 0 || n_elec > n_qubits) return -1;
     if (precision != VQE_C64 && precision != VQE_C128) return -1;
     std::vector<int> exc(excitations, excitations + 4 * size_t(n_exc));
     PcHostPlan pp;
     std::string err;
-    if (!make_pc_plan(n_qubits, vqe_precision(precision), exc, pp, err)) return -1;
+    const uint64_t hf = n_elec >= 64 ? ~uint64_t(0) : ((uint64_t(1) << n_elec) - 1);
+    if (!make_pc_plan(n_qubits, vqe_precision(precision), exc, hf, pp, err)) return -1;
     if (counts) {
         counts[0] = int(pp.passes.size());
         counts[1] = int(pp.gates.size());

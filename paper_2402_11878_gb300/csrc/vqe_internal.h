@@ -125,6 +125,14 @@ struct ExcPass {
     int hoff;                // first of the pass's 2^(k-m) high-part offsets
     uint32_t bmask;          // global bits taken from the tile number
     int grad_off;            // per-state column of the pass's gradient partials (tile-major)
+    // Support of the state: the gates change only their own modes, so before
+    // pass p every index that disagrees with psi_HF on a mode no earlier gate
+    // touched holds zero.  A forward tile with (base & zmask) != zval is zero
+    // (written as zeros by the first pass, skipped by later ones); a backward
+    // tile with (base & bzmask) != bzval lies outside the support of the state
+    // after this pass, so its gradient terms vanish and its lambda is never
+    // read again (zero partials).
+    uint32_t zmask, zval, bzmask, bzval;
 };
 
 template <typename T>

@@ -79,7 +79,8 @@ class WinTerm(ctypes.Structure):
 class ExcPass(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("m", ctypes.c_int), ("g_begin", ctypes.c_int),
                 ("n_gates", ctypes.c_int), ("hoff", ctypes.c_int), ("bmask", ctypes.c_uint32),
-                ("grad_off", ctypes.c_int)]
+                ("grad_off", ctypes.c_int), ("zmask", ctypes.c_uint32), ("zval", ctypes.c_uint32),
+                ("bzmask", ctypes.c_uint32), ("bzval", ctypes.c_uint32)]
 
 
 class ExcGate(ctypes.Structure):
@@ -185,22 +186,23 @@ def windows(n_qubits: int, precision: str, x, z, c, threshold: float = 0.0,
             "hoff": hoff[:nh], "wide": list(wide)[:nd]}
 
 
-def pc_plan(n_qubits: int, precision: str, excitations) -> dict:
-    """Pass plan of the particle-conserving ansatz as the library builds it."""
+def pc_plan(n_qubits: int, precision: str, excitations, n_elec: int = 0) -> dict:
+    """Pass plan of the particle-conserving ansatz as the library builds it
+    (n_elec: electrons of psi_HF, for the support masks)."""
     lib = load()
     _check_layouts(lib)
     prec = {"c64": 0, "c128": 1}[precision]
     exc = np.ascontiguousarray(excitations, dtype=np.int32).reshape(-1, 4)
     counts = (ctypes.c_int * 3)()
-    rc = lib.vqe_inspect_pc_plan(n_qubits, prec, exc.shape[0], exc.ctypes.data, None, 0, None, 0,
-                                 None, 0, counts)
+    rc = lib.vqe_inspect_pc_plan(n_qubits, n_elec, prec, exc.shape[0], exc.ctypes.data, None, 0,
+                                 None, 0, None, 0, counts)
     if counts[0] == 0:
         raise ValueError("vqe_inspect_pc_plan rejected the arguments")
     npass, ng, nh = counts[0], counts[1], counts[2]
     passes = (ExcPass * npass)()
     gates = (ExcGate * ng)()
     hoff = np.zeros(nh, dtype=np.uint32)
-    rc = lib.vqe_inspect_pc_plan(n_qubits, prec, exc.shape[0], exc.ctypes.data,
+    rc = lib.vqe_inspect_pc_plan(n_qubits, n_elec, prec, exc.shape[0], exc.ctypes.data,
                                  ctypes.addressof(passes), npass, ctypes.addressof(gates), ng,
                                  hoff.ctypes.data, nh, counts)
     if rc != 0:

@@ -10,9 +10,9 @@ import pytest
 import vqe_inputs as vi
 
 
-def _plan(n, prec, exc):
+def _plan(n, prec, exc, ne=0):
     from paper_2402_11878_gb300 import plans
-    return plans.pc_plan(n, prec, exc)
+    return plans.pc_plan(n, prec, exc, ne)
 
 
 def _tile_indices(n, P, hoff, tile):
@@ -44,12 +44,17 @@ def _parity(a):
 
 
 def emulate(n, ne, exc, theta, H=None, oracle_mod=None, prec="c128"):
-    pl = _plan(n, prec, exc)
+    pl = _plan(n, prec, exc, ne)
     psi = np.zeros(1 << n, dtype=complex)
     psi[(1 << ne) - 1] = 1.0
     for P in pl["passes"]:
         for tile in range(1 << (n - P.k)):
             base, g = _tile_indices(n, P, pl["hoff"], tile)
+            if (base & int(P.zmask)) != int(P.zval):
+                # outside the support: the kernel skips the tile (the first
+                # pass writes it as zeros); it must be zero
+                assert np.all(psi[g] == 0)
+                continue
             t = psi[g].copy()
             for G in pl["gates"][P.g_begin:P.g_begin + P.n_gates]:
                 e, e2 = _pairs(G, P.k)
@@ -66,6 +71,11 @@ def emulate(n, ne, exc, theta, H=None, oracle_mod=None, prec="c128"):
     for P in reversed(pl["passes"]):
         for tile in range(1 << (n - P.k)):
             base, g = _tile_indices(n, P, pl["hoff"], tile)
+            if (base & int(P.bzmask)) != int(P.bzval):
+                # outside the support of the state after this pass: skipped,
+                # zero partials; psi is zero there up to rounding
+                assert np.max(np.abs(psi[g])) <= 1e-12
+                continue
             t, l = psi[g].copy(), lam[g].copy()
             for G in reversed(pl["gates"][P.g_begin:P.g_begin + P.n_gates]):
                 e, e2 = _pairs(G, P.k)
@@ -92,7 +102,9 @@ def test_replayed_plan_matches_oracle(oracle_mod, lib_built, prec, n):
     psi, g = emulate(n, ne, exc, th, H, oracle_mod, prec)
     hf = np.zeros(1 << n)
     hf[(1 << ne) - 1] = 1.0
-    assert np.max(np.abs(psi - hf)) <= 1e-13          # the backward sweep undoes the circuit
+    # the backward sweep undoes the circuit on the tiles it visits (the
+    # skipped ones keep the rounding residue of the passes undone before)
+    assert np.max(np.abs(psi - hf)) <= 1e-12
     ref = oracle_mod.pc_ansatz_state(n, ne, exc, th)
     psi_f, _ = emulate(n, ne, exc, th, prec=prec)
     assert np.max(np.abs(psi_f - ref)) <= 1e-13
@@ -104,7 +116,7 @@ def test_plan_structure(lib_built):
     n = 20
     exc = vi.excitations(n, 10, 12, 40, seed=2)
     for prec, k, m in (("c128", 11, 4), ("c64", 12, 5)):
-        pl = _plan(n, prec, exc)
+        pl = _plan(n, prec, exc, 10)
         assert sum(P.n_gates for P in pl["passes"]) == len(exc)
         for P in pl["passes"]:
             assert (P.k, P.m) == (k, m) and 1 <= P.n_gates <= 16
@@ -116,3 +128,19 @@ def test_plan_structure(lib_built):
                 modes = [x for x in (p, q, r, s) if x >= 0]
                 assert all((tile_bits >> md) & 1 for md in modes)   # every mode in the tile
         assert [G.param for G in pl["gates"]] == list(range(len(exc)))   # order kept
+        # support masks: before the first pass only the Hartree-Fock tile is
+        # live; the masks lie in the tile-number bits with values of psi_HF;
+        # the modes touched after pass a (its backward mask) are those touched
+        # before pass a + 1 (the next forward mask), seen through each pass's
+        # own tile-number bits
+        hf = (1 << 10) - 1
+        P0 = pl["passes"][0]
+        assert P0.zmask == P0.bmask and P0.zval == hf & P0.bmask
+        for P in pl["passes"]:
+            for msk, val in ((P.zmask, P.zval), (P.bzmask, P.bzval)):
+                assert msk & ~P.bmask == 0 and val == hf & msk
+            assert P.bzmask & ~P.zmask == 0            # the support only grows
+        for a, b in zip(pl["passes"], pl["passes"][1:]):
+            touched_a = a.bmask & ~a.bzmask
+            touched_b = b.bmask & ~b.zmask
+            assert touched_a & b.bmask == touched_b & a.bmask

@@ -750,24 +750,29 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                 // taken before the diagonal is undone.  FP64: each thread stores
                 // its total (row k) and its signed sums over the chunk's own bits
                 // (rows k + 1 + j); the flush sums the rows, taking the sign of a
-                // bit outside the chunk from the thread's element base.
-                T u[NR];
-                T tot = T(0);
+                // bit outside the chunk from the thread's element base.  The
+                // total and the R signed sums come from one butterfly over the
+                // register bits (level j pairs the partial sums that differ in
+                // bit j): 2^(R+1) + R - 4 adds instead of (R + 1) 2^R.
+                T a[NR];
 #pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    u[r] = fma(w[r].x, v[r].y, -w[r].y * v[r].x);
-                    tot += u[r];
-                }
+                for (int r = 0; r < NR; ++r) a[r] = fma(w[r].x, v[r].y, -w[r].y * v[r].x);
                 const uint32_t gated = d.slot_gated[op.slot];
-                gsh[k * nthr + t] = tot;
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    if (!((gated >> (P + j)) & 1u)) continue;
-                    T gq = T(0);
+                    constexpr int kHalfMax = NR / 2;
+                    const int half = NR >> (j + 1);
+                    T dsum = T(0);
 #pragma unroll
-                    for (int r = 0; r < NR; ++r) gq += ((r >> j) & 1) ? -u[r] : u[r];
-                    gsh[(k + 1 + j) * nthr + t] = gq;
+                    for (int c = 0; c < kHalfMax; ++c) {
+                        if (c >= half) break;
+                        const T x0 = a[2 * c], x1 = a[2 * c + 1];
+                        dsum = c == 0 ? x0 - x1 : dsum + (x0 - x1);
+                        a[c] = x0 + x1;
+                    }
+                    if ((gated >> (P + j)) & 1u) gsh[(k + 1 + j) * nthr + t] = dsum;
                 }
+                gsh[k * nthr + t] = a[0];
                 diag_chunk = P;
             } else if constexpr (BWD) {
                 // dE/dphi_q = Im<l|Z_q|p> = sum_i u_i (-1)^{bit_q(i)}, u = Im(conj(l) p),

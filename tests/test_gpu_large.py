@@ -164,3 +164,70 @@ def test_32q_hubbard_2d_fp64_energy_and_c64_gradient():
         assert abs(g[j] - gs) <= 1e-4 * gmax, (j, g[j], gs)
     e64.close()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_32q_particle_conserving_fp64_and_c64():
+    """The particle-conserving ansatz at 32 qubits (4x4 lattice at half
+    filling, 102 doubles + 16 singles, the benchmark's pc32 workload): the
+    FP64 state keeps every amplitude outside the 16-electron sector exactly
+    zero and its norm at 1; the energy from the gradient call equals the
+    energy call; the FP64 adjoint gradient matches central differences of
+    FP64 energies on sampled components; complex64 agrees with FP64 within
+    its tolerances."""
+    if torch.cuda.get_device_properties(0).total_memory < 200e9:
+        pytest.skip("needs a GPU with at least 200 GB of memory")
+    import paper_2402_11878_gb300 as pkg
+    n, ne = 32, 16
+    H = vi.hubbard_2d_snake(4, 4, 1.0, 4.0)
+    sabs = H.sum_abs()
+    exc = vi.excitations(n, ne, n_singles=16, n_doubles=102, seed=32)
+    th = vi.excitation_params(3232, len(exc))
+    eng = pkg.Engine.particle_conserving(n, ne, exc, "c128")
+    eng.set_hamiltonian(H.x, H.z, H.c)
+    ws = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+    eng.bind_workspace(ws)
+    eng.apply_ansatz(th)
+    E, nrm = eng.energy()
+    assert abs(nrm - 1.0) <= 1e-12
+    idx = _indices(n, 4000, 5)
+    amp = _gather(ws, idx)
+    N = np.array([bin(int(i)).count("1") for i in idx])
+    assert np.max(np.abs(amp[N != ne])) == 0.0
+    assert abs(_gather(ws, np.array([(1 << ne) - 1]))[0]) > 0.0     # psi_HF itself stays
+
+    def energy_at(t):
+        eng.apply_ansatz(t)
+        return eng.energy()[0]
+
+    h = 1e-4
+    jobs = (0, 57, len(exc) - 1)                 # a double, a double, the last single
+    fd = {}
+    for j in jobs:
+        tp, tm = th.copy(), th.copy()
+        tp[j] += h
+        tm[j] -= h
+        fd[j] = (energy_at(tp) - energy_at(tm)) / (2 * h)
+    eng.bind_workspace(None)
+    del ws
+    torch.cuda.empty_cache()
+    P = torch.tensor(th[None, :], device="cuda")
+    G = torch.empty(1, len(exc), dtype=torch.float64, device="cuda")
+    Eg = torch.empty(1, dtype=torch.float64, device="cuda")
+    eng.gradient_batch_dev(P, G, Eg)
+    g = G[0].cpu().numpy()
+    assert abs(float(Eg[0]) - E) <= 1e-11 * sabs
+    gmax = max(1.0, float(np.max(np.abs(g))))
+    for j, v in fd.items():
+        assert abs(g[j] - v) <= 1e-6 * gmax, (j, g[j], v)   # central differences: O(h^2)
+    eng.close()
+    torch.cuda.empty_cache()
+
+    e64 = pkg.Engine.particle_conserving(n, ne, exc, "c64")
+    e64.set_hamiltonian(H.x, H.z, H.c)
+    G64 = torch.empty_like(G)
+    e64.gradient_batch_dev(P, G64, Eg)
+    assert abs(float(Eg[0]) - E) <= 1e-5 * sabs
+    assert float((G64[0].cpu() - torch.from_numpy(g)).abs().max()) <= 1e-4 * float(np.max(np.abs(g)))
+    e64.close()
+    torch.cuda.empty_cache()

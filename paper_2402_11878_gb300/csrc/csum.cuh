@@ -44,6 +44,15 @@ __device__ __forceinline__ F32c f32c_add(F32c a, F32c b) {
     return F32c{s2, e2};
 }
 
+// a + b of two pairs without the final renormalisation (the tree levels of
+// a block sum): the rounding error of hi joins lo, which stays a few ulps of
+// hi over the five levels of a warp tree.
+__device__ __forceinline__ F32c f32c_add_lazy(F32c a, F32c b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return F32c{s, e + (a.lo + b.lo)};
+}
+
 __device__ __forceinline__ F32c f32c_shfl_xor(unsigned mask, F32c v, int o) {
     return F32c{__shfl_xor_sync(mask, v.hi, o), __shfl_xor_sync(mask, v.lo, o)};
 }

@@ -250,13 +250,11 @@ k_pass(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::type *_
 }
 
 // Gradient scratch of a fixed-shape backward pass, rows of per-thread
-// partials summed at the flush: FP32 one row per (tile bit, component); FP64
-// one theta row per tile bit, plus the phi total row and one row per
-// register bit (R = 3 in every FP64 program).
-template <typename T>
+// partials summed at the flush: one theta row per tile bit, the phi total row
+// and one row per register bit.
+template <typename T, int R>
 __host__ __device__ inline size_t fixed_grad_scratch_bytes(int threads, int k) {
-    return sizeof(T) == 4 ? size_t(threads) * 2 * k * sizeof(float)
-                          : size_t(threads) * (k + 1 + 3) * sizeof(double);
+    return size_t(threads) * (k + 1 + R) * sizeof(T);
 }
 
 // Pass with a program shape fixed at compile time (run_tile_fixed); same
@@ -279,7 +277,7 @@ k_pass_fixed(const PassDesc *__restrict__ desc, int init_zero, typename V2<T>::t
     double *gsh = reinterpret_cast<double *>(sp + (BWD ? 2 * size : size));
     RotCoef<T> *scf = reinterpret_cast<RotCoef<T> *>(
         reinterpret_cast<unsigned char *>(gsh) +
-        (BWD ? fixed_grad_scratch_bytes<T>((int)blockDim.x, kk) : 0));
+        (BWD ? fixed_grad_scratch_bytes<T, R>((int)blockDim.x, kk) : 0));
     stage_pass<T>(desc, coefs + (size_t)b * coef_stride, &sd, scf);
     const PassDesc &d = sd;
     const int k = d.k, m = d.m, a = d.a;
@@ -317,7 +315,7 @@ cudaError_t launch_fixed(const PassDesc *desc_dev, const PassDesc &dh, int n_qub
     using C = typename V2<T>::type;
     const int threads = 1 << (dh.k - dh.R);
     size_t smem = pass_smem_bytes(dh, BWD, sizeof(C));
-    if (BWD) smem += fixed_grad_scratch_bytes<T>(threads, dh.k) - tile_grad_scratch_bytes(threads, dh.k);
+    if (BWD) smem += fixed_grad_scratch_bytes<T, R>(threads, dh.k) - tile_grad_scratch_bytes(threads, dh.k);
     auto kern = k_pass_fixed<T, R, BWD, Codes...>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -103,12 +103,6 @@ __device__ __forceinline__ float2 caxpy(float a, float2 x, float2 y) {
 __device__ __forceinline__ double2 caxpy(double a, double2 x, double2 y) {
     return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
 }
-template <typename C>
-__device__ __forceinline__ C cneg(C x) {
-    x.x = -x.x;
-    x.y = -x.y;
-    return x;
-}
 
 template <typename C>
 __device__ __forceinline__ C cmul(C x, C d) {
@@ -364,7 +358,7 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                                 u[r1].x = fma(cv, x.x, y.x);  u[r1].y = fma(cv, x.y, y.y);
                             } else {      // transpose: [[1,t],[-t,1]], packed f32x2
                                 u[r] = caxpy(cv, y, x);
-                                u[r1] = caxpy(cv, cneg(x), y);
+                                u[r1] = caxpy(-cv, x, y);
                             }
                         }
                     }
@@ -382,7 +376,10 @@ __device__ __forceinline__ void run_tile(const PassDesc &d, const PassOp *ops, i
                                 u[r1].x = fma(cv, y.x, x.x);  u[r1].y = fma(cv, y.y, x.y);
                             } else {      // transpose: [[u,1],[-1,u]]
                                 u[r] = caxpy(cv, x, y);
-                                u[r1] = caxpy(cv, y, cneg(x));
+                                // u y - x as two scalar FMAs (a negated addend is
+                                // free there, not in the packed form)
+                                u[r1].x = fma(cv, y.x, -x.x);
+                                u[r1].y = fma(cv, y.y, -x.y);
                             }
                         }
                     }
@@ -559,6 +556,16 @@ __host__ __device__ constexpr int prog_chunk_at(int i) {
     return -1;
 }
 
+// Largest round chunk of a program: the tile has this many bits plus R.
+template <int... Codes>
+__host__ __device__ constexpr int prog_top_chunk() {
+    constexpr int code[] = {Codes...};
+    int top = 0;
+    for (int c : code)
+        if ((c >> 8) == 1 && (c & 255) > top) top = c & 255;
+    return top;
+}
+
 template <typename T, int R, bool BWD, class Env, int... Codes>
 __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *ops, uint64_t gbase,
                                                typename V2<T>::type *buf,
@@ -566,6 +573,7 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                                                Env &env) {
     static_assert(Env::kLoad == 1 && Env::kStore == 1 && Env::kDiagRow, "direct environment");
     static_assert(!(BWD && sizeof(T) == 8) || R == 3, "FP64 gradient rows are sized for R = 3");
+    static_assert(!(BWD && sizeof(T) == 4) || R == 4, "FP32 gradient rows are sized for R = 4");
     using C = typename V2<T>::type;
     constexpr int NR = 1 << R;
     constexpr int N = sizeof...(Codes);
@@ -574,8 +582,6 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
     const uint32_t t = threadIdx.x;
     const uint32_t nthr = 1u << (k - R);   // == blockDim.x for these kernels
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned wmask = nthr >= 32 ? 0xffffffffu : ((1u << nthr) - 1u);
-    const int wlanes = nthr >= 32 ? 32 : (int)nthr;
     const uint32_t lowmask = (1u << m) - 1u;
     auto g32 = [&](uint32_t e) -> uint32_t {
         return (uint32_t)(gbase | (uint64_t)(e & lowmask) | ((uint64_t)(e >> m) << a));
@@ -599,7 +605,7 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
     };
     C v[NR];
     C w[NR];
-    int diag_chunk = 0;   // chunk of the last diagonal op (FP64 backward flush)
+    int diag_chunk = 0;   // chunk of the last diagonal op (backward flush)
     static_for<0, N>([&](auto I) {
         constexpr int i = decltype(I)::value;
         constexpr int kind = code[i] >> 8;
@@ -656,15 +662,16 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                     // dE/dtheta = Im<l|Y|p>; per pair Re(conj(l1) p0) - Re(conj(l0) p1)
                     T gt = T(0);
                     if constexpr (sizeof(T) == 4) {
-                        // packed: both components in one f32x2 accumulator
-                        float2 g2 = make_float2(0.f, 0.f);
+                        // packed: both components in f32x2 accumulators, the two
+                        // orientations apart (no negation per pair)
+                        float2 gp = make_float2(0.f, 0.f), gn = make_float2(0.f, 0.f);
 #pragma unroll
                         for (int r = 0; r < NR; ++r) {
                             if (r & (1 << j)) continue;
-                            g2 = __ffma2_rn(w[r | (1 << j)], v[r], g2);
-                            g2 = __ffma2_rn(cneg(w[r]), v[r | (1 << j)], g2);
+                            gp = __ffma2_rn(w[r | (1 << j)], v[r], gp);
+                            gn = __ffma2_rn(w[r], v[r | (1 << j)], gn);
                         }
-                        gt = g2.x + g2.y;
+                        gt = (gp.x + gp.y) - (gn.x + gn.y);
                     } else {
 #pragma unroll
                         for (int r = 0; r < NR; ++r) {
@@ -678,8 +685,8 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                         }
                     }
                     if constexpr (sizeof(T) == 4) {
-                        // FP32: one shared-memory row per (bit, component), summed at the flush
-                        reinterpret_cast<float *>(gsh)[(2 * (P + j) + 0) * nthr + t] = gt * rc.gs;
+                        // FP32: row P + j, already scaled by gs, summed at the flush
+                        reinterpret_cast<float *>(gsh)[(P + j) * nthr + t] = gt * rc.gs;
                     } else {
                         // FP64: row P + j of per-thread partials, summed (and scaled by gs)
                         // at the flush: no shuffle tree per bit on the scarce FP64 pipe
@@ -721,7 +728,7 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                                 u[r1].x = fma(cv, x.x, y.x);  u[r1].y = fma(cv, x.y, y.y);
                             } else {      // transpose: [[1,t],[-t,1]], packed f32x2
                                 u[r] = caxpy(cv, y, x);
-                                u[r1] = caxpy(cv, cneg(x), y);
+                                u[r1] = caxpy(-cv, x, y);
                             }
                         }
                     } else {
@@ -735,7 +742,10 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                                 u[r1].x = fma(cv, y.x, x.x);  u[r1].y = fma(cv, y.y, x.y);
                             } else {      // transpose: [[u,1],[-1,u]]
                                 u[r] = caxpy(cv, x, y);
-                                u[r1] = caxpy(cv, y, cneg(x));
+                                // u y - x as two scalar FMAs (a negated addend is
+                                // free there, not in the packed form)
+                                u[r1].x = fma(cv, y.x, -x.x);
+                                u[r1].y = fma(cv, y.y, -x.y);
                             }
                         }
                     }
@@ -745,10 +755,10 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
             const PassOp op = ops[i];
             const uint32_t cz = d.slot_czmask[op.slot];
             const uint32_t e0 = elem_of(t, 0, P, R);
-            if constexpr (BWD && sizeof(T) == 8) {
+            if constexpr (BWD) {
                 // dE/dphi_q = Im<l|Z_q|p> = sum_i u_i (-1)^{bit_q(i)}, u = Im(conj(l) p),
-                // taken before the diagonal is undone.  FP64: each thread stores
-                // its total (row k) and its signed sums over the chunk's own bits
+                // taken before the diagonal is undone.  Each thread stores its
+                // total (row k) and its signed sums over the chunk's own bits
                 // (rows k + 1 + j); the flush sums the rows, taking the sign of a
                 // bit outside the chunk from the thread's element base.  The
                 // total and the R signed sums come from one butterfly over the
@@ -758,6 +768,7 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
 #pragma unroll
                 for (int r = 0; r < NR; ++r) a[r] = fma(w[r].x, v[r].y, -w[r].y * v[r].x);
                 const uint32_t gated = d.slot_gated[op.slot];
+                T *rows = reinterpret_cast<T *>(gsh);
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
                     constexpr int kHalfMax = NR / 2;
@@ -770,38 +781,10 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                         dsum = c == 0 ? x0 - x1 : dsum + (x0 - x1);
                         a[c] = x0 + x1;
                     }
-                    if ((gated >> (P + j)) & 1u) gsh[(k + 1 + j) * nthr + t] = dsum;
+                    if ((gated >> (P + j)) & 1u) rows[(k + 1 + j) * nthr + t] = dsum;
                 }
-                gsh[k * nthr + t] = a[0];
+                rows[k * nthr + t] = a[0];
                 diag_chunk = P;
-            } else if constexpr (BWD) {
-                // dE/dphi_q = Im<l|Z_q|p> = sum_i u_i (-1)^{bit_q(i)}, u = Im(conj(l) p),
-                // taken before the diagonal is undone
-                T u[NR];
-                T tot = T(0);
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    u[r] = fma(w[r].x, v[r].y, -w[r].y * v[r].x);
-                    tot += u[r];
-                }
-                const uint32_t gated = d.slot_gated[op.slot];
-                for (int q = 0; q < k; ++q) {
-                    if (!((gated >> q) & 1u)) continue;
-                    T gq;
-                    if (q >= P && q < P + R) {
-                        gq = T(0);
-#pragma unroll
-                        for (int r = 0; r < NR; ++r) gq += ((r >> (q - P)) & 1) ? -u[r] : u[r];
-                    } else {
-                        gq = ((e0 >> q) & 1u) ? -tot : tot;
-                    }
-                    if constexpr (sizeof(T) == 4) {
-                        reinterpret_cast<float *>(gsh)[(2 * q + 1) * nthr + t] = gq;
-                    } else {
-                        for (int o = wlanes >> 1; o > 0; o >>= 1) gq += __shfl_xor_sync(wmask, gq, o);
-                        if (lane == 0) gsh[(warp * k + q) * 2 + 1] = (double)gq;
-                    }
-                }
             }
             const uint32_t g0 = g32(e0);
             // CZ signs of the NR registers as one mask (see run_tile)
@@ -841,47 +824,95 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
                 }
             }
         } else if constexpr (kind == 4) {       // block totals of a slot's gradient partials
+            // The tile shape is fixed by the program: k = top chunk + R bits,
+            // NT = 2^(k - R) threads, NW warps.  Warp w sums rows w, w + NW, ...
+            // (RPW of them) together, so that the loads and the shuffle trees of
+            // its rows interleave instead of forming one dependent chain per row;
+            // lanes add a strided part of each row, then a shuffle tree, in a
+            // fixed order (bitwise reproducible).
+            constexpr int KT = prog_top_chunk<Codes...>() + R;
+            constexpr int NT = 1 << (KT - R);
+            constexpr int NW = NT / 32;
+            [[maybe_unused]] constexpr int RPW = (2 * KT + NW - 1) / NW;
+            static_assert(NT >= 32, "fixed programs run whole warps");
             if constexpr (BWD && sizeof(T) == 4) {
-                // each warp sums whole rows in a fixed order: lanes add a strided
-                // part of the row, then a shuffle tree (bitwise reproducible);
-                // every add is a compensated FP32 add (csum.cuh)
+                // compensated FP32 sums (csum.cuh); theta rows come scaled by gs,
+                // phi from the chunk rows or the signed total row
                 const PassOp op = ops[i];
                 __syncthreads();
                 const uint32_t gated = d.slot_gated[op.slot];
-                const int nw = (int)((nthr + 31) >> 5);
+                const int dp = diag_chunk;
                 const float *gpt = reinterpret_cast<const float *>(gsh);
-                for (int idx = warp; idx < 2 * k; idx += nw) {
-                    if (!((gated >> (idx >> 1)) & 1u)) continue;
-                    F32c sum = f32c_zero();
-                    for (uint32_t tt = lane; tt < nthr; tt += 32) f32c_add(sum, gpt[idx * nthr + tt]);
-                    sum = f32c_warp_sum(sum, 0xffffffffu, 32);
-                    if (lane == 0) env.grad(op.slot, idx >> 1, idx & 1, f32c_value(sum));
+                F32c sum[RPW];
+#pragma unroll
+                for (int r = 0; r < RPW; ++r) {
+                    const int idx = warp + r * NW;
+                    const int q = idx >> 1, comp = idx & 1;
+                    sum[r] = f32c_zero();
+                    if (idx < 2 * KT && ((gated >> q) & 1u)) {
+                        const bool in_chunk = q >= dp && q < dp + R;
+                        const float *src = gpt + (comp == 0 ? q : (in_chunk ? k + 1 + q - dp : k)) * NT;
+                        const bool signed_total = comp == 1 && !in_chunk;
+                        auto term = [&](uint32_t tt) {
+                            const float v = src[tt];
+                            return signed_total ? flip_sign(v, (elem_of(tt, 0, dp, R) >> q) & 1u) : v;
+                        };
+                        sum[r].hi = term(lane);
+#pragma unroll
+                        for (int c = 1; c < NT / 32; ++c) f32c_add(sum[r], term(lane + 32 * c));
+                    }
+                }
+#pragma unroll 1
+                for (int r = 0; r < RPW; ++r)
+                    for (int o = 16; o > 0; o >>= 1) sum[r] = f32c_add_lazy(sum[r], f32c_shfl_xor(0xffffffffu, sum[r], o));
+                if (lane == 0) {
+#pragma unroll
+                    for (int r = 0; r < RPW; ++r) {
+                        const int idx = warp + r * NW;
+                        if (idx < 2 * KT && ((gated >> (idx >> 1)) & 1u))
+                            env.grad(op.slot, idx >> 1, idx & 1, f32c_value(sum[r]));
+                    }
                 }
                 __syncthreads();
             } else if constexpr (BWD) {
-                // FP64: each warp sums whole rows in a fixed order (lanes add a
-                // strided part, then a shuffle tree): theta rows scaled by the
-                // bit's gs, phi from the chunk rows or the signed total row
+                // FP64: theta rows scaled by the bit's gs, phi from the chunk
+                // rows or the signed total row
                 const PassOp op = ops[i];
                 __syncthreads();
                 const uint32_t gated = d.slot_gated[op.slot];
-                const int nw = (int)((nthr + 31) >> 5);
                 const int dp = diag_chunk;
-                for (int idx = warp; idx < 2 * k; idx += nw) {
+                double sum[RPW];
+#pragma unroll
+                for (int r = 0; r < RPW; ++r) {
+                    const int idx = warp + r * NW;
                     const int q = idx >> 1, comp = idx & 1;
-                    if (!((gated >> q) & 1u)) continue;
-                    double sum = 0.0;
-                    if (comp == 0) {
-                        for (uint32_t tt = lane; tt < nthr; tt += 32) sum += gsh[q * nthr + tt];
-                    } else if (q >= dp && q < dp + R) {
-                        for (uint32_t tt = lane; tt < nthr; tt += 32) sum += gsh[(k + 1 + q - dp) * nthr + tt];
-                    } else {
-                        for (uint32_t tt = lane; tt < nthr; tt += 32)
-                            sum += flip_sign(gsh[k * nthr + tt], (elem_of(tt, 0, dp, R) >> q) & 1u);
+                    sum[r] = 0.0;
+                    if (idx < 2 * KT && ((gated >> q) & 1u)) {
+                        const bool in_chunk = q >= dp && q < dp + R;
+                        const double *src = gsh + (comp == 0 ? q : (in_chunk ? k + 1 + q - dp : k)) * NT;
+                        const bool signed_total = comp == 1 && !in_chunk;
+                        auto term = [&](uint32_t tt) {
+                            const double v = src[tt];
+                            return signed_total ? flip_sign(v, (elem_of(tt, 0, dp, R) >> q) & 1u) : v;
+                        };
+                        sum[r] = term(lane);
+#pragma unroll
+                        for (int c = 1; c < NT / 32; ++c) sum[r] += term(lane + 32 * c);
                     }
-                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-                    if (lane == 0)
-                        env.grad(op.slot, q, comp, comp == 0 ? sum * (double)env.coef(op.slot, q).gs : sum);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int r = 0; r < RPW; ++r) sum[r] += __shfl_xor_sync(0xffffffffu, sum[r], o);
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int r = 0; r < RPW; ++r) {
+                        const int idx = warp + r * NW;
+                        const int q = idx >> 1, comp = idx & 1;
+                        if (idx < 2 * KT && ((gated >> q) & 1u))
+                            env.grad(op.slot, q, comp, comp == 0 ? sum[r] * (double)env.coef(op.slot, q).gs : sum[r]);
+                    }
                 }
                 __syncthreads();
             }

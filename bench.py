@@ -448,6 +448,7 @@ def run_gpu(args, world, rank, local, pg):
                            "tflops": fl_f / (fwd_ms / 1e3) / 1e12,
                            "hbm_gbs": by_f / (fwd_ms / 1e3) / 1e9},
         "apply_h": {"ms": app_ms, "launches": prof["apply_h"]["launches"] / steps,
+                    "form": tuned["apply_form"] if tuned else None,
                     "hbm_gbs_algorithmic": 2 * state_b / (app_ms / 1e3) / 1e9},
         "backward_passes": {"ms": bwd_ms, "launches": bwd_launches,
                             "tflops": fl_b / (bwd_ms / 1e3) / 1e12,
@@ -523,6 +524,9 @@ def run_gpu(args, world, rank, local, pg):
     if not args.no_extras:
         e64 = pkg.Engine(n, D, "c64", stream=stream)
         e64.set_hamiltonian(H.x, H.z, H.c)
+        tuned64 = None
+        if not args.no_autotune:
+            tuned64 = e64.autotune(p_last, gradient=True, budget_ms=args.tune_ms)
         G64 = torch.empty_like(G)
         f64 = lambda: e64.gradient_batch_dev(p_last, G64, E)  # noqa: E731
         f64()
@@ -545,6 +549,7 @@ def run_gpu(args, world, rank, local, pg):
                "gradient_rel_err_vs_fp64": float(np.max(np.abs(g64 - g128)) / np.max(np.abs(g128))),
                "kernels": {"forward_passes": {"ms": f_ms, "hbm_gbs": b_f / (f_ms / 1e3) / 1e9},
                            "apply_h": {"ms": a_ms,
+                                       "form": tuned64["apply_form"] if tuned64 else None,
                                        "hbm_gbs_algorithmic": 2 * st64 / (a_ms / 1e3) / 1e9},
                            "backward_passes": {"ms": b_ms, "hbm_gbs": b_b / (b_ms / 1e3) / 1e9}},
                "hbm_gbs_algorithmic_eval": (6 * D + 2) * st64 / (t64 / 1e3) / 1e9,
@@ -729,7 +734,7 @@ def run_workload(name: str, args):
                 by_f += tile * (2 * live_f + (tiles - live_f if i == 0 else 0))
                 by_b += tile * 4 * live_b
             out[prec] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms, "energy": float(E[0]),
-                         "passes": npass, "apply_windowed": tune["apply_windowed"],
+                         "passes": npass, "apply_form": tune["apply_form"],
                          "forward_ms": f_ms, "apply_h_ms": pr["apply_h"]["ms"] / reps,
                          "backward_ms": b_ms,
                          "forward_hbm_gbs": by_f / (f_ms / 1e3) / 1e9,
@@ -883,7 +888,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tune-ms", type=float, default=0.0,
                     help="autotuner budget: plans after the default are timed while the "
-                         "summed time stays below it (0: the default plan and both apply-H forms)")
+                         "summed time stays below it (0: the default plan and every apply-H form)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     args = ap.parse_args()

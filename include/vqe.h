@@ -132,12 +132,16 @@ vqe_status vqe_set_plan_options(vqe_handle h, int tile_bits_max, int run_bits, i
 /* Form of lambda = H psi in gradient evaluations (the adjoint's apply-H):
  * mode 0 = one sweep over the state that gathers psi_{i^x} for every X-mask
  * group; mode 1 = accumulated window by window over the expectation's tile
- * windows (where every group fits a window, else the sweep); mode -1
- * (default) = windows when they hold at least 10 groups each.  The choice
- * persists across vqe_set_hamiltonian and vqe_slim; *windowed (may be NULL)
- * reports the form the current Hamiltonian will use.  Results agree to
- * rounding order. */
-vqe_status vqe_set_apply_mode(vqe_handle h, int mode, int *windowed);
+ * windows (where every group fits a window); mode 2 = bit-ordered sweeps:
+ * the groups are split into a few sweeps whose state order makes the X bits
+ * of their groups run fastest, so that the gathered partners are read from
+ * L2 (where every group's terms fit a sweep); a form the Hamiltonian cannot
+ * use falls back to mode 0.  Mode -1 (default) = windows when they hold
+ * at least 10 groups each, else mode 0; the autotuner times all three.  The
+ * choice persists across vqe_set_hamiltonian and vqe_slim; *form (may be
+ * NULL) reports the form (0, 1 or 2) the current Hamiltonian will use.
+ * Results agree to rounding order.  VQE_ERR_ARG for a mode outside -1..2. */
+vqe_status vqe_set_apply_mode(vqe_handle h, int mode, int *form);
 
 /* Set the Hamiltonian H = sum_t coeffs[t] * P(x_masks[t], z_masks[t])
  * (Sec. II-B, Eqs. 2-4).  Host arrays of length n_terms; masks must have no
@@ -200,8 +204,8 @@ vqe_status vqe_get_stats(vqe_handle h, vqe_stats *out);
  * memory, as the *_batch_dev calls take them; gradient = 1 times energy +
  * adjoint gradient, 0 the energy) under candidate tile plans (the default
  * first, then other tile sizes -- the qubits fused per pass --, register
- * counts and run lengths; see vqe_set_plan_options), and, for gradients, both
- * forms of lambda = H psi (vqe_set_apply_mode) on the same state.  It keeps
+ * counts and run lengths; see vqe_set_plan_options), and, for gradients, the
+ * possible forms of lambda = H psi (vqe_set_apply_mode) on the same state.  It keeps
  * the fastest plan and form on the handle.  Candidates after the default are
  * tried while the summed timed milliseconds stay below budget_ms.  Each
  * candidate runs once untimed (while evaluations take under 2 s) and once
@@ -210,10 +214,11 @@ vqe_status vqe_get_stats(vqe_handle h, vqe_stats *out);
  * vqe_apply_ansatz is discarded.  out (may be NULL) receives the choice. */
 typedef struct {
     int tile_bits_max, run_bits, reg_bits;   /* chosen plan options (resolved values) */
-    int apply_windowed;                      /* 1: lambda = H psi over windows */
+    int apply_form;                          /* chosen form of lambda = H psi (vqe_set_apply_mode) */
     int candidates;                          /* plans timed */
     double ms_default, ms_best;              /* per evaluation: default plan, chosen plan */
-    double apply_ms_global, apply_ms_windows;   /* per state, gradient tuning only (else 0) */
+    /* per state, gradient tuning only; 0 for a form not possible or not timed */
+    double apply_ms_global, apply_ms_windows, apply_ms_sweeps;
 } vqe_tuning;
 vqe_status vqe_autotune(vqe_handle h, const double *params_dev, int batch, int gradient,
                         double budget_ms, vqe_tuning *out);

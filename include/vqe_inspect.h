@@ -19,7 +19,8 @@ extern "C" {
 
 /* sizeof of internal record `which`: 0 = pass descriptor, 1 = staging slot,
  * 2 = term group, 3 = energy window, 4 = window group, 5 = window term,
- * 6 = excitation pass, 7 = excitation gate; 0 for an unknown `which`. */
+ * 6 = excitation pass, 7 = excitation gate, 8 = apply-H sweep, 9 = sweep
+ * group; 0 for an unknown `which`. */
 size_t vqe_inspect_sizeof(int which);
 
 /* Tile-pass plan of the ansatz for (n, depth, precision, options) -- options
@@ -63,6 +64,22 @@ int vqe_inspect_windows(int n_qubits, int precision, const uint64_t *x_masks,
                         int max_windows,
                         void *wgroups, int max_wgroups, void *wterms, int max_wterms,
                         uint32_t *hoff, int max_hoff, void *wide, int max_wide, int counts[5]);
+
+/* Sweeps of the sweep form of lambda = H psi (vqe_set_apply_mode 2) for the
+ * same prepared terms: sweep records (max_sweeps), sweep groups
+ * (max_groups), pattern entries (first term | count << 16, max_pat), merged terms (Z bits and
+ * A / B coefficients, max_terms), and the sweeps' bit-order tables (1024
+ * entries per sweep: counter byte b with value v maps to order[1024 * w +
+ * 256 * b + v]).  diag_terms as for vqe_inspect_windows.  counts[4] =
+ * sweeps, groups, pattern entries, terms.  Returns 0, or -1 on invalid
+ * input, too-small buffers, or a Hamiltonian whose groups do not fit the
+ * sweeps (the library then uses another form). */
+int vqe_inspect_sweeps(int n_qubits, int precision, const uint64_t *x_masks,
+                       const uint64_t *z_masks, const double *coeffs, size_t n_terms,
+                       double threshold, int diag_terms, void *sweeps, int max_sweeps,
+                       void *groups, int max_groups, uint32_t *pat, int max_pat, uint32_t *tz,
+                       double *ta, double *tb, int max_terms, uint32_t *order, int max_order,
+                       int counts[4]);
 
 /* Pass plan of the particle-conserving ansatz (vqe_create_pc) for the same
  * arguments: excitation passes (max_passes) with their support masks, their

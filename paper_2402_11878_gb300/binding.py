@@ -26,7 +26,7 @@ EXPORTED = [
     "vqe_gradient", "vqe_energy_batch_dev", "vqe_gradient_batch_dev", "vqe_energy_batch",
     "vqe_gradient_batch", "vqe_energy_batch_pergate_dev", "vqe_get_stats", "vqe_last_error",
     "vqe_version", "vqe_profile", "vqe_profile_read", "vqe_inspect_sizeof", "vqe_inspect_plan",
-    "vqe_inspect_hamiltonian", "vqe_inspect_windows", "vqe_inspect_pc_plan", "vqe_energy_noalloc", "vqe_batch_create", "vqe_batch_destroy",
+    "vqe_inspect_hamiltonian", "vqe_inspect_windows", "vqe_inspect_sweeps", "vqe_inspect_pc_plan", "vqe_energy_noalloc", "vqe_batch_create", "vqe_batch_destroy",
     "vqe_batch_set_hamiltonian", "vqe_batch_param_offsets", "vqe_batch_run_dev", "vqe_batch_run",
     "vqe_batch_set_tile_bits", "vqe_batch_autotune", "vqe_batch_launch_count",
     "vqe_batch_last_error", "vqe_measure_fma_peak", "vqe_testing_fail_allocations",
@@ -49,10 +49,10 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_bits_max", ctypes.c_int), ("run_bits", ctypes.c_int),
-                ("reg_bits", ctypes.c_int), ("apply_windowed", ctypes.c_int),
+                ("reg_bits", ctypes.c_int), ("apply_form", ctypes.c_int),
                 ("candidates", ctypes.c_int), ("ms_default", ctypes.c_double),
                 ("ms_best", ctypes.c_double), ("apply_ms_global", ctypes.c_double),
-                ("apply_ms_windows", ctypes.c_double)]
+                ("apply_ms_windows", ctypes.c_double), ("apply_ms_sweeps", ctypes.c_double)]
 
 
 class KernelTimes(ctypes.Structure):
@@ -121,6 +121,8 @@ def load() -> ctypes.CDLL:
                                     vp, vp],
         "vqe_inspect_windows": [i, i, vp, vp, vp, sz, ctypes.c_double, i, vp, i, vp, i, vp,
                                 i, vp, i, vp, i, vp],
+        "vqe_inspect_sweeps": [i, i, vp, vp, vp, sz, ctypes.c_double, i, vp, i, vp, i, vp, i,
+                               vp, vp, vp, i, vp, i, vp],
         "vqe_inspect_pc_plan": [i, i, i, i, vp, vp, i, vp, i, vp, i, vp],
     }
     for name, args in sig.items():
@@ -302,12 +304,12 @@ class Engine:
         """Choose the tile plan (0 = default); see vqe_set_plan_options."""
         self._check(self._lib.vqe_set_plan_options(self._h, tile_bits_max, run_bits, reg_bits))
 
-    def set_apply_mode(self, mode: int) -> bool:
-        """lambda = H psi form: -1 automatic, 0 global sweep, 1 windows; returns
-        whether the current Hamiltonian will use the windows."""
+    def set_apply_mode(self, mode: int) -> int:
+        """lambda = H psi form: -1 automatic, 0 global sweep, 1 windows, 2
+        bit-ordered sweeps; returns the form the current Hamiltonian will use."""
         out = ctypes.c_int()
         self._check(self._lib.vqe_set_apply_mode(self._h, int(mode), ctypes.byref(out)))
-        return bool(out.value)
+        return out.value
 
     def autotune(self, params_dev, gradient: bool = True, budget_ms: float = 60000.0) -> dict:
         """Time candidate tile plans (and apply-H forms) on device params and

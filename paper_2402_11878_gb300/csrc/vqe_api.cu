@@ -60,12 +60,16 @@ struct HamDev {
     std::vector<WinDesc> wins;
     DevBuf d_wgroups, d_wterms, d_whoff, d_wide;
     int n_wide = 0;
-    // lambda = H psi over the windows above (else one global sweep): possible
-    // when every group fits a window, chosen by default when the windows hold
-    // many groups each, else as vqe_set_apply_mode says
-    bool apply_possible = false, apply_default = false;
-    bool apply_windows = false;
+    // lambda = H psi: form 0 = one global sweep gathering psi_{i^x} per
+    // group; 1 = over the windows above (possible when every group fits a
+    // window); 2 = bit-ordered sweeps (SweepDesc; possible when every group's
+    // merged terms fit a sweep).  apply_default is the form of mode -1;
+    // apply_form the one in use.
+    bool win_possible = false, sweep_possible = false;
+    int apply_default = 0, apply_form = 0;
     int win_tiles = 0;   // columns of all windows per state
+    std::vector<SweepDesc> sweeps;
+    DevBuf d_sorder, d_sgroups, d_spat, d_stz, d_sta, d_stb;
     // diagonal of H (one T per basis state), built when it fits in a quarter
     // of the free device memory; null: the x = 0 terms are evaluated inline
     DevBuf d_hdiag, d_hdiag_z, d_hdiag_c;
@@ -73,10 +77,20 @@ struct HamDev {
     const void *hdiag() const { return hdiag_ok ? d_hdiag.p : nullptr; }
     void release() {
         for (DevBuf *b : {&d_groups, &d_tz, &d_tc, &d_wgroups, &d_wterms, &d_whoff, &d_wide,
-                          &d_hdiag, &d_hdiag_z, &d_hdiag_c})
+                          &d_hdiag, &d_hdiag_z, &d_hdiag_c, &d_sorder, &d_sgroups, &d_spat, &d_stz,
+                          &d_sta, &d_stb})
             b->release();
     }
 };
+
+// Form of apply-H for vqe_set_apply_mode's mode: -1 the plan's default; a
+// form the Hamiltonian cannot use falls back to the global sweep.
+int resolve_apply_form(int mode, const HamDev &d) {
+    if (mode < 0) return d.apply_default;
+    if (mode == 1 && d.win_possible) return 1;
+    if (mode == 2 && d.sweep_possible) return 2;
+    return 0;
+}
 
 }  // namespace
 
@@ -118,6 +132,7 @@ struct vqe_ctx {
     bool ws_owned = false;
     DevBuf ws_own;
     DevBuf d_params, d_coefs, d_dtab, d_gpart, d_epart, d_out;
+    DevBuf d_sctr;   // chunk counters of the sweep form of apply-H
     DevBuf hb_params, hb_e, hb_n, hb_g;   // device copies for the host-buffer batch calls
     int scratch_batch = 0;
 
@@ -1237,6 +1252,205 @@ void plan_windows(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms,
     }
 }
 
+// Sweeps of the sweep form of apply-H (see SweepDesc): the groups are
+// assigned greedily, in decreasing X-mask order, to the sweep whose fast
+// bits grow least by the group's X bits above the low run, while the fast
+// bits stay within kSweepFastBits - mlo; groups with more such bits join the
+// last sweep (their partners then come from DRAM).  The diagonal goes to the
+// first sweep: D_i psi_i from the precomputed diagonal, or the x = 0 group's
+// terms when `diag_terms`.
+struct SweepPlan {
+    std::vector<SweepDesc> sweeps;
+    std::vector<SGroup> groups;
+    std::vector<uint32_t> pat;
+    std::vector<uint32_t> tz;
+    std::vector<double> ta, tb;
+    std::vector<uint32_t> order;   // 1024 per sweep
+    bool ok = false;               // false: a group has more terms than a sweep holds
+};
+
+void plan_sweeps(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms, SweepPlan &sp) {
+    sp = SweepPlan{};
+    const int mlo = std::min(n, prec == VQE_C128 ? 4 : 5);   // runs of 256 bytes
+    const int fmax = std::max(0, std::min(n, kSweepFastBits) - mlo);
+    const uint32_t lowm = (1u << mlo) - 1u;
+    // one group in pattern form: per pattern of its X bits, the terms merged
+    // by z & ~x (A and B coefficients); a group with more X bits keeps its
+    // terms (one pattern, z unmasked)
+    struct MTerm { uint32_t z; double a, b; };
+    struct MGroup {
+        uint32_t x = 0;
+        std::vector<int> xb;
+        std::vector<std::vector<MTerm>> pats;
+        bool has_b = false;
+        int n_terms = 0;
+    };
+    auto merge = [&](const GroupDesc &G) {
+        MGroup mg;
+        mg.x = G.x;
+        const int nx = __builtin_popcount(G.x);
+        const bool pattern_form = nx <= kSweepMaxXBits;
+        if (pattern_form)
+            for (int q = 0; q < 32; ++q)
+                if ((G.x >> q) & 1u) mg.xb.push_back(q);
+        const int np = pattern_form ? 1 << nx : 1;
+        mg.pats.resize(np);
+        for (int pv = 0; pv < np; ++pv) {
+            const uint32_t v = pattern_form ? deposit_bits(uint32_t(pv), G.x) : 0u;
+            std::vector<MTerm> &ts = mg.pats[pv];
+            for (int t = G.t_begin; t < G.t_end; ++t) {
+                const bool cls_b = t >= G.t_mid;
+                const uint32_t z = hp.tz[t];
+                const uint32_t zk = pattern_form ? (z & ~G.x) : z;
+                const double c = (__builtin_popcount(v & z) & 1) ? -hp.tc[t] : hp.tc[t];
+                size_t k = 0;
+                while (k < ts.size() && ts[k].z != zk) ++k;
+                if (k == ts.size()) ts.push_back({zk, 0.0, 0.0});
+                (cls_b ? ts[k].b : ts[k].a) += c;
+            }
+            std::vector<MTerm> kept;
+            for (const MTerm &m : ts)
+                if (m.a != 0.0 || m.b != 0.0) {
+                    kept.push_back(m);
+                    mg.has_b = mg.has_b || m.b != 0.0;
+                }
+            ts.swap(kept);
+            mg.n_terms += int(ts.size());
+        }
+        return mg;
+    };
+    struct SC {
+        uint32_t F = 0;                  // fast bits above the low run
+        std::vector<MGroup> groups;
+        int terms = 0, pats = 0;
+    };
+    std::vector<SC> sc(1);
+    std::vector<MGroup> wide;
+    // term slots and pattern entries a group takes: a group whose patterns
+    // hold at most one term each takes one slot per pattern and no entry
+    auto slots = [](const MGroup &mg) {
+        bool multi = false;
+        for (const auto &ts : mg.pats) multi = multi || ts.size() > 1;
+        return multi ? std::make_pair(mg.n_terms, int(mg.pats.size())) : std::make_pair(int(mg.pats.size()), 0);
+    };
+    auto fits = [&](const SC &c, const MGroup &mg) {
+        const auto sl = slots(mg);
+        return int(c.groups.size()) + 1 <= kSweepMaxGroups && c.terms + sl.first <= kSweepMaxTerms &&
+               c.pats + sl.second <= kSweepMaxPat;
+    };
+    auto add = [&](SC &c, MGroup &&mg) {
+        const auto sl = slots(mg);
+        c.terms += sl.first;
+        c.pats += sl.second;
+        c.groups.push_back(std::move(mg));
+    };
+    std::vector<int> order_g;
+    for (size_t g = 0; g < hp.groups.size(); ++g) {
+        if (hp.groups[g].x != 0u) {
+            order_g.push_back(int(g));
+        } else if (diag_terms) {                    // first, in the first sweep
+            MGroup mg = merge(hp.groups[g]);
+            if (mg.n_terms == 0) continue;
+            if (!fits(sc[0], mg)) return;           // more terms than a sweep holds (sp.ok false)
+            add(sc[0], std::move(mg));
+        }
+    }
+    std::stable_sort(order_g.begin(), order_g.end(),
+                     [&](int p, int q) { return hp.groups[p].x > hp.groups[q].x; });
+    for (int g : order_g) {
+        const GroupDesc &G = hp.groups[g];
+        MGroup mg = merge(G);
+        if (mg.n_terms == 0) continue;              // every term cancels
+        if (!fits(SC{}, mg)) return;                // more terms than a sweep holds
+        const uint32_t H = G.x & ~lowm;
+        if (__builtin_popcount(H) > fmax) {
+            wide.push_back(std::move(mg));
+            continue;
+        }
+        int best = -1, best_add = 1 << 30;
+        for (size_t c = 0; c < sc.size(); ++c) {
+            const int sz = __builtin_popcount(sc[c].F | H);
+            if (sz > fmax || !fits(sc[c], mg)) continue;
+            const int add = sz - __builtin_popcount(sc[c].F);
+            if (add < best_add) {
+                best_add = add;
+                best = int(c);
+            }
+        }
+        if (best < 0) {
+            sc.push_back(SC{});
+            best = int(sc.size()) - 1;
+        }
+        sc[best].F |= H;
+        add(sc[best], std::move(mg));
+    }
+    for (MGroup &mg : wide) {
+        if (!fits(sc.back(), mg)) sc.push_back(SC{});
+        add(sc.back(), std::move(mg));
+    }
+    for (size_t c = 0; c < sc.size(); ++c) {
+        SweepDesc W{};
+        W.g_begin = int(sp.groups.size());
+        W.p_begin = int(sp.pat.size());
+        W.t_begin = int(sp.tz.size());
+        W.order = int(c);
+        W.diag = c == 0 ? 1 : 0;
+        W.fast = lowm | sc[c].F;
+        for (const MGroup &mg : sc[c].groups) {
+            SGroup sg{};
+            sg.x = mg.x;
+            bool multi = false;
+            for (const auto &ts : mg.pats) multi = multi || ts.size() > 1;
+            for (size_t k = 0; k < mg.xb.size(); ++k) sg.xbits |= uint32_t(mg.xb[k]) << (5 * k);
+            if (!multi) {
+                // one term slot per pattern, in pattern order (zero for an
+                // empty pattern): the pattern indexes its term directly
+                sg.pat = int(sp.tz.size()) - W.t_begin;
+                for (const auto &ts : mg.pats) {
+                    const MTerm m = ts.empty() ? MTerm{0u, 0.0, 0.0} : ts[0];
+                    sp.tz.push_back(m.z);
+                    sp.ta.push_back(m.a);
+                    sp.tb.push_back(m.b);
+                }
+            } else {
+                sg.pat = int(sp.pat.size()) - W.p_begin;
+                for (const auto &ts : mg.pats) {
+                    const uint32_t first = ts.empty() ? 0u : uint32_t(int(sp.tz.size()) - W.t_begin);
+                    sp.pat.push_back(first | uint32_t(ts.size()) << 16);
+                    for (const MTerm &m : ts) {
+                        sp.tz.push_back(m.z);
+                        sp.ta.push_back(m.a);
+                        sp.tb.push_back(m.b);
+                    }
+                }
+            }
+            sg.flags = uint32_t(mg.xb.size()) | (mg.has_b ? 1u << 8 : 0u) | (multi ? 1u << 9 : 0u);
+            sp.groups.push_back(sg);
+        }
+        W.g_end = int(sp.groups.size());
+        W.n_pat = int(sp.pat.size()) - W.p_begin;
+        W.t_count = int(sp.tz.size()) - W.t_begin;
+        // counter bit k -> global bit ord[k]: the low run, the fast bits, the rest
+        std::vector<int> ord;
+        for (int q = 0; q < mlo; ++q) ord.push_back(q);
+        for (int q = mlo; q < n; ++q)
+            if ((sc[c].F >> q) & 1u) ord.push_back(q);
+        for (int q = mlo; q < n; ++q)
+            if (!((sc[c].F >> q) & 1u)) ord.push_back(q);
+        for (int byte = 0; byte < 4; ++byte)
+            for (uint32_t v = 0; v < 256; ++v) {
+                uint32_t a = 0;
+                for (int t = 0; t < 8; ++t) {
+                    const int k = 8 * byte + t;
+                    if (k < n && ((v >> t) & 1u)) a |= 1u << ord[k];
+                }
+                sp.order.push_back(a);
+            }
+        sp.sweeps.push_back(W);
+    }
+    sp.ok = true;
+}
+
 // Builds the device plan of the kept terms into a new HamDev and swaps it
 // into the handle only when every step has succeeded; on failure the
 // handle keeps its previous plan.
@@ -1294,14 +1508,39 @@ vqe_status build_ham_plan(vqe_ctx *h) {
         if ((st = upload(h, nd.d_wide, wp.wide, "wide groups")) != VQE_OK) return bail(st);
         // windowed apply-H (same windows and groups): psi is read and lambda
         // read and written once per window, against one gathered read of psi
-        // per group in the global sweep.  By default it is used when the
-        // windows hold many groups each (measured at 24 qubits in complex64:
-        // the 25 Hubbard groups in 2 windows favour the global sweep, the
-        // molecular 5,479 groups the windows); vqe_set_apply_mode and the
-        // autotuner override the choice.
-        nd.apply_possible = wp.wide.empty() && !wp.wins.empty();
-        nd.apply_default = nd.apply_possible && hp.groups.size() >= 10 * wp.wins.size();
-        nd.apply_windows = h->apply_mode < 0 ? nd.apply_default : (nd.apply_possible && h->apply_mode == 1);
+        // per group in the global sweep.
+        nd.win_possible = wp.wide.empty() && !wp.wins.empty();
+    }
+    {
+        // bit-ordered sweeps: psi read and lambda written once per sweep, the
+        // gathers served by L2
+        SweepPlan sp;
+        plan_sweeps(h->n, h->prec, hp, !nd.hdiag_ok, sp);
+        nd.sweep_possible = sp.ok && !sp.sweeps.empty();
+        if (nd.sweep_possible) {
+            nd.sweeps = sp.sweeps;
+            if ((st = upload(h, nd.d_sorder, sp.order, "sweep orders")) != VQE_OK) return bail(st);
+            if ((st = upload(h, nd.d_sgroups, sp.groups, "sweep groups")) != VQE_OK) return bail(st);
+            if ((st = upload(h, nd.d_spat, sp.pat, "sweep patterns")) != VQE_OK) return bail(st);
+            if ((st = upload(h, nd.d_stz, sp.tz, "sweep terms")) != VQE_OK) return bail(st);
+            if (h->prec == VQE_C128) {
+                if ((st = upload(h, nd.d_sta, sp.ta, "sweep terms")) != VQE_OK) return bail(st);
+                if ((st = upload(h, nd.d_stb, sp.tb, "sweep terms")) != VQE_OK) return bail(st);
+            } else {
+                std::vector<float> fa(sp.ta.begin(), sp.ta.end()), fb(sp.tb.begin(), sp.tb.end());
+                if ((st = upload(h, nd.d_sta, fa, "sweep terms")) != VQE_OK) return bail(st);
+                if ((st = upload(h, nd.d_stb, fb, "sweep terms")) != VQE_OK) return bail(st);
+            }
+        }
+        // default form (mode -1): the windows when they hold many groups each
+        // (measured at 24 qubits in complex64: the 25 Hubbard groups in 2
+        // windows favour the global sweep, the molecular 5,479 groups the
+        // windows), else the global sweep.  The bit-ordered sweeps win on
+        // lattice Hamiltonians at 32 qubits (complex64 326 against 342 ms
+        // for the windows) and lose on molecular ones (215 against 69 ms at
+        // 24 qubits): vqe_set_apply_mode and the autotuner choose them.
+        nd.apply_default = nd.win_possible && hp.groups.size() >= 10 * nd.wins.size() ? 1 : 0;
+        nd.apply_form = resolve_apply_form(h->apply_mode, nd);
     }
     if ((st = upload(h, nd.d_groups, hp.groups, "groups")) != VQE_OK) return bail(st);
     if ((st = upload(h, nd.d_tz, hp.tz, "terms")) != VQE_OK) return bail(st);
@@ -1541,8 +1780,43 @@ vqe_status run_apply_h(vqe_ctx *h, int B, void *psi, void *lam, double *E) {
     cudaStream_t s = h->stream;
     const size_t N = h->state_elems();
     const int mk_h = prof_begin(h, 2);
-    const uint64_t atiles = h->hd.apply_windows ? (uint64_t(1) << (h->n - h->hd.wins[0].k)) : 0;
-    if (h->hd.apply_windows && atiles * B >= uint64_t(2 * h->sms)) {
+    const bool windows = h->hd.apply_form == 1;
+    const uint64_t atiles = windows ? (uint64_t(1) << (h->n - h->hd.wins[0].k)) : 0;
+    if (h->hd.apply_form == 2) {
+        // bit-ordered sweeps: lambda accumulated sweep by sweep; the last
+        // sweep writes the energy partials of its chunks (summed in chunk
+        // order).  Blocks take chunks from one zeroed counter per sweep and
+        // state; as many blocks as are resident at once.
+        const int ns = int(h->hd.sweeps.size());
+        const uint64_t nchunks = ((uint64_t(1) << h->n) + kSweepChunk - 1) / kSweepChunk;
+        vqe_status st2 = ensure(h, h->d_sctr, sizeof(unsigned long long) * size_t(ns) * B, "sweep counters");
+        if (st2 == VQE_OK)
+            st2 = ensure(h, h->d_epart, sizeof(double) * 3 * size_t(nchunks) * B + 16, "partials");
+        if (st2 != VQE_OK) return st2;
+        VQE_CUDA(h, cudaMemsetAsync(h->d_sctr.p, 0, sizeof(unsigned long long) * size_t(ns) * B, s));
+        size_t smem = 0;
+        for (const SweepDesc &W : h->hd.sweeps)
+            smem = std::max(smem, sweep_smem_bytes(W, h->prec == VQE_C128 ? 8 : 4));
+        const int occ = sweep_blocks_per_sm(h->prec == VQE_C128 ? 16 : 8, smem);
+        const int blocks = int(std::max<uint64_t>(1, std::min<uint64_t>(nchunks, uint64_t(h->sms) * occ / B)));
+        auto *ctr = static_cast<unsigned long long *>(h->d_sctr.p);
+        for (int w = 0; w < ns; ++w) {
+            const SweepDesc &W = h->hd.sweeps[w];
+            VQE_CUDA(h, launch_apply_h_sweep<T>(W, static_cast<const uint32_t *>(h->hd.d_sorder.p) + size_t(W.order) * 1024,
+                                                static_cast<const SGroup *>(h->hd.d_sgroups.p),
+                                                static_cast<const uint32_t *>(h->hd.d_spat.p),
+                                                static_cast<const uint32_t *>(h->hd.d_stz.p),
+                                                h->hd.d_sta.p, h->hd.d_stb.p, h->hd.hdiag(), h->n, B,
+                                                psi, lam, N, w == 0 ? 1 : 0, w == ns - 1 ? 1 : 0,
+                                                ctr + size_t(w) * B, static_cast<double *>(h->d_epart.p),
+                                                blocks, s));
+            h->stats.kernel_launches++;
+        }
+        prof_end(h, mk_h, ns);
+        VQE_CUDA(h, launch_energy_finish(static_cast<double *>(h->d_epart.p), int(nchunks), B, E, nullptr,
+                                         nullptr, s));
+        h->stats.kernel_launches++;
+    } else if (windows && atiles * B >= uint64_t(2 * h->sms)) {
         // windowed: lambda accumulated window by window; the last window's
         // blocks hold the partials of the energy
         const int bps_w = int(atiles);
@@ -1765,7 +2039,7 @@ vqe_status vqe_destroy(vqe_handle h) {
     h->hd.release();
     h->d_pc_gates.release();
     h->d_pc_hoff.release();
-    for (DevBuf *b : {&h->ws_own, &h->d_params, &h->d_coefs, &h->d_dtab, &h->d_gpart, &h->d_epart,
+    for (DevBuf *b : {&h->ws_own, &h->d_params, &h->d_coefs, &h->d_dtab, &h->d_gpart, &h->d_epart, &h->d_sctr,
                       &h->d_out, &h->hb_params, &h->hb_e, &h->hb_n, &h->hb_g})
         b->release();
     delete h;
@@ -1802,12 +2076,12 @@ vqe_status vqe_set_plan_options(vqe_handle h, int tile_bits_max, int run_bits, i
     return VQE_OK;
 }
 
-vqe_status vqe_set_apply_mode(vqe_handle h, int mode, int *windowed) {
+vqe_status vqe_set_apply_mode(vqe_handle h, int mode, int *form) {
     if (!h) return VQE_ERR_ARG;
-    if (mode < -1 || mode > 1) return fail(h, VQE_ERR_ARG, "apply mode must be -1, 0 or 1");
+    if (mode < -1 || mode > 2) return fail(h, VQE_ERR_ARG, "apply mode must be -1, 0, 1 or 2");
     h->apply_mode = mode;
-    h->hd.apply_windows = mode < 0 ? h->hd.apply_default : (h->hd.apply_possible && mode == 1);
-    if (windowed) *windowed = h->hd.apply_windows ? 1 : 0;
+    h->hd.apply_form = resolve_apply_form(mode, h->hd);
+    if (form) *form = h->hd.apply_form;
     return VQE_OK;
 }
 
@@ -2135,26 +2409,29 @@ vqe_status vqe_autotune(vqe_handle h, const double *params_dev, int batch, int g
         cudaEventDestroy(eb);
         return st;
     }
-    // the apply-H form of gradient evaluations: both forms on the same psi
-    float ms_glob = 0.f, ms_win = 0.f;
-    if (gradient && h->hd.apply_possible) {
-        const bool keep = h->hd.apply_windows;
+    // the apply-H form of gradient evaluations: every possible form on the same psi
+    float ms_form[3] = {0.f, 0.f, 0.f};
+    if (gradient && (h->hd.win_possible || h->hd.sweep_possible)) {
+        const int keep = h->hd.apply_form;
         void *psi = h->ws;
         const int B = std::max(1, std::min(batch, capacity(h, true)));
         void *lam = static_cast<char *>(h->ws) + h->state_bytes() * size_t(B);
         st = c128 ? run_forward<double>(h, 1, params_dev, B, psi) : run_forward<float>(h, 1, params_dev, B, psi);
-        for (int form = 0; form < 2 && st == VQE_OK; ++form) {
-            h->hd.apply_windows = form == 1;
+        int best_form = -1;
+        for (int form = 0; form < 3 && st == VQE_OK; ++form) {
+            if ((form == 1 && !h->hd.win_possible) || (form == 2 && !h->hd.sweep_possible)) continue;
+            h->hd.apply_form = form;
             auto app = [&]() {
                 return c128 ? run_apply_h<double>(h, B, psi, lam, E) : run_apply_h<float>(h, B, psi, lam, E);
             };
             if ((st = app()) != VQE_OK) break;
-            st = timed(app, form ? ms_win : ms_glob);
+            if ((st = timed(app, ms_form[form])) != VQE_OK) break;
+            if (best_form < 0 || ms_form[form] < ms_form[best_form]) best_form = form;
         }
-        h->hd.apply_windows = keep;
-        if (st == VQE_OK) {
-            h->apply_mode = ms_win < ms_glob ? 1 : 0;
-            h->hd.apply_windows = h->apply_mode == 1;
+        h->hd.apply_form = keep;
+        if (st == VQE_OK && best_form >= 0) {
+            h->apply_mode = best_form;
+            h->hd.apply_form = best_form;
         }
     }
     cudaEventDestroy(ea);
@@ -2166,12 +2443,14 @@ vqe_status vqe_autotune(vqe_handle h, const double *params_dev, int batch, int g
         out->tile_bits_max = r.tile_bits_max;
         out->run_bits = r.run_bits;
         out->reg_bits = r.reg_bits;
-        out->apply_windowed = h->hd.apply_windows ? 1 : 0;
+        out->apply_form = h->hd.apply_form;
         out->candidates = tried;
         out->ms_default = default_ms / batch;
         out->ms_best = best_ms / batch;
-        out->apply_ms_global = ms_glob / (gradient ? std::max(1, std::min(batch, capacity(h, true))) : 1);
-        out->apply_ms_windows = ms_win / (gradient ? std::max(1, std::min(batch, capacity(h, true))) : 1);
+        const double per = gradient ? std::max(1, std::min(batch, capacity(h, true))) : 1;
+        out->apply_ms_global = ms_form[0] / per;
+        out->apply_ms_windows = ms_form[1] / per;
+        out->apply_ms_sweeps = ms_form[2] / per;
     }
     return VQE_OK;
 }
@@ -2200,6 +2479,8 @@ size_t vqe_inspect_sizeof(int which) {
         case 5: return sizeof(WinTerm);
         case 6: return sizeof(ExcPass);
         case 7: return sizeof(ExcGate);
+        case 8: return sizeof(SweepDesc);
+        case 9: return sizeof(SGroup);
         default: return 0;
     }
 }
@@ -2295,6 +2576,48 @@ int vqe_inspect_hamiltonian(int n_qubits, const uint64_t *x_masks, const uint64_
     if (groups) std::memcpy(groups, hp.groups.data(), hp.groups.size() * sizeof(GroupDesc));
     if (tz) std::memcpy(tz, hp.tz.data(), hp.tz.size() * sizeof(uint32_t));
     if (tc) std::memcpy(tc, hp.tc.data(), hp.tc.size() * sizeof(double));
+    return 0;
+}
+
+int vqe_inspect_sweeps(int n_qubits, int precision, const uint64_t *x_masks,
+                       const uint64_t *z_masks, const double *coeffs, size_t n_terms,
+                       double threshold, int diag_terms, void *sweeps, int max_sweeps,
+                       void *groups, int max_groups, uint32_t *pat, int max_pat, uint32_t *tz,
+                       double *ta, double *tb, int max_terms, uint32_t *order, int max_order,
+                       int counts[4]) {
+    if (n_qubits < 1 || n_qubits > 32 || (precision != 0 && precision != 1)) return -1;
+    if (n_terms && (!x_masks || !z_masks || !coeffs)) return -1;
+    const uint64_t lim = (uint64_t(1) << n_qubits) - 1;
+    for (size_t t = 0; t < n_terms; ++t)
+        if ((x_masks[t] & ~lim) || (z_masks[t] & ~lim) || !std::isfinite(coeffs[t])) return -1;
+    std::vector<uint64_t> cx, cz;
+    std::vector<double> cc;
+    canonicalise(x_masks, z_masks, coeffs, n_terms, cx, cz, cc);
+    std::vector<uint8_t> keep;
+    size_t kept = 0;
+    slim_keep(cc, threshold, keep, kept);
+    HamPlan hp;
+    make_ham_plan(cx, cz, cc, keep, hp);
+    SweepPlan sp;
+    plan_sweeps(n_qubits, vqe_precision(precision), hp, diag_terms != 0, sp);
+    if (counts) {
+        counts[0] = int(sp.sweeps.size());
+        counts[1] = int(sp.groups.size());
+        counts[2] = int(sp.pat.size());
+        counts[3] = int(sp.tz.size());
+    }
+    if (!sp.ok) return -1;
+    if (int(sp.sweeps.size()) > max_sweeps || int(sp.groups.size()) > max_groups ||
+        int(sp.pat.size()) > max_pat || int(sp.tz.size()) > max_terms ||
+        int(sp.order.size()) > max_order)
+        return -1;
+    if (sweeps) std::memcpy(sweeps, sp.sweeps.data(), sp.sweeps.size() * sizeof(SweepDesc));
+    if (groups) std::memcpy(groups, sp.groups.data(), sp.groups.size() * sizeof(SGroup));
+    if (pat) std::memcpy(pat, sp.pat.data(), sp.pat.size() * sizeof(uint32_t));
+    if (tz) std::memcpy(tz, sp.tz.data(), sp.tz.size() * sizeof(uint32_t));
+    if (ta) std::memcpy(ta, sp.ta.data(), sp.ta.size() * sizeof(double));
+    if (tb) std::memcpy(tb, sp.tb.data(), sp.tb.size() * sizeof(double));
+    if (order) std::memcpy(order, sp.order.data(), sp.order.size() * sizeof(uint32_t));
     return 0;
 }
 

@@ -232,6 +232,57 @@ struct WinTerm {
     double c;
 };
 
+// ---------------------------------------------------------------- sweeps
+//
+// lambda = H psi (and the expectation it yields) by sweeps over the whole
+// state in a bit order chosen per sweep.  A sweep visits the basis states in
+// the order of a counter s whose low bits run fastest: counter bit k is
+// global bit order[k], with the low global bits [0, mlo) first (contiguous
+// runs for coalescing), then the "fast" bits F of the sweep's groups, then
+// the rest.  Every group of the sweep has its X mask inside [0, mlo) + F, so
+// the partner psi_{i^x} of a state lies in the same block of 2^|F| states
+// (the counter's low |F| + mlo bits), which all threads traverse together: a
+// block is read from DRAM once and its gathers hit L2.  Per state i and
+// group, lambda_i += psi_{i^x} (FA(i) - i FB(i)) with the sign sums FA, FB
+// of the group's A and B terms at i.  The terms are merged per "pattern",
+// the values of i at the group's X bits (up to kSweepMaxXBits of them):
+// with z' = z & ~x,
+//     FA(i) = sum_{z'} cA(pattern, z') (-1)^{popc(i & z')},
+// so that most hopping-like groups need one term and no add per state, and
+// patterns whose terms cancel (an XX + YY pair at equal bits) skip the
+// gather.  Groups with more X bits keep their terms unmerged (one pattern).
+constexpr int kSweepThreads = 256;
+constexpr int kSweepJ = 4;             // states per thread and iteration
+constexpr int kSweepChunk = 4096;      // counter values a block takes at a time
+constexpr int kSweepFastBits = 20;     // low + fast bits: blocks of 2^20 states
+constexpr int kSweepMaxXBits = 5;      // X bits of a group in pattern form
+constexpr int kSweepMaxGroups = 256;   // per sweep
+constexpr int kSweepMaxTerms = 4096;   // merged terms per sweep
+constexpr int kSweepMaxPat = 8192;     // pattern offsets per sweep
+
+struct SweepDesc {
+    int g_begin, g_end;    // SGroup range
+    int p_begin, n_pat;    // pattern offsets [p_begin, p_begin + n_pat)
+    int t_begin, t_count;  // merged terms [t_begin, t_begin + t_count)
+    int order;             // index of the sweep's 4 x 256 bit-order table
+    int diag;              // 1: this sweep adds D_i psi_i (the diagonal of H)
+    uint32_t fast;         // global bits of the counter's low part (informational)
+};
+
+// A group in a sweep.  Pattern p of a state i is bit ((xbits >> 5k) & 31)
+// of i at bit k of p (k < nxb).  When no pattern has more than one merged
+// term, pattern p's term is term slot pat + p of the sweep (a zero term for
+// an empty pattern).  Otherwise ("multi") entry p of the group's pattern
+// array (at offset `pat` of the sweep's) is first | count << 16: its merged
+// terms [first, first + count), sweep-relative.  flags: nxb | has_b << 8
+// (class-B terms) | multi << 9.
+struct SGroup {
+    uint32_t x;
+    int pat;
+    uint32_t xbits;
+    uint32_t flags;
+};
+
 // ---------------------------------------------------------------- launchers
 // Each returns cudaGetLastError() after queueing.
 
@@ -273,6 +324,22 @@ cudaError_t launch_apply_h_win(const WinDesc &W, const WinGroup *wgroups, const 
                                const uint32_t *hoff, const void *hdiag, int n_qubits, int batch,
                                const void *psi, void *lam, size_t state_stride, int first,
                                int last, double *partials, cudaStream_t s);
+// Sweep form of apply-H: `first` writes lambda, later sweeps add to it; the
+// `last` sweep writes chunk partials (Re<psi|lambda>, norm, 0) at
+// cpart[(state * nchunks + chunk) * 3], nchunks = ceil(2^n / kSweepChunk).
+// `ctr` holds one zeroed counter per state for this launch.  `order` points
+// at the sweep's 1024-entry bit-order table; terms, groups and patterns are
+// the whole plan's arrays (the sweep's ranges are in W); coefficients are T.
+// `blocks` blocks per state.
+template <typename T>
+cudaError_t launch_apply_h_sweep(const SweepDesc &W, const uint32_t *order, const SGroup *groups,
+                                 const uint32_t *pat, const uint32_t *tz, const void *ca,
+                                 const void *cb, const void *hdiag, int n_qubits, int batch,
+                                 const void *psi, void *lam, size_t state_stride, int first,
+                                 int last, unsigned long long *ctr, double *cpart, int blocks,
+                                 cudaStream_t s);
+size_t sweep_smem_bytes(const SweepDesc &W, size_t real_bytes);
+int sweep_blocks_per_sm(int elem_bytes, size_t smem);
 // Tile bits (log2 of elements) of the windowed expectation for a precision:
 // 512 threads hold 2^(kWinBits - 9) elements each.
 constexpr int win_tile_bits(bool c128) { return c128 ? 12 : 13; }

@@ -90,9 +90,20 @@ class ExcGate(ctypes.Structure):
                 ("fixed", ctypes.c_uint8 * 4), ("param", ctypes.c_int)]
 
 
+class SweepDesc(ctypes.Structure):
+    _fields_ = [("g_begin", ctypes.c_int), ("g_end", ctypes.c_int), ("p_begin", ctypes.c_int),
+                ("n_pat", ctypes.c_int), ("t_begin", ctypes.c_int), ("t_count", ctypes.c_int),
+                ("order", ctypes.c_int), ("diag", ctypes.c_int), ("fast", ctypes.c_uint32)]
+
+
+class SGroup(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_uint32), ("pat", ctypes.c_int), ("xbits", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
+
+
 def _check_layouts(lib):
     for which, cls in enumerate((PassDesc, StageSlot, GroupDesc, WinDesc, WinGroup, WinTerm,
-                                 ExcPass, ExcGate)):
+                                 ExcPass, ExcGate, SweepDesc, SGroup)):
         got = lib.vqe_inspect_sizeof(which)
         if got != ctypes.sizeof(cls):
             raise RuntimeError(f"record layout mismatch for {cls.__name__}: library {got}, "
@@ -184,6 +195,41 @@ def windows(n_qubits: int, precision: str, x, z, c, threshold: float = 0.0,
         raise ValueError("vqe_inspect_windows rejected the input")
     return {"windows": list(wins)[:nw], "wgroups": list(wg)[:ng], "wterms": list(wt)[:nt],
             "hoff": hoff[:nh], "wide": list(wide)[:nd]}
+
+
+def sweeps(n_qubits: int, precision: str, x, z, c, threshold: float = 0.0,
+           diag_terms: bool = True) -> dict:
+    """Sweeps of the sweep form of lambda = H psi, as the library plans them:
+    sweep records, sweep groups, pattern entries (first term | count << 16),
+    merged terms (z, A and B coefficients) and the bit-order tables (1024 per
+    sweep)."""
+    lib = load()
+    _check_layouts(lib)
+    prec = {"c64": 0, "c128": 1}[precision]
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    z = np.ascontiguousarray(z, dtype=np.uint64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    counts = (ctypes.c_int * 4)()
+    lib.vqe_inspect_sweeps(n_qubits, prec, x.ctypes.data, z.ctypes.data, c.ctypes.data, c.size,
+                           float(threshold), int(diag_terms), None, 0, None, 0, None, 0, None,
+                           None, None, 0, None, 0, counts)
+    ns, ng, npat, nt = (counts[i] for i in range(4))
+    sw = (SweepDesc * max(ns, 1))()
+    sg = (SGroup * max(ng, 1))()
+    pat = np.zeros(max(npat, 1), dtype=np.uint32)
+    tz = np.zeros(max(nt, 1), dtype=np.uint32)
+    ta = np.zeros(max(nt, 1), dtype=np.float64)
+    tb = np.zeros(max(nt, 1), dtype=np.float64)
+    order = np.zeros(max(1024 * ns, 1), dtype=np.uint32)
+    rc = lib.vqe_inspect_sweeps(n_qubits, prec, x.ctypes.data, z.ctypes.data, c.ctypes.data,
+                                c.size, float(threshold), int(diag_terms), ctypes.addressof(sw),
+                                ns, ctypes.addressof(sg), ng, pat.ctypes.data, npat,
+                                tz.ctypes.data, ta.ctypes.data, tb.ctypes.data, nt,
+                                order.ctypes.data, 1024 * ns, counts)
+    if rc != 0:
+        raise ValueError("vqe_inspect_sweeps rejected the input")
+    return {"sweeps": list(sw)[:ns], "groups": list(sg)[:ng], "pat": pat[:npat], "tz": tz[:nt],
+            "ta": ta[:nt], "tb": tb[:nt], "order": order[:1024 * ns]}
 
 
 def pc_plan(n_qubits: int, precision: str, excitations, n_elec: int = 0) -> dict:

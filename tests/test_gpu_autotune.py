@@ -1,5 +1,5 @@
 """The single-handle autotuner (vqe_autotune): every plan it may choose, and
-both forms of lambda = H psi, give the oracle's energies and adjoint
+every form of lambda = H psi, give the oracle's energies and adjoint
 gradients; the tuned handle keeps producing them.
 
 CANDIDATES mirrors the plans (tile_bits_max, run_bits, reg_bits; 0 = the
@@ -42,8 +42,8 @@ def test_every_candidate_plan_and_apply_form_matches_oracle(lib_built, oracle_mo
     eng.set_hamiltonian(H.x, H.z, H.c)
     for plan in CANDIDATES[prec]:
         eng.set_plan_options(*plan)
-        for form in (0, 1):
-            eng.set_apply_mode(form)
+        for form in (0, 1, 2):
+            assert eng.set_apply_mode(form) == form
             g, E = eng.gradient(p)
             _check(prec, E, g, E_ref, g_ref, H)
     eng.close()
@@ -61,7 +61,8 @@ def test_autotuned_handle_matches_oracle(lib_built, oracle_mod, prec):
     t = eng.autotune(Pd, gradient=True, budget_ms=1e9)
     assert t["candidates"] == len(CANDIDATES[prec])
     assert t["ms_best"] <= t["ms_default"] + 1e-9
-    assert t["apply_ms_global"] > 0 and t["apply_ms_windows"] > 0
+    assert t["apply_ms_global"] > 0 and t["apply_ms_windows"] > 0 and t["apply_ms_sweeps"] > 0
+    assert t["apply_form"] in (0, 1, 2)
     G, E = eng.gradient_batch(P)
     for b in (0, B - 1):
         g_ref, E_ref = oracle_mod.gradient_adjoint(n, D, P[b], H.x, H.z, H.c)

@@ -118,21 +118,24 @@ def test_adjoint_gradient(eng_mod, oracle_mod, prec, n, D, plan):
 def test_windowed_apply_h_gradient(eng_mod, oracle_mod, prec, case):
     """20 qubits, a batch large enough for the windowed apply-H (lambda = H psi
     accumulated window by window): adjoint gradients and energies vs the
-    oracle's adjoint gradient."""
+    oracle's adjoint gradient, with every form of lambda = H psi (global
+    sweep, windows, bit-ordered sweeps)."""
     n, D, B = 20, 2, 4
     H = vi.hubbard_1d(10, 1.0, 4.0, periodic=True) if case == "hubbard" else vi.synthetic_molecular(10, seed=3)
     P = np.stack([vi.ansatz_params(500 + b, n, D) for b in range(B)])
     eng = make(eng_mod, n, D, prec, H)
-    G, E = eng.gradient_batch(P)
-    for b in (0, B - 1):
-        g_ref, E_ref = oracle_mod.gradient_adjoint(n, D, P[b], H.x, H.z, H.c)
-        check_energy(E[b], E_ref, H, prec)
-        scale = max(np.max(np.abs(g_ref)), 1e-30)
-        err = np.max(np.abs(G[b] - g_ref))
-        if prec == "c64":
-            assert err / scale <= 1e-4, (err, scale)
-        else:
-            assert err <= 1e-10 * max(1.0, scale), (err, scale)
+    refs = {b: oracle_mod.gradient_adjoint(n, D, P[b], H.x, H.z, H.c) for b in (0, B - 1)}
+    for form in (0, 1, 2):
+        assert eng.set_apply_mode(form) == form
+        G, E = eng.gradient_batch(P)
+        for b, (g_ref, E_ref) in refs.items():
+            check_energy(E[b], E_ref, H, prec)
+            scale = max(np.max(np.abs(g_ref)), 1e-30)
+            err = np.max(np.abs(G[b] - g_ref))
+            if prec == "c64":
+                assert err / scale <= 1e-4, (form, err, scale)
+            else:
+                assert err <= 1e-10 * max(1.0, scale), (form, err, scale)
 
 
 def test_gradient_batch_matches_single(eng_mod, oracle_mod):

@@ -385,3 +385,102 @@ def test_window_cover_of_the_molecular_hamiltonian():
         assert len(win["windows"]) <= most
         for W in win["windows"]:
             assert W.g_end - W.g_begin <= P.K_WIN_MAX_GROUPS and W.t_count <= P.K_WIN_MAX_TERMS
+
+
+def _popc_parity(v):
+    v = np.asarray(v, dtype=np.uint64)
+    p = np.zeros(v.shape, dtype=np.int64)
+    for b in range(64):
+        p ^= ((v >> np.uint64(b)) & np.uint64(1)).astype(np.int64)
+    return p
+
+
+def emulate_sweeps(n, prec, H, psi, diag_terms=True):
+    """NumPy replay of the sweep form of lambda = H psi from the library's
+    plan (vqe_inspect_sweeps): per sweep and group, the pattern of each state
+    at the group's X bits selects its merged terms, whose sign sums multiply
+    the gathered partner; the first sweep adds the diagonal."""
+    sp = P.sweeps(n, prec, H.x, H.z, H.c, diag_terms=diag_terms)
+    a = np.arange(1 << n, dtype=np.uint64)
+    lam = np.zeros(1 << n, dtype=complex)
+    for S in sp["sweeps"]:
+        # the bit order maps the counter one to one onto the states
+        tab = sp["order"][1024 * S.order:1024 * (S.order + 1)].astype(np.uint64)
+        s = a
+        img = (tab[(s & np.uint64(255)).astype(np.int64)] |
+               tab[256 + ((s >> np.uint64(8)) & np.uint64(255)).astype(np.int64)] |
+               tab[512 + ((s >> np.uint64(16)) & np.uint64(255)).astype(np.int64)] |
+               tab[768 + ((s >> np.uint64(24)) & np.uint64(255)).astype(np.int64)])
+        assert np.array_equal(np.sort(img), a)
+        if S.diag and not diag_terms:
+            lam += diag_of(n, H) * psi
+        for G in sp["groups"][S.g_begin:S.g_end]:
+            nxb = G.flags & 255
+            pv = np.zeros(1 << n, dtype=np.int64)
+            for k in range(nxb):
+                pv |= ((a >> np.uint64((G.xbits >> (5 * k)) & 31)) & np.uint64(1)).astype(np.int64) << k
+            multi = (G.flags >> 9) & 1
+            fa = np.zeros(1 << n)
+            fb = np.zeros(1 << n)
+            for u in range(1 << nxb):
+                sel = pv == u
+                if multi:       # pattern entries: first term | count << 16
+                    e = int(sp["pat"][S.p_begin + G.pat + u])
+                    r0, cnt = e & 0xFFFF, e >> 16
+                else:           # one term slot per pattern (zero when empty)
+                    r0, cnt = G.pat + u, 1
+                assert ((G.flags >> 8) & 1) or all(sp["tb"][S.t_begin + r] == 0 for r in range(r0, r0 + cnt))
+                for r in range(r0, r0 + cnt):
+                    t = S.t_begin + r
+                    sg = 1 - 2 * _popc_parity(a[sel] & np.uint64(sp["tz"][t]))
+                    fa[sel] += sp["ta"][t] * sg
+                    fb[sel] += sp["tb"][t] * sg
+            lam += psi[(a ^ np.uint64(G.x)).astype(np.int64)] * (fa - 1j * fb)
+    return lam, sp
+
+
+def diag_of(n, H):
+    a = np.arange(1 << n, dtype=np.uint64)
+    d = np.zeros(1 << n)
+    for x, z, c in zip(H.x, H.z, H.c):
+        if int(x) == 0:
+            d += np.real(c) * (1 - 2 * _popc_parity(a & np.uint64(z)))
+    return d
+
+
+SWEEP_CASES = {
+    "hubbard1d": lambda: vi.hubbard_1d(6, 1.0, 4.0, periodic=True),
+    "lattice": lambda: vi.hubbard_2d_snake(3, 2, 1.0, 4.0),
+    "molecular": lambda: vi.synthetic_molecular(6, 2024),
+    "random": lambda: vi.random_pauli_sum(11, 40, seed=11),
+    "tiny": lambda: vi.random_pauli_sum(2, 6, seed=2),
+}
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("case", sorted(SWEEP_CASES))
+@pytest.mark.parametrize("diag_terms", [True, False])
+def test_apply_h_sweeps_emulated(oracle_mod, prec, case, diag_terms):
+    """The sweep form of lambda = H psi (vqe_set_apply_mode 2), replayed from
+    the library's plan, equals the oracle's H psi; every group sits in one
+    sweep, inside that sweep's fast bits unless it has more X bits than a
+    sweep holds."""
+    H = SWEEP_CASES[case]()
+    n = H.n
+    rng = np.random.default_rng(n)
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    lam, sp = emulate_sweeps(n, prec, H, psi, diag_terms)
+    ref = oracle_mod.apply_h(psi, H.x, H.z, H.c)
+    assert np.max(np.abs(lam - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+    hp = P.hamiltonian(n, H.x, H.z, H.c)
+    xs = sorted(int(G.x) for G in hp["groups"] if G.x != 0)
+    got = sorted(int(G.x) for G in sp["groups"] if G.x != 0)
+    assert set(got) <= set(xs) and len(got) == len(set(got))   # a group at most once (vanishing ones dropped)
+    mlo = min(n, 4 if prec == "c128" else 5)
+    for S in sp["sweeps"]:
+        assert S.fast & ((1 << mlo) - 1) == (1 << mlo) - 1
+        assert bin(S.fast).count("1") <= max(20, mlo)
+        for G in sp["groups"][S.g_begin:S.g_end]:
+            high = int(G.x) & ~((1 << mlo) - 1)
+            if bin(high).count("1") <= 20 - mlo:
+                assert int(G.x) & ~S.fast == 0

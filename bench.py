@@ -50,10 +50,10 @@ FP64_UNITS_PEAK = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x 
 # DRAM read + write bytes of the FP64 backward pass kernel per byte it must
 # move (psi and lambda read and written per live tile), from an ncu capture
 # of its three launch shapes at 24 qubits on the 4x3 lattice (dram__bytes
-# read + write: 3.086 GB against 3.221 GB); the per-tile traffic of these
+# read + write: 3.110 GB against 3.221 GB); the per-tile traffic of these
 # passes does not depend on the qubit count.  None once the kernel changes,
 # until it is captured again.
-BWD_TRAFFIC_PER_ALGORITHMIC_BYTE = 3085833216 / 3221225472
+BWD_TRAFFIC_PER_ALGORITHMIC_BYTE = 3110332160 / 3221225472
 
 
 # ---------------------------------------------------------------- work models
@@ -821,6 +821,8 @@ def run_case(name: str, batch: int):
         "pcl24c64": (24, 0, "c64", True, "pc"),
         "latw24c64": (24, 2, "c64", True, "lattice"),    # windowed apply-H forced (batch >= 3)
         "latw24c128": (24, 2, "c128", True, "lattice"),
+        "lats24c64": (24, 2, "c64", True, "lattice"),    # bit-ordered sweeps of apply-H forced
+        "lats24c128": (24, 2, "c128", True, "lattice"),
     }
     if name == "batch512":
         inst = vi.batched_instances(512, seed=7)
@@ -856,6 +858,8 @@ def run_case(name: str, batch: int):
     eng.set_hamiltonian(H.x, H.z, H.c)
     if name.startswith("latw"):
         eng.set_apply_mode(1)
+    elif name.startswith("lats"):
+        eng.set_apply_mode(2)
     E = torch.empty(batch, dtype=torch.float64, device="cuda")
     G = torch.empty(batch, eng.n_params, dtype=torch.float64, device="cuda")
     for _ in range(2):

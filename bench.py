@@ -558,6 +558,12 @@ def run_gpu(args, world, rank, local, pg):
         del e64
         torch.cuda.empty_cache()
 
+    # the cutoff study of Sec. III-D on the molecular Hamiltonian (24 qubits)
+    sweep_rows = None
+    if not args.no_extras and rank == 0:
+        sweep_rows, _ = cutoff_sweep_molecular24(dev)
+        torch.cuda.empty_cache()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
@@ -575,6 +581,8 @@ def run_gpu(args, world, rank, local, pg):
             line["fp64_energy"] = energy
         if c64:
             line["c64_energy_gradient"] = c64
+        if sweep_rows:
+            line["cutoff_sweep_molecular24"] = {"workload": MOLECULAR24, "rows": sweep_rows}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline_sample(args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -593,6 +601,43 @@ def _timed(fn, reps):
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+MOLECULAR24 = ("24q complex64 synthetic molecular (12 spatial orbitals, JW), HEA depth 12, "
+               "energy + adjoint gradient, cutoff sweep")
+
+
+def cutoff_sweep_molecular24(dev):
+    """The cutoff study of Sec. III-D (Fig. 7) on the synthetic molecular
+    Hamiltonian at 24 qubits, complex64: per threshold the kept terms and
+    groups, sum|c_dropped| (the Sec. II-D bound) and the time of an energy and
+    of an energy + adjoint gradient evaluation."""
+    import numpy as np
+    import torch
+    import paper_2402_11878_gb300 as pkg
+    import vqe_inputs as vi
+    H = vi.synthetic_molecular(12, seed=2024)
+    n, D, B = 24, 12, 2
+    eng = pkg.Engine(n, D, "c64")
+    eng.set_hamiltonian(H.x, H.z, H.c)
+    P = torch.tensor(np.stack([vi.ansatz_params(9000 + j, n, D) for j in range(B)]), device=dev)
+    E = torch.empty(B, dtype=torch.float64, device=dev)
+    G = torch.empty(B, 2 * n * D, dtype=torch.float64, device=dev)
+    rows = []
+    for th in (0.0, 1e-6, 1e-4, 1e-3, 1e-2):
+        kept, dropped = eng.slim(th)
+        eng.profile(True)
+        ms_e = _timed(lambda: eng.energy_batch_dev(P, E), 2) / B
+        pe = eng.profile_read()
+        ms_g = _timed(lambda: eng.gradient_batch_dev(P, G, E), 1) / B
+        eng.profile(False)
+        rows.append({"threshold": th, "terms_kept": kept, "sum_abs_dropped": dropped,
+                     "groups": eng.stats()["n_groups"], "energy_ms": ms_e,
+                     "energy_kernel_ms": pe["energy"]["ms"] / 3 / B,
+                     "forward_ms": pe["forward_passes"]["ms"] / 3 / B,
+                     "energy_gradient_ms": ms_g, "energy": float(E[0])})
+    eng.close()
+    return rows, H
 
 
 def run_workload(name: str, args):
@@ -635,33 +680,11 @@ def run_workload(name: str, args):
         for e in engs:
             e.close()
     elif name == "molecular24":
-        # 24 qubits complex64: synthetic molecular-style Pauli sum, cutoff sweep
-        H = vi.synthetic_molecular(12, seed=2024)
-        n, D, B = 24, 12, 2
-        eng = pkg.Engine(n, D, "c64")
-        eng.set_hamiltonian(H.x, H.z, H.c)
-        P = torch.tensor(np.stack([vi.ansatz_params(9000 + j, n, D) for j in range(B)]), device=dev)
-        E = torch.empty(B, dtype=torch.float64, device=dev)
-        G = torch.empty(B, 2 * n * D, dtype=torch.float64, device=dev)
-        rows = []
-        for th in (0.0, 1e-6, 1e-4, 1e-3):
-            kept, dropped = eng.slim(th)
-            eng.profile(True)
-            ms_e = _timed(lambda: eng.energy_batch_dev(P, E), 2) / B
-            pe = eng.profile_read()
-            ms_g = _timed(lambda: eng.gradient_batch_dev(P, G, E), 1) / B
-            eng.profile(False)
-            rows.append({"threshold": th, "terms_kept": kept, "sum_abs_dropped": dropped,
-                         "groups": eng.stats()["n_groups"], "energy_ms": ms_e,
-                         "energy_kernel_ms": pe["energy"]["ms"] / 3 / B,
-                         "forward_ms": pe["forward_passes"]["ms"] / 3 / B,
-                         "energy_gradient_ms": ms_g})
+        rows, H = cutoff_sweep_molecular24(dev)
         line.update({"value": 1e3 / rows[0]["energy_gradient_ms"], "dtype": "c64",
-                     "config": {"workload": "24q complex64 synthetic molecular (12 spatial orbitals, "
-                                "JW), HEA depth 12, energy + adjoint gradient, cutoff sweep",
+                     "config": {"workload": MOLECULAR24,
                                 "terms": len(H), "groups": H.n_groups},
                      "cutoff_sweep": rows})
-        eng.close()
     elif name == "batch512":
         inst = vi.batched_instances(512, seed=7)
         b = pkg.Batch([d["n"] for d in inst], [d["depth"] for d in inst], "c64",

@@ -165,55 +165,71 @@ k_apply_h_sweep(SweepDesc W, const uint32_t *__restrict__ order, const SGroup *_
                 const uint32_t x = gw.x, xbits = gw.z, flags = gw.w;
                 const uint32_t nxb = flags & 255u;
                 const bool has_b = (flags >> 8) & 1u, multi = (flags >> 9) & 1u;
-                // pattern of each state at the group's X bits (group-uniform
-                // branch on their number; pattern bit 1 taken with one shift
-                // since the X bits are increasing)
-                uint32_t pv[J];
-                const uint32_t s0b = xbits & 31u, s1b = ((xbits >> 5) & 31u) - 1u;
-                if (nxb == 2u) {
-#pragma unroll
-                    for (int j = 0; j < J; ++j) pv[j] = ((a[j] >> s0b) & 1u) | ((a[j] >> s1b) & 2u);
-                } else if (nxb == 1u) {
-#pragma unroll
-                    for (int j = 0; j < J; ++j) pv[j] = (a[j] >> s0b) & 1u;
-                } else if (nxb == 0u) {
-#pragma unroll
-                    for (int j = 0; j < J; ++j) pv[j] = 0u;
-                } else {
-#pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        uint32_t v = 0u;
-                        for (uint32_t k = 0; k < nxb; ++k) v |= ((a[j] >> ((xbits >> (5 * k)) & 31u)) & 1u) << k;
-                        pv[j] = v;
-                    }
-                }
                 T fa[J], fb[J];
                 bool nz[J];
-                if (!multi) {
-                    // the pattern's term slot (a zero term for an empty pattern)
+                if ((flags >> 10) & 1u) {
+                    // parity form: one term, taken where popc(i & x) has parity p
+                    const uint32_t pk = (flags >> 11) & 1u;
+                    const uint32_t t = (uint32_t)gw.y;
+                    const uint32_t z = sz[t];
+                    const T c_a = sca[t];
+                    const T c_b = has_b ? scb[t] : T(0);
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        const uint32_t t = (uint32_t)gw.y + pv[j];
-                        const uint32_t par = __popc(a[j] & sz[t]) & 1u;
-                        const T c_a = sca[t];
-                        const T c_b = has_b ? scb[t] : T(0);
-                        nz[j] = nonzero(c_a) || nonzero(c_b);   // integer test, off the FP64 pipe
+                        nz[j] = ((__popc(a[j] & x) ^ pk) & 1u) == 0u;
+                        const uint32_t par = __popc(a[j] & z) & 1u;
                         fa[j] = sw_sign(c_a, par);
                         fb[j] = sw_sign(c_b, par);
                     }
                 } else {
-                    const uint32_t *gp = spat + gw.y;
+                    // pattern of each state at the group's X bits (group-uniform
+                    // branch on their number; pattern bit 1 taken with one shift
+                    // since the X bits are increasing)
+                    uint32_t pv[J];
+                    const uint32_t s0b = xbits & 31u, s1b = ((xbits >> 5) & 31u) - 1u;
+                    if (nxb == 2u) {
 #pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        const uint32_t e = gp[pv[j]];
-                        const uint32_t r0 = e & 0xffffu, cnt = e >> 16;
-                        nz[j] = cnt != 0u;
-                        fa[j] = T(0);
-                        fb[j] = T(0);
-                        for (uint32_t r = r0; r < r0 + cnt; ++r) {
-                            const uint32_t pr = __popc(a[j] & sz[r]) & 1u;
-                            fa[j] += sw_sign(sca[r], pr);
-                            if (has_b) fb[j] += sw_sign(scb[r], pr);
+                        for (int j = 0; j < J; ++j) pv[j] = ((a[j] >> s0b) & 1u) | ((a[j] >> s1b) & 2u);
+                    } else if (nxb == 1u) {
+#pragma unroll
+                        for (int j = 0; j < J; ++j) pv[j] = (a[j] >> s0b) & 1u;
+                    } else if (nxb == 0u) {
+#pragma unroll
+                        for (int j = 0; j < J; ++j) pv[j] = 0u;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < J; ++j) {
+                            uint32_t v = 0u;
+                            for (uint32_t k = 0; k < nxb; ++k) v |= ((a[j] >> ((xbits >> (5 * k)) & 31u)) & 1u) << k;
+                            pv[j] = v;
+                        }
+                    }
+                    if (!multi) {
+                        // the pattern's term slot (a zero term for an empty pattern)
+#pragma unroll
+                        for (int j = 0; j < J; ++j) {
+                            const uint32_t t = (uint32_t)gw.y + pv[j];
+                            const uint32_t par = __popc(a[j] & sz[t]) & 1u;
+                            const T c_a = sca[t];
+                            const T c_b = has_b ? scb[t] : T(0);
+                            nz[j] = nonzero(c_a) || nonzero(c_b);   // integer test, off the FP64 pipe
+                            fa[j] = sw_sign(c_a, par);
+                            fb[j] = sw_sign(c_b, par);
+                        }
+                    } else {
+                        const uint32_t *gp = spat + gw.y;
+#pragma unroll
+                        for (int j = 0; j < J; ++j) {
+                            const uint32_t e = gp[pv[j]];
+                            const uint32_t r0 = e & 0xffffu, cnt = e >> 16;
+                            nz[j] = cnt != 0u;
+                            fa[j] = T(0);
+                            fb[j] = T(0);
+                            for (uint32_t r = r0; r < r0 + cnt; ++r) {
+                                const uint32_t pr = __popc(a[j] & sz[r]) & 1u;
+                                fa[j] += sw_sign(sca[r], pr);
+                                if (has_b) fb[j] += sw_sign(scb[r], pr);
+                            }
                         }
                     }
                 }

@@ -1402,7 +1402,43 @@ void plan_sweeps(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms, 
             bool multi = false;
             for (const auto &ts : mg.pats) multi = multi || ts.size() > 1;
             for (size_t k = 0; k < mg.xb.size(); ++k) sg.xbits |= uint32_t(mg.xb[k]) << (5 * k);
-            if (!multi) {
+            // parity form: the nonempty patterns are exactly those of one
+            // parity of the X bits and share one merged term (a hopping
+            // XX + YY pair: the states whose two bits differ); the kernel
+            // then tests popc(i & x) instead of indexing patterns
+            int parity = -1;
+            if (!multi && !mg.xb.empty()) {
+                const MTerm *first = nullptr;
+                bool same = true;
+                int par_nonempty = -1;
+                for (size_t pv = 0; pv < mg.pats.size() && same; ++pv) {
+                    const int pp = __builtin_popcount(uint32_t(pv)) & 1;
+                    const auto &ts = mg.pats[pv];
+                    if (ts.empty()) {
+                        if (par_nonempty == pp) same = false;
+                        continue;
+                    }
+                    if (par_nonempty < 0) par_nonempty = pp;
+                    if (par_nonempty != pp) same = false;
+                    if (!first) first = &ts[0];
+                    else same = same && ts[0].z == first->z && ts[0].a == first->a && ts[0].b == first->b;
+                }
+                // every pattern of that parity must be nonempty
+                if (same && first && par_nonempty >= 0) {
+                    for (size_t pv = 0; pv < mg.pats.size(); ++pv)
+                        if ((__builtin_popcount(uint32_t(pv)) & 1) == par_nonempty && mg.pats[pv].empty()) same = false;
+                }
+                if (same && first) parity = par_nonempty;
+                if (parity >= 0) {
+                    sg.pat = int(sp.tz.size()) - W.t_begin;
+                    sp.tz.push_back(first->z);
+                    sp.ta.push_back(first->a);
+                    sp.tb.push_back(first->b);
+                }
+            }
+            if (parity >= 0) {
+                // one term slot (above)
+            } else if (!multi) {
                 // one term slot per pattern, in pattern order (zero for an
                 // empty pattern): the pattern indexes its term directly
                 sg.pat = int(sp.tz.size()) - W.t_begin;
@@ -1424,7 +1460,8 @@ void plan_sweeps(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms, 
                     }
                 }
             }
-            sg.flags = uint32_t(mg.xb.size()) | (mg.has_b ? 1u << 8 : 0u) | (multi ? 1u << 9 : 0u);
+            sg.flags = uint32_t(mg.xb.size()) | (mg.has_b ? 1u << 8 : 0u) | (multi ? 1u << 9 : 0u) |
+                       (parity >= 0 ? 1u << 10 | uint32_t(parity) << 11 : 0u);
             sp.groups.push_back(sg);
         }
         W.g_end = int(sp.groups.size());

@@ -274,8 +274,11 @@ struct SweepDesc {
 // term, pattern p's term is term slot pat + p of the sweep (a zero term for
 // an empty pattern).  Otherwise ("multi") entry p of the group's pattern
 // array (at offset `pat` of the sweep's) is first | count << 16: its merged
-// terms [first, first + count), sweep-relative.  flags: nxb | has_b << 8
-// (class-B terms) | multi << 9.
+// terms [first, first + count), sweep-relative.  "Parity" groups (the
+// nonempty patterns are those of one parity p of the X bits and share one
+// merged term) keep that term in slot pat alone: a state takes it when
+// popc(i & x) has parity p.  flags: nxb | has_b << 8 (class-B terms) |
+// multi << 9 | parity form << 10 | p << 11.
 struct SGroup {
     uint32_t x;
     int pat;

@@ -416,6 +416,15 @@ def emulate_sweeps(n, prec, H, psi, diag_terms=True):
             lam += diag_of(n, H) * psi
         for G in sp["groups"][S.g_begin:S.g_end]:
             nxb = G.flags & 255
+            if (G.flags >> 10) & 1:
+                # parity form: one term where popc(i & x) has parity p
+                pk = (G.flags >> 11) & 1
+                t = S.t_begin + G.pat
+                kept = _popc_parity(a & np.uint64(G.x)) == pk
+                sg = 1 - 2 * _popc_parity(a & np.uint64(sp["tz"][t]))
+                f = np.where(kept, (sp["ta"][t] - 1j * sp["tb"][t]) * sg, 0)
+                lam += psi[(a ^ np.uint64(G.x)).astype(np.int64)] * f
+                continue
             pv = np.zeros(1 << n, dtype=np.int64)
             for k in range(nxb):
                 pv |= ((a >> np.uint64((G.xbits >> (5 * k)) & 31)) & np.uint64(1)).astype(np.int64) << k
@@ -467,6 +476,10 @@ def test_apply_h_sweeps_emulated(oracle_mod, prec, case, diag_terms):
     sweep holds."""
     H = SWEEP_CASES[case]()
     n = H.n
+    if case in ("hubbard1d", "lattice"):
+        # every hopping group takes the parity form
+        sp0 = P.sweeps(n, prec, H.x, H.z, H.c, diag_terms=diag_terms)
+        assert all((G.flags >> 10) & 1 for G in sp0["groups"] if G.x != 0)
     rng = np.random.default_rng(n)
     psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
     lam, sp = emulate_sweeps(n, prec, H, psi, diag_terms)

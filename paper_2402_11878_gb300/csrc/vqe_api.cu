@@ -1573,8 +1573,8 @@ vqe_status build_ham_plan(vqe_ctx *h) {
         // (measured at 24 qubits in complex64: the 25 Hubbard groups in 2
         // windows favour the global sweep, the molecular 5,479 groups the
         // windows), else the global sweep.  The bit-ordered sweeps win on
-        // lattice Hamiltonians at 32 qubits (complex64 326 against 342 ms
-        // for the windows) and lose on molecular ones (215 against 69 ms at
+        // lattice Hamiltonians at 32 qubits (complex64 269 against 342 ms
+        // for the windows) and lose on molecular ones (229 against 69 ms at
         // 24 qubits): vqe_set_apply_mode and the autotuner choose them.
         nd.apply_default = nd.win_possible && hp.groups.size() >= 10 * nd.wins.size() ? 1 : 0;
         nd.apply_form = resolve_apply_form(h->apply_mode, nd);

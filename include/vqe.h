@@ -136,8 +136,10 @@ vqe_status vqe_set_plan_options(vqe_handle h, int tile_bits_max, int run_bits, i
  * the groups are split into a few sweeps whose state order makes the X bits
  * of their groups run fastest, so that the gathered partners are read from
  * L2 (where every group's terms fit a sweep); a form the Hamiltonian cannot
- * use falls back to mode 0.  Mode -1 (default) = windows when they hold
- * at least 10 groups each, else mode 0; the autotuner times all three.  The
+ * use falls back to mode 0.  Mode -1 (default) = mode 2 when every group's
+ * nonzero terms form one merged term on one parity of its X bits (hopping
+ * Hamiltonians), else windows when they hold at least 10 groups each, else
+ * mode 0; the autotuner times all three.  The
  * choice persists across vqe_set_hamiltonian and vqe_slim; *form (may be
  * NULL) reports the form (0, 1 or 2) the current Hamiltonian will use.
  * Results agree to rounding order.  VQE_ERR_ARG for a mode outside -1..2. */

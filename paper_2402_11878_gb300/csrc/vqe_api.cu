@@ -1267,6 +1267,7 @@ struct SweepPlan {
     std::vector<double> ta, tb;
     std::vector<uint32_t> order;   // 1024 per sweep
     bool ok = false;               // false: a group has more terms than a sweep holds
+    bool all_parity = true;        // every group with an X mask in the parity form
 };
 
 void plan_sweeps(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms, SweepPlan &sp) {
@@ -1462,6 +1463,7 @@ void plan_sweeps(int n, vqe_precision prec, const HamPlan &hp, bool diag_terms, 
             }
             sg.flags = uint32_t(mg.xb.size()) | (mg.has_b ? 1u << 8 : 0u) | (multi ? 1u << 9 : 0u) |
                        (parity >= 0 ? 1u << 10 | uint32_t(parity) << 11 : 0u);
+            if (mg.x != 0u && parity < 0) sp.all_parity = false;
             sp.groups.push_back(sg);
         }
         W.g_end = int(sp.groups.size());
@@ -1548,12 +1550,14 @@ vqe_status build_ham_plan(vqe_ctx *h) {
         // per group in the global sweep.
         nd.win_possible = wp.wide.empty() && !wp.wins.empty();
     }
+    bool sweep_all_parity = false;
     {
         // bit-ordered sweeps: psi read and lambda written once per sweep, the
         // gathers served by L2
         SweepPlan sp;
         plan_sweeps(h->n, h->prec, hp, !nd.hdiag_ok, sp);
         nd.sweep_possible = sp.ok && !sp.sweeps.empty();
+        sweep_all_parity = sp.all_parity;
         if (nd.sweep_possible) {
             nd.sweeps = sp.sweeps;
             if ((st = upload(h, nd.d_sorder, sp.order, "sweep orders")) != VQE_OK) return bail(st);
@@ -1569,14 +1573,16 @@ vqe_status build_ham_plan(vqe_ctx *h) {
                 if ((st = upload(h, nd.d_stb, fb, "sweep terms")) != VQE_OK) return bail(st);
             }
         }
-        // default form (mode -1): the windows when they hold many groups each
-        // (measured at 24 qubits in complex64: the 25 Hubbard groups in 2
-        // windows favour the global sweep, the molecular 5,479 groups the
-        // windows), else the global sweep.  The bit-ordered sweeps win on
-        // lattice Hamiltonians at 32 qubits (complex64 269 against 342 ms
-        // for the windows) and lose on molecular ones (229 against 69 ms at
-        // 24 qubits): vqe_set_apply_mode and the autotuner choose them.
-        nd.apply_default = nd.win_possible && hp.groups.size() >= 10 * nd.wins.size() ? 1 : 0;
+        // default form (mode -1): the bit-ordered sweeps when every group
+        // takes their parity form (hopping Hamiltonians: at 32 qubits
+        // complex64 269 ms against 342 for the windows and 393 for the
+        // global sweep, FP64 877 / 896 / 2000 ms; at 24 qubits the sweeps
+        // are fastest too), else the windows when they hold many groups each
+        // (the synthetic molecular Hamiltonian at 24 qubits: windows 69 ms,
+        // sweeps 229 ms, global 167 ms), else the global sweep.
+        // vqe_set_apply_mode and the autotuner override the choice.
+        nd.apply_default = nd.sweep_possible && sweep_all_parity ? 2
+                         : (nd.win_possible && hp.groups.size() >= 10 * nd.wins.size() ? 1 : 0);
         nd.apply_form = resolve_apply_form(h->apply_mode, nd);
     }
     if ((st = upload(h, nd.d_groups, hp.groups, "groups")) != VQE_OK) return bail(st);

@@ -138,6 +138,61 @@ def test_windowed_apply_h_gradient(eng_mod, oracle_mod, prec, case):
                 assert err <= 1e-10 * max(1.0, scale), (form, err, scale)
 
 
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n", [1, 2, 5, 9, 13, 17])
+def test_sweep_apply_h_random_sums(eng_mod, oracle_mod, prec, n):
+    """The sweep form of lambda = H psi on random Pauli sums with Y terms:
+    groups in pattern form with several terms per pattern, groups with more
+    X bits than the pattern form takes (terms unmerged), the diagonal; from
+    one qubit (a single sweep smaller than a chunk) up."""
+    D = 2
+    H = vi.random_pauli_sum(n, 40, seed=700 + n, duplicates=3)
+    p = vi.ansatz_params(710 + n, n, D)
+    eng = make(eng_mod, n, D, prec, H)
+    assert eng.set_apply_mode(2) == 2
+    g, E = eng.gradient(p)
+    g_ref, E_ref = oracle_mod.gradient_adjoint(n, D, p, H.x, H.z, H.c)
+    check_energy(E, E_ref, H, prec)
+    scale = max(np.max(np.abs(g_ref)), 1e-30)
+    err = np.max(np.abs(g - g_ref))
+    if prec == "c64":
+        assert err / scale <= 1e-4, (err, scale)
+    else:
+        assert err <= 1e-10 * max(1.0, scale), (err, scale)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_sweep_apply_h_several_sweeps_22q(eng_mod, oracle_mod, prec):
+    """22 qubits on the 4x3 open lattice minus one site (hopping groups whose
+    X bits span more than one sweep's fast bits): the sweep form runs several
+    sweeps, lambda accumulated across them; the energy it yields against the
+    oracle, its gradient against the windowed form's (checked against the
+    oracle in test_windowed_apply_h_gradient) and, in FP64, the oracle's
+    gradient."""
+    from paper_2402_11878_gb300 import plans
+    n, D = 22, 1
+    H = vi.hubbard_2d_snake(11, 1, 1.0, 4.0, periodic=True)
+    assert H.n == n
+    sp = plans.sweeps(n, prec, H.x, H.z, H.c, diag_terms=False)
+    assert len(sp["sweeps"]) >= 2
+    p = vi.ansatz_params(2222, n, D)
+    eng = make(eng_mod, n, D, prec, H)
+    assert eng.set_apply_mode(2) == 2
+    g2, E2 = eng.gradient(p)
+    assert eng.set_apply_mode(1) == 1
+    g1, E1 = eng.gradient(p)
+    ref = oracle_mod.ansatz_state(n, D, p)
+    E_ref, _ = oracle_mod.energy(ref, H.x, H.z, H.c)
+    check_energy(E2, E_ref, H, prec)
+    scale = max(np.max(np.abs(g1)), 1e-30)
+    if prec == "c64":
+        assert np.max(np.abs(g2 - g1)) / scale <= 1e-5
+    else:
+        assert np.max(np.abs(g2 - g1)) <= 1e-12 * max(1.0, scale)
+        g_ref, _ = oracle_mod.gradient_adjoint(n, D, p, H.x, H.z, H.c)
+        assert np.max(np.abs(g2 - g_ref)) <= 1e-10 * max(1.0, np.max(np.abs(g_ref)))
+
+
 def test_gradient_batch_matches_single(eng_mod, oracle_mod):
     n, D, B = 9, 2, 3
     H = vi.random_pauli_sum(n, 25, seed=9)

@@ -25,6 +25,8 @@
 //        0 = `buf`/`lbuf` in plain order, 1 = the state in global memory (P, L)
 #pragma once
 
+#include <type_traits>
+
 #include "csum.cuh"
 #include "vqe_internal.h"
 
@@ -825,93 +827,97 @@ __device__ __forceinline__ void run_tile_fixed(const PassDesc &d, const PassOp *
             }
         } else if constexpr (kind == 4) {       // block totals of a slot's gradient partials
             // The tile shape is fixed by the program: k = top chunk + R bits,
-            // NT = 2^(k - R) threads, NW warps.  Warp w sums rows w, w + NW, ...
-            // (RPW of them) together, so that the loads and the shuffle trees of
-            // its rows interleave instead of forming one dependent chain per row;
-            // lanes add a strided part of each row, then a shuffle tree, in a
-            // fixed order (bitwise reproducible).
+            // NT = 2^(k - R) threads, NW warps.  Two stages, both in a fixed
+            // order (bitwise reproducible):
+            //  1. warp w takes rows w, w + NW, ... (RPW of them); each lane adds
+            //     its strided part of each row (NT / 32 values);
+            //  2. the lane partials go to shared memory (the psi tile buffer,
+            //     row stride 33: the lanes of stage 2 read different banks) and
+            //     lane r of warp 0 adds the 32 partials of row r, all rows at
+            //     once, in place of a shuffle tree per row (5 adds per lane and
+            //     row, with lanes that carry no needed value).
+            // Rows: 2q = theta of tile bit q, 2q + 1 = phi of bit q (from the
+            // chunk rows, or from the total row with the sign of the element's
+            // bit q); 2k <= 28 rows fit the lanes of one warp.
             constexpr int KT = prog_top_chunk<Codes...>() + R;
             constexpr int NT = 1 << (KT - R);
             constexpr int NW = NT / 32;
             [[maybe_unused]] constexpr int RPW = (2 * KT + NW - 1) / NW;
             static_assert(NT >= 32, "fixed programs run whole warps");
-            if constexpr (BWD && sizeof(T) == 4) {
-                // compensated FP32 sums (csum.cuh); theta rows come scaled by gs,
-                // phi from the chunk rows or the signed total row
+            static_assert(2 * KT <= 32, "one lane per row in the second stage");
+            if constexpr (BWD) {
+                using A = typename std::conditional<sizeof(T) == 4, F32c, double>::type;
+                // stage-2 partials go to the psi tile buffer, free between rounds
+                // (the tile is in registers; the next round exchange starts
+                // with a barrier): 2 KT rows of 33
+                static_assert(2 * KT * 33 * sizeof(A) <= (1u << KT) * sizeof(typename V2<T>::type),
+                              "partials fit the tile buffer");
                 const PassOp op = ops[i];
                 __syncthreads();
                 const uint32_t gated = d.slot_gated[op.slot];
                 const int dp = diag_chunk;
-                const float *gpt = reinterpret_cast<const float *>(gsh);
-                F32c sum[RPW];
-#pragma unroll
-                for (int r = 0; r < RPW; ++r) {
+                const T *rows = reinterpret_cast<const T *>(gsh);
+                A *sp2 = reinterpret_cast<A *>(buf);
+                auto stage1 = [&](int r) {
                     const int idx = warp + r * NW;
                     const int q = idx >> 1, comp = idx & 1;
-                    sum[r] = f32c_zero();
                     if (idx < 2 * KT && ((gated >> q) & 1u)) {
                         const bool in_chunk = q >= dp && q < dp + R;
-                        const float *src = gpt + (comp == 0 ? q : (in_chunk ? k + 1 + q - dp : k)) * NT;
+                        const T *src = rows + (comp == 0 ? q : (in_chunk ? k + 1 + q - dp : k)) * NT;
                         const bool signed_total = comp == 1 && !in_chunk;
                         auto term = [&](uint32_t tt) {
-                            const float v = src[tt];
+                            const T v = src[tt];
                             return signed_total ? flip_sign(v, (elem_of(tt, 0, dp, R) >> q) & 1u) : v;
                         };
-                        sum[r].hi = term(lane);
+                        A part;
+                        if constexpr (sizeof(T) == 4) {
+                            part = F32c{term(lane), 0.f};
 #pragma unroll
-                        for (int c = 1; c < NT / 32; ++c) f32c_add(sum[r], term(lane + 32 * c));
+                            for (int c = 1; c < NT / 32; ++c) f32c_add(part, term(lane + 32 * c));
+                        } else {
+                            part = term(lane);
+#pragma unroll
+                            for (int c = 1; c < NT / 32; ++c) part += term(lane + 32 * c);
+                        }
+                        sp2[idx * 33 + lane] = part;
                     }
-                }
+                };
+                if constexpr (sizeof(T) == 4) {
+                    // one row at a time (its NT / 32 loads together): the
+                    // tile's registers stay live across the flush
 #pragma unroll 1
-                for (int r = 0; r < RPW; ++r)
-                    for (int o = 16; o > 0; o >>= 1) sum[r] = f32c_add_lazy(sum[r], f32c_shfl_xor(0xffffffffu, sum[r], o));
-                if (lane == 0) {
+                    for (int r = 0; r < RPW; ++r) stage1(r);
+                } else {
 #pragma unroll
-                    for (int r = 0; r < RPW; ++r) {
-                        const int idx = warp + r * NW;
-                        if (idx < 2 * KT && ((gated >> (idx >> 1)) & 1u))
-                            env.grad(op.slot, idx >> 1, idx & 1, f32c_value(sum[r]));
-                    }
+                    for (int r = 0; r < RPW; ++r) stage1(r);
                 }
                 __syncthreads();
-            } else if constexpr (BWD) {
-                // FP64: theta rows scaled by the bit's gs, phi from the chunk
-                // rows or the signed total row
-                const PassOp op = ops[i];
-                __syncthreads();
-                const uint32_t gated = d.slot_gated[op.slot];
-                const int dp = diag_chunk;
-                double sum[RPW];
-#pragma unroll
-                for (int r = 0; r < RPW; ++r) {
-                    const int idx = warp + r * NW;
-                    const int q = idx >> 1, comp = idx & 1;
-                    sum[r] = 0.0;
+                if (warp == 0) {
+                    const int idx = lane, q = idx >> 1, comp = idx & 1;
                     if (idx < 2 * KT && ((gated >> q) & 1u)) {
-                        const bool in_chunk = q >= dp && q < dp + R;
-                        const double *src = gsh + (comp == 0 ? q : (in_chunk ? k + 1 + q - dp : k)) * NT;
-                        const bool signed_total = comp == 1 && !in_chunk;
-                        auto term = [&](uint32_t tt) {
-                            const double v = src[tt];
-                            return signed_total ? flip_sign(v, (elem_of(tt, 0, dp, R) >> q) & 1u) : v;
-                        };
-                        sum[r] = term(lane);
+                        // four interleaved chains (lanes l = m mod 4), then
+                        // (0 + 1) + (2 + 3): a fixed order, a quarter of the latency
+                        const A *row = sp2 + idx * 33;
+                        A ch[4] = {row[0], row[1], row[2], row[3]};
 #pragma unroll
-                        for (int c = 1; c < NT / 32; ++c) sum[r] += term(lane + 32 * c);
-                    }
-                }
+                        for (int l = 4; l < 32; l += 4) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                    for (int r = 0; r < RPW; ++r) sum[r] += __shfl_xor_sync(0xffffffffu, sum[r], o);
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int r = 0; r < RPW; ++r) {
-                        const int idx = warp + r * NW;
-                        const int q = idx >> 1, comp = idx & 1;
-                        if (idx < 2 * KT && ((gated >> q) & 1u))
-                            env.grad(op.slot, q, comp, comp == 0 ? sum[r] * (double)env.coef(op.slot, q).gs : sum[r]);
+                            for (int m = 0; m < 4; ++m) {
+                                if constexpr (sizeof(T) == 4) ch[m] = f32c_add_lazy(ch[m], row[l + m]);
+                                else ch[m] += row[l + m];
+                            }
+                        }
+                        A tot;
+                        if constexpr (sizeof(T) == 4)
+                            tot = f32c_add_lazy(f32c_add_lazy(ch[0], ch[1]), f32c_add_lazy(ch[2], ch[3]));
+                        else
+                            tot = (ch[0] + ch[1]) + (ch[2] + ch[3]);
+                        if constexpr (sizeof(T) == 4) {
+                            // theta rows came scaled by gs
+                            env.grad(op.slot, q, comp, f32c_value(tot));
+                        } else {
+                            env.grad(op.slot, q, comp, comp == 0 ? tot * (double)env.coef(op.slot, q).gs : tot);
+                        }
                     }
                 }
                 __syncthreads();

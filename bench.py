@@ -50,10 +50,10 @@ FP64_UNITS_PEAK = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x 
 # DRAM read + write bytes of the FP64 backward pass kernel per byte it must
 # move (psi and lambda read and written per live tile), from an ncu capture
 # of its three launch shapes at 24 qubits on the 4x3 lattice (dram__bytes
-# read + write: 3.110 GB against 3.221 GB); the per-tile traffic of these
+# read + write: 3.119 GB against 3.221 GB); the per-tile traffic of these
 # passes does not depend on the qubit count.  None once the kernel changes,
 # until it is captured again.
-BWD_TRAFFIC_PER_ALGORITHMIC_BYTE = 3110332160 / 3221225472
+BWD_TRAFFIC_PER_ALGORITHMIC_BYTE = 3119003392 / 3221225472
 
 
 # ---------------------------------------------------------------- work models

@@ -497,3 +497,31 @@ def test_apply_h_sweeps_emulated(oracle_mod, prec, case, diag_terms):
             high = int(G.x) & ~((1 << mlo) - 1)
             if bin(high).count("1") <= 20 - mlo:
                 assert int(G.x) & ~S.fast == 0
+
+
+def test_sweep_plan_caps(oracle_mod):
+    """More groups than one sweep holds split over several sweeps (the replay
+    still equals the oracle's H psi); a group with more merged terms than a
+    sweep holds makes the sweep form impossible (the library then keeps
+    another form)."""
+    n = 12
+    rng = np.random.default_rng(12)
+    # 300 distinct X masks with two terms each: more than the 256 groups a sweep takes
+    xs = rng.choice(np.arange(1, 1 << n), size=300, replace=False).astype(np.uint64)
+    x = np.concatenate([xs, xs])
+    z = rng.integers(0, 1 << n, size=x.size).astype(np.uint64)
+    c = rng.standard_normal(x.size)
+    H = vi.PauliSum(n, x, z, c)
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    lam, sp = emulate_sweeps(n, "c128", H, psi)
+    assert len(sp["sweeps"]) >= 2
+    assert all(S.g_end - S.g_begin <= 256 for S in sp["sweeps"])
+    ref = oracle_mod.apply_h(psi, H.x, H.z, H.c)
+    assert np.max(np.abs(lam - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+    # one X mask with 4100 distinct Z masks (> 4096 merged terms in one pattern)
+    n2 = 14
+    zz = rng.choice(np.arange(1 << n2), size=4100, replace=False).astype(np.uint64)
+    x2 = np.full(zz.size, (1 << n2) - 1, dtype=np.uint64)
+    H2 = vi.PauliSum(n2, x2, zz, rng.standard_normal(zz.size))
+    with pytest.raises(ValueError):
+        P.sweeps(n2, "c64", H2.x, H2.z, H2.c)

@@ -238,7 +238,12 @@ k_apply_h_sweep(SweepDesc W, const uint32_t *__restrict__ order, const SGroup *_
                 for (int j = 0; j < J; ++j) p[j] = nz[j] ? P[a[j] ^ x] : C{T(0), T(0)};
                 // multiply-adds only where a lane of the warp has a nonzero
                 // term: the patterns of X bits above the lanes' bits are
-                // warp-uniform, so most zero halves of a group skip whole warps
+                // warp-uniform, so the zero half of such a group could skip
+                // whole warps.  The compiler mostly keeps the multiply-adds
+                // and selects (FP64 at 24 qubits: 64.8 DFMA per state in a
+                // 34-group sweep against 49 with every skip taken); an empty
+                // volatile asm that keeps the branch serialised the kernel
+                // (2.0 s against 0.88 s at 32 qubits).
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
                     if (!__any_sync(0xffffffffu, nz[j])) continue;

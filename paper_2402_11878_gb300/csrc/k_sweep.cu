@@ -233,27 +233,45 @@ k_apply_h_sweep(SweepDesc W, const uint32_t *__restrict__ order, const SGroup *_
                         }
                     }
                 }
-                C p[J];
+                if constexpr (sizeof(T) == 8) {
+                    // FP64 (bound by the FP64 pipe): the gather and the
+                    // multiply-adds of a state inside a warp-uniform branch.
+                    // The patterns of X bits above the lanes' bits are
+                    // warp-uniform, so warps of the zero half of such a group
+                    // skip their DFMAs (24 qubits: 49 DFMA per state in a
+                    // 34-group sweep, 64.8 when the gathers were issued
+                    // before the vote and the compiler made it a select).
 #pragma unroll
-                for (int j = 0; j < J; ++j) p[j] = nz[j] ? P[a[j] ^ x] : C{T(0), T(0)};
-                // multiply-adds only where a lane of the warp has a nonzero
-                // term: the patterns of X bits above the lanes' bits are
-                // warp-uniform, so the zero half of such a group could skip
-                // whole warps.  The compiler mostly keeps the multiply-adds
-                // and selects (FP64 at 24 qubits: 64.8 DFMA per state in a
-                // 34-group sweep against 49 with every skip taken); an empty
-                // volatile asm that keeps the branch serialised the kernel
-                // (2.0 s against 0.88 s at 32 qubits).
+                    for (int j = 0; j < J; ++j) {
+                        if (__any_sync(0xffffffffu, nz[j])) {
+                            const C pj = nz[j] ? P[a[j] ^ x] : C{T(0), T(0)};
+                            if (has_b) {
+                                lv[j].x = fma(pj.x, fa[j], fma(pj.y, fb[j], lv[j].x));
+                                lv[j].y = fma(pj.y, fa[j], fma(-pj.x, fb[j], lv[j].y));
+                            } else {
+                                lv[j].x = fma(pj.x, fa[j], lv[j].x);
+                                lv[j].y = fma(pj.y, fa[j], lv[j].y);
+                            }
+                        }
+                    }
+                } else {
+                    C p[J];
 #pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    if (!__any_sync(0xffffffffu, nz[j])) continue;
-                    if (has_b) {
-                        // (px + i py)(fa - i fb)
-                        lv[j].x = fma(p[j].x, fa[j], fma(p[j].y, fb[j], lv[j].x));
-                        lv[j].y = fma(p[j].y, fa[j], fma(-p[j].x, fb[j], lv[j].y));
-                    } else {
-                        lv[j].x = fma(p[j].x, fa[j], lv[j].x);
-                        lv[j].y = fma(p[j].y, fa[j], lv[j].y);
+                    for (int j = 0; j < J; ++j) p[j] = nz[j] ? P[a[j] ^ x] : C{T(0), T(0)};
+                    // complex64 (issue-bound): the gathers of the J states
+                    // issued together, the multiply-adds after a warp vote
+                    // (which the compiler may turn into a select)
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        if (!__any_sync(0xffffffffu, nz[j])) continue;
+                        if (has_b) {
+                            // (px + i py)(fa - i fb)
+                            lv[j].x = fma(p[j].x, fa[j], fma(p[j].y, fb[j], lv[j].x));
+                            lv[j].y = fma(p[j].y, fa[j], fma(-p[j].x, fb[j], lv[j].y));
+                        } else {
+                            lv[j].x = fma(p[j].x, fa[j], lv[j].x);
+                            lv[j].y = fma(p[j].y, fa[j], lv[j].y);
+                        }
                     }
                 }
             }

@@ -1576,7 +1576,7 @@ vqe_status build_ham_plan(vqe_ctx *h) {
         // default form (mode -1): the bit-ordered sweeps when every group
         // takes their parity form (hopping Hamiltonians: at 32 qubits
         // complex64 269 ms against 342 for the windows and 393 for the
-        // global sweep, FP64 877 / 896 / 2000 ms; at 24 qubits the sweeps
+        // global sweep, FP64 671 / 898 / 2000 ms; at 24 qubits the sweeps
         // are fastest too), else the windows when they hold many groups each
         // (the synthetic molecular Hamiltonian at 24 qubits: windows 69 ms,
         // sweeps 229 ms, global 167 ms), else the global sweep.
